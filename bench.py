@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Jacobi-PCG hot path (arxiv 2603.23343, Sec. VII).
+
+Headline workload: 3D 7-point Poisson on a 256^3 interior grid (h = 1/257),
+b ~ U[-1,1) seed 0, x0 = 0, Jacobi, stop at ||r||/||b|| <= 1e-6 (maxit 2000),
+FP32 vectors, FP64 scalars.  One step = one full solve (reset x0, whole PCG
+loop in one CUDA graph, FP64 true residual) with b already resident in HBM.
+b and x are FP64 (only the init, the residual replacements and the finalize
+touch them); the iteration vectors z, p0, p1, d are FP32.  The working set
+(512 MiB) is larger than the 126 MB L2, so steps need no L2 flush.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas
+(one solve per GPU per step); the path has no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time-to-1e-6 residual & HBM GB/s at 256^3, plain FP32 vs learned/mixed"
+N_GRID = 256
+TOL = 1e-6
+MAXIT = 2000
+# algorithmic bytes per grid point of each data pass (FP32): pass A reads z, p, x and
+# writes p, x; pass B reads p, z and writes z.  An iteration is 32 B/pt.
+PASS_BYTES = {"pass_a": 20, "pass_b": 12}
+ITER_BYTES = 32
+THREE_KERNEL_BYTES = 44
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_GRID, help="grid points per axis (default 256)")
+    ap.add_argument("--cpu-iters", type=int, default=200, help="oracle iterations in the CPU-baseline sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thr.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n_gpus > 1 else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(n, gpu_iters, sample_iters):
+    """The FP64 oracle as it stands on the host cores: a bounded number of
+    iterations of the same solve, scaled to the full iteration count."""
+    import oracle
+    from paper_2603_23343_gb300 import inputs
+    oracle.build()
+    b = inputs.poisson_problem(n, 0, np.float64)
+    t0 = time.perf_counter()
+    res = oracle.pcg(b, tol=TOL, maxit=sample_iters)
+    dt = time.perf_counter() - t0
+    done = max(1, res["iters"])
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    est_ms = dt / done * gpu_iters * 1e3
+    return {"value": est_ms, "unit": "ms", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {gpu_iters} iterations of the {n}^3 FP64 oracle solve "
+                      f"({dt:.1f} s, OpenMP {cores} threads), scaled by {gpu_iters}/{done}"}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("engine.cuh", "launch.cuh", "common.cuh", "pcg.cu"):
+        with open(os.path.join(ROOT, "paper_2603_23343_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "pass_traffic.json")) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e.get("source_sha") != source_hash():
+            return None
+        return e["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (there is no reference code)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2603_23343_gb300 import inputs
+    oracle.build()
+    n = args.n
+    gold = os.path.join(ROOT, "tests", "golden", f"pcg_poisson{n}_seed0.json")
+    full_iters = json.load(open(gold))["iters"] if os.path.exists(gold) else 678
+    b = inputs.poisson_problem(n, 0, np.float64)
+    sample = max(10, min(args.cpu_iters, 60))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = oracle.pcg(b, tol=TOL, maxit=sample)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt / max(1, res["iters"]) * full_iters * 1e3)
+    v = float(np.mean(times))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"poisson {n}^3 Jacobi-PCG to 1e-6 (b~U[-1,1) seed 0, x0=0)",
+                       "n": n, "tol": TOL, "oracle_iters_full_solve": full_iters},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: {sample} of {full_iters} iterations of the FP64 oracle "
+                                       f"solve, scaled by {full_iters}/{sample}"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    from paper_2603_23343_gb300 import binding as B
+    from paper_2603_23343_gb300 import inputs
+
+    n = args.n
+    N = n ** 3
+    # b and x in FP64 (touched only by init, residual replacements and finalize);
+    # the iteration vectors z, p, d are FP32
+    b = torch.from_numpy(inputs.poisson_problem(n, 0, np.float64)).cuda()
+    x = torch.zeros_like(b)
+    ws = B.alloc_workspace(b.shape, io_dtype=B.F64)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        return B.pcg_solve(b, x, tol=TOL, maxit=MAXIT, workspace=ws, stream=stream)[1]
+
+    for _ in range(max(3, args.warmup)):
+        res = step()
+    iters = res["iters"]
+
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        results = [step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_total = e0.elapsed_time(e1)
+    ms_step = max_over_ranks(ms_total / args.steps, world)
+    res = results[-1]
+    iters = res["iters"]
+
+    # per-kernel durations: the same solve with every pass launch bracketed by CUDA events
+    x.zero_()
+    _, prof = B.pcg_solve(b, x, tol=TOL, maxit=MAXIT, workspace=ws, profile=True, stream=stream)
+    avg = {k: prof["pass_ms"][i] / max(1, prof["pass_launches"][i]) for i, k in enumerate(("pass_a", "pass_b"))}
+    dom = "pass_a" if prof["pass_ms"][0] >= prof["pass_ms"][1] else "pass_b"
+    peak, peak_kind = peaks()
+    bytes_launch = PASS_BYTES[dom] * N
+    achieved = bytes_launch / (avg[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dom), "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_us": avg[dom] * 1e3,
+                "other_pass": {k: {"avg_launch_us": avg[k] * 1e3,
+                                   "achieved_gbs": PASS_BYTES[k] * N / (avg[k] * 1e-3) / 1e9}
+                               for k in avg}}
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    bh = b.cpu().pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    ws_io = B.alloc_workspace(b.shape, host_io=True, io_dtype=B.F64)
+    B.pcg_solve(bh, xh, tol=TOL, maxit=MAXIT, workspace=ws_io, host_io=True, stream=stream)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        xh.zero_()
+        _, r_io = B.pcg_solve(bh, xh, tol=TOL, maxit=MAXIT, workspace=ws_io, host_io=True, stream=stream)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / args.steps, world)
+
+    # the same solve with FP32 x and b (x's own rounding then bounds the true residual)
+    b32 = b.float()
+    x32 = torch.zeros_like(b32)
+    w32 = B.alloc_workspace(b.shape)
+    for _ in range(2):
+        x32.zero_()
+        _, r32 = B.pcg_solve(b32, x32, tol=TOL, maxit=MAXIT, workspace=w32, stream=stream)
+
+    # the paper's Table 3 grid (512 x 112 x 64), context for the H100's 0.28 ms/iteration
+    bc = torch.from_numpy(inputs.uniform_rhs((64, 112, 512), 0, dtype=np.float64)).cuda()
+    xc = torch.zeros_like(bc)
+    wc = B.alloc_workspace(bc.shape, io_dtype=B.F64)
+    for _ in range(2):
+        xc.zero_()
+        _, rc = B.pcg_solve(bc, xc, tol=TOL, maxit=MAXIT, workspace=wc, stream=stream)
+
+    iter_us = ms_step * 1e3 / max(1, iters)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, iters, args.cpu_iters)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {
+                "workload": f"poisson {n}^3 FP32 Jacobi-PCG to 1e-6 (b~U[-1,1) seed 0, x0=0, h=1/{n + 1})",
+                "n": n, "tol": TOL, "iters": iters, "status": res["status_name"],
+                "rel_res_true_fp64": res["rel_res_true"], "replicas": world,
+                "residual_replacements": res["replacements"],
+                "vectors": "iteration vectors z, p0, p1, d FP32; b, x FP64",
+                "l2": "no flush: working set b,x (FP64) + z,p0,p1,d (FP32) = %d MiB > L2" % ((2 * 8 + 4 * 4) * N >> 20),
+                "fp32_x": {"iters": r32["iters"], "status": r32["status_name"], "ms": r32["time_ms"],
+                           "rel_res_true_fp64": r32["rel_res_true"]},
+                "iteration": {"us": iter_us, "algorithmic_bytes_per_pt": ITER_BYTES,
+                              "gbs": ITER_BYTES * N / (iter_us * 1e-6) / 1e9,
+                              "frac": ITER_BYTES * N / (iter_us * 1e-6) / 1e9 / peak,
+                              "gbs_44B_three_kernel_equiv": THREE_KERNEL_BYTES * N / (iter_us * 1e-6) / 1e9,
+                              "frac_44B_three_kernel_equiv":
+                                  THREE_KERNEL_BYTES * N / (iter_us * 1e-6) / 1e9 / peak},
+                "table3_grid_512x112x64": {"iters": rc["iters"], "ms_per_iter": rc["time_ms"] / max(1, rc["iters"]),
+                                           "h100_ms_per_iter_paper": 0.28},
+            },
+            "roofline": roofline,
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,
+                    "d2h_bytes_per_step": N * 8 + 256},
+            "gpu_launches": args.steps * (2 * iters + 4 + 2 * res["replacements"]),
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,233 @@
+"""Python binding of libgbpcg.so (ctypes): argument marshalling only.
+
+Every function here converts torch tensors / numbers into the C ABI of
+``include/gbpcg.h`` and calls it; all arithmetic runs in the library's CUDA
+kernels.  There is no CPU path: if the library cannot be loaded the call
+raises.
+
+Grids are torch tensors of shape (nz, ny, nx) (x fastest), matching the
+library's index (k*ny + j)*nx + i.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbpcg.so")
+
+OK, ERR_ARG, ERR_CUDA, NOT_CONVERGED, BREAKDOWN, TIMEOUT, FALLBACK_USED = range(7)
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "NOT_CONVERGED", 4: "BREAKDOWN", 5: "TIMEOUT",
+                6: "FALLBACK_USED"}
+F32, BF16, F16, F64 = 0, 1, 2, 3
+FLAG_HOST_IO = 1
+FLAG_PROFILE = 2
+
+_DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
+
+EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbpcg_stencil_apply", "gbpcg_dot",
+           "gbpcg_axpy", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("k_block", ctypes.c_void_p), ("kbx", ctypes.c_int32), ("kby", ctypes.c_int32),
+                ("kbz", ctypes.c_int32)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("io_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("pass_ms", ctypes.c_double * 2), ("pass_launches", ctypes.c_int32 * 2),
+                ("replacements", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, status=self.status, status_name=STATUS_NAMES.get(self.status, "?"),
+                    rel_res_recursive=self.rel_res_recursive, rel_res_true=self.rel_res_true,
+                    time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches), replacements=self.replacements)
+
+
+class GbpcgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gbpcg status {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads the CUDA library (building it in-tree first if it is absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            from . import build as _build
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, I32, I64, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        lib.gbpcg_version.restype = ctypes.c_char_p
+        lib.gbpcg_last_error.restype = ctypes.c_char_p
+        lib.gbpcg_dot_workspace_size.restype = SZ
+        lib.gbpcg_stencil_apply.restype = ctypes.c_int
+        lib.gbpcg_stencil_apply.argtypes = [ctypes.POINTER(Grid), I32, P, P, P]
+        lib.gbpcg_dot.restype = ctypes.c_int
+        lib.gbpcg_dot.argtypes = [I64, I32, P, P, P, P, SZ, P]
+        lib.gbpcg_axpy.restype = ctypes.c_int
+        lib.gbpcg_axpy.argtypes = [I64, I32, D, P, P, P]
+        lib.gbpcg_workspace_size.restype = ctypes.c_int
+        lib.gbpcg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), ctypes.POINTER(SZ)]
+        lib.gbpcg_pcg_solve.restype = ctypes.c_int
+        lib.gbpcg_pcg_solve.argtypes = [ctypes.POINTER(Grid), P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
+        _lib = lib
+        return lib
+
+
+def version() -> str:
+    return load().gbpcg_version().decode()
+
+
+def last_error() -> str:
+    return load().gbpcg_last_error().decode()
+
+
+def _check(rc: int, allowed=(OK,)):
+    if rc not in allowed:
+        raise GbpcgError(rc, last_error())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    try:
+        return _DTYPES[t.dtype]
+    except KeyError:
+        raise GbpcgError(ERR_ARG, f"unsupported dtype {t.dtype}") from None
+
+
+def make_grid(shape, k_block: torch.Tensor | None = None, kb=8) -> Grid:
+    nz, ny, nx = (int(s) for s in shape)
+    if isinstance(kb, int):
+        kb = (kb, kb, kb)
+    g = Grid(nx, ny, nz, None, 1, 1, 1)
+    if k_block is not None:
+        if k_block.dtype != torch.float32 or not k_block.is_cuda or not k_block.is_contiguous():
+            raise GbpcgError(ERR_ARG, "k_block must be a contiguous float32 CUDA tensor")
+        g.k_block = k_block.data_ptr()
+        g.kbx, g.kby, g.kbz = (int(v) for v in kb)
+    return g
+
+
+def stencil_apply(p: torch.Tensor, q: torch.Tensor | None = None, k_block=None, kb=8, stream=None) -> torch.Tensor:
+    """q = A p (gbpcg_stencil_apply)."""
+    if p.dim() != 3 or not p.is_contiguous():
+        raise GbpcgError(ERR_ARG, "p must be a contiguous (nz, ny, nx) tensor")
+    if q is None:
+        q = torch.empty_like(p)
+    g = make_grid(p.shape, k_block, kb)
+    _check(load().gbpcg_stencil_apply(ctypes.byref(g), _dtype(p), _ptr(p), _ptr(q), _stream(stream)))
+    return q
+
+
+def dot_workspace_size() -> int:
+    return int(load().gbpcg_dot_workspace_size())
+
+
+def dot(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+        stream=None) -> torch.Tensor:
+    """Device scalar (float64 tensor) x . y (gbpcg_dot)."""
+    if x.numel() != y.numel() or x.dtype != y.dtype:
+        raise GbpcgError(ERR_ARG, "x and y must have the same size and dtype")
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=x.device)
+    if workspace is None:
+        workspace = torch.empty(dot_workspace_size(), dtype=torch.uint8, device=x.device)
+    _check(load().gbpcg_dot(x.numel(), _dtype(x), _ptr(x), _ptr(y), _ptr(out), _ptr(workspace),
+                            workspace.numel(), _stream(stream)))
+    return out
+
+
+def axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+    """y = alpha x + y in place (gbpcg_axpy)."""
+    if x.numel() != y.numel() or x.dtype != y.dtype:
+        raise GbpcgError(ERR_ARG, "x and y must have the same size and dtype")
+    _check(load().gbpcg_axpy(x.numel(), _dtype(x), float(alpha), _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
+              profile=False) -> Opts:
+    o = Opts()
+    o.tol = float(tol)
+    o.maxit = int(maxit)
+    o.precond = 0
+    o.storage = storage
+    o.io_dtype = io_dtype
+    o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0)
+    if workspace is not None:
+        o.workspace = workspace.data_ptr()
+        o.workspace_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def workspace_size(shape, k_block=None, kb=8, **opt_kw) -> int:
+    g = make_grid(shape, k_block, kb)
+    o = make_opts(**opt_kw)
+    n = ctypes.c_size_t(0)
+    _check(load().gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)))
+    return int(n.value)
+
+
+def alloc_workspace(shape, k_block=None, kb=8, device="cuda", **opt_kw) -> torch.Tensor:
+    return torch.empty(workspace_size(shape, k_block, kb, **opt_kw), dtype=torch.uint8, device=device)
+
+
+def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
+              workspace: torch.Tensor | None = None, host_io=False, profile=False, stream=None):
+    """Jacobi-PCG solve of A x = b (gbpcg_pcg_solve).  Returns (x, result dict).
+
+    b and x are float32 or float64 (the solution accumulates in that type; the
+    iteration vectors are float32 either way).  They may be CPU tensors
+    (pinned for speed) when host_io=True; the
+    copies then happen inside the library call.  profile=True runs the
+    iteration kernels one by one, each timed with CUDA events, and reports
+    the summed pass times in result["pass_ms"].
+    """
+    if b.dim() != 3 or not b.is_contiguous():
+        raise GbpcgError(ERR_ARG, "b must be a contiguous (nz, ny, nx) tensor")
+    if x is None:
+        x = torch.zeros_like(b)
+    if x.dtype != b.dtype or x.shape != b.shape or not x.is_contiguous():
+        raise GbpcgError(ERR_ARG, "x must be a contiguous tensor of b's shape and dtype")
+    io = _dtype(b)
+    dev = b.device if b.is_cuda else torch.device("cuda", torch.cuda.current_device())
+    if workspace is None:
+        workspace = alloc_workspace(b.shape, k_block, kb, device=dev, io_dtype=io, host_io=host_io)
+    g = make_grid(b.shape, k_block, kb)
+    o = make_opts(tol, maxit, F32, io, host_io, workspace, profile)
+    r = Result()
+    rc = load().gbpcg_pcg_solve(ctypes.byref(g), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
+                                _stream(stream))
+    _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
+    return x, r.as_dict()

@@ -1,0 +1,413 @@
+// Z-marching stencil engine: the data path shared by the stencil apply and
+// the fused PCG passes.
+//
+// Each CTA owns a TX x TY tile of the (x, y) plane and marches through a
+// contiguous range of z planes [k0, k1).  Plane m of every input array
+// arrives in shared memory as one box: the "halo" arrays with one extra row
+// above/below and XH extra columns left/right (XH = 16 bytes of elements, so
+// the box's x origin stays 16-byte aligned as TMA requires), the "center"
+// arrays without halo.  Boxes reaching outside the grid are zero-filled by
+// the TMA unit, which is exactly the zero Dirichlet boundary (the paper's
+// explicit zero fill, Sec. VI-C, costs nothing here).  An S-stage ring of
+// boxes is kept in flight, each stage completed by one mbarrier.
+//
+// The seven-point operator at plane k needs the input at planes k-1, k, k+1
+// in the thread's own column (kept in registers as a 3-deep queue) and the
+// four in-plane neighbours (read from the plane-k box).  One thread computes
+// four consecutive x points of one row.
+//
+// Pass kinds (Sec. VII's PCG split into two data passes plus setup):
+//   K_STENCIL  q = A p
+//   K_PASSA    p_k = z_k + beta_{k-1} p_{k-1} formed on the fly for every
+//              stencil input (no D needed: z, not r, is the stored vector);
+//              d += alpha_{k-1} p_{k-1} (deferred update of the previous
+//              iteration into the correction vector d, see pcg.cu); stores
+//              p_k; sum p_k . A p_k -> alpha_k
+//   K_PASSB    q = A p_k recomputed (cheaper than storing it),
+//              r = D z - alpha_k q, z = D^-1 r; stores z; sums r.r, r.z
+//              -> beta_k, the convergence test and the residual-replacement
+//              trigger
+#pragma once
+
+#include "common.cuh"
+
+namespace gb {
+
+enum PassKind { K_STENCIL = 0, K_PASSA = 2, K_PASSB = 3 };
+
+// Device-resident solver scalars (one per solve).
+struct __align__(16) SolveState {
+    double rz;      // r_k . z_k
+    double pq;      // p_k . A p_k
+    double alpha;   // alpha_k
+    double beta;    // beta_{k-1}
+    double rr;      // ||r_k||^2 (recursive)
+    double bb;      // ||b||^2
+    double tol2;    // tol^2
+    double rr_true; // ||b - A x||^2, FP64
+    double bb_true; // ||b||^2, FP64
+    int it;         // completed iterations
+    int maxit;
+    int done;       // 1: stop iterating
+    int status;     // gbpcg_status
+    int pending;    // 1: x still lacks alpha_{it-1} p_{it-1}
+    int zero_x;     // 1: b == 0, x must be zeroed
+    int timeout;    // a bounded wait gave up somewhere
+    int replace;    // 1: flush d into x and replace r by b - A x (FP64) now
+    double rr_rep;  // ||r||^2 at the last residual replacement
+    double rr_conf; // ||b - A x||^2 at the last confirmation (recursive residual had met tol)
+    int n_replace;  // residual replacements done
+    int pad1;
+    unsigned int ticket[8];
+};
+
+// A residual replacement is triggered whenever ||r|| has dropped by this
+// factor squared since the last one (a decade of residual norm), and when
+// the recursive residual meets the tolerance.
+constexpr double kReplaceDrop2 = 1e-2;
+
+// Constant-coefficient operator: face weights 1/h_d^2.
+struct OpConst {
+    static constexpr bool kConst = true;
+    float cx, cy, cz;
+    float inv_d;  // 1 / (2 (cx + cy + cz))
+    __device__ __forceinline__ void weights(int, int, int, float w[6]) const {
+        w[0] = cx; w[1] = cx; w[2] = cy; w[3] = cy; w[4] = cz; w[5] = cz;
+    }
+};
+
+// Block-constant coefficient k (one float per kbx*kby*kbz block): face
+// weight k_f / h_d^2 with k_f the harmonic mean across a block face, the
+// cell's own k inside a block and on the domain boundary.
+struct OpBlock {
+    static constexpr bool kConst = false;
+    float inv_d;  // unused
+    const float *kb;
+    int nx, ny, nz, nbx, nby, kbx, kby, kbz;
+    float cx, cy, cz;
+    __device__ __forceinline__ float K(int bx, int by, int bz) const {
+        return __ldg(kb + ((size_t)bz * nby + by) * nbx + bx);
+    }
+    __device__ __forceinline__ static float hm(float a, float b) { return 2.0f * a * b / (a + b); }
+    __device__ __forceinline__ void weights(int i, int j, int k, float w[6]) const {
+        const int bx = i / kbx, by = j / kby, bz = k / kbz;
+        const int ix = i - bx * kbx, iy = j - by * kby, iz = k - bz * kbz;
+        const float kc = K(bx, by, bz);
+        w[0] = cx * ((ix == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
+        w[1] = cx * ((ix == kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
+        w[2] = cy * ((iy == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
+        w[3] = cy * ((iy == kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
+        w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
+        w[5] = cz * ((iz == kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
+    }
+};
+
+struct __align__(128) PassMaps {
+    CUtensorMap h0[2];  // halo array 0 (two candidates, chosen by iteration parity)
+    CUtensorMap h1[2];  // halo array 1
+    CUtensorMap c0;     // center array
+};
+
+struct PassArgs {
+    int nx, ny, nz;
+    int tiles_x, zchunk;
+    const void *h0[2];
+    const void *h1[2];
+    const void *c0;
+    void *o0[2];
+    void *o1;
+    SolveState *st;
+    double *partials;
+    cudaGraphConditionalHandle cond;          // WHILE condition of the iteration loop
+    cudaGraphConditionalHandle cond_replace;  // IF condition of the residual replacement
+    int use_cond;
+    float scale;  // stencil apply: output multiplier (1 normally)
+};
+
+constexpr uint32_t round128(uint32_t v) { return (v + 127u) & ~127u; }
+
+template <typename T, int TX, int TY, int KIND>
+struct Geometry {
+    static constexpr int NT = TX / 4 * TY;
+    static constexpr int XH = 16 / (int)sizeof(T);
+    static constexpr int HX = TX + 2 * XH, HY = TY + 2;
+    static constexpr int NH = KIND == K_PASSA ? 2 : 1;
+    static constexpr int NC = KIND == K_STENCIL ? 0 : 1;
+    static constexpr int NV = KIND == K_PASSA ? 1 : KIND == K_PASSB ? 2 : 0;
+    static constexpr uint32_t HBYTES = HX * HY * sizeof(T);
+    static constexpr uint32_t CBYTES = TX * TY * sizeof(T);
+    static constexpr uint32_t HB = round128(HBYTES), CB = round128(CBYTES);
+    static constexpr uint32_t SB = NH * HB + NC * CB;
+};
+
+template <typename T, int TX, int TY, int S, int KIND>
+constexpr size_t zmarch_smem_bytes() {
+    return (size_t)S * Geometry<T, TX, TY, KIND>::SB;
+}
+
+// Copies one box (w x h at (xs, ys, m)) into shared memory with plain loads,
+// zero outside the grid.  Used when the arrays do not meet TMA's alignment.
+template <typename T, int NT>
+__device__ __forceinline__ void manual_box(const T *src, T *dst, int nx, int ny, int nz, int xs,
+                                           int ys, int m, int w, int h) {
+    for (int e = threadIdx.x; e < w * h; e += NT) {
+        const int r = e / w, c = e - r * w;
+        const int gx = xs + c, gy = ys + r;
+        T v = from_f<T>(0.0f);
+        if (m >= 0 && m < nz && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+            v = src[((size_t)m * ny + gy) * nx + gx];
+        dst[e] = v;
+    }
+}
+
+template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
+__global__ void __launch_bounds__(TX / 4 * TY)
+    zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
+    using G = Geometry<T, TX, TY, KIND>;
+    constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV;
+    constexpr uint32_t HB = G::HB, SB = G::SB;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ int s_timeout;
+
+    SolveState *st = a.st;
+    int it = 0;
+    float alpha = 0.f, beta = 0.f, alpha_prev = 0.f;
+    bool first = false, do_x = false;
+    if constexpr (KIND == K_PASSA || KIND == K_PASSB) {
+        if (st->done) return;  // uniform across the grid
+        it = st->it;
+    }
+    if constexpr (KIND == K_PASSA) {
+        first = (it == 0);
+        beta = (float)st->beta;
+        alpha_prev = (float)st->alpha;
+        do_x = st->pending != 0;
+    }
+    if constexpr (KIND == K_PASSB) alpha = (float)st->alpha;
+
+    int sh0 = 0, sh1 = 0, so0 = 0;
+    if constexpr (KIND == K_PASSA) { sh1 = (it + 1) & 1; so0 = it & 1; }
+    if constexpr (KIND == K_PASSB) sh0 = it & 1;
+    const T *H0 = static_cast<const T *>(a.h0[sh0]);
+    const T *H1 = static_cast<const T *>(a.h1[sh1]);
+    const T *C0 = static_cast<const T *>(a.c0);
+    T *O0 = static_cast<T *>(a.o0[so0]);
+    T *O1 = static_cast<T *>(a.o1);
+    const CUtensorMap *M0 = &maps.h0[sh0];
+    const CUtensorMap *M1 = &maps.h1[sh1];
+    const CUtensorMap *MC = &maps.c0;
+
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+    const int k0 = blockIdx.y * a.zchunk, k1 = min(nz, k0 + a.zchunk);
+    const int lx = threadIdx.x % (TX / 4), ly = threadIdx.x / (TX / 4);
+    const int gx = x0 + 4 * lx, gy = y0 + ly;
+    bool ok[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ok[i] = gy < ny && gx + i < nx;
+
+    const bool load_h1 = NH == 2 && !first;
+    const bool load_c = G::NC == 1 && !(KIND == K_PASSA && !do_x);
+
+    float acc[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int i = 0; i < (NV > 0 ? NV : 1); ++i) acc[i] = 0.f;
+
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        if constexpr (TMA) {
+            for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+            fence_mbar_init();
+        }
+    }
+    __syncthreads();
+
+    const int m_first = k0 - 1, m_last = k1;  // planes loaded (k0-1 and k1 are halo planes)
+
+    auto issue = [&](int m) {
+        const int s = (m - m_first) % S;
+        unsigned char *base = smem + (size_t)s * SB;
+        const bool cen = load_c && m >= k0 && m < k1;
+        if constexpr (TMA) {
+            if (threadIdx.x == 0) {
+                const uint32_t bytes = G::HBYTES + (load_h1 ? G::HBYTES : 0u) + (cen ? G::CBYTES : 0u);
+                mbar_arrive_expect_tx(&full[s], bytes);
+                tma_load_3d(base, M0, &full[s], x0 - XH, y0 - 1, m);
+                if (load_h1) tma_load_3d(base + HB, M1, &full[s], x0 - XH, y0 - 1, m);
+                if (cen) tma_load_3d(base + NH * HB, MC, &full[s], x0, y0, m);
+            }
+        } else {
+            manual_box<T, NT>(H0, reinterpret_cast<T *>(base), nx, ny, nz, x0 - XH, y0 - 1, m, HX, TY + 2);
+            if (load_h1)
+                manual_box<T, NT>(H1, reinterpret_cast<T *>(base + HB), nx, ny, nz, x0 - XH, y0 - 1, m, HX,
+                                  TY + 2);
+            if (cen) manual_box<T, NT>(C0, reinterpret_cast<T *>(base + NH * HB), nx, ny, nz, x0, y0, m, TX, TY);
+            __syncthreads();
+        }
+    };
+
+    // stencil-input value at (row, col) of a stage box
+    auto in_val = [&](const unsigned char *base, int idx) -> float {
+        float v = to_f(reinterpret_cast<const T *>(base)[idx]);
+        if constexpr (KIND == K_PASSA) {
+            if (!first) v = fmaf(beta, to_f(reinterpret_cast<const T *>(base + HB)[idx]), v);
+        }
+        return v;
+    };
+    auto in_val4 = [&](const unsigned char *base, int idx, float v[4]) {
+        ld4<T>(reinterpret_cast<const T *>(base) + idx, v);
+        if constexpr (KIND == K_PASSA) {
+            if (!first) {
+                float p[4];
+                ld4<T>(reinterpret_cast<const T *>(base + HB) + idx, p);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = fmaf(beta, p[i], v[i]);
+            }
+        }
+    };
+
+    int issued_hi = m_first - 1;
+    int consumed = m_first - 1;
+    if (k0 < k1) {
+        for (int m = m_first; m <= m_last && m < m_first + S; ++m) {
+            issue(m);
+            issued_hi = m;
+        }
+        float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f}, qc[4] = {0.f, 0.f, 0.f, 0.f};
+        const int cidx = (ly + 1) * HX + XH + 4 * lx;  // this thread's first point in a halo box
+        for (int m = m_first; m <= m_last; ++m) {
+            const int s = (m - m_first) % S;
+            const unsigned char *base = smem + (size_t)s * SB;
+            if constexpr (TMA) {
+                if (!mbar_wait_bounded(&full[s], ((m - m_first) / S) & 1)) s_timeout = 1;
+            }
+            consumed = m;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
+            in_val4(base, cidx, qc);
+            if (m >= k0 + 1) {
+                // ---- output plane k = m - 1 from the stage of plane k ----
+                const int k = m - 1;
+                const unsigned char *bk = smem + (size_t)((k - m_first) % S) * SB;
+                float ym[4], yp[4];
+                in_val4(bk, cidx - HX, ym);
+                in_val4(bk, cidx + HX, yp);
+                const float xl = in_val(bk, cidx - 1), xr = in_val(bk, cidx + 4);
+                float q[4], dg[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float c = qb[i];
+                    const float xm = i == 0 ? xl : qb[i - 1];
+                    const float xp = i == 3 ? xr : qb[i + 1];
+                    float w[6];
+                    // masked-off points past the grid edge use an in-range
+                    // position so the coefficient lookup stays inside k_block
+                    op.weights(min(gx + i, nx - 1), min(gy, ny - 1), k, w);
+                    q[i] = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym[i]) + w[3] * (c - yp[i]) +
+                           w[4] * (c - qa[i]) + w[5] * (c - qc[i]);
+                    dg[i] = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
+                }
+                const size_t g = ((size_t)k * ny + gy) * nx + gx;
+                const T *cen = reinterpret_cast<const T *>(bk + NH * HB) + ly * TX + 4 * lx;
+                float out0[4], out1[4];
+                bool st1 = false;
+                if constexpr (KIND == K_STENCIL) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) out0[i] = q[i] * a.scale;
+                } else if constexpr (KIND == K_PASSA) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        out0[i] = qb[i];
+                        if (ok[i]) acc[0] = fmaf(qb[i], q[i], acc[0]);
+                    }
+                    if (do_x) {
+                        float xv[4], po[4];
+                        ld4<T>(cen, xv);
+                        ld4<T>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
+                        st1 = true;
+                    }
+                } else {  // K_PASSB
+                    float zv[4];
+                    ld4<T>(cen, zv);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
+                        const float z = Op::kConst ? r * op.inv_d : r / dg[i];
+                        out0[i] = z;
+                        if (ok[i]) {
+                            acc[0] = fmaf(r, r, acc[0]);
+                            acc[1] = fmaf(r, z, acc[1]);
+                        }
+                    }
+                }
+                if (ok[0] && ok[3] && TMA) {
+                    st4<T>(O0 + g, out0);
+                    if (st1) st4<T>(O1 + g, out1);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (ok[i]) {
+                            O0[g + i] = from_f<T>(out0[i]);
+                            if (st1) O1[g + i] = from_f<T>(out1[i]);
+                        }
+                }
+            }
+            __syncthreads();
+            if (s_timeout) break;
+            if (m >= k0 && m - 1 + S <= m_last) {
+                issue(m - 1 + S);
+                issued_hi = m - 1 + S;
+            }
+        }
+        if constexpr (TMA) {
+            if (s_timeout) {
+                // give copies still in flight a bounded chance to land before exit
+                for (int m = consumed + 1; m <= issued_hi; ++m)
+                    mbar_wait_bounded(&full[(m - m_first) % S], ((m - m_first) / S) & 1);
+                if (threadIdx.x == 0) atomicExch(&st->timeout, 1);
+            }
+        }
+    }
+
+    if constexpr (NV > 0) {
+        double part[NV], tot[NV];
+        block_sum<NV, NT>(acc, part);
+        if (grid_sum_last<NV, NT>(part, a.partials, &st->ticket[KIND], tot) && threadIdx.x == 0) {
+            __threadfence();
+            const bool tmo = atomicAdd(&st->timeout, 0) != 0;
+            if constexpr (KIND == K_PASSA) {
+                const double pq = tot[0];
+                st->pq = pq;
+                st->pending = 0;
+                st->replace = 0;
+                if (!(pq > 0.0) || !isfinite(pq)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+                else st->alpha = st->rz / pq;
+            } else {
+                const double rr = tot[0], rz = tot[1];
+                st->it = it + 1;
+                st->rr = rr;
+                st->pending = 1;
+                if (!isfinite(rr) || !isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+                else if (rr <= st->tol2 * st->bb || rr <= kReplaceDrop2 * st->rr_rep) {
+                    // flush d into x and recompute r = b - A x in FP64 before
+                    // deciding (the replacement pass sets beta and the flags);
+                    // 2 marks a confirmation of convergence
+                    st->replace = rr <= st->tol2 * st->bb ? 2 : 1;
+                } else if (it + 1 >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+                else { st->beta = rz / st->rz; st->rz = rz; }
+            }
+            if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
+            if (a.use_cond) {
+                cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
+                cudaGraphSetConditional(a.cond_replace, st->replace ? 1u : 0u);
+            }
+        }
+    }
+}
+
+}  // namespace gb

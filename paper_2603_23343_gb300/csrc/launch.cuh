@@ -1,0 +1,140 @@
+// Host side of the z-marching engine: tile configurations, grid geometry,
+// tensor-map set-up and the templated launcher.
+#pragma once
+
+#include <algorithm>
+
+#include "engine.cuh"
+
+namespace gb {
+
+// Tile configurations the library is built with (x width, y height, stages).
+enum TileCfg { CFG_64x16 = 0, CFG_32x16 = 1, CFG_128x8 = 2, CFG_64x8 = 3, NUM_CFG = 4 };
+struct CfgDims { int tx, ty, s; };
+inline CfgDims cfg_dims(int c) {
+    switch (c) {
+        case CFG_64x16: return {64, 16, 4};
+        case CFG_32x16: return {32, 16, 4};
+        case CFG_128x8: return {128, 8, 4};
+        default: return {64, 8, 4};
+    }
+}
+
+struct PassGeom {
+    int cfg;
+    int tiles_x, tiles_y, zchunk, zchunks;
+    int threads;
+    size_t smem;
+    dim3 grid() const { return dim3((unsigned)(tiles_x * tiles_y), (unsigned)zchunks, 1); }
+    unsigned nblocks() const { return (unsigned)(tiles_x * tiles_y * zchunks); }
+};
+
+// Upper bound on the CTAs of one pass (sizes the partial-sum scratch).
+constexpr unsigned kMaxPassBlocks = 4096;
+
+int device_sm_count();
+
+// Splits z into chunks so that tiles * zchunks fills the resident CTA slots
+// of the GPU (one wave), never exceeding kMaxPassBlocks.
+inline PassGeom make_geom(int cfg, int nx, int ny, int nz, int ctas_per_sm, size_t smem,
+                          int min_zchunk = 4) {
+    CfgDims d = cfg_dims(cfg);
+    PassGeom g;
+    g.cfg = cfg;
+    g.threads = d.tx / 4 * d.ty;
+    g.smem = smem;
+    g.tiles_x = (nx + d.tx - 1) / d.tx;
+    g.tiles_y = (ny + d.ty - 1) / d.ty;
+    const long tiles = (long)g.tiles_x * g.tiles_y;
+    const long slots = (long)device_sm_count() * std::max(1, ctas_per_sm);
+    long zc = std::max(1L, slots / std::max(1L, tiles));
+    zc = std::min<long>(zc, std::max(1L, (long)kMaxPassBlocks / std::max(1L, tiles)));
+    int zchunk = (int)((nz + zc - 1) / zc);
+    zchunk = std::max(zchunk, std::min(nz, min_zchunk));
+    zchunk = std::max(zchunk, 1);
+    g.zchunk = zchunk;
+    g.zchunks = (nz + zchunk - 1) / zchunk;
+    return g;
+}
+
+// True when every array meets TMA's rules: 16-byte aligned base and a row
+// pitch that is a multiple of 16 bytes.
+inline bool tma_ok(size_t esize, int nx, std::initializer_list<const void *> ptrs) {
+    if (((size_t)nx * esize) % 16 != 0) return false;
+    for (const void *p : ptrs)
+        if (p && (reinterpret_cast<uintptr_t>(p) & 15u)) return false;
+    return true;
+}
+
+template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
+struct PassKernel {
+    static constexpr size_t smem = zmarch_smem_bytes<T, TX, TY, S, KIND>();
+    static constexpr int threads = TX / 4 * TY;
+    static void *fn() { return reinterpret_cast<void *>(&zmarch_kernel<T, TX, TY, S, KIND, TMA, Op>); }
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(zmarch_kernel<T, TX, TY, S, KIND, TMA, Op>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    static int occupancy() {
+        int n = 0;
+        if (prepare() != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, zmarch_kernel<T, TX, TY, S, KIND, TMA, Op>,
+                                                          threads, smem) != cudaSuccess)
+            return 1;
+        return std::max(n, 1);
+    }
+    static cudaError_t launch(const PassMaps &maps, const PassArgs &a, const Op &op, dim3 grid,
+                              cudaStream_t s) {
+        zmarch_kernel<T, TX, TY, S, KIND, TMA, Op><<<grid, threads, smem, s>>>(maps, a, op);
+        return cudaGetLastError();
+    }
+};
+
+// Runtime dispatch over the tile configuration.
+#define GB_CFG_DISPATCH(cfg, T, KIND, TMA, Op, CALL)                             \
+    [&]() {                                                                    \
+        switch (cfg) {                                                         \
+            case CFG_64x16: { using K = PassKernel<T, 64, 16, 4, KIND, TMA, Op>; return CALL; } \
+            case CFG_32x16: { using K = PassKernel<T, 32, 16, 4, KIND, TMA, Op>; return CALL; } \
+            case CFG_128x8: { using K = PassKernel<T, 128, 8, 4, KIND, TMA, Op>; return CALL; } \
+            default: { using K = PassKernel<T, 64, 8, 4, KIND, TMA, Op>; return CALL; }        \
+        }                                                                      \
+    }()
+
+// Encodes the tensor map of one array for a configuration: halo boxes
+// ((TX + 2 XH) x (TY + 2) x 1) or center boxes (TX x TY x 1).
+template <typename T>
+int make_pass_map(CUtensorMap *m, int cfg, bool halo, const void *base, int nx, int ny, int nz) {
+    CfgDims d = cfg_dims(cfg);
+    const int xh = 16 / (int)sizeof(T);
+    if (halo) return make_map_3d(m, TypeTag<T>::tma, sizeof(T), base, nx, ny, nz, d.tx + 2 * xh, d.ty + 2, 1);
+    return make_map_3d(m, TypeTag<T>::tma, sizeof(T), base, nx, ny, nz, d.tx, d.ty, 1);
+}
+
+inline OpConst make_op_const(int nx, int ny, int nz, float scale = 1.0f) {
+    auto c = [](int n) { double h = 1.0 / (n + 1); return 1.0 / (h * h); };
+    OpConst o;
+    o.cx = (float)(c(nx) * scale);
+    o.cy = (float)(c(ny) * scale);
+    o.cz = (float)(c(nz) * scale);
+    o.inv_d = (float)(1.0 / (2.0 * ((double)o.cx + (double)o.cy + (double)o.cz)));
+    return o;
+}
+
+inline OpBlock make_op_block(const gbpcg_grid &g, float scale = 1.0f) {
+    auto c = [](int n) { double h = 1.0 / (n + 1); return 1.0 / (h * h); };
+    OpBlock o;
+    o.inv_d = 0.0f;
+    o.kb = g.k_block;
+    o.nx = g.nx; o.ny = g.ny; o.nz = g.nz;
+    o.kbx = g.kbx; o.kby = g.kby; o.kbz = g.kbz;
+    o.nbx = (g.nx + g.kbx - 1) / g.kbx;
+    o.nby = (g.ny + g.kby - 1) / g.kby;
+    o.cx = (float)(c(g.nx) * scale); o.cy = (float)(c(g.ny) * scale); o.cz = (float)(c(g.nz) * scale);
+    return o;
+}
+
+// Validates a grid description; returns GBPCG_OK or GBPCG_ERR_ARG.
+int check_grid(const gbpcg_grid *g);
+
+}  // namespace gb

@@ -1,0 +1,135 @@
+"""Host-side checks of the C ABI: the library loads without a GPU, exports
+every entry point the header declares, the ctypes structures match the C
+layout, and argument validation rejects bad calls before any launch."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2603_23343_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gbpcg.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbpcg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return B.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert names, "no declarations parsed"
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in gbpcg.h but not exported"
+    assert sorted(B.EXPORTS) == sorted(names)
+
+
+def test_version_string(lib):
+    assert B.version().startswith("gbpcg") and "sm_103a" in B.version()
+
+
+def test_struct_layout_matches_header(tmp_path):
+    probe = tmp_path / "probe.c"
+    probe.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "gbpcg.h"\n'
+        "int main(void){\n"
+        ' printf("%zu %zu %zu %zu\\n", sizeof(gbpcg_grid), offsetof(gbpcg_grid, k_block), offsetof(gbpcg_grid, kbx), offsetof(gbpcg_grid, kbz));\n'
+        ' printf("%zu %zu %zu %zu\\n", sizeof(gbpcg_opts), offsetof(gbpcg_opts, flags), offsetof(gbpcg_opts, workspace), offsetof(gbpcg_opts, workspace_bytes));\n'
+        ' printf("%zu %zu %zu %zu %zu\\n", sizeof(gbpcg_result), offsetof(gbpcg_result, rel_res_recursive), offsetof(gbpcg_result, time_ms), offsetof(gbpcg_result, pass_launches), offsetof(gbpcg_result, replacements));\n'
+        " return 0;}\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-std=c11", f"-I{os.path.dirname(HEADER)}", str(probe), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    g = [int(v) for v in out[0].split()]
+    o = [int(v) for v in out[1].split()]
+    r = [int(v) for v in out[2].split()]
+    assert g == [ctypes.sizeof(B.Grid), B.Grid.k_block.offset, B.Grid.kbx.offset, B.Grid.kbz.offset]
+    assert o == [ctypes.sizeof(B.Opts), B.Opts.flags.offset, B.Opts.workspace.offset, B.Opts.workspace_bytes.offset]
+    assert r == [ctypes.sizeof(B.Result), B.Result.rel_res_recursive.offset, B.Result.time_ms.offset,
+                 B.Result.pass_launches.offset, B.Result.replacements.offset]
+
+
+def test_workspace_size_is_host_logic(lib):
+    n = 64 * 48 * 40
+    ws = B.workspace_size((40, 48, 64))
+    assert ws >= 3 * 4 * n  # z and two p buffers in FP32
+    ws_io = B.workspace_size((40, 48, 64), host_io=True)
+    assert ws_io >= ws + 2 * 4 * n
+
+
+def _grid(nx, ny, nz):
+    return B.Grid(nx, ny, nz, None, 1, 1, 1)
+
+
+@pytest.mark.parametrize("dims", [(0, 4, 4), (4, -1, 4), (4, 4, 0)])
+def test_bad_grid_is_rejected_before_launch(lib, dims):
+    g = _grid(*dims)
+    rc = lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, ctypes.c_void_p(16), ctypes.c_void_p(32), None)
+    assert rc == B.ERR_ARG
+    assert "invalid argument" in B.last_error()
+
+
+def test_bad_dtype_and_aliasing_rejected(lib):
+    g = _grid(8, 8, 8)
+    assert lib.gbpcg_stencil_apply(ctypes.byref(g), 7, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == B.ERR_ARG
+    assert lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, ctypes.c_void_p(16), ctypes.c_void_p(16), None) == B.ERR_ARG
+    assert lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, None, ctypes.c_void_p(16), None) == B.ERR_ARG
+
+
+def test_block_coefficient_needs_block_edges(lib):
+    g = B.Grid(8, 8, 8, 4096, 0, 8, 8)
+    assert lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == B.ERR_ARG
+
+
+def test_dot_argument_checks(lib):
+    small = ctypes.c_size_t(16)
+    rc = lib.gbpcg_dot(10, B.F32, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(64),
+                       ctypes.c_void_p(256), small, None)
+    assert rc == B.ERR_ARG and "workspace" in B.last_error()
+    rc = lib.gbpcg_dot(-1, B.F32, None, None, ctypes.c_void_p(64), ctypes.c_void_p(256),
+                       B.dot_workspace_size(), None)
+    assert rc == B.ERR_ARG
+    rc = lib.gbpcg_dot(10, B.F32, ctypes.c_void_p(16), ctypes.c_void_p(32), None, ctypes.c_void_p(256),
+                       B.dot_workspace_size(), None)
+    assert rc == B.ERR_ARG
+
+
+def test_axpy_argument_checks(lib):
+    assert lib.gbpcg_axpy(-5, B.F32, 1.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == B.ERR_ARG
+    assert lib.gbpcg_axpy(5, B.F32, 1.0, None, ctypes.c_void_p(32), None) == B.ERR_ARG
+    assert lib.gbpcg_axpy(0, B.F32, 1.0, None, None, None) == B.OK  # empty is a no-op
+
+
+def test_solve_argument_checks(lib):
+    g = _grid(16, 16, 16)
+    o = B.make_opts()
+    r = B.Result()
+    # no workspace
+    rc = lib.gbpcg_pcg_solve(ctypes.byref(g), ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.byref(o),
+                             ctypes.byref(r), None)
+    assert rc == B.ERR_ARG and "workspace" in B.last_error()
+    o.tol = -1.0
+    n = ctypes.c_size_t(0)
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    o = B.make_opts(storage=5)
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+
+
+def test_last_error_is_cleared_on_success(lib):
+    g = _grid(0, 1, 1)
+    lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, None, None, None)
+    assert B.last_error() != ""
+    n = ctypes.c_size_t(0)
+    g2 = _grid(4, 4, 4)
+    o = B.make_opts()
+    assert lib.gbpcg_workspace_size(ctypes.byref(g2), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    assert B.last_error() == ""
