@@ -136,6 +136,27 @@ int gbpcg_dot(int64_t n, int32_t dtype, const void *x, const void *y, double *re
               void *workspace, size_t workspace_bytes, gbpcg_stream stream);
 
 /*
+ * *result = sum_i x_i y_i, like gbpcg_dot, without any memory from the
+ * caller or the allocator.  (The paper has no counterpart; this exists for
+ * callers that cannot allocate device memory: code running while a stream is
+ * being captured into a CUDA graph, where cudaMalloc is not allowed; code
+ * that runs under another framework's memory pool and must not create
+ * allocations of its own; and latency-critical loops that cannot afford the
+ * device synchronisation cudaMalloc/cudaFree may cause.)
+ *
+ * Its scratch is a static 128 KiB device array inside the library, present on
+ * every GPU that loads it until the process exits.  The first call on a
+ * device looks up that array's device address, so make that first call
+ * outside any stream capture.  n is limited to 2^30 elements; larger n
+ * returns GBPCG_ERR_ARG.  All calls share the one array: calls that may
+ * overlap on the GPU (different streams, or different host threads without
+ * ordering) race and must be serialised by the caller.  x, y: DEVICE arrays
+ * of n elements of dtype; result: DEVICE double; n = 0 writes 0.
+ */
+int gbpcg_dot_noalloc(int64_t n, int32_t dtype, const void *x, const void *y, double *result,
+                      gbpcg_stream stream);
+
+/*
  * y = alpha x + y  (Sec. IV: element-wise arithmetic).  x, y: DEVICE arrays of
  * n elements of dtype (F32, BF16, F16: FP32 arithmetic; F64); in place on y.
  */

@@ -29,7 +29,7 @@ FLAG_PROFILE = 2
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
 
 EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbpcg_stencil_apply", "gbpcg_dot",
-           "gbpcg_axpy", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
+           "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
 
 
 class Grid(ctypes.Structure):
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_stencil_apply.argtypes = [ctypes.POINTER(Grid), I32, P, P, P]
         lib.gbpcg_dot.restype = ctypes.c_int
         lib.gbpcg_dot.argtypes = [I64, I32, P, P, P, P, SZ, P]
+        lib.gbpcg_dot_noalloc.restype = ctypes.c_int
+        lib.gbpcg_dot_noalloc.argtypes = [I64, I32, P, P, P, P]
         lib.gbpcg_axpy.restype = ctypes.c_int
         lib.gbpcg_axpy.argtypes = [I64, I32, D, P, P, P]
         lib.gbpcg_workspace_size.restype = ctypes.c_int
@@ -165,6 +167,18 @@ def dot(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, works
         workspace = torch.empty(dot_workspace_size(), dtype=torch.uint8, device=x.device)
     _check(load().gbpcg_dot(x.numel(), _dtype(x), _ptr(x), _ptr(y), _ptr(out), _ptr(workspace),
                             workspace.numel(), _stream(stream)))
+    return out
+
+
+def dot_noalloc(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """x . y through gbpcg_dot_noalloc, which takes no workspace and allocates
+    nothing: its scratch is a static array inside the library (calls must not
+    overlap on the GPU).  ``out`` is the caller's float64 device scalar."""
+    if x.numel() != y.numel() or x.dtype != y.dtype:
+        raise GbpcgError(ERR_ARG, "x and y must have the same size and dtype")
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=x.device)
+    _check(load().gbpcg_dot_noalloc(x.numel(), _dtype(x), _ptr(x), _ptr(y), _ptr(out), _stream(stream)))
     return out
 
 

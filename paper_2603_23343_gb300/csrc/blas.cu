@@ -7,6 +7,7 @@
 // the data, one launch, a bitwise-reproducible result (the GPU analogue of
 // the paper's "reduce locally, then forward one partial" routing).
 #include <algorithm>
+#include <mutex>
 
 #include "launch.cuh"
 
@@ -155,6 +156,54 @@ static int axpy_typed(int64_t n, double alpha, const void *x, void *y, cudaStrea
     return GBPCG_OK;
 }
 
+// ------------------------------------------------ dot without allocation --
+//
+// Scratch for gbpcg_dot_noalloc lives in this file-scope device array: a
+// ticket word (first 256 bytes) and one FP64 partial sum per block.  The
+// array exists once per GPU that loads the library and stays until the
+// process exits.  The launch uses one block per kNoAllocPerBlock elements,
+// so kNoAllocMaxBlocks partials bound n.
+constexpr unsigned kNoAllocMaxBlocks = 16384;
+constexpr int64_t kNoAllocPerBlock = 65536;
+constexpr int64_t kNoAllocMaxN = (int64_t)kNoAllocMaxBlocks * kNoAllocPerBlock;  // 2^30
+constexpr size_t kNoAllocScratchBytes = 256 + sizeof(double) * kNoAllocMaxBlocks;
+
+static __device__ __align__(256) unsigned char g_dot_scratch[kNoAllocScratchBytes];
+
+// Host code cannot use g_dot_scratch's name as a device address; the real
+// address is fetched once per device (with that device current) and cached.
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64] = {nullptr};
+
+static int noalloc_scratch(void **out) {
+    int dev = -1;
+    GB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail_arg("device ordinal out of range for the static scratch table");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dot_scratch);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress(g_dot_scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return GBPCG_OK;
+}
+
+template <typename T>
+static int dot_noalloc_typed(int64_t n, const void *x, const void *y, double *out, void *scratch, cudaStream_t s) {
+    unsigned *ticket = static_cast<unsigned *>(scratch);
+    double *partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+    // the array keeps the previous call's contents: the ticket must restart at zero
+    GB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+    const int vec = sizeof(T) == 4 ? (aligned16(x) && aligned16(y)) : (((uintptr_t)x | (uintptr_t)y) & 7u) == 0;
+    dot_kernel<T><<<blocks, kDotThreads, 0, s>>>(n, static_cast<const T *>(x), static_cast<const T *>(y), partials,
+                                                 ticket, out, vec);
+    GB_CUDA(cudaGetLastError());
+    return GBPCG_OK;
+}
+
 }  // namespace gb
 
 using namespace gb;
@@ -215,6 +264,40 @@ int gbpcg_axpy(int64_t n, int32_t dtype, double alpha, const void *x, void *y, g
             return GBPCG_OK;
         }
         default: return fail_arg("unknown dtype");
+    }
+}
+
+int gbpcg_dot_noalloc(int64_t n, int32_t dtype, const void *x, const void *y, double *result, gbpcg_stream stream) {
+    clear_error();
+    if (n < 0) return fail_arg("n must be >= 0");
+    if (n > kNoAllocMaxN)
+        return fail_arg("n = " + std::to_string(n) + " exceeds gbpcg_dot_noalloc's static scratch limit of " +
+                        std::to_string(kNoAllocMaxN) + " elements; use gbpcg_dot with a workspace");
+    if (!result) return fail_arg("result must be a device pointer");
+    if (n > 0 && (!x || !y)) return fail_arg("x and y must be non-NULL");
+    if (dtype != GBPCG_F32 && dtype != GBPCG_BF16 && dtype != GBPCG_F16 && dtype != GBPCG_F64)
+        return fail_arg("unknown dtype");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    if (int rc = noalloc_scratch(&scratch)) return rc;
+    if (n == 0) {
+        GB_CUDA(cudaMemsetAsync(result, 0, sizeof(double), s));
+        return GBPCG_OK;
+    }
+    switch (dtype) {
+        case GBPCG_F32: return dot_noalloc_typed<float>(n, x, y, result, scratch, s);
+        case GBPCG_BF16: return dot_noalloc_typed<__nv_bfloat16>(n, x, y, result, scratch, s);
+        case GBPCG_F16: return dot_noalloc_typed<__half>(n, x, y, result, scratch, s);
+        default: {
+            unsigned *ticket = static_cast<unsigned *>(scratch);
+            double *partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
+            const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+            GB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+            dot_f64_kernel<<<blocks, kDotThreads, 0, s>>>(n, static_cast<const double *>(x),
+                                                         static_cast<const double *>(y), partials, ticket, result);
+            GB_CUDA(cudaGetLastError());
+            return GBPCG_OK;
+        }
     }
 }
 

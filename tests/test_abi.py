@@ -103,6 +103,14 @@ def test_dot_argument_checks(lib):
     assert rc == B.ERR_ARG
 
 
+def test_dot_noalloc_rejects_n_beyond_its_static_scratch(lib):
+    # checked before any CUDA call: n above 2^30 does not fit the static partial-sum array
+    rc = lib.gbpcg_dot_noalloc((1 << 30) + 1, B.F32, ctypes.c_void_p(16), ctypes.c_void_p(32),
+                               ctypes.c_void_p(64), None)
+    assert rc == B.ERR_ARG and "static scratch" in B.last_error()
+    assert lib.gbpcg_dot_noalloc(-1, B.F32, None, None, ctypes.c_void_p(64), None) == B.ERR_ARG
+
+
 def test_axpy_argument_checks(lib):
     assert lib.gbpcg_axpy(-5, B.F32, 1.0, ctypes.c_void_p(16), ctypes.c_void_p(32), None) == B.ERR_ARG
     assert lib.gbpcg_axpy(5, B.F32, 1.0, None, ctypes.c_void_p(32), None) == B.ERR_ARG
