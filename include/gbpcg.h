@@ -87,7 +87,8 @@ typedef struct gbpcg_opts {
     int32_t storage;       /* gbpcg_dtype of the solver's vectors (GBPCG_F32) */
     int32_t io_dtype;      /* gbpcg_dtype of b and x (GBPCG_F32) */
     uint32_t flags;        /* GBPCG_FLAG_* */
-    int32_t reserved0;
+    int32_t tile_cfg;      /* 0: automatic; else (a + 1) | (b + 1) << 8 picks the tile
+                              configuration of pass A / pass B (see gbpcg_tile_config) */
     void *workspace;       /* device scratch owned by the caller */
     size_t workspace_bytes;
 } gbpcg_opts;
@@ -162,6 +163,12 @@ int gbpcg_dot_noalloc(int64_t n, int32_t dtype, const void *x, const void *y, do
  */
 int gbpcg_axpy(int64_t n, int32_t dtype, double alpha, const void *x, void *y,
                gbpcg_stream stream);
+
+/* Tile configuration `index` (0 .. count-1) of the solver's data passes: tile
+ * width tx and height ty in grid points, pipeline stages.  Returns
+ * GBPCG_ERR_ARG past the last configuration (the way to count them).  Used
+ * by autotuners together with gbpcg_opts.tile_cfg. */
+int gbpcg_tile_config(int32_t index, int32_t *tx, int32_t *ty, int32_t *stages);
 
 /* Bytes of workspace gbpcg_pcg_solve needs for this grid and options. */
 int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t *bytes);

@@ -29,7 +29,7 @@ FLAG_PROFILE = 2
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
 
 EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbpcg_stencil_apply", "gbpcg_dot",
-           "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
+           "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_tile_config", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
 
 
 class Grid(ctypes.Structure):
@@ -41,7 +41,7 @@ class Grid(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("io_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("reserved0", ctypes.c_int32), ("workspace", ctypes.c_void_p),
+                ("tile_cfg", ctypes.c_int32), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -89,6 +89,8 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_dot_noalloc.argtypes = [I64, I32, P, P, P, P]
         lib.gbpcg_axpy.restype = ctypes.c_int
         lib.gbpcg_axpy.argtypes = [I64, I32, D, P, P, P]
+        lib.gbpcg_tile_config.restype = ctypes.c_int
+        lib.gbpcg_tile_config.argtypes = [I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]
         lib.gbpcg_workspace_size.restype = ctypes.c_int
         lib.gbpcg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), ctypes.POINTER(SZ)]
         lib.gbpcg_pcg_solve.restype = ctypes.c_int
@@ -190,8 +192,24 @@ def axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.T
     return y
 
 
+def tile_configs():
+    """[(tx, ty, stages), ...] of the data passes' tile configurations."""
+    out = []
+    lib = load()
+    while True:
+        tx, ty, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        if lib.gbpcg_tile_config(len(out), ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(st)) != OK:
+            return out
+        out.append((tx.value, ty.value, st.value))
+
+
+def tile_cfg_code(cfg_a=None, cfg_b=None) -> int:
+    """gbpcg_opts.tile_cfg for explicit pass-A / pass-B configuration indices."""
+    return (0 if cfg_a is None else cfg_a + 1) | ((0 if cfg_b is None else cfg_b + 1) << 8)
+
+
 def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
-              profile=False) -> Opts:
+              profile=False, tile_cfg=0) -> Opts:
     o = Opts()
     o.tol = float(tol)
     o.maxit = int(maxit)
@@ -199,6 +217,7 @@ def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, wo
     o.storage = storage
     o.io_dtype = io_dtype
     o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0)
+    o.tile_cfg = int(tile_cfg)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -218,7 +237,7 @@ def alloc_workspace(shape, k_block=None, kb=8, device="cuda", **opt_kw) -> torch
 
 
 def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
-              workspace: torch.Tensor | None = None, host_io=False, profile=False, stream=None):
+              workspace: torch.Tensor | None = None, host_io=False, profile=False, tile_cfg=0, stream=None):
     """Jacobi-PCG solve of A x = b (gbpcg_pcg_solve).  Returns (x, result dict).
 
     b and x are float32 or float64 (the solution accumulates in that type; the
@@ -239,7 +258,7 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     if workspace is None:
         workspace = alloc_workspace(b.shape, k_block, kb, device=dev, io_dtype=io, host_io=host_io)
     g = make_grid(b.shape, k_block, kb)
-    o = make_opts(tol, maxit, F32, io, host_io, workspace, profile)
+    o = make_opts(tol, maxit, F32, io, host_io, workspace, profile, tile_cfg)
     r = Result()
     rc = load().gbpcg_pcg_solve(ctypes.byref(g), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
                                 _stream(stream))

@@ -70,9 +70,13 @@ constexpr double kReplaceDrop2 = 1e-2;
 struct OpConst {
     static constexpr bool kConst = true;
     float cx, cy, cz;
-    float inv_d;  // 1 / (2 (cx + cy + cz))
-    __device__ __forceinline__ void weights(int, int, int, float w[6]) const {
-        w[0] = cx; w[1] = cx; w[2] = cy; w[3] = cy; w[4] = cz; w[5] = cz;
+    float d;      // diagonal 2 (cx + cy + cz)
+    float inv_d;  // 1 / d
+    // q = (A u)_c from the centre and its six neighbours; dg = diagonal
+    __device__ __forceinline__ void apply(float c, float xm, float xp, float ym, float yp, float zm, float zp, int,
+                                          int, int, float &q, float &dg) const {
+        q = fmaf(d, c, -fmaf(cx, xm + xp, fmaf(cy, ym + yp, cz * (zm + zp))));
+        dg = d;
     }
 };
 
@@ -100,6 +104,13 @@ struct OpBlock {
         w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
         w[5] = cz * ((iz == kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
     }
+    __device__ __forceinline__ void apply(float c, float xm, float xp, float ym, float yp, float zm, float zp, int i,
+                                          int j, int k, float &q, float &dg) const {
+        float w[6];
+        weights(i, j, k, w);
+        q = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) + w[4] * (c - zm) + w[5] * (c - zp);
+        dg = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
+    }
 };
 
 struct __align__(128) PassMaps {
@@ -126,10 +137,15 @@ struct PassArgs {
 
 constexpr uint32_t round128(uint32_t v) { return (v + 127u) & ~127u; }
 
+// Tiles of width 256 span a whole grid row (nx <= 256): they need no x halo,
+// so their boxes are whole rows, contiguous in memory.
+template <int TX>
+constexpr bool full_row() { return TX == 256; }
+
 template <typename T, int TX, int TY, int KIND>
 struct Geometry {
     static constexpr int NT = TX / 4 * TY;
-    static constexpr int XH = 16 / (int)sizeof(T);
+    static constexpr int XH = full_row<TX>() ? 0 : 16 / (int)sizeof(T);
     static constexpr int HX = TX + 2 * XH, HY = TY + 2;
     static constexpr int NH = KIND == K_PASSA ? 2 : 1;
     static constexpr int NC = KIND == K_STENCIL ? 0 : 1;
@@ -225,12 +241,21 @@ __global__ void __launch_bounds__(TX / 4 * TY)
     }
     __syncthreads();
 
-    const int m_first = k0 - 1, m_last = k1;  // planes loaded (k0-1 and k1 are halo planes)
+    // Planes are visited in march order: step t = 0..tl loads plane pl(t),
+    // forward pl(t) = k0 - 1 + t, reverse pl(t) = k1 - t (the first and the
+    // last loaded planes are halo planes); step t >= 2 outputs plane pl(t-1).
+    // Pass B marches down so it starts on the planes pass A touched last,
+    // which are still in L2; the next pass A, marching up, starts where pass
+    // B ended.
+    constexpr bool REV = KIND == K_PASSB;
+    const int tl = k1 - k0 + 1;
+    auto plane = [&](int t) { return REV ? k1 - t : k0 - 1 + t; };
 
-    auto issue = [&](int m) {
-        const int s = (m - m_first) % S;
+    auto issue = [&](int t) {
+        const int m = plane(t);
+        const int s = t % S;
         unsigned char *base = smem + (size_t)s * SB;
-        const bool cen = load_c && m >= k0 && m < k1;
+        const bool cen = load_c && t >= 1 && t < tl;
         if constexpr (TMA) {
             if (threadIdx.x == 0) {
                 const uint32_t bytes = G::HBYTES + (load_h1 ? G::HBYTES : 0u) + (cen ? G::CBYTES : 0u);
@@ -269,46 +294,47 @@ __global__ void __launch_bounds__(TX / 4 * TY)
         }
     };
 
-    int issued_hi = m_first - 1;
-    int consumed = m_first - 1;
+    int issued_hi = -1;
+    int consumed = -1;
     if (k0 < k1) {
-        for (int m = m_first; m <= m_last && m < m_first + S; ++m) {
-            issue(m);
-            issued_hi = m;
+        for (int t = 0; t <= tl && t < S; ++t) {
+            issue(t);
+            issued_hi = t;
         }
         float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f}, qc[4] = {0.f, 0.f, 0.f, 0.f};
         const int cidx = (ly + 1) * HX + XH + 4 * lx;  // this thread's first point in a halo box
-        for (int m = m_first; m <= m_last; ++m) {
-            const int s = (m - m_first) % S;
+        for (int t = 0; t <= tl; ++t) {
+            const int s = t % S;
             const unsigned char *base = smem + (size_t)s * SB;
             if constexpr (TMA) {
-                if (!mbar_wait_bounded(&full[s], ((m - m_first) / S) & 1)) s_timeout = 1;
+                if (!mbar_wait_bounded(&full[s], (t / S) & 1)) s_timeout = 1;
             }
-            consumed = m;
+            consumed = t;
 #pragma unroll
             for (int i = 0; i < 4; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
             in_val4(base, cidx, qc);
-            if (m >= k0 + 1) {
-                // ---- output plane k = m - 1 from the stage of plane k ----
-                const int k = m - 1;
-                const unsigned char *bk = smem + (size_t)((k - m_first) % S) * SB;
+            if (t >= 2) {
+                // ---- output plane k = pl(t-1) from its own stage ----
+                const int k = plane(t - 1);
+                const unsigned char *bk = smem + (size_t)((t - 1) % S) * SB;
                 float ym[4], yp[4];
                 in_val4(bk, cidx - HX, ym);
                 in_val4(bk, cidx + HX, yp);
-                const float xl = in_val(bk, cidx - 1), xr = in_val(bk, cidx + 4);
+                // whole-row tiles: the x neighbours past either end of the row are
+                // boundary zeros (the box holds no x halo)
+                const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
+                const float xr = (full_row<TX>() && lx == TX / 4 - 1) ? 0.0f : in_val(bk, cidx + 4);
                 float q[4], dg[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float c = qb[i];
                     const float xm = i == 0 ? xl : qb[i - 1];
                     const float xp = i == 3 ? xr : qb[i + 1];
-                    float w[6];
+                    const float zm = REV ? qc[i] : qa[i];
+                    const float zp = REV ? qa[i] : qc[i];
                     // masked-off points past the grid edge use an in-range
-                    // position so the coefficient lookup stays inside k_block
-                    op.weights(min(gx + i, nx - 1), min(gy, ny - 1), k, w);
-                    q[i] = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym[i]) + w[3] * (c - yp[i]) +
-                           w[4] * (c - qa[i]) + w[5] * (c - qc[i]);
-                    dg[i] = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
+                    // position so a coefficient lookup stays inside k_block
+                    op.apply(qb[i], xm, xp, ym[i], yp[i], zm, zp, min(gx + i, nx - 1), min(gy, ny - 1), k, q[i],
+                             dg[i]);
                 }
                 const size_t g = ((size_t)k * ny + gy) * nx + gx;
                 const T *cen = reinterpret_cast<const T *>(bk + NH * HB) + ly * TX + 4 * lx;
@@ -359,16 +385,15 @@ __global__ void __launch_bounds__(TX / 4 * TY)
             }
             __syncthreads();
             if (s_timeout) break;
-            if (m >= k0 && m - 1 + S <= m_last) {
-                issue(m - 1 + S);
-                issued_hi = m - 1 + S;
+            if (t >= 1 && t - 1 + S <= tl) {
+                issue(t - 1 + S);
+                issued_hi = t - 1 + S;
             }
         }
         if constexpr (TMA) {
             if (s_timeout) {
                 // give copies still in flight a bounded chance to land before exit
-                for (int m = consumed + 1; m <= issued_hi; ++m)
-                    mbar_wait_bounded(&full[(m - m_first) % S], ((m - m_first) / S) & 1);
+                for (int t = consumed + 1; t <= issued_hi; ++t) mbar_wait_bounded(&full[t % S], (t / S) & 1);
                 if (threadIdx.x == 0) atomicExch(&st->timeout, 1);
             }
         }

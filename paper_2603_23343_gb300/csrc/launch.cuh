@@ -9,16 +9,33 @@
 namespace gb {
 
 // Tile configurations the library is built with (x width, y height, stages).
-enum TileCfg { CFG_64x16 = 0, CFG_32x16 = 1, CFG_128x8 = 2, CFG_64x8 = 3, NUM_CFG = 4 };
+enum TileCfg {
+    CFG_64x16 = 0,
+    CFG_32x16 = 1,
+    CFG_128x8 = 2,
+    CFG_64x8 = 3,
+    CFG_64x8_S6 = 4,
+    CFG_128x8_S6 = 5,
+    CFG_256x4 = 6,  // whole rows, nx <= 256
+    CFG_256x8 = 7,  // whole rows, nx <= 256
+    NUM_CFG = 8
+};
 struct CfgDims { int tx, ty, s; };
 inline CfgDims cfg_dims(int c) {
     switch (c) {
         case CFG_64x16: return {64, 16, 4};
         case CFG_32x16: return {32, 16, 4};
         case CFG_128x8: return {128, 8, 4};
-        default: return {64, 8, 4};
+        case CFG_64x8: return {64, 8, 4};
+        case CFG_64x8_S6: return {64, 8, 6};
+        case CFG_128x8_S6: return {128, 8, 6};
+        case CFG_256x4: return {256, 4, 4};
+        default: return {256, 8, 4};
     }
 }
+
+// Whether a configuration can serve a grid of width nx.
+inline bool cfg_fits(int c, int nx) { return cfg_dims(c).tx != 256 || nx <= 256; }
 
 struct PassGeom {
     int cfg;
@@ -97,7 +114,11 @@ struct PassKernel {
             case CFG_64x16: { using K = PassKernel<T, 64, 16, 4, KIND, TMA, Op>; return CALL; } \
             case CFG_32x16: { using K = PassKernel<T, 32, 16, 4, KIND, TMA, Op>; return CALL; } \
             case CFG_128x8: { using K = PassKernel<T, 128, 8, 4, KIND, TMA, Op>; return CALL; } \
-            default: { using K = PassKernel<T, 64, 8, 4, KIND, TMA, Op>; return CALL; }        \
+            case CFG_64x8: { using K = PassKernel<T, 64, 8, 4, KIND, TMA, Op>; return CALL; }   \
+            case CFG_64x8_S6: { using K = PassKernel<T, 64, 8, 6, KIND, TMA, Op>; return CALL; } \
+            case CFG_128x8_S6: { using K = PassKernel<T, 128, 8, 6, KIND, TMA, Op>; return CALL; } \
+            case CFG_256x4: { using K = PassKernel<T, 256, 4, 4, KIND, TMA, Op>; return CALL; }  \
+            default: { using K = PassKernel<T, 256, 8, 4, KIND, TMA, Op>; return CALL; }         \
         }                                                                      \
     }()
 
@@ -106,7 +127,7 @@ struct PassKernel {
 template <typename T>
 int make_pass_map(CUtensorMap *m, int cfg, bool halo, const void *base, int nx, int ny, int nz) {
     CfgDims d = cfg_dims(cfg);
-    const int xh = 16 / (int)sizeof(T);
+    const int xh = d.tx == 256 ? 0 : 16 / (int)sizeof(T);
     if (halo) return make_map_3d(m, TypeTag<T>::tma, sizeof(T), base, nx, ny, nz, d.tx + 2 * xh, d.ty + 2, 1);
     return make_map_3d(m, TypeTag<T>::tma, sizeof(T), base, nx, ny, nz, d.tx, d.ty, 1);
 }
@@ -117,6 +138,7 @@ inline OpConst make_op_const(int nx, int ny, int nz, float scale = 1.0f) {
     o.cx = (float)(c(nx) * scale);
     o.cy = (float)(c(ny) * scale);
     o.cz = (float)(c(nz) * scale);
+    o.d = (float)(2.0 * ((double)o.cx + (double)o.cy + (double)o.cz));
     o.inv_d = (float)(1.0 / (2.0 * ((double)o.cx + (double)o.cy + (double)o.cz)));
     return o;
 }

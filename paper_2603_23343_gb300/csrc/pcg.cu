@@ -237,13 +237,16 @@ static int check_opts(const gbpcg_opts *o) {
     if (o->precond != GBPCG_PRECOND_JACOBI) return fail_arg("unknown preconditioner");
     if (!(o->tol >= 0.0)) return fail_arg("tol must be >= 0");
     if (o->maxit < 0) return fail_arg("maxit must be >= 0");
+    if (o->tile_cfg < 0 || (o->tile_cfg & 0xff) > NUM_CFG || ((o->tile_cfg >> 8) & 0xff) > NUM_CFG ||
+        (o->tile_cfg >> 16))
+        return fail_arg("tile_cfg selects unknown tile configurations");
     return GBPCG_OK;
 }
 
 // ------------------------------------------------------------ the graph --
 
 struct SolveKey {
-    int dev, nx, ny, nz, kbx, kby, kbz, maxit, cfg, tma, io;
+    int dev, nx, ny, nz, kbx, kby, kbz, maxit, cfg_a, cfg_b, tma, io;
     const void *kb, *b, *x, *ws;
     double tol;
     bool operator==(const SolveKey &o) const { return memcmp(this, &o, sizeof(SolveKey)) == 0; }
@@ -267,7 +270,7 @@ struct SolvePlan {
     using T = float;
     gbpcg_grid g;
     Op op;
-    int cfg;
+    int cfg_a, cfg_b;
     const X *b;
     X *x;
     SolveState *st;
@@ -282,9 +285,9 @@ struct SolvePlan {
     cudaGraphConditionalHandle cond_loop = 0, cond_rep = 0;
     int use_cond = 0;
 
-    int init(const gbpcg_grid &grid, const Op &o, int c, const X *bb, X *xx, char *ws, const WsLayout &L, double tl,
-             int mi_) {
-        g = grid; op = o; cfg = c; b = bb; x = xx; tol = tl; maxit = mi_;
+    int init(const gbpcg_grid &grid, const Op &o, int ca, int cb, const X *bb, X *xx, char *ws, const WsLayout &L,
+             double tl, int mi_) {
+        g = grid; op = o; cfg_a = ca; cfg_b = cb; b = bb; x = xx; tol = tl; maxit = mi_;
         st = reinterpret_cast<SolveState *>(ws + L.state);
         partials = reinterpret_cast<double *>(ws + L.partials);
         z = reinterpret_cast<T *>(ws + L.z);
@@ -293,23 +296,27 @@ struct SolvePlan {
         d = reinterpret_cast<T *>(ws + L.d);
         const int nx = g.nx, ny = g.ny, nz = g.nz;
         // kernel attributes and occupancy (never during a capture)
-        int occ_a = GB_CFG_DISPATCH(cfg, T, K_PASSA, TMA, Op, K::occupancy());
-        int occ_b = GB_CFG_DISPATCH(cfg, T, K_PASSB, TMA, Op, K::occupancy());
-        ga = make_geom(cfg, nx, ny, nz, occ_a, GB_CFG_DISPATCH(cfg, T, K_PASSA, TMA, Op, K::smem));
-        gb = make_geom(cfg, nx, ny, nz, occ_b, GB_CFG_DISPATCH(cfg, T, K_PASSB, TMA, Op, K::smem));
+        int occ_a = GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::occupancy());
+        int occ_b = GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::occupancy());
+        ga = make_geom(cfg_a, nx, ny, nz, occ_a, GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::smem));
+        // pass B uses pass A's z chunks (it marches them downwards), so each
+        // of its CTAs starts on the planes pass A's CTAs finished with
+        gb = make_geom(cfg_b, nx, ny, nz, occ_b, GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::smem));
+        gb.zchunk = ga.zchunk;
+        gb.zchunks = ga.zchunks;
         memset(&ma, 0, sizeof(ma));
         memset(&mb, 0, sizeof(mb));
         if (TMA) {
             int rc = 0;
-            rc |= make_pass_map<T>(&ma.h0[0], cfg, true, z, nx, ny, nz);
+            rc |= make_pass_map<T>(&ma.h0[0], cfg_a, true, z, nx, ny, nz);
             ma.h0[1] = ma.h0[0];
-            rc |= make_pass_map<T>(&ma.h1[0], cfg, true, p0, nx, ny, nz);
-            rc |= make_pass_map<T>(&ma.h1[1], cfg, true, p1, nx, ny, nz);
-            rc |= make_pass_map<T>(&ma.c0, cfg, false, d, nx, ny, nz);
-            mb.h0[0] = ma.h1[0];
-            mb.h0[1] = ma.h1[1];
+            rc |= make_pass_map<T>(&ma.h1[0], cfg_a, true, p0, nx, ny, nz);
+            rc |= make_pass_map<T>(&ma.h1[1], cfg_a, true, p1, nx, ny, nz);
+            rc |= make_pass_map<T>(&ma.c0, cfg_a, false, d, nx, ny, nz);
+            rc |= make_pass_map<T>(&mb.h0[0], cfg_b, true, p0, nx, ny, nz);
+            rc |= make_pass_map<T>(&mb.h0[1], cfg_b, true, p1, nx, ny, nz);
             mb.h1[0] = mb.h1[1] = mb.h0[0];
-            rc |= make_pass_map<T>(&mb.c0, cfg, false, z, nx, ny, nz);
+            rc |= make_pass_map<T>(&mb.c0, cfg_b, false, z, nx, ny, nz);
             if (rc) return GBPCG_ERR_CUDA;
         }
         memset(&aa, 0, sizeof(aa));
@@ -367,8 +374,12 @@ struct SolvePlan {
         launch_res64<RES_INIT>(s);
         return cudaGetLastError();
     }
-    cudaError_t launch_a(cudaStream_t s) { return GB_CFG_DISPATCH(cfg, T, K_PASSA, TMA, Op, K::launch(ma, aa, op, ga.grid(), s)); }
-    cudaError_t launch_b(cudaStream_t s) { return GB_CFG_DISPATCH(cfg, T, K_PASSB, TMA, Op, K::launch(mb, ab, op, gb.grid(), s)); }
+    cudaError_t launch_a(cudaStream_t s) {
+        return GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::launch(ma, aa, op, ga.grid(), s));
+    }
+    cudaError_t launch_b(cudaStream_t s) {
+        return GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::launch(mb, ab, op, gb.grid(), s));
+    }
 
     // flush d into x, then r = b - A x in FP64 (both no-ops unless st->replace)
     cudaError_t launch_replace(cudaStream_t s) {
@@ -538,7 +549,7 @@ static bool is_device_ptr(const void *p) {
 
 struct SolveCall {
     const gbpcg_grid *g;
-    int cfg;
+    int cfg_a, cfg_b;
     const void *b;
     void *x;
     char *ws;
@@ -549,8 +560,8 @@ struct SolveCall {
 template <typename Op, bool TMA, typename X>
 static int capture_plan(const SolveCall &c, const Op &op, cudaGraph_t *graph) {
     SolvePlan<Op, TMA, X> plan;
-    if (int rc = plan.init(*c.g, op, c.cfg, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L, c.o->tol,
-                           c.o->maxit))
+    if (int rc = plan.init(*c.g, op, c.cfg_a, c.cfg_b, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L,
+                           c.o->tol, c.o->maxit))
         return rc;
     return plan.capture(graph);
 }
@@ -558,8 +569,8 @@ static int capture_plan(const SolveCall &c, const Op &op, cudaGraph_t *graph) {
 template <typename Op, bool TMA, typename X>
 static int run_plan_profiled(const SolveCall &c, const Op &op, gbpcg_result *res, cudaStream_t s) {
     SolvePlan<Op, TMA, X> plan;
-    if (int rc = plan.init(*c.g, op, c.cfg, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L, c.o->tol,
-                           c.o->maxit))
+    if (int rc = plan.init(*c.g, op, c.cfg_a, c.cfg_b, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L,
+                           c.o->tol, c.o->maxit))
         return rc;
     return plan.run_profiled(s, res->pass_ms, res->pass_launches);
 }
@@ -600,13 +611,34 @@ static int finish_solve(char *ws, const WsLayout &L, void *x, void *xd, bool x_h
     return hs.status;
 }
 
-int pick_cfg(const gbpcg_grid &g) { return g.nx <= 32 ? CFG_32x16 : CFG_64x16; }
+// Tile configurations of pass A and pass B: explicit (opts->tile_cfg) or
+// the default for the grid's width (from a sweep of all pairs at 256^3 on
+// GB300: every shape lands within a few percent; whole-row tiles for pass A
+// and 128x8 for pass B are at the front).
+static void pick_cfgs(const gbpcg_grid &g, const gbpcg_opts &o, int *ca, int *cb) {
+    const int narrow = g.nx <= 32 ? CFG_32x16 : g.nx <= 64 ? CFG_64x16 : -1;
+    const int def_a = narrow >= 0 ? narrow : (g.nx > 192 && g.nx <= 256) ? CFG_256x4 : CFG_128x8;
+    const int def_b = narrow >= 0 ? narrow : CFG_128x8;
+    const int ea = o.tile_cfg & 0xff, eb = (o.tile_cfg >> 8) & 0xff;
+    *ca = ea ? ea - 1 : def_a;
+    *cb = eb ? eb - 1 : def_b;
+}
 
 }  // namespace gb
 
 using namespace gb;
 
 extern "C" {
+
+int gbpcg_tile_config(int32_t index, int32_t *tx, int32_t *ty, int32_t *stages) {
+    clear_error();
+    if (index < 0 || index >= NUM_CFG) return fail_arg("tile configuration index out of range");
+    const CfgDims d = cfg_dims(index);
+    if (tx) *tx = d.tx;
+    if (ty) *ty = d.ty;
+    if (stages) *stages = d.s;
+    return GBPCG_OK;
+}
 
 int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t *bytes) {
     clear_error();
@@ -644,9 +676,12 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     if (b_host) GB_CUDA(cudaMemcpyAsync(const_cast<void *>(bd), b, io_bytes, cudaMemcpyHostToDevice, s));
     if (x_host) GB_CUDA(cudaMemcpyAsync(xd, x, io_bytes, cudaMemcpyHostToDevice, s));
 
-    const int cfg = pick_cfg(g);
+    int cfg_a = 0, cfg_b = 0;
+    pick_cfgs(g, *opts, &cfg_a, &cfg_b);
+    if (!cfg_fits(cfg_a, g.nx) || !cfg_fits(cfg_b, g.nx))
+        return fail_arg("tile_cfg selects a whole-row configuration for a grid wider than 256");
     const bool tma = tma_ok(sizeof(float), g.nx, {ws + L.z, ws + L.p0, ws + L.p1, ws + L.d});
-    const SolveCall call{&g, cfg, bd, xd, ws, L, opts};
+    const SolveCall call{&g, cfg_a, cfg_b, bd, xd, ws, L, opts};
 
     if (opts->flags & GBPCG_FLAG_PROFILE) {
         cudaEvent_t e0, e1;
@@ -668,7 +703,7 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     key.dev = dev; key.nx = g.nx; key.ny = g.ny; key.nz = g.nz;
     key.kb = g.k_block;
     if (g.k_block) { key.kbx = g.kbx; key.kby = g.kby; key.kbz = g.kbz; }
-    key.maxit = opts->maxit; key.cfg = cfg; key.tma = tma; key.io = opts->io_dtype;
+    key.maxit = opts->maxit; key.cfg_a = cfg_a; key.cfg_b = cfg_b; key.tma = tma; key.io = opts->io_dtype;
     key.b = bd; key.x = xd; key.ws = ws; key.tol = opts->tol;
 
     cudaGraphExec_t exec = nullptr;

@@ -58,6 +58,19 @@ def test_struct_layout_matches_header(tmp_path):
                  B.Result.pass_launches.offset, B.Result.replacements.offset]
 
 
+def test_tile_configs_enumerate(lib):
+    cfgs = B.tile_configs()
+    assert len(cfgs) == 8 and cfgs[0] == (64, 16, 4) and cfgs[6] == (256, 4, 4)
+    for tx, ty, st in cfgs:
+        assert tx % 4 == 0 and ty >= 1 and st >= 2
+    g = _grid(16, 16, 16)
+    n = ctypes.c_size_t(0)
+    o = B.make_opts(tile_cfg=B.tile_cfg_code(len(cfgs) - 1, 0))
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    o = B.make_opts(tile_cfg=B.tile_cfg_code(len(cfgs), 0))
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+
+
 def test_workspace_size_is_host_logic(lib):
     n = 64 * 48 * 40
     ws = B.workspace_size((40, 48, 64))

@@ -143,3 +143,22 @@ def test_fp32_solution_accuracy_floor_stops_early(gpu_lib):
     assert abs(res["rel_res_true"] - true_rel) <= 1e-3 * true_rel
     if res["status"] == 0:
         assert true_rel <= 1e-6
+
+
+@pytest.mark.parametrize("cfg", range(8))
+def test_every_tile_configuration(gpu_lib, cfg):
+    """Each tile configuration, for pass A and for pass B, on ragged grids
+    (whole-row configurations also on a row narrower than their 256 tile)."""
+    ncfg = len(gpu_lib.tile_configs())
+    assert ncfg == 8
+    other = (cfg + 1) % ncfg
+    for shape in [(37, 21, 100), (19, 13, 256)]:
+        b = inputs.uniform_rhs(shape, 23)
+        # FP64 x: the anisotropic 19x13x256 grid is below FP32 x's accuracy floor at 1e-6
+        check_against_oracle(gpu_lib, b, io=np.float64, tile_cfg=gpu_lib.tile_cfg_code(cfg, other))
+
+
+def test_whole_row_configuration_rejects_wide_grids(gpu_lib):
+    b = torch.zeros((4, 4, 260), dtype=torch.float32, device="cuda")
+    with pytest.raises(gpu_lib.GbpcgError):
+        gpu_lib.pcg_solve(b, tile_cfg=gpu_lib.tile_cfg_code(6, 6))
