@@ -309,6 +309,43 @@ def main():
         xc.zero_()
         _, rc = B.pcg_solve(bc, xc, tol=TOL, maxit=MAXIT, workspace=wc, stream=stream)
 
+    # mixed precision (16-bit iteration vectors, FP64 refinement) next to plain FP32
+    def timed_solve(bb, **kw):
+        xx = torch.zeros_like(bb)
+        wsx = B.alloc_workspace(bb.shape, io_dtype=B.F64, storage=B._DTYPES.get(kw.get("storage"), B.F32),
+                                k_block=kw.get("k_block"), kb=kw.get("kb", 8))
+        B.pcg_solve(bb, xx, workspace=wsx, **kw)  # warm-up: graphs built and cached
+        xx.zero_()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        _, rr = B.pcg_solve(bb, xx, workspace=wsx, stream=stream, **kw)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        del wsx, xx
+        return {"ms": t0.elapsed_time(t1), "iters": rr["iters"], "outer_steps": rr["refine_steps"],
+                "status": rr["status_name"], "rel_res_true_fp64": rr["rel_res_true"]}
+
+    mixed = {"poisson256_tol1e-6": {"fp32_plain": {"ms": ms_step, "iters": iters}}}
+    for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
+        mixed["poisson256_tol1e-6"][name] = timed_solve(b, tol=TOL, maxit=MAXIT, storage=dt, inner_tol=1e-2,
+                                                        max_outer=10)
+    if N <= 256 ** 3:
+        k512, b512 = inputs.varcoeff_problem(512, 512, 512, seed=1, kb=8)
+        kd = torch.from_numpy(k512).cuda()
+        bd = torch.from_numpy(b512.astype(np.float64)).cuda()
+        del b512
+        c2 = {}
+        c2["fp32_plain"] = timed_solve(bd, tol=1e-8, maxit=20000, k_block=kd, kb=8)
+        c2["fp16"] = timed_solve(bd, tol=1e-8, maxit=8000, k_block=kd, kb=8, storage=torch.float16, inner_tol=1e-2,
+                                 max_outer=10)
+        c2["bf16"] = timed_solve(bd, tol=1e-8, maxit=6000, k_block=kd, kb=8, storage=torch.bfloat16,
+                                 inner_tol=1e-2, max_outer=4)
+        mixed["config2_512_lognormal_tol1e-8"] = c2
+        del bd, kd
+        torch.cuda.empty_cache()
+
     iter_us = ms_step * 1e3 / max(1, iters)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -337,6 +374,7 @@ def main():
                 "table3_grid_512x112x64": {"iters": rc["iters"], "ms_per_iter": rc["time_ms"] / max(1, rc["iters"]),
                                            "h100_ms_per_iter_paper": 0.28},
             },
+            "mixed_precision": mixed,
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,
                     "d2h_bytes_per_step": N * 8 + 256},

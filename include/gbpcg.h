@@ -84,13 +84,17 @@ typedef struct gbpcg_opts {
     double tol;            /* stop when ||r_k||_2 / ||b||_2 <= tol (recursive residual) */
     int32_t maxit;         /* iteration cap (number of A.p products) */
     int32_t precond;       /* gbpcg_precond */
-    int32_t storage;       /* gbpcg_dtype of the solver's vectors (GBPCG_F32) */
-    int32_t io_dtype;      /* gbpcg_dtype of b and x (GBPCG_F32) */
+    int32_t storage;       /* gbpcg_dtype of the iteration vectors: F32, or BF16 / F16 for
+                              mixed precision with FP64 iterative refinement */
+    int32_t io_dtype;      /* gbpcg_dtype of b and x: F32 or F64 (F64 required with 16-bit storage) */
     uint32_t flags;        /* GBPCG_FLAG_* */
     int32_t tile_cfg;      /* 0: automatic; else (a + 1) | (b + 1) << 8 picks the tile
                               configuration of pass A / pass B (see gbpcg_tile_config) */
     void *workspace;       /* device scratch owned by the caller */
     size_t workspace_bytes;
+    double inner_tol;      /* refinement (16-bit storage): relative tolerance of each inner solve */
+    int32_t max_outer;     /* refinement: maximum outer FP64 steps */
+    int32_t reserved1;
 } gbpcg_opts;
 
 typedef struct gbpcg_result {
@@ -102,7 +106,7 @@ typedef struct gbpcg_result {
     double pass_ms[2];         /* GBPCG_FLAG_PROFILE: summed time of the pass-A / pass-B launches */
     int32_t pass_launches[2];  /* GBPCG_FLAG_PROFILE: number of timed launches of each pass */
     int32_t replacements;      /* residual replacements (x flushed, r = b - A x in FP64) */
-    int32_t reserved1;
+    int32_t refine_steps;      /* outer refinement steps (16-bit storage), else 0 */
 } gbpcg_result;
 
 /* Library version string, e.g. "gbpcg 0.1 sm_103a". */
@@ -179,6 +183,14 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
  * decade of residual reduction and at recursive convergence, flushed into x
  * while the residual is replaced by b - A x computed in FP64 (reliable
  * updates), so the returned x meets the tolerance in its true residual.
+ *
+ * Mixed precision (opts->storage BF16 or F16, FP64 b and x): iterative
+ * refinement.  Each outer step computes r = b - A x in FP64 and stops when
+ * ||r||/||b|| <= tol; otherwise it solves the scaled correction equation
+ * with 16-bit vectors and FP32 arithmetic to opts->inner_tol (at most maxit
+ * iterations) and adds the correction to x in FP64; at most opts->max_outer
+ * steps.  result->iters counts all inner iterations.
+ *
  * b (read) and x (initial
  * guess in, solution out) hold nx*ny*nz elements of opts->io_dtype; they are
  * DEVICE pointers, or HOST pointers when opts->flags has GBPCG_FLAG_HOST_IO

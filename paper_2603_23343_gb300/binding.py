@@ -42,19 +42,21 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("io_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("tile_cfg", ctypes.c_int32), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("pass_ms", ctypes.c_double * 2), ("pass_launches", ctypes.c_int32 * 2),
-                ("replacements", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("replacements", ctypes.c_int32), ("refine_steps", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, status=self.status, status_name=STATUS_NAMES.get(self.status, "?"),
                     rel_res_recursive=self.rel_res_recursive, rel_res_true=self.rel_res_true,
-                    time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches), replacements=self.replacements)
+                    time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches), replacements=self.replacements,
+                    refine_steps=self.refine_steps)
 
 
 class GbpcgError(RuntimeError):
@@ -209,7 +211,7 @@ def tile_cfg_code(cfg_a=None, cfg_b=None) -> int:
 
 
 def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
-              profile=False, tile_cfg=0) -> Opts:
+              profile=False, tile_cfg=0, inner_tol=1e-2, max_outer=30) -> Opts:
     o = Opts()
     o.tol = float(tol)
     o.maxit = int(maxit)
@@ -218,6 +220,8 @@ def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, wo
     o.io_dtype = io_dtype
     o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0)
     o.tile_cfg = int(tile_cfg)
+    o.inner_tol = float(inner_tol)
+    o.max_outer = int(max_outer)
     if workspace is not None:
         o.workspace = workspace.data_ptr()
         o.workspace_bytes = workspace.numel() * workspace.element_size()
@@ -233,11 +237,13 @@ def workspace_size(shape, k_block=None, kb=8, **opt_kw) -> int:
 
 
 def alloc_workspace(shape, k_block=None, kb=8, device="cuda", **opt_kw) -> torch.Tensor:
+    """Caller-owned device workspace for gbpcg_pcg_solve (make_opts keywords)."""
     return torch.empty(workspace_size(shape, k_block, kb, **opt_kw), dtype=torch.uint8, device=device)
 
 
 def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
-              workspace: torch.Tensor | None = None, host_io=False, profile=False, tile_cfg=0, stream=None):
+              workspace: torch.Tensor | None = None, host_io=False, profile=False, tile_cfg=0, storage=None,
+              inner_tol=1e-2, max_outer=30, stream=None):
     """Jacobi-PCG solve of A x = b (gbpcg_pcg_solve).  Returns (x, result dict).
 
     b and x are float32 or float64 (the solution accumulates in that type; the
@@ -245,7 +251,9 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     (pinned for speed) when host_io=True; the
     copies then happen inside the library call.  profile=True runs the
     iteration kernels one by one, each timed with CUDA events, and reports
-    the summed pass times in result["pass_ms"].
+    the summed pass times in result["pass_ms"].  storage=torch.bfloat16 or
+    torch.float16 (with float64 b and x) selects mixed precision: FP64
+    iterative refinement around 16-bit inner solves to inner_tol.
     """
     if b.dim() != 3 or not b.is_contiguous():
         raise GbpcgError(ERR_ARG, "b must be a contiguous (nz, ny, nx) tensor")
@@ -254,11 +262,13 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     if x.dtype != b.dtype or x.shape != b.shape or not x.is_contiguous():
         raise GbpcgError(ERR_ARG, "x must be a contiguous tensor of b's shape and dtype")
     io = _dtype(b)
+    st = F32 if storage is None else _DTYPES[storage]
     dev = b.device if b.is_cuda else torch.device("cuda", torch.cuda.current_device())
     if workspace is None:
-        workspace = alloc_workspace(b.shape, k_block, kb, device=dev, io_dtype=io, host_io=host_io)
+        workspace = alloc_workspace(b.shape, k_block, kb, device=dev, io_dtype=io, host_io=host_io, storage=st,
+                                    inner_tol=inner_tol, max_outer=max_outer)
     g = make_grid(b.shape, k_block, kb)
-    o = make_opts(tol, maxit, F32, io, host_io, workspace, profile, tile_cfg)
+    o = make_opts(tol, maxit, st, io, host_io, workspace, profile, tile_cfg, inner_tol, max_outer)
     r = Result()
     rc = load().gbpcg_pcg_solve(ctypes.byref(g), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
                                 _stream(stream))

@@ -29,6 +29,8 @@
 //              trigger
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace gb {
@@ -67,8 +69,11 @@ struct __align__(16) SolveState {
 constexpr double kReplaceDrop2 = 1e-2;
 
 // Constant-coefficient operator: face weights 1/h_d^2.
+struct NoCache {};
+
 struct OpConst {
     static constexpr bool kConst = true;
+    using Cache = NoCache;
     float cx, cy, cz;
     float d;      // diagonal 2 (cx + cy + cz)
     float inv_d;  // 1 / d
@@ -78,6 +83,10 @@ struct OpConst {
         q = fmaf(d, c, -fmaf(cx, xm + xp, fmaf(cy, ym + yp, cz * (zm + zp))));
         dg = d;
     }
+    template <typename Self = OpConst>
+    __device__ __forceinline__ void apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
+                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
+                                           int k, int nx, int ny, float q[4], float dg[4]) const;
 };
 
 // Block-constant coefficient k (one float per kbx*kby*kbz block): face
@@ -85,6 +94,7 @@ struct OpConst {
 // cell's own k inside a block and on the domain boundary.
 struct OpBlock {
     static constexpr bool kConst = false;
+    using Cache = NoCache;
     float inv_d;  // unused
     const float *kb;
     int nx, ny, nz, nbx, nby, kbx, kby, kbz;
@@ -110,6 +120,114 @@ struct OpBlock {
         weights(i, j, k, w);
         q = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) + w[4] * (c - zm) + w[5] * (c - zp);
         dg = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
+    }
+    template <typename Self = OpBlock>
+    __device__ __forceinline__ void apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
+                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
+                                           int k, int nx_, int ny_, float q[4], float dg[4]) const;
+};
+
+// The operator at one thread's four consecutive x points: c = centre values,
+// xl / xr = the x neighbours left of point 0 and right of point 3, y and z
+// neighbours per point.  Point positions past the grid edge (masked lanes)
+// are clamped into the grid before any coefficient lookup.
+template <typename Op>
+__device__ __forceinline__ void apply4_pointwise(const Op &op, const float c[4], float xl, float xr, const float ym[4],
+                                                 const float yp[4], const float zm[4], const float zp[4], int gx,
+                                                 int gy, int k, int nx, int ny, float q[4], float dg[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float xm = i == 0 ? xl : c[i - 1];
+        const float xp = i == 3 ? xr : c[i + 1];
+        op.apply(c[i], xm, xp, ym[i], yp[i], zm[i], zp[i], min(gx + i, nx - 1), min(gy, ny - 1), k, q[i], dg[i]);
+    }
+}
+
+template <typename Self>
+__device__ __forceinline__ void OpConst::apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
+                                                const float yp[4], const float zm[4], const float zp[4], int gx,
+                                                int gy, int k, int nx, int ny, float q[4], float dg[4]) const {
+    apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx, ny, q, dg);
+}
+template <typename Self>
+__device__ __forceinline__ void OpBlock::apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
+                                                const float yp[4], const float zm[4], const float zp[4], int gx,
+                                                int gy, int k, int nx_, int ny_, float q[4], float dg[4]) const {
+    apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+}
+
+// Block-constant coefficient through a per-block face table built once per
+// solve (build_face_table in solver.cuh): for block b, tab[2b] = {k, k_x-,
+// k_x+, k_y-}, tab[2b+1] = {k_y+, k_z-, k_z+, 0}, each face value the
+// harmonic mean with the neighbouring block or, on the domain boundary, k
+// itself.  One lookup serves a thread's four points when kbx is a multiple
+// of 4; the weights are bitwise those of OpBlock.
+struct OpTable {
+    static constexpr bool kConst = false;
+    float inv_d;  // unused
+    const float4 *tab;
+    int nx, ny, nz, nbx, nby, kbx, kby, kbz;
+    int grouped;  // kbx % 4 == 0: a thread's four points share one block
+    float cx, cy, cz;
+    __device__ __forceinline__ void lookup(int bx, int by, int bz, float4 &t0, float4 &t1) const {
+        const float4 *t = tab + 2 * (((size_t)bz * nby + by) * nbx + bx);
+        t0 = __ldg(t);
+        t1 = __ldg(t + 1);
+    }
+    __device__ __forceinline__ void apply(float c, float xm, float xp, float ym, float yp, float zm, float zp, int i,
+                                          int j, int k, float &q, float &dg) const {
+        const int bx = i / kbx, by = j / kby, bz = k / kbz;
+        const int ix = i - bx * kbx, iy = j - by * kby, iz = k - bz * kbz;
+        float4 t0, t1;
+        lookup(bx, by, bz, t0, t1);
+        const float kc = t0.x;
+        const float w0 = cx * (ix == 0 ? t0.y : kc), w1 = cx * (ix == kbx - 1 ? t0.z : kc);
+        const float w2 = cy * (iy == 0 ? t0.w : kc), w3 = cy * (iy == kby - 1 ? t1.x : kc);
+        const float w4 = cz * (iz == 0 ? t1.y : kc), w5 = cz * (iz == kbz - 1 ? t1.z : kc);
+        q = w0 * (c - xm) + w1 * (c - xp) + w2 * (c - ym) + w3 * (c - yp) + w4 * (c - zm) + w5 * (c - zp);
+        dg = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
+    }
+    // A thread's block column (bx, by, x/y offsets) is fixed; its table entry
+    // changes only when the march crosses a z block, so it is kept in
+    // registers and reloaded then.
+    struct Cache {
+        int bz = -1, bx = 0, by = 0, ix0 = 0, iy = 0;
+        float4 t0, t1;
+    };
+    __device__ __forceinline__ void apply4(Cache &cc, const float c[4], float xl, float xr, const float ym[4],
+                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
+                                           int k, int nx_, int ny_, float q[4], float dg[4]) const {
+        if (!grouped) {
+            apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+            return;
+        }
+        const int bz = k / kbz, iz = k - bz * kbz;
+        if (bz != cc.bz) {
+            if (cc.bz < 0) {
+                const int i0 = min(gx, (nx - 1) & ~3), j = min(gy, ny - 1);  // gx is a multiple of 4
+                cc.bx = i0 / kbx;
+                cc.by = j / kby;
+                cc.ix0 = i0 - cc.bx * kbx;
+                cc.iy = j - cc.by * kby;
+            }
+            cc.bz = bz;
+            lookup(cc.bx, cc.by, bz, cc.t0, cc.t1);
+        }
+        const float4 t0 = cc.t0, t1 = cc.t1;
+        const float kc = t0.x;
+        const float w2 = cy * (cc.iy == 0 ? t0.w : kc), w3 = cy * (cc.iy == kby - 1 ? t1.x : kc);
+        const float w4 = cz * (iz == 0 ? t1.y : kc), w5 = cz * (iz == kbz - 1 ? t1.z : kc);
+        const float wyz = (w2 + w3) + (w4 + w5);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int ix = cc.ix0 + i;
+            const float xm = i == 0 ? xl : c[i - 1];
+            const float xp = i == 3 ? xr : c[i + 1];
+            const float w0 = cx * (ix == 0 ? t0.y : kc), w1 = cx * (ix == kbx - 1 ? t0.z : kc);
+            q[i] = w0 * (c[i] - xm) + w1 * (c[i] - xp) + w2 * (c[i] - ym[i]) + w3 * (c[i] - yp[i]) +
+                   w4 * (c[i] - zm[i]) + w5 * (c[i] - zp[i]);
+            dg[i] = (w0 + w1) + wyz;
+        }
     }
 };
 
@@ -142,6 +260,13 @@ constexpr uint32_t round128(uint32_t v) { return (v + 127u) & ~127u; }
 template <int TX>
 constexpr bool full_row() { return TX == 256; }
 
+// Type of the centre array and of the second output: pass A's correction
+// vector d is FP32 whatever the storage type of z and p (16-bit d rounds at
+// the scale of |d|, and A amplifies that noise far beyond a 16-bit solve's
+// residual on fine grids); elsewhere it is the storage type.
+template <typename T, int KIND>
+using CenterT = typename std::conditional<KIND == K_PASSA, float, T>::type;
+
 template <typename T, int TX, int TY, int KIND>
 struct Geometry {
     static constexpr int NT = TX / 4 * TY;
@@ -151,7 +276,7 @@ struct Geometry {
     static constexpr int NC = KIND == K_STENCIL ? 0 : 1;
     static constexpr int NV = KIND == K_PASSA ? 1 : KIND == K_PASSB ? 2 : 0;
     static constexpr uint32_t HBYTES = HX * HY * sizeof(T);
-    static constexpr uint32_t CBYTES = TX * TY * sizeof(T);
+    static constexpr uint32_t CBYTES = TX * TY * sizeof(CenterT<T, KIND>);
     static constexpr uint32_t HB = round128(HBYTES), CB = round128(CBYTES);
     static constexpr uint32_t SB = NH * HB + NC * CB;
 };
@@ -180,6 +305,7 @@ template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
 __global__ void __launch_bounds__(TX / 4 * TY)
     zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
     using G = Geometry<T, TX, TY, KIND>;
+    using TC = CenterT<T, KIND>;
     constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV;
     constexpr uint32_t HB = G::HB, SB = G::SB;
 
@@ -208,9 +334,9 @@ __global__ void __launch_bounds__(TX / 4 * TY)
     if constexpr (KIND == K_PASSB) sh0 = it & 1;
     const T *H0 = static_cast<const T *>(a.h0[sh0]);
     const T *H1 = static_cast<const T *>(a.h1[sh1]);
-    const T *C0 = static_cast<const T *>(a.c0);
+    const TC *C0 = static_cast<const TC *>(a.c0);
     T *O0 = static_cast<T *>(a.o0[so0]);
-    T *O1 = static_cast<T *>(a.o1);
+    TC *O1 = static_cast<TC *>(a.o1);
     const CUtensorMap *M0 = &maps.h0[sh0];
     const CUtensorMap *M1 = &maps.h1[sh1];
     const CUtensorMap *MC = &maps.c0;
@@ -269,7 +395,7 @@ __global__ void __launch_bounds__(TX / 4 * TY)
             if (load_h1)
                 manual_box<T, NT>(H1, reinterpret_cast<T *>(base + HB), nx, ny, nz, x0 - XH, y0 - 1, m, HX,
                                   TY + 2);
-            if (cen) manual_box<T, NT>(C0, reinterpret_cast<T *>(base + NH * HB), nx, ny, nz, x0, y0, m, TX, TY);
+            if (cen) manual_box<TC, NT>(C0, reinterpret_cast<TC *>(base + NH * HB), nx, ny, nz, x0, y0, m, TX, TY);
             __syncthreads();
         }
     };
@@ -302,6 +428,7 @@ __global__ void __launch_bounds__(TX / 4 * TY)
             issued_hi = t;
         }
         float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f}, qc[4] = {0.f, 0.f, 0.f, 0.f};
+        typename Op::Cache opc;
         const int cidx = (ly + 1) * HX + XH + 4 * lx;  // this thread's first point in a halo box
         for (int t = 0; t <= tl; ++t) {
             const int s = t % S;
@@ -325,19 +452,9 @@ __global__ void __launch_bounds__(TX / 4 * TY)
                 const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
                 const float xr = (full_row<TX>() && lx == TX / 4 - 1) ? 0.0f : in_val(bk, cidx + 4);
                 float q[4], dg[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float xm = i == 0 ? xl : qb[i - 1];
-                    const float xp = i == 3 ? xr : qb[i + 1];
-                    const float zm = REV ? qc[i] : qa[i];
-                    const float zp = REV ? qa[i] : qc[i];
-                    // masked-off points past the grid edge use an in-range
-                    // position so a coefficient lookup stays inside k_block
-                    op.apply(qb[i], xm, xp, ym[i], yp[i], zm, zp, min(gx + i, nx - 1), min(gy, ny - 1), k, q[i],
-                             dg[i]);
-                }
+                op.apply4(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q, dg);
                 const size_t g = ((size_t)k * ny + gy) * nx + gx;
-                const T *cen = reinterpret_cast<const T *>(bk + NH * HB) + ly * TX + 4 * lx;
+                const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + 4 * lx;
                 float out0[4], out1[4];
                 bool st1 = false;
                 if constexpr (KIND == K_STENCIL) {
@@ -351,7 +468,7 @@ __global__ void __launch_bounds__(TX / 4 * TY)
                     }
                     if (do_x) {
                         float xv[4], po[4];
-                        ld4<T>(cen, xv);
+                        ld4<TC>(cen, xv);
                         ld4<T>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
 #pragma unroll
                         for (int i = 0; i < 4; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
@@ -359,7 +476,7 @@ __global__ void __launch_bounds__(TX / 4 * TY)
                     }
                 } else {  // K_PASSB
                     float zv[4];
-                    ld4<T>(cen, zv);
+                    ld4<TC>(cen, zv);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
@@ -373,13 +490,13 @@ __global__ void __launch_bounds__(TX / 4 * TY)
                 }
                 if (ok[0] && ok[3] && TMA) {
                     st4<T>(O0 + g, out0);
-                    if (st1) st4<T>(O1 + g, out1);
+                    if (st1) st4<TC>(O1 + g, out1);
                 } else {
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         if (ok[i]) {
                             O0[g + i] = from_f<T>(out0[i]);
-                            if (st1) O1[g + i] = from_f<T>(out1[i]);
+                            if (st1) O1[g + i] = from_f<TC>(out1[i]);
                         }
                 }
             }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cmath>
 
 #include "engine.cuh"
 
@@ -51,10 +52,12 @@ constexpr unsigned kMaxPassBlocks = 4096;
 
 int device_sm_count();
 
-// Splits z into chunks so that tiles * zchunks fills the resident CTA slots
-// of the GPU (one wave), never exceeding kMaxPassBlocks.
+// Splits z into chunks: among chunk counts that keep chunks at least
+// min_zchunk planes deep (and the grid within kMaxPassBlocks), picks the one
+// whose CTAs fill the resident slots of the GPU most evenly (the fraction of
+// the last wave that is occupied), preferring fewer, deeper chunks on ties.
 inline PassGeom make_geom(int cfg, int nx, int ny, int nz, int ctas_per_sm, size_t smem,
-                          int min_zchunk = 4) {
+                          int min_zchunk = 8) {
     CfgDims d = cfg_dims(cfg);
     PassGeom g;
     g.cfg = cfg;
@@ -64,13 +67,22 @@ inline PassGeom make_geom(int cfg, int nx, int ny, int nz, int ctas_per_sm, size
     g.tiles_y = (ny + d.ty - 1) / d.ty;
     const long tiles = (long)g.tiles_x * g.tiles_y;
     const long slots = (long)device_sm_count() * std::max(1, ctas_per_sm);
-    long zc = std::max(1L, slots / std::max(1L, tiles));
-    zc = std::min<long>(zc, std::max(1L, (long)kMaxPassBlocks / std::max(1L, tiles)));
-    int zchunk = (int)((nz + zc - 1) / zc);
-    zchunk = std::max(zchunk, std::min(nz, min_zchunk));
-    zchunk = std::max(zchunk, 1);
-    g.zchunk = zchunk;
-    g.zchunks = (nz + zchunk - 1) / zchunk;
+    const int zmin = std::max(1, std::min(nz, min_zchunk));
+    long best_zc = 1;
+    double best = -1.0;
+    for (long zc = 1; zc <= nz / zmin && tiles * zc <= (long)kMaxPassBlocks; ++zc) {
+        const int zchunk = (int)((nz + zc - 1) / zc);
+        const long chunks = (nz + zchunk - 1) / zchunk;  // chunks actually formed
+        const double waves = (double)(tiles * chunks) / (double)slots;
+        const double fill = waves / std::ceil(waves);
+        if (fill > best + 0.02) {
+            best = fill;
+            best_zc = zc;
+        }
+    }
+    int zchunk = (int)((nz + best_zc - 1) / best_zc);
+    g.zchunk = std::max(zchunk, 1);
+    g.zchunks = (nz + g.zchunk - 1) / g.zchunk;
     return g;
 }
 
@@ -154,6 +166,25 @@ inline OpBlock make_op_block(const gbpcg_grid &g, float scale = 1.0f) {
     o.nby = (g.ny + g.kby - 1) / g.kby;
     o.cx = (float)(c(g.nx) * scale); o.cy = (float)(c(g.ny) * scale); o.cz = (float)(c(g.nz) * scale);
     return o;
+}
+
+inline OpTable make_op_table(const gbpcg_grid &g, float scale, const float4 *tab) {
+    auto c = [](int n) { double h = 1.0 / (n + 1); return 1.0 / (h * h); };
+    OpTable o;
+    o.inv_d = 0.0f;
+    o.tab = tab;
+    o.nx = g.nx; o.ny = g.ny; o.nz = g.nz;
+    o.kbx = g.kbx; o.kby = g.kby; o.kbz = g.kbz;
+    o.nbx = (g.nx + g.kbx - 1) / g.kbx;
+    o.nby = (g.ny + g.kby - 1) / g.kby;
+    o.grouped = g.kbx % 4 == 0;
+    o.cx = (float)(c(g.nx) * scale); o.cy = (float)(c(g.ny) * scale); o.cz = (float)(c(g.nz) * scale);
+    return o;
+}
+
+inline int64_t block_count(const gbpcg_grid &g) {
+    if (!g.k_block) return 0;
+    return (int64_t)((g.nx + g.kbx - 1) / g.kbx) * ((g.ny + g.kby - 1) / g.kby) * ((g.nz + g.kbz - 1) / g.kbz);
 }
 
 // Validates a grid description; returns GBPCG_OK or GBPCG_ERR_ARG.

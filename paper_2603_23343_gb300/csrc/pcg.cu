@@ -1,239 +1,206 @@
-// Jacobi-preconditioned CG (Sec. VII) as one CUDA graph per problem:
+// C ABI of the solver (Sec. VII): argument checks, host staging, the graph
+// cache, and mixed-precision iterative refinement around 16-bit inner solves.
 //
-//   reset -> init (r0 = b - A x0 in FP64) ->
-//   while (cond) { K_PASSA ; K_PASSB ; if (replace) { flush ; replace } } ->
-//   finalize -> FP64 true residual
-//
-// The loop is a conditional WHILE node; the last CTA of each pass decides
-// (from the grid-wide sums it has just finished) whether to continue and sets
-// the condition from the device, so no scalar goes back to the host during
-// the solve.  Per iteration the two data passes move 20 + 12 bytes per grid
-// point in FP32 (see engine.cuh), against 44 for a three-kernel
-// stencil / update-x-r / update-p split.
-//
-// Accuracy with FP32 vectors (reliable updates, van der Vorst & Ye, SIAM J.
-// Sci. Comput. 22, 2000): the updates alpha p go into a correction vector d
-// instead of x, so their rounding is relative to |d|, not |x|.  Whenever
-// ||r|| has dropped by a decade since the last time, and when the recursive
-// residual meets the tolerance, d is flushed into x and the recursive
-// residual is replaced by b - A x evaluated in FP64; the iteration continues
-// from the replaced residual (p is kept).  Convergence is therefore decided
-// on a true residual.  x and b may be FP32 or FP64: they are only touched by
-// the init, the replacements and the finalize, never by the per-iteration
-// passes.  With FP32 x the rounding of x itself bounds the attainable true
-// residual (about 1e-6 relative at 256^3); the solve stops with
-// GBPCG_NOT_CONVERGED if confirmations stop making progress.
-#include <algorithm>
+// Refinement (Wilkinson; Moler, J. ACM 14, 1967) with x and b in FP64:
+//   r = b - A x (FP64 arithmetic; stored as FP32), s = max |r|
+//   stop if ||r||/||b|| <= tol
+//   inner: solve (sigma A) d = r / s to inner_tol with BF16/FP16 vectors
+//          (sigma = 1 / max_d c_d keeps the operator's entries O(k), r / s
+//          keeps the right-hand side O(1): both inside FP16's range)
+//   x += sigma s d (FP64)
+// The host reads ||r||, ||b|| once per outer step; each inner solve is the
+// cached CUDA graph of solver.cuh with 16-bit storage.
+#include <cmath>
 #include <cstring>
 #include <list>
 #include <mutex>
-#include <type_traits>
 
-#include "launch.cuh"
+#include "solver.cuh"
 
 namespace gb {
 
-// ------------------------------------------------------------- kernels --
+// ------------------------------------------------------------ graph cache --
 
-__global__ void reset_state_kernel(SolveState *st, double tol, int maxit) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        memset(st, 0, sizeof(SolveState));
-        st->tol2 = tol * tol;
-        st->maxit = maxit;
-        st->status = GBPCG_NOT_CONVERGED;
-    }
+namespace {
+struct SolveGraph {
+    SolveKey key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_cache_mu;
+std::list<SolveGraph> g_cache;  // most recently used first
+constexpr size_t kCacheMax = 32;
+}  // namespace
+
+cudaGraphExec_t graph_cache_find(const SolveKey &key) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
+        if (it->key == key) {
+            g_cache.splice(g_cache.begin(), g_cache, it);
+            return g_cache.front().exec;
+        }
+    return nullptr;
 }
 
-enum ResMode { RES_INIT = 0, RES_REPLACE = 1, RES_TRUE = 2 };
+cudaGraphExec_t graph_cache_put(const SolveKey &key, cudaGraph_t graph, cudaGraphExec_t exec) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto &e : g_cache)
+        if (e.key == key) {  // another thread built it first
+            cudaGraphExecDestroy(exec);
+            cudaGraphDestroy(graph);
+            return e.exec;
+        }
+    SolveGraph sg;
+    sg.key = key;
+    sg.graph = graph;
+    sg.exec = exec;
+    g_cache.push_front(sg);
+    while (g_cache.size() > kCacheMax) {
+        cudaGraphExecDestroy(g_cache.back().exec);
+        cudaGraphDestroy(g_cache.back().graph);
+        g_cache.pop_back();
+    }
+    return exec;
+}
 
-struct Res64Args {
-    int nx, ny, nz;
-    const void *x, *b;
-    float *z, *d;
-    double cx, cy, cz;
-    const float *kb;
-    int kbx, kby, kbz;
-    SolveState *st;
-    double *partials;
-    cudaGraphConditionalHandle cond;
-    int use_cond;
+// ------------------------------------------------------------ refinement --
+
+struct __align__(16) OuterState {
+    double rr, bb;                 // ||b - A x||^2, ||b||^2 (FP64)
+    unsigned long long rmax_bits;  // max |r| as the bit pattern of a non-negative double
+    double bscale;                 // 1 / max |r|: scales the inner right-hand side
+    double corr;                   // sigma * max |r|: scales the inner solution into x
+    double sigma;
+    unsigned int ticket;
+    unsigned int pad;
+    double applied;                // the corr of the last applied update (to undo it)
 };
 
-constexpr double kHuge = 1e300;
-
-// r = b - A x with FP64 arithmetic, one block per grid row (x fastest).
-//   RES_INIT     z = D^-1 r, d = 0; sums r.r, r.z, b.b  -> start state
-//   RES_REPLACE  z = D^-1 r;        sums r.r, r.z       -> replacement decisions
-//   RES_TRUE     sums r.r, b.b                          -> reported true residual
-template <int MODE, typename X, typename Bt, bool BLOCK>
-__global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
-    SolveState *st = a.st;
-    if (MODE == RES_REPLACE && (!st->replace || st->done)) return;
-    const X *__restrict__ x = static_cast<const X *>(a.x);
-    const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
+// r = b - A x in FP64 (unscaled operator), r32 = (float) r; sums ||r||^2,
+// ||b||^2 and max |r|; the last block derives the inner scalings.
+template <bool BLOCK>
+__global__ void __launch_bounds__(256)
+    outer_residual_kernel(int nx, int ny, int nz, const double *__restrict__ x, const double *__restrict__ b,
+                          float *r32, double cx, double cy, double cz, const float *__restrict__ kb,
+                          int kbx, int kby, int kbz, OuterState *os, double *partials) {
     const int64_t pl = (int64_t)nx * ny;
-    const int nbx = BLOCK ? (nx + a.kbx - 1) / a.kbx : 0, nby = BLOCK ? (ny + a.kby - 1) / a.kby : 0;
-    const double cx = a.cx, cy = a.cy, cz = a.cz;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const int nbx = BLOCK ? (nx + kbx - 1) / kbx : 0, nby = BLOCK ? (ny + kby - 1) / kby : 0;
+    double rr = 0.0, bb = 0.0, mx = 0.0;
     const int rows = ny * nz;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % ny, k = row / ny;
         const int64_t base = (int64_t)row * nx;
         for (int i = threadIdx.x; i < nx; i += 256) {
             const int64_t g = base + i;
-            auto L = [&](int64_t o) { return (double)__ldg(x + o); };
-            const double c = L(g);
-            const double xm = i > 0 ? L(g - 1) : 0.0, xp = i < nx - 1 ? L(g + 1) : 0.0;
-            const double ym = j > 0 ? L(g - nx) : 0.0, yp = j < ny - 1 ? L(g + nx) : 0.0;
-            const double zm = k > 0 ? L(g - pl) : 0.0, zp = k < nz - 1 ? L(g + pl) : 0.0;
+            const double c = x[g];
+            const double xm = i > 0 ? x[g - 1] : 0.0, xp = i < nx - 1 ? x[g + 1] : 0.0;
+            const double ym = j > 0 ? x[g - nx] : 0.0, yp = j < ny - 1 ? x[g + nx] : 0.0;
+            const double zm = k > 0 ? x[g - pl] : 0.0, zp = k < nz - 1 ? x[g + pl] : 0.0;
             double w[6] = {cx, cx, cy, cy, cz, cz};
             if (BLOCK) {
-                const float *kb = a.kb;
                 auto K = [&](int p, int q, int r) { return (double)__ldg(kb + ((int64_t)r * nby + q) * nbx + p); };
                 auto hm = [](double u, double v) { return 2.0 * u * v / (u + v); };
-                const int bx = i / a.kbx, by = j / a.kby, bz = k / a.kbz;
-                const int ix = i - bx * a.kbx, iy = j - by * a.kby, iz = k - bz * a.kbz;
+                const int bx = i / kbx, by = j / kby, bz = k / kbz;
+                const int ix = i - bx * kbx, iy = j - by * kby, iz = k - bz * kbz;
                 const double kc = K(bx, by, bz);
                 w[0] = cx * ((ix == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
-                w[1] = cx * ((ix == a.kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
+                w[1] = cx * ((ix == kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
                 w[2] = cy * ((iy == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
-                w[3] = cy * ((iy == a.kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
+                w[3] = cy * ((iy == kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
                 w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
-                w[5] = cz * ((iz == a.kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
+                w[5] = cz * ((iz == kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
             }
             const double ax = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) +
                               w[4] * (c - zm) + w[5] * (c - zp);
-            const double bv = (double)__ldg(b + g);
+            const double bv = b[g];
             const double r = bv - ax;
-            s0 = fma(r, r, s0);
-            if (MODE == RES_TRUE) {
-                s1 = fma(bv, bv, s1);
-            } else {
-                const float dg = (float)(((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]));
-                const float zf = (float)r / dg;
-                a.z[g] = zf;
-                s1 = fma(r, (double)zf, s1);
-                if (MODE == RES_INIT) {
-                    a.d[g] = 0.0f;
-                    s2 = fma(bv, bv, s2);
-                }
-            }
+            r32[g] = (float)r;
+            rr = fma(r, r, rr);
+            bb = fma(bv, bv, bb);
+            mx = fmax(mx, fabs(r));
         }
     }
-    constexpr int NV = MODE == RES_INIT ? 3 : 2;
     __shared__ double red[8][3];
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
+    rr = warp_sum(rr);
+    bb = warp_sum(bb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) {
-        red[threadIdx.x >> 5][0] = s0;
-        red[threadIdx.x >> 5][1] = s1;
-        red[threadIdx.x >> 5][2] = s2;
+        red[threadIdx.x >> 5][0] = rr;
+        red[threadIdx.x >> 5][1] = bb;
+        red[threadIdx.x >> 5][2] = mx;
     }
     __syncthreads();
-    double part[NV], tot[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) part[v] = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < 8; ++w)
-#pragma unroll
-            for (int v = 0; v < NV; ++v) part[v] += red[w][v];
-    if (!grid_sum_last<NV, 256>(part, a.partials, &st->ticket[4 + MODE], tot) || threadIdx.x != 0) return;
-    if (MODE == RES_TRUE) {
-        st->rr_true = tot[0];
-        st->bb_true = tot[1];
-        return;
-    }
-    if (MODE == RES_INIT) {
-        const double rr = tot[0], rz = tot[1], bb = tot[2];
-        st->bb = bb; st->rr = rr; st->rz = rz; st->rr_rep = rr; st->rr_conf = kHuge;
-        st->it = 0; st->pending = 0; st->zero_x = 0; st->replace = 0;
-        if (bb == 0.0) { st->zero_x = 1; st->done = 1; st->status = GBPCG_OK; }
-        else if (rr <= st->tol2 * bb) { st->done = 1; st->status = GBPCG_OK; }
-        else if (!isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
-        else if (st->maxit <= 0) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
-        else { st->done = 0; st->status = GBPCG_NOT_CONVERGED; }
-    } else {
-        const double rrt = tot[0], rzt = tot[1];
-        const int kind = st->replace;  // 1: decade of progress, 2: recursive residual met tol
-        st->rr = rrt;
-        st->rr_rep = rrt;
-        st->replace = 0;
-        st->pending = 0;
-        st->n_replace += 1;
-        if (rrt <= st->tol2 * st->bb) { st->done = 1; st->status = GBPCG_OK; }
-        else if (!isfinite(rrt) || !isfinite(rzt) || !(rzt > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
-        else if (st->it >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
-        else if (kind == 2 && rrt > 0.25 * st->rr_conf) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
-        else {
-            if (kind == 2) st->rr_conf = rrt;
-            st->beta = rzt / st->rz;
-            st->rz = rzt;
+    double part[2] = {0.0, 0.0}, tot[2];
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            part[0] += red[w][0];
+            part[1] += red[w][1];
+            m = fmax(m, red[w][2]);
         }
+        // max of non-negative doubles = max of their bit patterns (published before the ticket)
+        atomicMax(&os->rmax_bits, (unsigned long long)__double_as_longlong(m));
     }
-    if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
+    if (grid_sum_last<2, 256>(part, partials, &os->ticket, tot) && threadIdx.x == 0) {
+        const double rmax = __longlong_as_double((long long)atomicAdd(&os->rmax_bits, 0ull));
+        os->rr = tot[0];
+        os->bb = tot[1];
+        os->bscale = rmax > 0.0 ? 1.0 / rmax : 1.0;
+        os->corr = os->sigma * rmax;
+    }
 }
 
-// Residual replacement, step 1: x += d + alpha_{it-1} p_{it-1} (pending), d = 0.
-template <typename X, typename T>
-__global__ void flush_kernel(SolveState *st, X *x, T *d, const T *p0, const T *p1, int64_t n) {
-    if (!st->replace || st->done) return;
+// x += sign * c * din (FP64); c = corr (apply) or the last applied corr (undo)
+__global__ void refine_update_kernel(double *x, const float *din, OuterState *os, int64_t n, int undo) {
+    const double c = undo ? -os->applied : os->corr;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-    const T *p = ((st->it - 1) & 1) ? p1 : p0;
-    const float a = st->pending ? (float)st->alpha : 0.0f;
-    for (int64_t i = tid; i < n; i += nth) {
-        x[i] = x[i] + (X)fmaf(a, to_f(p[i]), to_f(d[i]));
-        d[i] = from_f<T>(0.0f);
-    }
+    for (int64_t i = tid; i < n; i += nth) x[i] = fma(c, (double)din[i], x[i]);
 }
 
-// x += d + alpha_{it-1} p_{it-1} (the pending update, if any); x = 0 when b = 0.
-template <typename X, typename T>
-__global__ void finalize_kernel(const SolveState *st, X *x, const T *d, const T *p0, const T *p1, int64_t n) {
+__global__ void zero_f64_kernel(double *x, int64_t n) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
-    if (st->zero_x) {
-        for (int64_t i = tid; i < n; i += nth) x[i] = X(0);
-        return;
-    }
-    const T *p = ((st->it - 1) & 1) ? p1 : p0;
-    const float a = st->pending ? (float)st->alpha : 0.0f;
-    for (int64_t i = tid; i < n; i += nth) x[i] = x[i] + (X)fmaf(a, to_f(p[i]), to_f(d[i]));
+    for (int64_t i = tid; i < n; i += nth) x[i] = 0.0;
 }
 
-// ----------------------------------------------------------- workspace --
-
-struct WsLayout {
-    size_t state, partials, z, p0, p1, d, bstage, xstage, total;
+struct RefineLayout {
+    size_t outer, partials, r32, din, inner, total;
+    WsLayout in;
 };
 
-static size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
-
-static WsLayout ws_layout(const gbpcg_grid &g, const gbpcg_opts &o) {
+static RefineLayout refine_layout(const gbpcg_grid &g, const gbpcg_opts &o) {
     const size_t n = (size_t)g.nx * g.ny * g.nz;
-    const size_t vs = round256(n * dtype_size(o.storage));
-    const size_t io = round256(n * dtype_size(o.io_dtype));
-    WsLayout w;
+    RefineLayout r;
     size_t off = 0;
-    w.state = off; off += 256;
-    w.partials = off; off += round256(sizeof(double) * 4 * kMaxPassBlocks);
-    w.z = off; off += vs;
-    w.p0 = off; off += vs;
-    w.p1 = off; off += vs;
-    w.d = off; off += vs;
-    w.bstage = w.xstage = 0;
-    if (o.flags & GBPCG_FLAG_HOST_IO) {
-        w.bstage = off; off += io;
-        w.xstage = off; off += io;
-    }
-    w.total = off;
-    return w;
+    r.outer = off; off += 256;
+    r.partials = off; off += round256(sizeof(double) * 2 * 8192);
+    r.r32 = off; off += round256(n * 4);
+    r.din = off; off += round256(n * 4);
+    r.inner = off;
+    r.in = ws_layout_n(n, o.storage, GBPCG_F32, false, block_count(g));
+    off += r.in.total;
+    if (o.flags & GBPCG_FLAG_HOST_IO) off += 2 * round256(n * 8);  // staging of b and x (FP64)
+    r.total = off;
+    return r;
+}
+
+static bool refine_mode(const gbpcg_opts &o) { return o.storage == GBPCG_BF16 || o.storage == GBPCG_F16; }
+
+static size_t workspace_total(const gbpcg_grid &g, const gbpcg_opts &o) {
+    if (refine_mode(o)) return refine_layout(g, o).total;
+    return ws_layout_n((size_t)g.nx * g.ny * g.nz, o.storage, o.io_dtype, o.flags & GBPCG_FLAG_HOST_IO,
+                       block_count(g)).total;
 }
 
 static int check_opts(const gbpcg_opts *o) {
     if (!o) return fail_arg("opts is NULL");
-    if (o->storage != GBPCG_F32) return fail_arg("storage dtype not supported by this solver (F32 only)");
+    if (o->storage != GBPCG_F32 && o->storage != GBPCG_BF16 && o->storage != GBPCG_F16)
+        return fail_arg("storage dtype must be F32, BF16 or F16");
     if (o->io_dtype != GBPCG_F32 && o->io_dtype != GBPCG_F64) return fail_arg("io dtype must be F32 or F64");
+    if (refine_mode(*o) && o->io_dtype != GBPCG_F64)
+        return fail_arg("16-bit storage (iterative refinement) needs FP64 b and x");
+    if (refine_mode(*o) && !(o->inner_tol > 0.0 && o->inner_tol < 1.0)) return fail_arg("inner_tol must be in (0, 1)");
+    if (refine_mode(*o) && o->max_outer < 0) return fail_arg("max_outer must be >= 0");
     if (o->precond != GBPCG_PRECOND_JACOBI) return fail_arg("unknown preconditioner");
     if (!(o->tol >= 0.0)) return fail_arg("tol must be >= 0");
     if (o->maxit < 0) return fail_arg("maxit must be >= 0");
@@ -242,301 +209,6 @@ static int check_opts(const gbpcg_opts *o) {
         return fail_arg("tile_cfg selects unknown tile configurations");
     return GBPCG_OK;
 }
-
-// ------------------------------------------------------------ the graph --
-
-struct SolveKey {
-    int dev, nx, ny, nz, kbx, kby, kbz, maxit, cfg_a, cfg_b, tma, io;
-    const void *kb, *b, *x, *ws;
-    double tol;
-    bool operator==(const SolveKey &o) const { return memcmp(this, &o, sizeof(SolveKey)) == 0; }
-};
-
-struct SolveGraph {
-    SolveKey key;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-};
-
-static std::mutex g_cache_mu;
-static std::list<SolveGraph> g_cache;  // most recently used first
-constexpr size_t kCacheMax = 16;
-
-// Everything one solve launches, set up once: geometry, tensor maps, kernel
-// arguments.  The same launch functions serve graph capture and the
-// event-timed profile mode.  X is the type of x and b (float or double).
-template <typename Op, bool TMA, typename X>
-struct SolvePlan {
-    using T = float;
-    gbpcg_grid g;
-    Op op;
-    int cfg_a, cfg_b;
-    const X *b;
-    X *x;
-    SolveState *st;
-    double *partials;
-    T *z, *p0, *p1, *d;
-    PassGeom ga, gb;
-    PassMaps ma, mb;
-    PassArgs aa, ab;
-    Res64Args ra;
-    double tol;
-    int maxit;
-    cudaGraphConditionalHandle cond_loop = 0, cond_rep = 0;
-    int use_cond = 0;
-
-    int init(const gbpcg_grid &grid, const Op &o, int ca, int cb, const X *bb, X *xx, char *ws, const WsLayout &L,
-             double tl, int mi_) {
-        g = grid; op = o; cfg_a = ca; cfg_b = cb; b = bb; x = xx; tol = tl; maxit = mi_;
-        st = reinterpret_cast<SolveState *>(ws + L.state);
-        partials = reinterpret_cast<double *>(ws + L.partials);
-        z = reinterpret_cast<T *>(ws + L.z);
-        p0 = reinterpret_cast<T *>(ws + L.p0);
-        p1 = reinterpret_cast<T *>(ws + L.p1);
-        d = reinterpret_cast<T *>(ws + L.d);
-        const int nx = g.nx, ny = g.ny, nz = g.nz;
-        // kernel attributes and occupancy (never during a capture)
-        int occ_a = GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::occupancy());
-        int occ_b = GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::occupancy());
-        ga = make_geom(cfg_a, nx, ny, nz, occ_a, GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::smem));
-        // pass B uses pass A's z chunks (it marches them downwards), so each
-        // of its CTAs starts on the planes pass A's CTAs finished with
-        gb = make_geom(cfg_b, nx, ny, nz, occ_b, GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::smem));
-        gb.zchunk = ga.zchunk;
-        gb.zchunks = ga.zchunks;
-        memset(&ma, 0, sizeof(ma));
-        memset(&mb, 0, sizeof(mb));
-        if (TMA) {
-            int rc = 0;
-            rc |= make_pass_map<T>(&ma.h0[0], cfg_a, true, z, nx, ny, nz);
-            ma.h0[1] = ma.h0[0];
-            rc |= make_pass_map<T>(&ma.h1[0], cfg_a, true, p0, nx, ny, nz);
-            rc |= make_pass_map<T>(&ma.h1[1], cfg_a, true, p1, nx, ny, nz);
-            rc |= make_pass_map<T>(&ma.c0, cfg_a, false, d, nx, ny, nz);
-            rc |= make_pass_map<T>(&mb.h0[0], cfg_b, true, p0, nx, ny, nz);
-            rc |= make_pass_map<T>(&mb.h0[1], cfg_b, true, p1, nx, ny, nz);
-            mb.h1[0] = mb.h1[1] = mb.h0[0];
-            rc |= make_pass_map<T>(&mb.c0, cfg_b, false, z, nx, ny, nz);
-            if (rc) return GBPCG_ERR_CUDA;
-        }
-        memset(&aa, 0, sizeof(aa));
-        memset(&ab, 0, sizeof(ab));
-        for (PassArgs *a : {&aa, &ab}) {
-            a->nx = nx; a->ny = ny; a->nz = nz;
-            a->st = st;
-            a->partials = partials;
-            a->scale = 1.0f;
-        }
-        aa.tiles_x = ga.tiles_x; aa.zchunk = ga.zchunk;
-        aa.h0[0] = aa.h0[1] = z; aa.h1[0] = p0; aa.h1[1] = p1; aa.c0 = d; aa.o0[0] = p0; aa.o0[1] = p1; aa.o1 = d;
-        ab.tiles_x = gb.tiles_x; ab.zchunk = gb.zchunk;
-        ab.h0[0] = p0; ab.h0[1] = p1; ab.h1[0] = ab.h1[1] = p0; ab.c0 = z; ab.o0[0] = ab.o0[1] = z; ab.o1 = z;
-        auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
-        memset(&ra, 0, sizeof(ra));
-        ra.nx = nx; ra.ny = ny; ra.nz = nz;
-        ra.x = x; ra.b = b; ra.z = z; ra.d = d;
-        ra.cx = cc(nx); ra.cy = cc(ny); ra.cz = cc(nz);
-        ra.kb = g.k_block;
-        ra.kbx = g.k_block ? g.kbx : 1; ra.kby = g.k_block ? g.kby : 1; ra.kbz = g.k_block ? g.kbz : 1;
-        ra.st = st;
-        ra.partials = partials;
-        return GBPCG_OK;
-    }
-
-    void set_cond(cudaGraphConditionalHandle c, cudaGraphConditionalHandle cr, int use) {
-        cond_loop = c;
-        cond_rep = cr;
-        use_cond = use;
-        aa.cond = ab.cond = c;
-        aa.cond_replace = ab.cond_replace = cr;
-        aa.use_cond = ab.use_cond = use;
-        ra.cond = c;
-        ra.use_cond = use;
-    }
-
-    unsigned stream_blocks(int64_t n, int per) const {
-        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, (int64_t)device_sm_count() * 8));
-    }
-    unsigned row_blocks() const {
-        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)g.ny * g.nz, (int64_t)device_sm_count() * 8));
-    }
-
-    template <int MODE>
-    void launch_res64(cudaStream_t s) {
-        if (g.k_block)
-            residual64_kernel<MODE, X, X, true><<<row_blocks(), 256, 0, s>>>(ra);
-        else
-            residual64_kernel<MODE, X, X, false><<<row_blocks(), 256, 0, s>>>(ra);
-    }
-
-    cudaError_t launch_setup(cudaStream_t s) {
-        reset_state_kernel<<<1, 32, 0, s>>>(st, tol, maxit);
-        launch_res64<RES_INIT>(s);
-        return cudaGetLastError();
-    }
-    cudaError_t launch_a(cudaStream_t s) {
-        return GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::launch(ma, aa, op, ga.grid(), s));
-    }
-    cudaError_t launch_b(cudaStream_t s) {
-        return GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::launch(mb, ab, op, gb.grid(), s));
-    }
-
-    // flush d into x, then r = b - A x in FP64 (both no-ops unless st->replace)
-    cudaError_t launch_replace(cudaStream_t s) {
-        const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-        flush_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
-        launch_res64<RES_REPLACE>(s);
-        return cudaGetLastError();
-    }
-
-    cudaError_t launch_final(cudaStream_t s) {
-        const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-        finalize_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
-        launch_res64<RES_TRUE>(s);
-        return cudaGetLastError();
-    }
-
-    // reset -> init -> while(cond){A; B; if(replace){flush; replace}} -> finalize -> true residual
-    int capture(cudaGraph_t *out_graph) {
-        cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
-        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        GB_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-        GB_CUDA(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
-        int rc = GBPCG_OK;
-        cudaGraph_t graph = nullptr;
-        auto end_capture = [](cudaStream_t s, bool destroy) {
-            cudaStreamCaptureStatus stt;
-            if (cudaStreamIsCapturing(s, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone) {
-                cudaGraph_t tmp = nullptr;
-                cudaStreamEndCapture(s, &tmp);
-                if (destroy && tmp) cudaGraphDestroy(tmp);
-            }
-        };
-        auto fail = [&](cudaError_t e, const char *what) {
-            rc = fail_cuda(e, what);
-            end_capture(rs, false);
-            end_capture(bs, false);
-            end_capture(cs, true);
-            cudaGetLastError();
-        };
-        // adds a conditional node after the current capture dependencies of s
-        auto add_cond = [&](cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
-                            cudaGraph_t *body_out) -> cudaError_t {
-            cudaStreamCaptureStatus cst;
-            cudaGraph_t cap = nullptr;
-            const cudaGraphNode_t *deps = nullptr;
-            size_t ndeps = 0;
-            cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &ndeps);
-            if (e) return e;
-            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-            cp.conditional.handle = h;
-            cp.conditional.type = type;
-            cp.conditional.size = 1;
-            cudaGraphNode_t node;
-            e = cudaGraphAddNode(&node, cap, deps, nullptr, ndeps, &cp);
-            if (e) return e;
-            *body_out = cp.conditional.phGraph_out[0];
-            return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-        };
-        do {
-            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "begin capture"); break; }
-            cudaStreamCaptureStatus cst;
-            cudaGraph_t cap = nullptr;
-            e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap, nullptr, nullptr, nullptr);
-            if (e) { fail(e, "capture info"); break; }
-            cudaGraphConditionalHandle cond;
-            e = cudaGraphConditionalHandleCreate(&cond, cap, 1, cudaGraphCondAssignDefault);
-            if (e) { fail(e, "conditional handle"); break; }
-            set_cond(cond, 0, 1);
-            e = launch_setup(cs);
-            if (e) { fail(e, "init"); break; }
-            cudaGraph_t body = nullptr;
-            e = add_cond(cs, cond, cudaGraphCondTypeWhile, &body);
-            if (e) { fail(e, "loop node"); break; }
-            cudaGraphConditionalHandle rep;
-            e = cudaGraphConditionalHandleCreate(&rep, body, 0, cudaGraphCondAssignDefault);
-            if (e) { fail(e, "replace handle"); break; }
-            set_cond(cond, rep, 1);
-            e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "body capture"); break; }
-            e = launch_a(bs);
-            if (e) { fail(e, "pass A"); break; }
-            e = launch_b(bs);
-            if (e) { fail(e, "pass B"); break; }
-            cudaGraph_t rbody = nullptr;
-            e = add_cond(bs, rep, cudaGraphCondTypeIf, &rbody);
-            if (e) { fail(e, "replace node"); break; }
-            e = cudaStreamBeginCaptureToGraph(rs, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "replace capture"); break; }
-            e = launch_replace(rs);
-            if (e) { fail(e, "replace kernels"); break; }
-            cudaGraph_t tmp = nullptr;
-            e = cudaStreamEndCapture(rs, &tmp);
-            if (e) { fail(e, "end replace capture"); break; }
-            e = cudaStreamEndCapture(bs, &tmp);
-            if (e) { fail(e, "end body capture"); break; }
-            e = launch_final(cs);
-            if (e) { fail(e, "finalize"); break; }
-            e = cudaStreamEndCapture(cs, &graph);
-            if (e) { fail(e, "end capture"); break; }
-        } while (0);
-        cudaStreamDestroy(rs);
-        cudaStreamDestroy(bs);
-        cudaStreamDestroy(cs);
-        if (rc) return rc;
-        *out_graph = graph;
-        return GBPCG_OK;
-    }
-
-    // Profile mode: the same kernels launched one by one on `s`, each pass
-    // launch bracketed by CUDA events; the loop polls the device flag every
-    // kChunk iterations.  Only launches of real iterations are summed.
-    int run_profiled(cudaStream_t s, double pass_ms[2], int launches[2]) {
-        constexpr int kChunk = 32;
-        set_cond(0, 0, 0);
-        GB_CUDA(launch_setup(s));
-        cudaEvent_t ev[kChunk][4];
-        for (int i = 0; i < kChunk; ++i)
-            for (int j = 0; j < 4; ++j) GB_CUDA(cudaEventCreate(&ev[i][j]));
-        pass_ms[0] = pass_ms[1] = 0.0;
-        launches[0] = launches[1] = 0;
-        int flags_h[2] = {0, 0};
-        int rc = GBPCG_OK;
-        for (int base = 0; base < std::max(maxit, 1); base += kChunk) {
-            const int cnt = std::min(kChunk, std::max(maxit, 1) - base);
-            for (int i = 0; i < cnt; ++i) {
-                cudaEventRecord(ev[i][0], s);
-                launch_a(s);
-                cudaEventRecord(ev[i][1], s);
-                cudaEventRecord(ev[i][2], s);
-                launch_b(s);
-                cudaEventRecord(ev[i][3], s);
-                launch_replace(s);
-            }
-            cudaMemcpyAsync(&flags_h[0], &st->it, sizeof(int), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(&flags_h[1], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
-            cudaError_t e = cudaStreamSynchronize(s);
-            if (e) { rc = fail_cuda(e, "profiled iteration"); break; }
-            const int real = std::min(cnt, flags_h[0] - base);  // iterations completed in this chunk
-            for (int i = 0; i < real; ++i) {
-                float ta = 0.f, tb = 0.f;
-                cudaEventElapsedTime(&ta, ev[i][0], ev[i][1]);
-                cudaEventElapsedTime(&tb, ev[i][2], ev[i][3]);
-                pass_ms[0] += ta;
-                pass_ms[1] += tb;
-                launches[0] += 1;
-                launches[1] += 1;
-            }
-            if (flags_h[1]) break;
-        }
-        for (int i = 0; i < kChunk; ++i)
-            for (int j = 0; j < 4; ++j) cudaEventDestroy(ev[i][j]);
-        if (rc) return rc;
-        GB_CUDA(launch_final(s));
-        return GBPCG_OK;
-    }
-};
 
 static bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
@@ -547,54 +219,24 @@ static bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-struct SolveCall {
-    const gbpcg_grid *g;
-    int cfg_a, cfg_b;
-    const void *b;
-    void *x;
-    char *ws;
-    WsLayout L;
-    const gbpcg_opts *o;
-};
-
-template <typename Op, bool TMA, typename X>
-static int capture_plan(const SolveCall &c, const Op &op, cudaGraph_t *graph) {
-    SolvePlan<Op, TMA, X> plan;
-    if (int rc = plan.init(*c.g, op, c.cfg_a, c.cfg_b, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L,
-                           c.o->tol, c.o->maxit))
-        return rc;
-    return plan.capture(graph);
-}
-
-template <typename Op, bool TMA, typename X>
-static int run_plan_profiled(const SolveCall &c, const Op &op, gbpcg_result *res, cudaStream_t s) {
-    SolvePlan<Op, TMA, X> plan;
-    if (int rc = plan.init(*c.g, op, c.cfg_a, c.cfg_b, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L,
-                           c.o->tol, c.o->maxit))
-        return rc;
-    return plan.run_profiled(s, res->pass_ms, res->pass_launches);
-}
-
-// Dispatch over (operator, TMA path, io type).
-template <typename F>
-static int dispatch_plan(const SolveCall &c, bool tma, F &&f) {
-    const gbpcg_grid &g = *c.g;
-    const bool f64 = c.o->io_dtype == GBPCG_F64;
-    if (g.k_block) {
-        OpBlock op = make_op_block(g);
-        if (tma) return f64 ? f(op, std::true_type{}, double{}) : f(op, std::true_type{}, float{});
-        return f64 ? f(op, std::false_type{}, double{}) : f(op, std::false_type{}, float{});
-    }
-    OpConst op = make_op_const(g.nx, g.ny, g.nz);
-    if (tma) return f64 ? f(op, std::true_type{}, double{}) : f(op, std::true_type{}, float{});
-    return f64 ? f(op, std::false_type{}, double{}) : f(op, std::false_type{}, float{});
+// Tile configurations of pass A and pass B: explicit (opts->tile_cfg) or
+// the default for the grid's width (from a sweep of all pairs at 256^3 on
+// GB300: every shape lands within a few percent; whole-row tiles for pass A
+// and 128x8 for pass B are at the front).
+static void pick_cfgs(const gbpcg_grid &g, const gbpcg_opts &o, int *ca, int *cb) {
+    const int narrow = g.nx <= 32 ? CFG_32x16 : g.nx <= 64 ? CFG_64x16 : -1;
+    const int def_a = narrow >= 0 ? narrow : (g.nx > 192 && g.nx <= 256) ? CFG_256x4 : CFG_128x8;
+    const int def_b = narrow >= 0 ? narrow : CFG_128x8;
+    const int ea = o.tile_cfg & 0xff, eb = (o.tile_cfg >> 8) & 0xff;
+    *ca = ea ? ea - 1 : def_a;
+    *cb = eb ? eb - 1 : def_b;
 }
 
 // Reads the device scalars back (and x, for host buffers), fills *result.
-static int finish_solve(char *ws, const WsLayout &L, void *x, void *xd, bool x_host, size_t io_bytes, cudaEvent_t e0,
-                        cudaEvent_t e1, gbpcg_result *result, cudaStream_t s) {
+static int finish_solve(const SolveState *st_dev, void *x, const void *xd, bool x_host, size_t io_bytes,
+                        cudaEvent_t e0, cudaEvent_t e1, gbpcg_result *result, cudaStream_t s) {
     SolveState hs;
-    GB_CUDA(cudaMemcpyAsync(&hs, ws + L.state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaMemcpyAsync(&hs, st_dev, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     if (x_host) GB_CUDA(cudaMemcpyAsync(x, xd, io_bytes, cudaMemcpyDeviceToHost, s));
     GB_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
@@ -611,17 +253,123 @@ static int finish_solve(char *ws, const WsLayout &L, void *x, void *xd, bool x_h
     return hs.status;
 }
 
-// Tile configurations of pass A and pass B: explicit (opts->tile_cfg) or
-// the default for the grid's width (from a sweep of all pairs at 256^3 on
-// GB300: every shape lands within a few percent; whole-row tiles for pass A
-// and 128x8 for pass B are at the front).
-static void pick_cfgs(const gbpcg_grid &g, const gbpcg_opts &o, int *ca, int *cb) {
-    const int narrow = g.nx <= 32 ? CFG_32x16 : g.nx <= 64 ? CFG_64x16 : -1;
-    const int def_a = narrow >= 0 ? narrow : (g.nx > 192 && g.nx <= 256) ? CFG_256x4 : CFG_128x8;
-    const int def_b = narrow >= 0 ? narrow : CFG_128x8;
-    const int ea = o.tile_cfg & 0xff, eb = (o.tile_cfg >> 8) & 0xff;
-    *ca = ea ? ea - 1 : def_a;
-    *cb = eb ? eb - 1 : def_b;
+// Outer FP64 refinement loop; b and x are FP64 device arrays.  An outer step
+// whose correction does not reduce ||b - A x|| is undone and ends the solve
+// (status NOT_CONVERGED): the inner solves have stopped helping.
+static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const gbpcg_opts *o, char *ws,
+                        const RefineLayout &R, int cfg_a, int cfg_b, bool tma, gbpcg_result *result, cudaStream_t s) {
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
+    const double cmax = std::max(cc(g.nx), std::max(cc(g.ny), cc(g.nz)));
+    const float sigma = (float)(1.0 / cmax);
+    OuterState *os = reinterpret_cast<OuterState *>(ws + R.outer);
+    double *partials = reinterpret_cast<double *>(ws + R.partials);
+    float *r32 = reinterpret_cast<float *>(ws + R.r32);
+    float *din = reinterpret_cast<float *>(ws + R.din);
+    char *inner_ws = ws + R.inner;
+    SolveState *ist = reinterpret_cast<SolveState *>(inner_ws + R.in.state);
+    const SolveCall inner{&g, cfg_a, cfg_b, r32, din, inner_ws, R.in, o->inner_tol, o->maxit, GBPCG_F32, sigma,
+                          &os->bscale};
+    const unsigned rb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)g.ny * g.nz, device_sm_count() * 8));
+    const unsigned eb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, device_sm_count() * 8));
+    OuterState init;
+    memset(&init, 0, sizeof(init));
+    init.sigma = (double)sigma;
+    auto launch_outer = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(os, &init, sizeof(init), cudaMemcpyHostToDevice, s);
+        if (e) return e;
+        if (g.k_block)
+            outer_residual_kernel<true><<<rb, 256, 0, s>>>(g.nx, g.ny, g.nz, x, b, r32, cc(g.nx), cc(g.ny),
+                                                          cc(g.nz), g.k_block, g.kbx, g.kby, g.kbz, os, partials);
+        else
+            outer_residual_kernel<false><<<rb, 256, 0, s>>>(g.nx, g.ny, g.nz, x, b, r32, cc(g.nx), cc(g.ny),
+                                                           cc(g.nz), nullptr, 1, 1, 1, os, partials);
+        return cudaGetLastError();
+    };
+
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    GB_CUDA(cudaEventRecord(e0, s));
+    GB_CUDA(launch_outer());
+    int steps = 0, total_iters = 0, status = GBPCG_NOT_CONVERGED, replacements = 0;
+    double rel = 0.0, rel_prev = 0.0, corr_applied = 0.0;
+    bool have_inner = false;
+    for (;;) {
+        OuterState ho;
+        SolveState hi;
+        GB_CUDA(cudaMemcpyAsync(&ho, os, sizeof(ho), cudaMemcpyDeviceToHost, s));
+        if (have_inner) GB_CUDA(cudaMemcpyAsync(&hi, ist, sizeof(hi), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        if (have_inner) {
+            total_iters += hi.it;
+            replacements += hi.n_replace;
+            if (hi.status == GBPCG_BREAKDOWN || hi.status == GBPCG_TIMEOUT) {
+                status = hi.status;
+                break;
+            }
+        }
+        if (ho.bb == 0.0) {
+            zero_f64_kernel<<<eb, 256, 0, s>>>(x, n);
+            GB_CUDA(cudaGetLastError());
+            rel = 0.0;
+            status = GBPCG_OK;
+            break;
+        }
+        rel = sqrt(ho.rr / ho.bb);
+        if (have_inner && !(rel < rel_prev)) {
+            // the last correction did not reduce the residual: take it back and stop
+            init.applied = corr_applied;
+            GB_CUDA(cudaMemcpyAsync(os, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+            refine_update_kernel<<<eb, 256, 0, s>>>(x, din, os, n, 1);
+            GB_CUDA(cudaGetLastError());
+            GB_CUDA(launch_outer());
+            GB_CUDA(cudaMemcpyAsync(&ho, os, sizeof(ho), cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaStreamSynchronize(s));
+            rel = sqrt(ho.rr / ho.bb);
+            status = GBPCG_NOT_CONVERGED;
+            break;
+        }
+        if (!std::isfinite(rel)) {
+            status = GBPCG_BREAKDOWN;
+            break;
+        }
+        if (rel <= o->tol) {
+            status = GBPCG_OK;
+            break;
+        }
+        if (steps >= o->max_outer) {
+            status = GBPCG_NOT_CONVERGED;
+            break;
+        }
+        // the inner solve starts from d = 0 (din keeps the last correction until
+        // here, so a step can be undone)
+        GB_CUDA(cudaMemsetAsync(din, 0, (size_t)n * sizeof(float), s));
+        int rc = o->storage == GBPCG_BF16 ? solve_launch<__nv_bfloat16>(inner, tma, s)
+                                          : solve_launch<__half>(inner, tma, s);
+        if (rc) return rc;
+        refine_update_kernel<<<eb, 256, 0, s>>>(x, din, os, n, 0);
+        GB_CUDA(cudaGetLastError());
+        corr_applied = (double)sigma * __builtin_bit_cast(double, ho.rmax_bits);
+        rel_prev = rel;
+        GB_CUDA(launch_outer());
+        have_inner = true;
+        steps += 1;
+    }
+    GB_CUDA(cudaEventRecord(e1, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    result->iters = total_iters;
+    result->status = status;
+    result->refine_steps = steps;
+    result->replacements = replacements;
+    result->rel_res_recursive = rel;
+    result->rel_res_true = rel;
+    result->time_ms = ms;
+    return status;
 }
 
 }  // namespace gb
@@ -645,7 +393,7 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
     if (int rc = check_grid(grid)) return rc;
     if (int rc = check_opts(opts)) return rc;
     if (!bytes) return fail_arg("bytes is NULL");
-    *bytes = ws_layout(*grid, *opts).total;
+    *bytes = workspace_total(*grid, *opts);
     return GBPCG_OK;
 }
 
@@ -656,8 +404,8 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     if (int rc = check_opts(opts)) return rc;
     if (!b || !x || !result) return fail_arg("b, x and result must be non-NULL");
     memset(result, 0, sizeof(*result));
-    const WsLayout L = ws_layout(*grid, *opts);
-    if (!opts->workspace || opts->workspace_bytes < L.total) return fail_arg("workspace smaller than gbpcg_workspace_size()");
+    const size_t total = workspace_total(*grid, *opts);
+    if (!opts->workspace || opts->workspace_bytes < total) return fail_arg("workspace smaller than gbpcg_workspace_size()");
     if (reinterpret_cast<uintptr_t>(opts->workspace) & 255u) return fail_arg("workspace must be 256-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(opts->workspace);
@@ -667,88 +415,52 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     const size_t io_bytes = (size_t)n * esz;
     if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(x)) & (esz - 1))
         return fail_arg("b and x must be aligned to their element size");
-
-    // host buffers are staged through the workspace
-    const bool b_host = (opts->flags & GBPCG_FLAG_HOST_IO) && !is_device_ptr(b);
-    const bool x_host = (opts->flags & GBPCG_FLAG_HOST_IO) && !is_device_ptr(x);
-    const void *bd = b_host ? static_cast<const void *>(ws + L.bstage) : b;
-    void *xd = x_host ? static_cast<void *>(ws + L.xstage) : x;
-    if (b_host) GB_CUDA(cudaMemcpyAsync(const_cast<void *>(bd), b, io_bytes, cudaMemcpyHostToDevice, s));
-    if (x_host) GB_CUDA(cudaMemcpyAsync(xd, x, io_bytes, cudaMemcpyHostToDevice, s));
-
     int cfg_a = 0, cfg_b = 0;
     pick_cfgs(g, *opts, &cfg_a, &cfg_b);
     if (!cfg_fits(cfg_a, g.nx) || !cfg_fits(cfg_b, g.nx))
         return fail_arg("tile_cfg selects a whole-row configuration for a grid wider than 256");
-    const bool tma = tma_ok(sizeof(float), g.nx, {ws + L.z, ws + L.p0, ws + L.p1, ws + L.d});
-    const SolveCall call{&g, cfg_a, cfg_b, bd, xd, ws, L, opts};
 
-    if (opts->flags & GBPCG_FLAG_PROFILE) {
-        cudaEvent_t e0, e1;
-        GB_CUDA(cudaEventCreate(&e0));
-        GB_CUDA(cudaEventCreate(&e1));
-        GB_CUDA(cudaEventRecord(e0, s));
-        int rc = dispatch_plan(call, tma, [&](auto op, auto tm, auto xt) {
-            return run_plan_profiled<decltype(op), decltype(tm)::value, decltype(xt)>(call, op, result, s);
-        });
-        if (rc) return rc;
-        GB_CUDA(cudaEventRecord(e1, s));
-        return finish_solve(ws, L, x, xd, x_host, io_bytes, e0, e1, result, s);
-    }
+    // host buffers are staged through the end of the workspace
+    const bool host_io = opts->flags & GBPCG_FLAG_HOST_IO;
+    const bool b_host = host_io && !is_device_ptr(b);
+    const bool x_host = host_io && !is_device_ptr(x);
+    char *stage = ws + total - (host_io ? 2 * round256(io_bytes) : 0);
+    const void *bd = b_host ? static_cast<const void *>(stage) : b;
+    void *xd = x_host ? static_cast<void *>(stage + round256(io_bytes)) : x;
+    if (b_host) GB_CUDA(cudaMemcpyAsync(const_cast<void *>(bd), b, io_bytes, cudaMemcpyHostToDevice, s));
+    if (x_host) GB_CUDA(cudaMemcpyAsync(xd, x, io_bytes, cudaMemcpyHostToDevice, s));
 
-    int dev = 0;
-    GB_CUDA(cudaGetDevice(&dev));
-    SolveKey key;
-    memset(&key, 0, sizeof(key));
-    key.dev = dev; key.nx = g.nx; key.ny = g.ny; key.nz = g.nz;
-    key.kb = g.k_block;
-    if (g.k_block) { key.kbx = g.kbx; key.kby = g.kby; key.kbz = g.kbz; }
-    key.maxit = opts->maxit; key.cfg_a = cfg_a; key.cfg_b = cfg_b; key.tma = tma; key.io = opts->io_dtype;
-    key.b = bd; key.x = xd; key.ws = ws; key.tol = opts->tol;
-
-    cudaGraphExec_t exec = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_cache_mu);
-        for (auto it = g_cache.begin(); it != g_cache.end(); ++it)
-            if (it->key == key) {
-                g_cache.splice(g_cache.begin(), g_cache, it);
-                exec = g_cache.front().exec;
-                break;
-            }
-        if (!exec) {
-            cudaGraph_t graph = nullptr;
-            int rc = dispatch_plan(call, tma, [&](auto op, auto tm, auto xt) {
-                return capture_plan<decltype(op), decltype(tm)::value, decltype(xt)>(call, op, &graph);
-            });
-            if (rc) return rc;
-            cudaGraphExec_t ex = nullptr;
-            cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
-            if (e) {
-                cudaGraphDestroy(graph);
-                return fail_cuda(e, "graph instantiate");
-            }
-            cudaGraphUpload(ex, s);
-            SolveGraph sg;
-            sg.key = key;
-            sg.graph = graph;
-            sg.exec = ex;
-            g_cache.push_front(sg);
-            while (g_cache.size() > kCacheMax) {
-                cudaGraphExecDestroy(g_cache.back().exec);
-                cudaGraphDestroy(g_cache.back().graph);
-                g_cache.pop_back();
-            }
-            exec = ex;
+    if (refine_mode(*opts)) {
+        const RefineLayout R = refine_layout(g, *opts);
+        const bool tma = tma_ok(dtype_size(opts->storage), g.nx,
+                                {ws + R.inner + R.in.z, ws + R.inner + R.in.p0, ws + R.inner + R.in.p1,
+                                 ws + R.inner + R.in.d});
+        int rc = refine_solve(g, static_cast<const double *>(bd), static_cast<double *>(xd), opts, ws, R, cfg_a, cfg_b,
+                              tma, result, s);
+        if (x_host) {
+            GB_CUDA(cudaMemcpyAsync(x, xd, io_bytes, cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaStreamSynchronize(s));
         }
+        return rc;
     }
 
+    const WsLayout L = ws_layout_n((size_t)n, opts->storage, opts->io_dtype, false, block_count(g));
+    const bool tma = tma_ok(sizeof(float), g.nx, {ws + L.z, ws + L.p0, ws + L.p1, ws + L.d});
+    const SolveCall call{&g, cfg_a, cfg_b, bd, xd, ws, L, opts->tol, opts->maxit, opts->io_dtype, 1.0f, nullptr};
+    const SolveState *st = reinterpret_cast<const SolveState *>(ws + L.state);
     cudaEvent_t e0, e1;
     GB_CUDA(cudaEventCreate(&e0));
     GB_CUDA(cudaEventCreate(&e1));
     GB_CUDA(cudaEventRecord(e0, s));
-    GB_CUDA(cudaGraphLaunch(exec, s));
+    const int rc = (opts->flags & GBPCG_FLAG_PROFILE) ? solve_profiled<float>(call, tma, result, s)
+                                                      : solve_launch<float>(call, tma, s);
+    if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+    }
     GB_CUDA(cudaEventRecord(e1, s));
-    return finish_solve(ws, L, x, xd, x_host, io_bytes, e0, e1, result, s);
+    return finish_solve(st, x, xd, x_host, io_bytes, e0, e1, result, s);
 }
 
 }  // extern "C"

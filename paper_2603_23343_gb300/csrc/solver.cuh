@@ -1,0 +1,653 @@
+// Jacobi-preconditioned CG (Sec. VII) as one CUDA graph per problem:
+//
+//   reset -> init (r0 = b - A x0 in FP64) ->
+//   while (cond) { K_PASSA ; K_PASSB ; if (replace) { flush ; replace } } ->
+//   finalize -> FP64 true residual
+//
+// The loop is a conditional WHILE node; the last CTA of each pass decides
+// (from the grid-wide sums it has just finished) whether to continue and sets
+// the condition from the device, so no scalar goes back to the host during
+// the solve.  Per iteration the two data passes move 20 + 12 bytes per grid
+// point in FP32 (see engine.cuh), against 44 for a three-kernel
+// stencil / update-x-r / update-p split.
+//
+// Accuracy with FP32 vectors (reliable updates, van der Vorst & Ye, SIAM J.
+// Sci. Comput. 22, 2000): the updates alpha p go into a correction vector d
+// instead of x, so their rounding is relative to |d|, not |x|.  Whenever
+// ||r|| has dropped by a decade since the last time, and when the recursive
+// residual meets the tolerance, d is flushed into x and the recursive
+// residual is replaced by b - A x evaluated in FP64; the iteration continues
+// from the replaced residual (p is kept).  Convergence is therefore decided
+// on a true residual.  x and b may be FP32 or FP64: they are only touched by
+// the init, the replacements and the finalize, never by the per-iteration
+// passes.  With FP32 x the rounding of x itself bounds the attainable true
+// residual (about 1e-6 relative at 256^3); the solve stops with
+// GBPCG_NOT_CONVERGED if confirmations stop making progress.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+
+#include "launch.cuh"
+
+namespace gb {
+
+// ------------------------------------------------------------- kernels --
+
+static __global__ void reset_state_kernel(SolveState *st, double tol, int maxit) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        memset(st, 0, sizeof(SolveState));
+        st->tol2 = tol * tol;
+        st->maxit = maxit;
+        st->status = GBPCG_NOT_CONVERGED;
+    }
+}
+
+// Per-block face coefficients for OpTable: {k, k_x-, k_x+, k_y-},
+// {k_y+, k_z-, k_z+, 0}; a face towards a neighbouring block carries the
+// harmonic mean (the same FP32 expression as OpBlock), a face on the domain
+// boundary the block's own k.
+static __global__ void build_face_table(const float *__restrict__ kb, int nbx, int nby, int nbz, float4 *tab) {
+    const int64_t nb = (int64_t)nbx * nby * nbz;
+    auto hm = [](float a, float b) { return 2.0f * a * b / (a + b); };
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(t % nbx), by = (int)((t / nbx) % nby), bz = (int)(t / ((int64_t)nbx * nby));
+        auto K = [&](int x, int y, int z) { return __ldg(kb + ((int64_t)z * nby + y) * nbx + x); };
+        const float k = K(bx, by, bz);
+        tab[2 * t] = make_float4(k, bx > 0 ? hm(k, K(bx - 1, by, bz)) : k, bx < nbx - 1 ? hm(k, K(bx + 1, by, bz)) : k,
+                                 by > 0 ? hm(k, K(bx, by - 1, bz)) : k);
+        tab[2 * t + 1] = make_float4(by < nby - 1 ? hm(k, K(bx, by + 1, bz)) : k, bz > 0 ? hm(k, K(bx, by, bz - 1)) : k,
+                                     bz < nbz - 1 ? hm(k, K(bx, by, bz + 1)) : k, 0.0f);
+    }
+}
+
+enum ResMode { RES_INIT = 0, RES_REPLACE = 1, RES_TRUE = 2 };
+
+struct Res64Args {
+    int nx, ny, nz;
+    const void *x, *b;
+    void *z;   // storage type T of the kernel
+    float *d;  // the correction vector is FP32 for every storage type
+    double cx, cy, cz;
+    const float *kb;
+    int kbx, kby, kbz;
+    const double *bscale;  // NULL, or a device scalar multiplying b (inner refinement solves)
+    SolveState *st;
+    double *partials;
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+
+constexpr double kHuge = 1e300;
+
+// r = b - A x with FP64 arithmetic, one block per grid row (x fastest).
+//   RES_INIT     z = D^-1 r, d = 0; sums r.r, r.z, b.b  -> start state
+//   RES_REPLACE  z = D^-1 r;        sums r.r, r.z       -> replacement decisions
+//   RES_TRUE     sums r.r, b.b                          -> reported true residual
+template <int MODE, typename X, typename Bt, bool BLOCK, typename T>
+__global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
+    SolveState *st = a.st;
+    if (MODE == RES_REPLACE && (!st->replace || st->done)) return;
+    const X *__restrict__ x = static_cast<const X *>(a.x);
+    const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int64_t pl = (int64_t)nx * ny;
+    const int nbx = BLOCK ? (nx + a.kbx - 1) / a.kbx : 0, nby = BLOCK ? (ny + a.kby - 1) / a.kby : 0;
+    const double cx = a.cx, cy = a.cy, cz = a.cz;
+    const double bsc = a.bscale ? *a.bscale : 1.0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const int rows = ny * nz;
+    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int j = row % ny, k = row / ny;
+        const int64_t base = (int64_t)row * nx;
+        for (int i = threadIdx.x; i < nx; i += 256) {
+            const int64_t g = base + i;
+            auto L = [&](int64_t o) { return (double)__ldg(x + o); };
+            const double c = L(g);
+            const double xm = i > 0 ? L(g - 1) : 0.0, xp = i < nx - 1 ? L(g + 1) : 0.0;
+            const double ym = j > 0 ? L(g - nx) : 0.0, yp = j < ny - 1 ? L(g + nx) : 0.0;
+            const double zm = k > 0 ? L(g - pl) : 0.0, zp = k < nz - 1 ? L(g + pl) : 0.0;
+            double w[6] = {cx, cx, cy, cy, cz, cz};
+            if (BLOCK) {
+                const float *kb = a.kb;
+                auto K = [&](int p, int q, int r) { return (double)__ldg(kb + ((int64_t)r * nby + q) * nbx + p); };
+                auto hm = [](double u, double v) { return 2.0 * u * v / (u + v); };
+                const int bx = i / a.kbx, by = j / a.kby, bz = k / a.kbz;
+                const int ix = i - bx * a.kbx, iy = j - by * a.kby, iz = k - bz * a.kbz;
+                const double kc = K(bx, by, bz);
+                w[0] = cx * ((ix == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
+                w[1] = cx * ((ix == a.kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
+                w[2] = cy * ((iy == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
+                w[3] = cy * ((iy == a.kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
+                w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
+                w[5] = cz * ((iz == a.kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
+            }
+            const double ax = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) +
+                              w[4] * (c - zm) + w[5] * (c - zp);
+            const double bv = bsc * (double)__ldg(b + g);
+            const double r = bv - ax;
+            s0 = fma(r, r, s0);
+            if (MODE == RES_TRUE) {
+                s1 = fma(bv, bv, s1);
+            } else {
+                const float dg = (float)(((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]));
+                const T zt = from_f<T>((float)r / dg);
+                static_cast<T *>(a.z)[g] = zt;
+                s1 = fma(r, (double)to_f(zt), s1);
+                if (MODE == RES_INIT) {
+                    static_cast<float *>(a.d)[g] = 0.0f;
+                    s2 = fma(bv, bv, s2);
+                }
+            }
+        }
+    }
+    constexpr int NV = MODE == RES_INIT ? 3 : 2;
+    __shared__ double red[8][3];
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][0] = s0;
+        red[threadIdx.x >> 5][1] = s1;
+        red[threadIdx.x >> 5][2] = s2;
+    }
+    __syncthreads();
+    double part[NV], tot[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v] = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) part[v] += red[w][v];
+    if (!grid_sum_last<NV, 256>(part, a.partials, &st->ticket[4 + MODE], tot) || threadIdx.x != 0) return;
+    if (MODE == RES_TRUE) {
+        st->rr_true = tot[0];
+        st->bb_true = tot[1];
+        return;
+    }
+    if (MODE == RES_INIT) {
+        const double rr = tot[0], rz = tot[1], bb = tot[2];
+        st->bb = bb; st->rr = rr; st->rz = rz; st->rr_rep = rr; st->rr_conf = kHuge;
+        st->it = 0; st->pending = 0; st->zero_x = 0; st->replace = 0;
+        if (bb == 0.0) { st->zero_x = 1; st->done = 1; st->status = GBPCG_OK; }
+        else if (rr <= st->tol2 * bb) { st->done = 1; st->status = GBPCG_OK; }
+        else if (!isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+        else if (st->maxit <= 0) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+        else { st->done = 0; st->status = GBPCG_NOT_CONVERGED; }
+    } else {
+        const double rrt = tot[0], rzt = tot[1];
+        const int kind = st->replace;  // 1: decade of progress, 2: recursive residual met tol
+        st->rr = rrt;
+        st->rr_rep = rrt;
+        st->replace = 0;
+        st->pending = 0;
+        st->n_replace += 1;
+        if (rrt <= st->tol2 * st->bb) { st->done = 1; st->status = GBPCG_OK; }
+        else if (!isfinite(rrt) || !isfinite(rzt) || !(rzt > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+        else if (st->it >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+        else if (kind == 2 && rrt > 0.25 * st->rr_conf) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+        else {
+            if (kind == 2) st->rr_conf = rrt;
+            st->beta = rzt / st->rz;
+            st->rz = rzt;
+        }
+    }
+    if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
+}
+
+// Residual replacement, step 1: x += d + alpha_{it-1} p_{it-1} (pending), d = 0.
+template <typename X, typename T>
+__global__ void flush_kernel(SolveState *st, X *x, float *d, const T *p0, const T *p1, int64_t n) {
+    if (!st->replace || st->done) return;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    const T *p = ((st->it - 1) & 1) ? p1 : p0;
+    const float a = st->pending ? (float)st->alpha : 0.0f;
+    for (int64_t i = tid; i < n; i += nth) {
+        x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]);
+        d[i] = 0.0f;
+    }
+}
+
+// x += d + alpha_{it-1} p_{it-1} (the pending update, if any); x = 0 when b = 0.
+template <typename X, typename T>
+__global__ void finalize_kernel(const SolveState *st, X *x, const float *d, const T *p0, const T *p1, int64_t n) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    if (st->zero_x) {
+        for (int64_t i = tid; i < n; i += nth) x[i] = X(0);
+        return;
+    }
+    const T *p = ((st->it - 1) & 1) ? p1 : p0;
+    const float a = st->pending ? (float)st->alpha : 0.0f;
+    for (int64_t i = tid; i < n; i += nth) x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]);
+}
+
+// ----------------------------------------------------------- workspace --
+
+struct WsLayout {
+    size_t state, partials, z, p0, p1, d, tab, bstage, xstage, total;
+};
+
+static inline size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Solver workspace: scalars, partial sums, z, p0, p1, d (storage type) and,
+// for host I/O, staging copies of b and x.
+static inline WsLayout ws_layout_n(size_t n, int storage, int io_dtype, bool host_io, int64_t nblocks) {
+    const size_t vs = round256(n * dtype_size(storage));
+    const size_t io = round256(n * dtype_size(io_dtype));
+    WsLayout w;
+    size_t off = 0;
+    w.state = off; off += 256;
+    w.partials = off; off += round256(sizeof(double) * 4 * kMaxPassBlocks);
+    w.z = off; off += vs;
+    w.p0 = off; off += vs;
+    w.p1 = off; off += vs;
+    w.d = off; off += round256(n * sizeof(float));  // d is FP32 for every storage type
+    w.tab = off; off += round256((size_t)nblocks * 2 * sizeof(float4));  // face table (block coefficient)
+    w.bstage = w.xstage = 0;
+    if (host_io) {
+        w.bstage = off; off += io;
+        w.xstage = off; off += io;
+    }
+    w.total = off;
+    return w;
+}
+
+// ------------------------------------------------------------ the graph --
+
+struct SolveKey {
+    int dev, nx, ny, nz, kbx, kby, kbz, maxit, cfg_a, cfg_b, tma, io, storage;
+    float op_scale;
+    const void *kb, *b, *x, *ws, *bscale;
+    double tol;
+    bool operator==(const SolveKey &o) const { return memcmp(this, &o, sizeof(SolveKey)) == 0; }
+};
+
+// Instantiated solve graphs, cached by everything they bake in (pcg.cu).
+cudaGraphExec_t graph_cache_find(const SolveKey &key);
+cudaGraphExec_t graph_cache_put(const SolveKey &key, cudaGraph_t graph, cudaGraphExec_t exec);
+
+// Everything one solve launches, set up once: geometry, tensor maps, kernel
+// arguments.  The same launch functions serve graph capture and the
+// event-timed profile mode.  X is the type of x and b (float or double), T
+// the storage type of the iteration vectors z, p0, p1, d.
+template <typename Op, bool TMA, typename X, typename T>
+struct SolvePlan {
+    gbpcg_grid g;
+    Op op;
+    int cfg_a, cfg_b;
+    const X *b;
+    X *x;
+    SolveState *st;
+    double *partials;
+    T *z, *p0, *p1;
+    float *d;
+    char *tab;
+    PassGeom ga, gb;
+    PassMaps ma, mb;
+    PassArgs aa, ab;
+    Res64Args ra;
+    double tol;
+    int maxit;
+    cudaGraphConditionalHandle cond_loop = 0, cond_rep = 0;
+    int use_cond = 0;
+
+    int init(const gbpcg_grid &grid, const Op &o, int ca, int cb, const X *bb, X *xx, char *ws, const WsLayout &L,
+             double tl, int mi_, double op_scale, const double *bscale) {
+        g = grid; op = o; cfg_a = ca; cfg_b = cb; b = bb; x = xx; tol = tl; maxit = mi_;
+        st = reinterpret_cast<SolveState *>(ws + L.state);
+        partials = reinterpret_cast<double *>(ws + L.partials);
+        z = reinterpret_cast<T *>(ws + L.z);
+        p0 = reinterpret_cast<T *>(ws + L.p0);
+        p1 = reinterpret_cast<T *>(ws + L.p1);
+        d = reinterpret_cast<float *>(ws + L.d);
+        tab = ws + L.tab;
+        const int nx = g.nx, ny = g.ny, nz = g.nz;
+        // kernel attributes and occupancy (never during a capture)
+        int occ_a = GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::occupancy());
+        int occ_b = GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::occupancy());
+        ga = make_geom(cfg_a, nx, ny, nz, occ_a, GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::smem));
+        // pass B uses pass A's z chunks (it marches them downwards), so each
+        // of its CTAs starts on the planes pass A's CTAs finished with
+        gb = make_geom(cfg_b, nx, ny, nz, occ_b, GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::smem));
+        gb.zchunk = ga.zchunk;
+        gb.zchunks = ga.zchunks;
+        memset(&ma, 0, sizeof(ma));
+        memset(&mb, 0, sizeof(mb));
+        if (TMA) {
+            int rc = 0;
+            rc |= make_pass_map<T>(&ma.h0[0], cfg_a, true, z, nx, ny, nz);
+            ma.h0[1] = ma.h0[0];
+            rc |= make_pass_map<T>(&ma.h1[0], cfg_a, true, p0, nx, ny, nz);
+            rc |= make_pass_map<T>(&ma.h1[1], cfg_a, true, p1, nx, ny, nz);
+            rc |= make_pass_map<float>(&ma.c0, cfg_a, false, d, nx, ny, nz);
+            rc |= make_pass_map<T>(&mb.h0[0], cfg_b, true, p0, nx, ny, nz);
+            rc |= make_pass_map<T>(&mb.h0[1], cfg_b, true, p1, nx, ny, nz);
+            mb.h1[0] = mb.h1[1] = mb.h0[0];
+            rc |= make_pass_map<T>(&mb.c0, cfg_b, false, z, nx, ny, nz);
+            if (rc) return GBPCG_ERR_CUDA;
+        }
+        memset(&aa, 0, sizeof(aa));
+        memset(&ab, 0, sizeof(ab));
+        for (PassArgs *a : {&aa, &ab}) {
+            a->nx = nx; a->ny = ny; a->nz = nz;
+            a->st = st;
+            a->partials = partials;
+            a->scale = 1.0f;
+        }
+        aa.tiles_x = ga.tiles_x; aa.zchunk = ga.zchunk;
+        aa.h0[0] = aa.h0[1] = z; aa.h1[0] = p0; aa.h1[1] = p1; aa.c0 = d; aa.o0[0] = p0; aa.o0[1] = p1; aa.o1 = d;
+        ab.tiles_x = gb.tiles_x; ab.zchunk = gb.zchunk;
+        ab.h0[0] = p0; ab.h0[1] = p1; ab.h1[0] = ab.h1[1] = p0; ab.c0 = z; ab.o0[0] = ab.o0[1] = z; ab.o1 = z;
+        auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
+        memset(&ra, 0, sizeof(ra));
+        ra.nx = nx; ra.ny = ny; ra.nz = nz;
+        ra.x = x; ra.b = b; ra.z = z; ra.d = d;
+        ra.cx = cc(nx) * op_scale; ra.cy = cc(ny) * op_scale; ra.cz = cc(nz) * op_scale;
+        ra.bscale = bscale;
+        ra.kb = g.k_block;
+        ra.kbx = g.k_block ? g.kbx : 1; ra.kby = g.k_block ? g.kby : 1; ra.kbz = g.k_block ? g.kbz : 1;
+        ra.st = st;
+        ra.partials = partials;
+        return GBPCG_OK;
+    }
+
+    void set_cond(cudaGraphConditionalHandle c, cudaGraphConditionalHandle cr, int use) {
+        cond_loop = c;
+        cond_rep = cr;
+        use_cond = use;
+        aa.cond = ab.cond = c;
+        aa.cond_replace = ab.cond_replace = cr;
+        aa.use_cond = ab.use_cond = use;
+        ra.cond = c;
+        ra.use_cond = use;
+    }
+
+    unsigned stream_blocks(int64_t n, int per) const {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + per - 1) / per, (int64_t)device_sm_count() * 8));
+    }
+    unsigned row_blocks() const {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)g.ny * g.nz, (int64_t)device_sm_count() * 8));
+    }
+
+    template <int MODE>
+    void launch_res64(cudaStream_t s) {
+        if (g.k_block)
+            residual64_kernel<MODE, X, X, true, T><<<row_blocks(), 256, 0, s>>>(ra);
+        else
+            residual64_kernel<MODE, X, X, false, T><<<row_blocks(), 256, 0, s>>>(ra);
+    }
+
+    cudaError_t launch_setup(cudaStream_t s) {
+        reset_state_kernel<<<1, 32, 0, s>>>(st, tol, maxit);
+        if (g.k_block) {
+            const int nbx = (g.nx + g.kbx - 1) / g.kbx, nby = (g.ny + g.kby - 1) / g.kby, nbz = (g.nz + g.kbz - 1) / g.kbz;
+            const int64_t nb = (int64_t)nbx * nby * nbz;
+            build_face_table<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096)), 256, 0, s>>>(
+                g.k_block, nbx, nby, nbz, reinterpret_cast<float4 *>(tab));
+        }
+        launch_res64<RES_INIT>(s);
+        return cudaGetLastError();
+    }
+    cudaError_t launch_a(cudaStream_t s) {
+        return GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::launch(ma, aa, op, ga.grid(), s));
+    }
+    cudaError_t launch_b(cudaStream_t s) {
+        return GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::launch(mb, ab, op, gb.grid(), s));
+    }
+
+    // flush d into x, then r = b - A x in FP64 (both no-ops unless st->replace)
+    cudaError_t launch_replace(cudaStream_t s) {
+        const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+        flush_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
+        launch_res64<RES_REPLACE>(s);
+        return cudaGetLastError();
+    }
+
+    cudaError_t launch_final(cudaStream_t s) {
+        const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+        finalize_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
+        launch_res64<RES_TRUE>(s);
+        return cudaGetLastError();
+    }
+
+    // reset -> init -> while(cond){A; B; if(replace){flush; replace}} -> finalize -> true residual
+    int capture(cudaGraph_t *out_graph) {
+        cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
+        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        GB_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+        GB_CUDA(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
+        int rc = GBPCG_OK;
+        cudaGraph_t graph = nullptr;
+        auto end_capture = [](cudaStream_t s, bool destroy) {
+            cudaStreamCaptureStatus stt;
+            if (cudaStreamIsCapturing(s, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(s, &tmp);
+                if (destroy && tmp) cudaGraphDestroy(tmp);
+            }
+        };
+        auto fail = [&](cudaError_t e, const char *what) {
+            rc = fail_cuda(e, what);
+            end_capture(rs, false);
+            end_capture(bs, false);
+            end_capture(cs, true);
+            cudaGetLastError();
+        };
+        // adds a conditional node after the current capture dependencies of s
+        auto add_cond = [&](cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            cudaGraph_t *body_out) -> cudaError_t {
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cap = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &ndeps);
+            if (e) return e;
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = h;
+            cp.conditional.type = type;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            e = cudaGraphAddNode(&node, cap, deps, nullptr, ndeps, &cp);
+            if (e) return e;
+            *body_out = cp.conditional.phGraph_out[0];
+            return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        };
+        do {
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e) { fail(e, "begin capture"); break; }
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t cap = nullptr;
+            e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap, nullptr, nullptr, nullptr);
+            if (e) { fail(e, "capture info"); break; }
+            cudaGraphConditionalHandle cond;
+            e = cudaGraphConditionalHandleCreate(&cond, cap, 1, cudaGraphCondAssignDefault);
+            if (e) { fail(e, "conditional handle"); break; }
+            set_cond(cond, 0, 1);
+            e = launch_setup(cs);
+            if (e) { fail(e, "init"); break; }
+            cudaGraph_t body = nullptr;
+            e = add_cond(cs, cond, cudaGraphCondTypeWhile, &body);
+            if (e) { fail(e, "loop node"); break; }
+            cudaGraphConditionalHandle rep;
+            e = cudaGraphConditionalHandleCreate(&rep, body, 0, cudaGraphCondAssignDefault);
+            if (e) { fail(e, "replace handle"); break; }
+            set_cond(cond, rep, 1);
+            e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e) { fail(e, "body capture"); break; }
+            e = launch_a(bs);
+            if (e) { fail(e, "pass A"); break; }
+            e = launch_b(bs);
+            if (e) { fail(e, "pass B"); break; }
+            cudaGraph_t rbody = nullptr;
+            e = add_cond(bs, rep, cudaGraphCondTypeIf, &rbody);
+            if (e) { fail(e, "replace node"); break; }
+            e = cudaStreamBeginCaptureToGraph(rs, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e) { fail(e, "replace capture"); break; }
+            e = launch_replace(rs);
+            if (e) { fail(e, "replace kernels"); break; }
+            cudaGraph_t tmp = nullptr;
+            e = cudaStreamEndCapture(rs, &tmp);
+            if (e) { fail(e, "end replace capture"); break; }
+            e = cudaStreamEndCapture(bs, &tmp);
+            if (e) { fail(e, "end body capture"); break; }
+            e = launch_final(cs);
+            if (e) { fail(e, "finalize"); break; }
+            e = cudaStreamEndCapture(cs, &graph);
+            if (e) { fail(e, "end capture"); break; }
+        } while (0);
+        cudaStreamDestroy(rs);
+        cudaStreamDestroy(bs);
+        cudaStreamDestroy(cs);
+        if (rc) return rc;
+        *out_graph = graph;
+        return GBPCG_OK;
+    }
+
+    // Profile mode: the same kernels launched one by one on `s`, each pass
+    // launch bracketed by CUDA events; the loop polls the device flag every
+    // kChunk iterations.  Only launches of real iterations are summed.
+    int run_profiled(cudaStream_t s, double pass_ms[2], int launches[2]) {
+        constexpr int kChunk = 32;
+        set_cond(0, 0, 0);
+        GB_CUDA(launch_setup(s));
+        cudaEvent_t ev[kChunk][4];
+        for (int i = 0; i < kChunk; ++i)
+            for (int j = 0; j < 4; ++j) GB_CUDA(cudaEventCreate(&ev[i][j]));
+        pass_ms[0] = pass_ms[1] = 0.0;
+        launches[0] = launches[1] = 0;
+        int flags_h[2] = {0, 0};
+        int rc = GBPCG_OK;
+        for (int base = 0; base < std::max(maxit, 1); base += kChunk) {
+            const int cnt = std::min(kChunk, std::max(maxit, 1) - base);
+            for (int i = 0; i < cnt; ++i) {
+                cudaEventRecord(ev[i][0], s);
+                launch_a(s);
+                cudaEventRecord(ev[i][1], s);
+                cudaEventRecord(ev[i][2], s);
+                launch_b(s);
+                cudaEventRecord(ev[i][3], s);
+                launch_replace(s);
+            }
+            cudaMemcpyAsync(&flags_h[0], &st->it, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&flags_h[1], &st->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaError_t e = cudaStreamSynchronize(s);
+            if (e) { rc = fail_cuda(e, "profiled iteration"); break; }
+            const int real = std::min(cnt, flags_h[0] - base);  // iterations completed in this chunk
+            for (int i = 0; i < real; ++i) {
+                float ta = 0.f, tb = 0.f;
+                cudaEventElapsedTime(&ta, ev[i][0], ev[i][1]);
+                cudaEventElapsedTime(&tb, ev[i][2], ev[i][3]);
+                pass_ms[0] += ta;
+                pass_ms[1] += tb;
+                launches[0] += 1;
+                launches[1] += 1;
+            }
+            if (flags_h[1]) break;
+        }
+        for (int i = 0; i < kChunk; ++i)
+            for (int j = 0; j < 4; ++j) cudaEventDestroy(ev[i][j]);
+        if (rc) return rc;
+        GB_CUDA(launch_final(s));
+        return GBPCG_OK;
+    }
+};
+
+// One solve's arguments after validation (b and x already on the device).
+struct SolveCall {
+    const gbpcg_grid *g;
+    int cfg_a, cfg_b;
+    const void *b;
+    void *x;
+    char *ws;
+    WsLayout L;
+    double tol;
+    int maxit;
+    int io;                 // gbpcg_dtype of b and x
+    float op_scale;         // the operator is op_scale * A (1 normally)
+    const double *bscale;   // device scalar multiplying b, or NULL
+};
+
+template <typename Op, bool TMA, typename X, typename T>
+static int plan_init(SolvePlan<Op, TMA, X, T> &plan, const SolveCall &c, const Op &op) {
+    return plan.init(*c.g, op, c.cfg_a, c.cfg_b, static_cast<const X *>(c.b), static_cast<X *>(c.x), c.ws, c.L, c.tol,
+                     c.maxit, c.op_scale, c.bscale);
+}
+
+// Dispatch over (operator, TMA path, io type); 16-bit storage serves only
+// FP32 b and x (the inner solves of iterative refinement).
+template <typename T, typename F>
+static int dispatch_plan(const SolveCall &c, bool tma, F &&f) {
+    const gbpcg_grid &g = *c.g;
+    const bool f64 = c.io == GBPCG_F64;
+    if (!std::is_same<T, float>::value && f64) return fail_arg("16-bit storage needs FP32 b and x");
+    auto go = [&](auto op) -> int {
+        if constexpr (std::is_same<T, float>::value) {
+            if (tma) return f64 ? f(op, std::true_type{}, double{}) : f(op, std::true_type{}, float{});
+            return f64 ? f(op, std::false_type{}, double{}) : f(op, std::false_type{}, float{});
+        } else {
+            if (tma) return f(op, std::true_type{}, float{});
+            return f(op, std::false_type{}, float{});
+        }
+    };
+    if (g.k_block) return go(make_op_table(g, c.op_scale, reinterpret_cast<const float4 *>(c.ws + c.L.tab)));
+    return go(make_op_const(g.nx, g.ny, g.nz, c.op_scale));
+}
+
+// Graph mode: finds (or captures and instantiates) the solve's graph and
+// launches it on s; no synchronisation.
+template <typename T>
+int solve_launch(const SolveCall &c, bool tma, cudaStream_t s) {
+    const gbpcg_grid &g = *c.g;
+    int dev = 0;
+    GB_CUDA(cudaGetDevice(&dev));
+    SolveKey key;
+    memset(&key, 0, sizeof(key));
+    key.dev = dev; key.nx = g.nx; key.ny = g.ny; key.nz = g.nz;
+    key.kb = g.k_block;
+    if (g.k_block) { key.kbx = g.kbx; key.kby = g.kby; key.kbz = g.kbz; }
+    key.maxit = c.maxit; key.cfg_a = c.cfg_a; key.cfg_b = c.cfg_b; key.tma = tma; key.io = c.io;
+    key.storage = std::is_same<T, float>::value ? GBPCG_F32 : std::is_same<T, __half>::value ? GBPCG_F16 : GBPCG_BF16;
+    key.op_scale = c.op_scale;
+    key.b = c.b; key.x = c.x; key.ws = c.ws; key.bscale = c.bscale; key.tol = c.tol;
+    cudaGraphExec_t exec = graph_cache_find(key);
+    if (!exec) {
+        cudaGraph_t graph = nullptr;
+        int rc = dispatch_plan<T>(c, tma, [&](auto op, auto tm, auto xt) {
+            SolvePlan<decltype(op), decltype(tm)::value, decltype(xt), T> plan;
+            if (int r = plan_init(plan, c, op)) return r;
+            return plan.capture(&graph);
+        });
+        if (rc) return rc;
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+        if (e) {
+            cudaGraphDestroy(graph);
+            return fail_cuda(e, "graph instantiate");
+        }
+        cudaGraphUpload(ex, s);
+        exec = graph_cache_put(key, graph, ex);
+    }
+    GB_CUDA(cudaGraphLaunch(exec, s));
+    return GBPCG_OK;
+}
+
+// Profile mode: the same kernels launched one by one, pass launches timed
+// with CUDA events (synchronises s every few iterations).
+template <typename T>
+int solve_profiled(const SolveCall &c, bool tma, gbpcg_result *res, cudaStream_t s) {
+    return dispatch_plan<T>(c, tma, [&](auto op, auto tm, auto xt) {
+        SolvePlan<decltype(op), decltype(tm)::value, decltype(xt), T> plan;
+        if (int r = plan_init(plan, c, op)) return r;
+        return plan.run_profiled(s, res->pass_ms, res->pass_launches);
+    });
+}
+
+extern template int solve_launch<float>(const SolveCall &, bool, cudaStream_t);
+extern template int solve_launch<__nv_bfloat16>(const SolveCall &, bool, cudaStream_t);
+extern template int solve_launch<__half>(const SolveCall &, bool, cudaStream_t);
+extern template int solve_profiled<float>(const SolveCall &, bool, gbpcg_result *, cudaStream_t);
+extern template int solve_profiled<__nv_bfloat16>(const SolveCall &, bool, gbpcg_result *, cudaStream_t);
+extern template int solve_profiled<__half>(const SolveCall &, bool, gbpcg_result *, cudaStream_t);
+
+}  // namespace gb

@@ -43,7 +43,7 @@ def test_struct_layout_matches_header(tmp_path):
         '#include <stdio.h>\n#include <stddef.h>\n#include "gbpcg.h"\n'
         "int main(void){\n"
         ' printf("%zu %zu %zu %zu\\n", sizeof(gbpcg_grid), offsetof(gbpcg_grid, k_block), offsetof(gbpcg_grid, kbx), offsetof(gbpcg_grid, kbz));\n'
-        ' printf("%zu %zu %zu %zu\\n", sizeof(gbpcg_opts), offsetof(gbpcg_opts, flags), offsetof(gbpcg_opts, workspace), offsetof(gbpcg_opts, workspace_bytes));\n'
+        ' printf("%zu %zu %zu %zu %zu\\n", sizeof(gbpcg_opts), offsetof(gbpcg_opts, flags), offsetof(gbpcg_opts, workspace), offsetof(gbpcg_opts, workspace_bytes), offsetof(gbpcg_opts, max_outer));\n'
         ' printf("%zu %zu %zu %zu %zu\\n", sizeof(gbpcg_result), offsetof(gbpcg_result, rel_res_recursive), offsetof(gbpcg_result, time_ms), offsetof(gbpcg_result, pass_launches), offsetof(gbpcg_result, replacements));\n'
         " return 0;}\n")
     exe = tmp_path / "probe"
@@ -53,7 +53,8 @@ def test_struct_layout_matches_header(tmp_path):
     o = [int(v) for v in out[1].split()]
     r = [int(v) for v in out[2].split()]
     assert g == [ctypes.sizeof(B.Grid), B.Grid.k_block.offset, B.Grid.kbx.offset, B.Grid.kbz.offset]
-    assert o == [ctypes.sizeof(B.Opts), B.Opts.flags.offset, B.Opts.workspace.offset, B.Opts.workspace_bytes.offset]
+    assert o == [ctypes.sizeof(B.Opts), B.Opts.flags.offset, B.Opts.workspace.offset, B.Opts.workspace_bytes.offset,
+                 B.Opts.max_outer.offset]
     assert r == [ctypes.sizeof(B.Result), B.Result.rel_res_recursive.offset, B.Result.time_ms.offset,
                  B.Result.pass_launches.offset, B.Result.replacements.offset]
 
@@ -143,6 +144,14 @@ def test_solve_argument_checks(lib):
     assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
     o = B.make_opts(storage=5)
     assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    # 16-bit storage means iterative refinement: FP64 b/x and a sane inner tolerance
+    o = B.make_opts(storage=B.BF16, io_dtype=B.F32)
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    o = B.make_opts(storage=B.F16, io_dtype=B.F64, inner_tol=1.5)
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    o = B.make_opts(storage=B.F16, io_dtype=B.F64)
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    assert n.value >= 16 ** 3 * (4 + 4 + 4 * 2)
 
 
 def test_last_error_is_cleared_on_success(lib):
