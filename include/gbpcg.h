@@ -79,6 +79,9 @@ typedef struct gbpcg_grid {
 #define GBPCG_FLAG_HOST_IO 1u /* b and x may be host pointers; staged through the workspace */
 #define GBPCG_FLAG_PROFILE 2u /* launch the iteration kernels one by one (no graph), each
                                  bracketed by CUDA events; fills gbpcg_result.pass_ms */
+#define GBPCG_FLAG_AUTOTUNE 4u /* batched solves: pick each shape's tile configuration by timing
+                                  (cached per shape in the process); the workspace grows by a
+                                  scratch x per problem */
 
 typedef struct gbpcg_opts {
     double tol;            /* stop when ||r_k||_2 / ||b||_2 <= tol (recursive residual) */
@@ -203,6 +206,37 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
  */
 int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_opts *opts,
                     gbpcg_result *result, gbpcg_stream stream);
+
+/*
+ * Many independent problems (BASELINE config 3) solved as one CUDA graph:
+ * each problem's whole solve (its own device-driven loop, as in
+ * gbpcg_pcg_solve) is a branch of one graph, so one launch runs them all
+ * concurrently and no problem waits on another's convergence.  grids[i],
+ * b[i], x[i] (DEVICE pointers, opts->io_dtype) describe problem i; storage
+ * is F32; results[i] receives problem i's outcome (time_ms is the batch's).
+ * The workspace (gbpcg_workspace_size_batched) holds every problem's
+ * scratch.  Returns GBPCG_OK when all problems converged, else the first
+ * other status.  The instantiated graph is cached per argument set.
+ */
+int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts *opts,
+                                 size_t *bytes);
+int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *const *b, void *const *x,
+                            const gbpcg_opts *opts, gbpcg_result *results, gbpcg_stream stream);
+
+/*
+ * Autotuner (no counterpart in the paper; the paper hard-codes its tile
+ * layout, Sec. VI-A): times every tile configuration that fits the grid
+ * over a short solve of A x = b from x = 0 (x kept in workspace scratch, b
+ * only read), stores the fastest in the process-wide cache used by
+ * GBPCG_FLAG_AUTOTUNE and returns it as a gbpcg_opts.tile_cfg code, with the
+ * mean time of one iteration in *us_per_iter (may be NULL).  The workspace
+ * must be gbpcg_workspace_size() of opts with GBPCG_FLAG_AUTOTUNE set.
+ * gbpcg_autotune_record seeds the cache with a code found earlier (e.g. read
+ * back from a file).
+ */
+int gbpcg_autotune(const gbpcg_grid *grid, const gbpcg_opts *opts, const void *b, int32_t *tile_cfg,
+                   double *us_per_iter, gbpcg_stream stream);
+int gbpcg_autotune_record(const gbpcg_grid *grid, const gbpcg_opts *opts, int32_t tile_cfg);
 
 #ifdef __cplusplus
 }

@@ -25,11 +25,13 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "NOT_CONVERGED", 4: "BR
 F32, BF16, F16, F64 = 0, 1, 2, 3
 FLAG_HOST_IO = 1
 FLAG_PROFILE = 2
+FLAG_AUTOTUNE = 4
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
 
 EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbpcg_stencil_apply", "gbpcg_dot",
-           "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_tile_config", "gbpcg_workspace_size", "gbpcg_pcg_solve"]
+           "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_tile_config", "gbpcg_workspace_size", "gbpcg_pcg_solve",
+           "gbpcg_workspace_size_batched", "gbpcg_pcg_solve_batched", "gbpcg_autotune", "gbpcg_autotune_record"]
 
 
 class Grid(ctypes.Structure):
@@ -97,6 +99,17 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), ctypes.POINTER(SZ)]
         lib.gbpcg_pcg_solve.restype = ctypes.c_int
         lib.gbpcg_pcg_solve.argtypes = [ctypes.POINTER(Grid), P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
+        lib.gbpcg_workspace_size_batched.restype = ctypes.c_int
+        lib.gbpcg_workspace_size_batched.argtypes = [I32, ctypes.POINTER(Grid), ctypes.POINTER(Opts),
+                                                     ctypes.POINTER(SZ)]
+        lib.gbpcg_pcg_solve_batched.restype = ctypes.c_int
+        lib.gbpcg_pcg_solve_batched.argtypes = [I32, ctypes.POINTER(Grid), ctypes.POINTER(P), ctypes.POINTER(P),
+                                                ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
+        lib.gbpcg_autotune.restype = ctypes.c_int
+        lib.gbpcg_autotune.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), P, ctypes.POINTER(I32),
+                                       ctypes.POINTER(D), P]
+        lib.gbpcg_autotune_record.restype = ctypes.c_int
+        lib.gbpcg_autotune_record.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), I32]
         _lib = lib
         return lib
 
@@ -211,14 +224,14 @@ def tile_cfg_code(cfg_a=None, cfg_b=None) -> int:
 
 
 def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
-              profile=False, tile_cfg=0, inner_tol=1e-2, max_outer=30) -> Opts:
+              profile=False, tile_cfg=0, inner_tol=1e-2, max_outer=30, autotune=False) -> Opts:
     o = Opts()
     o.tol = float(tol)
     o.maxit = int(maxit)
     o.precond = 0
     o.storage = storage
     o.io_dtype = io_dtype
-    o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0)
+    o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0) | (FLAG_AUTOTUNE if autotune else 0)
     o.tile_cfg = int(tile_cfg)
     o.inner_tol = float(inner_tol)
     o.max_outer = int(max_outer)
@@ -274,3 +287,75 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
                                 _stream(stream))
     _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
     return x, r.as_dict()
+
+
+def pcg_solve_batched(bs, xs=None, tol=1e-6, maxit=2000, tile_cfg=0, autotune=False, workspace=None,
+                      stream=None):
+    """Solves len(bs) independent problems as one graph launch (gbpcg_pcg_solve_batched).
+
+    bs, xs: lists of contiguous (nz, ny, nx) CUDA tensors (all float32 or all
+    float64).  Returns (xs, [result dict per problem]).
+    """
+    n = len(bs)
+    if xs is None:
+        xs = [torch.zeros_like(b) for b in bs]
+    io = _dtype(bs[0])
+    for b, x in zip(bs, xs):
+        if b.dtype != bs[0].dtype or x.dtype != b.dtype or x.shape != b.shape or not (b.is_cuda and x.is_cuda):
+            raise GbpcgError(ERR_ARG, "b and x must be CUDA tensors of one dtype and matching shapes")
+    grids = (Grid * n)(*[make_grid(b.shape) for b in bs])
+    o = make_opts(tol, maxit, F32, io, False, None, False, tile_cfg, autotune=autotune)
+    lib = load()
+    if workspace is None:
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.gbpcg_workspace_size_batched(n, grids, ctypes.byref(o), ctypes.byref(nbytes)))
+        workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=bs[0].device)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    res = (Result * n)()
+    rc = lib.gbpcg_pcg_solve_batched(n, grids, bp, xp, ctypes.byref(o), res, _stream(stream))
+    _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
+    return xs, [r.as_dict() for r in res]
+
+
+def autotune(b: torch.Tensor, workspace=None, stream=None):
+    """Times the tile configurations on A x = b (x from 0, in scratch) and
+    returns (tile_cfg code, microseconds per iteration) (gbpcg_autotune)."""
+    g = make_grid(b.shape)
+    o = make_opts(io_dtype=_dtype(b), autotune=True)
+    if workspace is None:
+        workspace = alloc_workspace(b.shape, device=b.device, io_dtype=_dtype(b), autotune=True)
+    o.workspace = workspace.data_ptr()
+    o.workspace_bytes = workspace.numel()
+    code = ctypes.c_int32(0)
+    us = ctypes.c_double(0.0)
+    _check(load().gbpcg_autotune(ctypes.byref(g), ctypes.byref(o), _ptr(b), ctypes.byref(code), ctypes.byref(us),
+                                 _stream(stream)))
+    return code.value, us.value
+
+
+def autotune_record(shape, tile_cfg: int, io_dtype=F32):
+    """Seeds the process-wide autotune cache (e.g. from a saved file)."""
+    g = make_grid(shape)
+    o = make_opts(io_dtype=io_dtype)
+    _check(load().gbpcg_autotune_record(ctypes.byref(g), ctypes.byref(o), int(tile_cfg)))
+
+
+def save_autotune(path, entries):
+    """Writes {"nx,ny,nz,io": code} entries (from autotune()) as JSON."""
+    import json
+    with open(path, "w") as f:
+        json.dump(entries, f, indent=1, sort_keys=True)
+
+
+def load_autotune(path):
+    """Reads a file written by save_autotune and seeds the cache with it."""
+    import json
+    with open(path) as f:
+        entries = json.load(f)
+    for key, code in entries.items():
+        nx, ny, nz, io = (int(v) for v in key.split(","))
+        autotune_record((nz, ny, nx), code, io)
+    return entries

@@ -13,7 +13,10 @@
 #include <cmath>
 #include <cstring>
 #include <list>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "solver.cuh"
 
@@ -188,8 +191,10 @@ static bool refine_mode(const gbpcg_opts &o) { return o.storage == GBPCG_BF16 ||
 
 static size_t workspace_total(const gbpcg_grid &g, const gbpcg_opts &o) {
     if (refine_mode(o)) return refine_layout(g, o).total;
-    return ws_layout_n((size_t)g.nx * g.ny * g.nz, o.storage, o.io_dtype, o.flags & GBPCG_FLAG_HOST_IO,
-                       block_count(g)).total;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    size_t t = ws_layout_n(n, o.storage, o.io_dtype, o.flags & GBPCG_FLAG_HOST_IO, block_count(g)).total;
+    if (o.flags & GBPCG_FLAG_AUTOTUNE) t += round256(n * dtype_size(o.io_dtype));  // tuner's scratch x
+    return t;
 }
 
 static int check_opts(const gbpcg_opts *o) {
@@ -372,6 +377,87 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
     return status;
 }
 
+// ------------------------------------------------------------- batches --
+
+namespace {
+struct BatchGraph {
+    std::vector<SolveKey> keys;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mu;
+std::list<BatchGraph> g_batch_cache;
+constexpr size_t kBatchCacheMax = 4;
+
+// Autotuned tile configurations, per (device, shape, coefficient blocks, io type).
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+
+TuneKey tune_key(const gbpcg_grid &g, const gbpcg_opts &o) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return TuneKey(dev, g.nx, g.ny, g.nz, g.k_block ? g.kbx : 0, g.k_block ? g.kby : 0, g.k_block ? g.kbz : 0,
+                   o.storage, o.io_dtype);
+}
+}  // namespace
+
+// Workspace of one problem inside a batch (256-byte aligned pieces); with
+// GBPCG_FLAG_AUTOTUNE each piece ends with a scratch x for the tuner.
+static size_t batch_piece(const gbpcg_grid &g, const gbpcg_opts &o, WsLayout *L) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    *L = ws_layout_n(n, o.storage, o.io_dtype, false, block_count(g));
+    size_t t = L->total;
+    if (o.flags & GBPCG_FLAG_AUTOTUNE) t += round256(n * dtype_size(o.io_dtype));
+    return round256(t);
+}
+
+// Times each tile configuration that fits the grid (the same one for both
+// passes) over a short profiled solve from x = 0 into `xs`, and returns the
+// fastest as a tile_cfg code.
+static int autotune_one(const gbpcg_grid &g, const gbpcg_opts &o, const void *b, void *xs, char *ws,
+                        const WsLayout &L, cudaStream_t s, int *code_out, double *us_out) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const bool tma = tma_ok(sizeof(float), g.nx, {ws + L.z, ws + L.p0, ws + L.p1, ws + L.d});
+    double best = 1e300;
+    int best_code = 0;
+    for (int c = 0; c < NUM_CFG; ++c) {
+        if (!cfg_fits(c, g.nx)) continue;
+        if (cfg_dims(c).tx > 4 * ((g.nx + 3) / 4) + 64) continue;  // tiles far wider than the grid
+        GB_CUDA(cudaMemsetAsync(xs, 0, n * dtype_size(o.io_dtype), s));
+        const SolveCall call{&g, c, c, b, xs, ws, L, 0.0, 12, o.io_dtype, 1.0f, nullptr};
+        gbpcg_result r;
+        memset(&r, 0, sizeof(r));
+        if (int rc = solve_profiled<float>(call, tma, &r, s)) return rc;
+        GB_CUDA(cudaStreamSynchronize(s));
+        const int launches = r.pass_launches[0];
+        if (launches <= 1) continue;
+        const double us = (r.pass_ms[0] + r.pass_ms[1]) * 1e3 / launches;
+        if (us < best) {
+            best = us;
+            best_code = (c + 1) | ((c + 1) << 8);
+        }
+    }
+    if (!best_code) return fail_arg("no tile configuration could be timed for this grid");
+    *code_out = best_code;
+    if (us_out) *us_out = best;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(g, o)] = best_code;
+    return GBPCG_OK;
+}
+
+static int check_batch(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts *opts) {
+    if (nprob <= 0 || nprob > 4096) return fail_arg("nprob must be in 1..4096");
+    if (!grids) return fail_arg("grids is NULL");
+    for (int i = 0; i < nprob; ++i)
+        if (int rc = check_grid(&grids[i])) return rc;
+    if (int rc = check_opts(opts)) return rc;
+    if (opts->storage != GBPCG_F32) return fail_arg("batched solves use F32 storage");
+    if (opts->flags & (GBPCG_FLAG_HOST_IO | GBPCG_FLAG_PROFILE))
+        return fail_arg("batched solves take device buffers and no profile flag");
+    return GBPCG_OK;
+}
+
 }  // namespace gb
 
 using namespace gb;
@@ -461,6 +547,176 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     }
     GB_CUDA(cudaEventRecord(e1, s));
     return finish_solve(st, x, xd, x_host, io_bytes, e0, e1, result, s);
+}
+
+int gbpcg_autotune(const gbpcg_grid *grid, const gbpcg_opts *opts, const void *b, int32_t *tile_cfg,
+                   double *us_per_iter, gbpcg_stream stream) {
+    clear_error();
+    if (int rc = check_grid(grid)) return rc;
+    if (int rc = check_opts(opts)) return rc;
+    if (!b || !tile_cfg) return fail_arg("b and tile_cfg must be non-NULL");
+    if (opts->storage != GBPCG_F32) return fail_arg("the autotuner times F32 storage");
+    gbpcg_opts o = *opts;
+    o.flags |= GBPCG_FLAG_AUTOTUNE;
+    WsLayout L;
+    const size_t need = batch_piece(*grid, o, &L);
+    if (!opts->workspace || opts->workspace_bytes < need)
+        return fail_arg("workspace smaller than gbpcg_workspace_size() with GBPCG_FLAG_AUTOTUNE");
+    if (reinterpret_cast<uintptr_t>(opts->workspace) & 255u) return fail_arg("workspace must be 256-byte aligned");
+    char *ws = static_cast<char *>(opts->workspace);
+    int code = 0;
+    if (int rc = autotune_one(*grid, o, b, ws + L.total, ws, L, reinterpret_cast<cudaStream_t>(stream), &code,
+                              us_per_iter))
+        return rc;
+    *tile_cfg = code;
+    return GBPCG_OK;
+}
+
+int gbpcg_autotune_record(const gbpcg_grid *grid, const gbpcg_opts *opts, int32_t tile_cfg) {
+    clear_error();
+    if (int rc = check_grid(grid)) return rc;
+    if (int rc = check_opts(opts)) return rc;
+    gbpcg_opts o = *opts;
+    o.tile_cfg = tile_cfg;
+    if (int rc = check_opts(&o)) return rc;
+    if (!tile_cfg) return fail_arg("tile_cfg 0 is not a configuration");
+    int ca = 0, cb = 0;
+    pick_cfgs(*grid, o, &ca, &cb);
+    if (!cfg_fits(ca, grid->nx) || !cfg_fits(cb, grid->nx)) return fail_arg("configuration does not fit the grid");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(*grid, *opts)] = tile_cfg;
+    return GBPCG_OK;
+}
+
+int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts *opts, size_t *bytes) {
+    clear_error();
+    if (int rc = check_batch(nprob, grids, opts)) return rc;
+    if (!bytes) return fail_arg("bytes is NULL");
+    size_t total = 0;
+    for (int i = 0; i < nprob; ++i) {
+        WsLayout L;
+        total += batch_piece(grids[i], *opts, &L);
+    }
+    *bytes = total;
+    return GBPCG_OK;
+}
+
+int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *const *b, void *const *x,
+                            const gbpcg_opts *opts, gbpcg_result *results, gbpcg_stream stream) {
+    clear_error();
+    if (int rc = check_batch(nprob, grids, opts)) return rc;
+    if (!b || !x || !results) return fail_arg("b, x and results must be non-NULL");
+    const size_t esz = dtype_size(opts->io_dtype);
+    for (int i = 0; i < nprob; ++i) {
+        if (!b[i] || !x[i]) return fail_arg("every b[i] and x[i] must be a device pointer");
+        if ((reinterpret_cast<uintptr_t>(b[i]) | reinterpret_cast<uintptr_t>(x[i])) & (esz - 1))
+            return fail_arg("b[i] and x[i] must be aligned to their element size");
+    }
+    size_t need = 0;
+    std::vector<WsLayout> L(nprob);
+    std::vector<size_t> off(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        off[i] = need;
+        need += batch_piece(grids[i], *opts, &L[i]);
+    }
+    if (!opts->workspace || opts->workspace_bytes < need)
+        return fail_arg("workspace smaller than gbpcg_workspace_size_batched()");
+    if (reinterpret_cast<uintptr_t>(opts->workspace) & 255u) return fail_arg("workspace must be 256-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(opts->workspace);
+
+    // tile configurations: explicit, autotuned (cached per shape), or the defaults
+    std::vector<SolveCall> calls(nprob);
+    std::vector<int> tma(nprob);
+    for (int i = 0; i < nprob; ++i) {
+        const gbpcg_grid &g = grids[i];
+        gbpcg_opts o = *opts;
+        if (!o.tile_cfg && (o.flags & GBPCG_FLAG_AUTOTUNE)) {
+            int code = 0;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune.find(tune_key(g, o));
+                if (it != g_tune.end()) code = it->second;
+            }
+            if (!code) {
+                if (int rc = autotune_one(g, o, b[i], ws + off[i] + L[i].total, ws + off[i], L[i], s, &code, nullptr))
+                    return rc;
+            }
+            o.tile_cfg = code;
+        }
+        int ca = 0, cb = 0;
+        pick_cfgs(g, o, &ca, &cb);
+        if (!cfg_fits(ca, g.nx) || !cfg_fits(cb, g.nx))
+            return fail_arg("tile_cfg selects a whole-row configuration for a grid wider than 256");
+        char *w = ws + off[i];
+        tma[i] = tma_ok(sizeof(float), g.nx, {w + L[i].z, w + L[i].p0, w + L[i].p1, w + L[i].d});
+        calls[i] = SolveCall{&grids[i], ca, cb, b[i], x[i], w, L[i], opts->tol, opts->maxit, opts->io_dtype, 1.0f,
+                             nullptr};
+    }
+    std::vector<SolveKey> keys(nprob);
+    for (int i = 0; i < nprob; ++i) keys[i] = make_key<float>(calls[i], tma[i] != 0);
+
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto it = g_batch_cache.begin(); it != g_batch_cache.end(); ++it)
+            if (it->keys.size() == keys.size() &&
+                std::equal(keys.begin(), keys.end(), it->keys.begin(),
+                           [](const SolveKey &a, const SolveKey &c) { return a == c; })) {
+                g_batch_cache.splice(g_batch_cache.begin(), g_batch_cache, it);
+                exec = g_batch_cache.front().exec;
+                break;
+            }
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            if (int rc = batched_capture<float>(calls.data(), tma.data(), nprob, &graph)) return rc;
+            cudaGraphExec_t ex = nullptr;
+            cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+            if (e) {
+                cudaGraphDestroy(graph);
+                return fail_cuda(e, "batched graph instantiate");
+            }
+            cudaGraphUpload(ex, s);
+            BatchGraph bg;
+            bg.keys = keys;
+            bg.graph = graph;
+            bg.exec = ex;
+            g_batch_cache.push_front(bg);
+            while (g_batch_cache.size() > kBatchCacheMax) {
+                cudaGraphExecDestroy(g_batch_cache.back().exec);
+                cudaGraphDestroy(g_batch_cache.back().graph);
+                g_batch_cache.pop_back();
+            }
+            exec = ex;
+        }
+    }
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    GB_CUDA(cudaEventRecord(e0, s));
+    GB_CUDA(cudaGraphLaunch(exec, s));
+    GB_CUDA(cudaEventRecord(e1, s));
+    std::vector<SolveState> hs(nprob);
+    for (int i = 0; i < nprob; ++i)
+        GB_CUDA(cudaMemcpyAsync(&hs[i], ws + off[i] + L[i].state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int worst = GBPCG_OK;
+    for (int i = 0; i < nprob; ++i) {
+        gbpcg_result &r = results[i];
+        memset(&r, 0, sizeof(r));
+        r.iters = hs[i].it;
+        r.status = hs[i].status;
+        r.rel_res_recursive = hs[i].bb > 0 ? sqrt(hs[i].rr / hs[i].bb) : 0.0;
+        r.rel_res_true = hs[i].bb_true > 0 ? sqrt(hs[i].rr_true / hs[i].bb_true) : 0.0;
+        r.time_ms = ms;
+        r.replacements = hs[i].n_replace;
+        if (r.status != GBPCG_OK && worst == GBPCG_OK) worst = r.status;
+    }
+    return worst;
 }
 
 }  // extern "C"

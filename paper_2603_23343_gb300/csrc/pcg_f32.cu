@@ -4,5 +4,6 @@
 
 namespace gb {
 template int solve_launch<float>(const SolveCall &, bool, cudaStream_t);
+template int batched_capture<float>(const SolveCall *, const int *, int, cudaGraph_t *);
 template int solve_profiled<float>(const SolveCall &, bool, gbpcg_result *, cudaStream_t);
 }  // namespace gb

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "launch.cuh"
 
@@ -412,27 +413,25 @@ struct SolvePlan {
     }
 
     // reset -> init -> while(cond){A; B; if(replace){flush; replace}} -> finalize -> true residual
-    int capture(cudaGraph_t *out_graph) {
-        cudaStream_t cs = nullptr, bs = nullptr, rs = nullptr;
-        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        GB_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
-        GB_CUDA(cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking));
-        int rc = GBPCG_OK;
-        cudaGraph_t graph = nullptr;
-        auto end_capture = [](cudaStream_t s, bool destroy) {
+    // Records the whole solve onto cs, which is already capturing:
+    // reset, init, a WHILE node whose body is {pass A, pass B, IF(replace)
+    // {flush, replace}}, finalize, true residual.  The loop bodies are
+    // captured from helper streams straight into the conditional nodes.
+    cudaError_t capture_on(cudaStream_t cs) {
+        cudaStream_t bs = nullptr, rs = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        if (e) return e;
+        e = cudaStreamCreateWithFlags(&rs, cudaStreamNonBlocking);
+        if (e) {
+            cudaStreamDestroy(bs);
+            return e;
+        }
+        auto end_capture = [](cudaStream_t s) {
             cudaStreamCaptureStatus stt;
             if (cudaStreamIsCapturing(s, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone) {
                 cudaGraph_t tmp = nullptr;
                 cudaStreamEndCapture(s, &tmp);
-                if (destroy && tmp) cudaGraphDestroy(tmp);
             }
-        };
-        auto fail = [&](cudaError_t e, const char *what) {
-            rc = fail_cuda(e, what);
-            end_capture(rs, false);
-            end_capture(bs, false);
-            end_capture(cs, true);
-            cudaGetLastError();
         };
         // adds a conditional node after the current capture dependencies of s
         auto add_cond = [&](cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
@@ -441,65 +440,83 @@ struct SolvePlan {
             cudaGraph_t cap = nullptr;
             const cudaGraphNode_t *deps = nullptr;
             size_t ndeps = 0;
-            cudaError_t e = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &ndeps);
-            if (e) return e;
+            cudaError_t e2 = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cap, &deps, nullptr, &ndeps);
+            if (e2) return e2;
             cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
             cp.conditional.handle = h;
             cp.conditional.type = type;
             cp.conditional.size = 1;
             cudaGraphNode_t node;
-            e = cudaGraphAddNode(&node, cap, deps, nullptr, ndeps, &cp);
-            if (e) return e;
+            e2 = cudaGraphAddNode(&node, cap, deps, nullptr, ndeps, &cp);
+            if (e2) return e2;
             *body_out = cp.conditional.phGraph_out[0];
             return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
         };
         do {
-            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "begin capture"); break; }
             cudaStreamCaptureStatus cst;
             cudaGraph_t cap = nullptr;
             e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cap, nullptr, nullptr, nullptr);
-            if (e) { fail(e, "capture info"); break; }
+            if (e) break;
             cudaGraphConditionalHandle cond;
             e = cudaGraphConditionalHandleCreate(&cond, cap, 1, cudaGraphCondAssignDefault);
-            if (e) { fail(e, "conditional handle"); break; }
+            if (e) break;
             set_cond(cond, 0, 1);
             e = launch_setup(cs);
-            if (e) { fail(e, "init"); break; }
+            if (e) break;
             cudaGraph_t body = nullptr;
             e = add_cond(cs, cond, cudaGraphCondTypeWhile, &body);
-            if (e) { fail(e, "loop node"); break; }
+            if (e) break;
             cudaGraphConditionalHandle rep;
             e = cudaGraphConditionalHandleCreate(&rep, body, 0, cudaGraphCondAssignDefault);
-            if (e) { fail(e, "replace handle"); break; }
+            if (e) break;
             set_cond(cond, rep, 1);
             e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "body capture"); break; }
+            if (e) break;
             e = launch_a(bs);
-            if (e) { fail(e, "pass A"); break; }
+            if (e) break;
             e = launch_b(bs);
-            if (e) { fail(e, "pass B"); break; }
+            if (e) break;
             cudaGraph_t rbody = nullptr;
             e = add_cond(bs, rep, cudaGraphCondTypeIf, &rbody);
-            if (e) { fail(e, "replace node"); break; }
+            if (e) break;
             e = cudaStreamBeginCaptureToGraph(rs, rbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-            if (e) { fail(e, "replace capture"); break; }
+            if (e) break;
             e = launch_replace(rs);
-            if (e) { fail(e, "replace kernels"); break; }
+            if (e) break;
             cudaGraph_t tmp = nullptr;
             e = cudaStreamEndCapture(rs, &tmp);
-            if (e) { fail(e, "end replace capture"); break; }
+            if (e) break;
             e = cudaStreamEndCapture(bs, &tmp);
-            if (e) { fail(e, "end body capture"); break; }
+            if (e) break;
             e = launch_final(cs);
-            if (e) { fail(e, "finalize"); break; }
-            e = cudaStreamEndCapture(cs, &graph);
-            if (e) { fail(e, "end capture"); break; }
         } while (0);
+        if (e) {
+            end_capture(rs);
+            end_capture(bs);
+        }
         cudaStreamDestroy(rs);
         cudaStreamDestroy(bs);
+        return e;
+    }
+
+    // The solve as a graph of its own.
+    int capture(cudaGraph_t *out_graph) {
+        cudaStream_t cs = nullptr;
+        GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (!e) e = capture_on(cs);
+        cudaGraph_t graph = nullptr;
+        cudaStreamCaptureStatus stt;
+        if (cudaStreamIsCapturing(cs, &stt) == cudaSuccess && stt != cudaStreamCaptureStatusNone) {
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (!e) e = e2;
+        }
         cudaStreamDestroy(cs);
-        if (rc) return rc;
+        if (e) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail_cuda(e, "solve graph capture");
+        }
         *out_graph = graph;
         return GBPCG_OK;
     }
@@ -597,10 +614,10 @@ static int dispatch_plan(const SolveCall &c, bool tma, F &&f) {
 // Graph mode: finds (or captures and instantiates) the solve's graph and
 // launches it on s; no synchronisation.
 template <typename T>
-int solve_launch(const SolveCall &c, bool tma, cudaStream_t s) {
+SolveKey make_key(const SolveCall &c, bool tma) {
     const gbpcg_grid &g = *c.g;
     int dev = 0;
-    GB_CUDA(cudaGetDevice(&dev));
+    cudaGetDevice(&dev);
     SolveKey key;
     memset(&key, 0, sizeof(key));
     key.dev = dev; key.nx = g.nx; key.ny = g.ny; key.nz = g.nz;
@@ -610,6 +627,12 @@ int solve_launch(const SolveCall &c, bool tma, cudaStream_t s) {
     key.storage = std::is_same<T, float>::value ? GBPCG_F32 : std::is_same<T, __half>::value ? GBPCG_F16 : GBPCG_BF16;
     key.op_scale = c.op_scale;
     key.b = c.b; key.x = c.x; key.ws = c.ws; key.bscale = c.bscale; key.tol = c.tol;
+    return key;
+}
+
+template <typename T>
+int solve_launch(const SolveCall &c, bool tma, cudaStream_t s) {
+    const SolveKey key = make_key<T>(c, tma);
     cudaGraphExec_t exec = graph_cache_find(key);
     if (!exec) {
         cudaGraph_t graph = nullptr;
@@ -632,6 +655,57 @@ int solve_launch(const SolveCall &c, bool tma, cudaStream_t s) {
     return GBPCG_OK;
 }
 
+// Several solves as one graph: the capture forks from a root stream into one
+// stream per problem, records each problem's whole solve (its own device
+// loop and conditions) there and joins back, so one launch runs all of them
+// concurrently.  calls[i].x / .b / .ws are the problems' own buffers.
+template <typename T>
+int batched_capture(const SolveCall *calls, const int *tma, int n, cudaGraph_t *out) {
+    cudaStream_t root = nullptr;
+    GB_CUDA(cudaStreamCreateWithFlags(&root, cudaStreamNonBlocking));
+    std::vector<cudaStream_t> st(n, nullptr);
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && !e; ++i) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+    for (int i = 0; i <= n && !e; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    bool capturing = false;
+    int rc = GBPCG_OK;
+    if (!e) e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+    if (!e) {
+        capturing = true;
+        e = cudaEventRecord(ev[n], root);
+    }
+    for (int i = 0; i < n && !e && !rc; ++i) {
+        e = cudaStreamWaitEvent(st[i], ev[n], 0);
+        if (e) break;
+        rc = dispatch_plan<T>(calls[i], tma[i] != 0, [&](auto op, auto tm, auto xt) -> int {
+            SolvePlan<decltype(op), decltype(tm)::value, decltype(xt), T> plan;
+            if (int r = plan_init(plan, calls[i], op)) return r;
+            cudaError_t e2 = plan.capture_on(st[i]);
+            return e2 ? fail_cuda(e2, "batched capture") : GBPCG_OK;
+        });
+        if (!rc) e = cudaEventRecord(ev[i], st[i]);
+        if (!rc && !e) e = cudaStreamWaitEvent(root, ev[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    if (capturing) {
+        cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+        if (!e) e = e2;
+    }
+    for (auto s2 : st)
+        if (s2) cudaStreamDestroy(s2);
+    for (auto v : ev)
+        if (v) cudaEventDestroy(v);
+    cudaStreamDestroy(root);
+    if (rc || e) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc ? rc : fail_cuda(e, "batched graph capture");
+    }
+    *out = graph;
+    return GBPCG_OK;
+}
+
 // Profile mode: the same kernels launched one by one, pass launches timed
 // with CUDA events (synchronises s every few iterations).
 template <typename T>
@@ -643,6 +717,7 @@ int solve_profiled(const SolveCall &c, bool tma, gbpcg_result *res, cudaStream_t
     });
 }
 
+extern template int batched_capture<float>(const SolveCall *, const int *, int, cudaGraph_t *);
 extern template int solve_launch<float>(const SolveCall &, bool, cudaStream_t);
 extern template int solve_launch<__nv_bfloat16>(const SolveCall &, bool, cudaStream_t);
 extern template int solve_launch<__half>(const SolveCall &, bool, cudaStream_t);

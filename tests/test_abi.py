@@ -154,6 +154,38 @@ def test_solve_argument_checks(lib):
     assert n.value >= 16 ** 3 * (4 + 4 + 4 * 2)
 
 
+def test_batched_argument_checks(lib):
+    grids = (B.Grid * 2)(_grid(16, 16, 16), _grid(32, 8, 8))
+    n = ctypes.c_size_t(0)
+    o = B.make_opts()
+    assert lib.gbpcg_workspace_size_batched(2, grids, ctypes.byref(o), ctypes.byref(n)) == B.OK
+    single = ctypes.c_size_t(0)
+    total = 0
+    for i in range(2):
+        assert lib.gbpcg_workspace_size(ctypes.byref(grids[i]), ctypes.byref(o), ctypes.byref(single)) == B.OK
+        total += single.value
+    assert n.value >= total
+    ot = B.make_opts(autotune=True)
+    nt = ctypes.c_size_t(0)
+    assert lib.gbpcg_workspace_size_batched(2, grids, ctypes.byref(ot), ctypes.byref(nt)) == B.OK
+    assert nt.value >= n.value + 4 * (16 ** 3 + 32 * 64)
+    assert lib.gbpcg_workspace_size_batched(0, grids, ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    ob = B.make_opts(storage=B.BF16, io_dtype=B.F64)
+    assert lib.gbpcg_workspace_size_batched(2, grids, ctypes.byref(ob), ctypes.byref(n)) == B.ERR_ARG
+    oh = B.make_opts(host_io=True)
+    assert lib.gbpcg_workspace_size_batched(2, grids, ctypes.byref(oh), ctypes.byref(n)) == B.ERR_ARG
+    r = (B.Result * 2)()
+    assert lib.gbpcg_pcg_solve_batched(2, grids, None, None, ctypes.byref(o), r, None) == B.ERR_ARG
+
+
+def test_autotune_record_checks(lib):
+    g = _grid(300, 8, 8)
+    o = B.make_opts()
+    assert lib.gbpcg_autotune_record(ctypes.byref(g), ctypes.byref(o), 0) == B.ERR_ARG
+    assert lib.gbpcg_autotune_record(ctypes.byref(g), ctypes.byref(o), B.tile_cfg_code(6, 6)) == B.ERR_ARG
+    assert lib.gbpcg_autotune_record(ctypes.byref(g), ctypes.byref(o), B.tile_cfg_code(2, 2)) == B.OK
+
+
 def test_last_error_is_cleared_on_success(lib):
     g = _grid(0, 1, 1)
     lib.gbpcg_stencil_apply(ctypes.byref(g), B.F32, None, None, None)
