@@ -89,6 +89,66 @@ template <> __device__ __forceinline__ void st4<__half>(__half *p, const float v
     *reinterpret_cast<uint2 *>(p) = t;
 }
 
+// Eight consecutive elements <-> float[8] (16-byte aligned for 16-bit types,
+// 32-byte for float).
+template <typename T> __device__ __forceinline__ void ld8(const T *p, float v[8]);
+template <> __device__ __forceinline__ void ld8<float>(const float *p, float v[8]) {
+    ld4<float>(p, v);
+    ld4<float>(p + 4, v + 4);
+}
+template <> __device__ __forceinline__ void ld8<__nv_bfloat16>(const __nv_bfloat16 *p, float v[8]) {
+    uint4 t = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+        float2 f = __bfloat1622float2(h);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+template <> __device__ __forceinline__ void ld8<__half>(const __half *p, float v[8]) {
+    uint4 t = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+        float2 f = __half22float2(h);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+template <typename T> __device__ __forceinline__ void st8(T *p, const float v[8]);
+template <> __device__ __forceinline__ void st8<float>(float *p, const float v[8]) {
+    st4<float>(p, v);
+    st4<float>(p + 4, v + 4);
+}
+template <> __device__ __forceinline__ void st8<__nv_bfloat16>(__nv_bfloat16 *p, const float v[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+template <> __device__ __forceinline__ void st8<__half>(__half *p, const float v[8]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+// V (4 or 8) consecutive elements
+template <typename T, int V> __device__ __forceinline__ void ldv(const T *p, float v[V]) {
+    if constexpr (V == 4) ld4<T>(p, v); else ld8<T>(p, v);
+}
+template <typename T, int V> __device__ __forceinline__ void stv(T *p, const float v[V]) {
+    if constexpr (V == 4) st4<T>(p, v); else st8<T>(p, v);
+}
+
 // ------------------------------------------------------- TMA tensor maps --
 
 // Encodes a 3D tiled tensor map over a dense (nz, ny, nx) array with box

@@ -83,10 +83,10 @@ struct OpConst {
         q = fmaf(d, c, -fmaf(cx, xm + xp, fmaf(cy, ym + yp, cz * (zm + zp))));
         dg = d;
     }
-    template <typename Self = OpConst>
-    __device__ __forceinline__ void apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
-                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
-                                           int k, int nx, int ny, float q[4], float dg[4]) const;
+    template <int V>
+    __device__ __forceinline__ void applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
+                                           const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
+                                           int k, int nx, int ny, float q[V], float dg[V]) const;
 };
 
 // Block-constant coefficient k (one float per kbx*kby*kbz block): face
@@ -121,39 +121,39 @@ struct OpBlock {
         q = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) + w[4] * (c - zm) + w[5] * (c - zp);
         dg = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
     }
-    template <typename Self = OpBlock>
-    __device__ __forceinline__ void apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
-                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
-                                           int k, int nx_, int ny_, float q[4], float dg[4]) const;
+    template <int V>
+    __device__ __forceinline__ void applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
+                                           const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
+                                           int k, int nx_, int ny_, float q[V], float dg[V]) const;
 };
 
-// The operator at one thread's four consecutive x points: c = centre values,
-// xl / xr = the x neighbours left of point 0 and right of point 3, y and z
-// neighbours per point.  Point positions past the grid edge (masked lanes)
+// The operator at one thread's V consecutive x points: c = centre values,
+// xl / xr = the x neighbours left of point 0 and right of point V-1, y and
+// z neighbours per point.  Point positions past the grid edge (masked lanes)
 // are clamped into the grid before any coefficient lookup.
-template <typename Op>
-__device__ __forceinline__ void apply4_pointwise(const Op &op, const float c[4], float xl, float xr, const float ym[4],
-                                                 const float yp[4], const float zm[4], const float zp[4], int gx,
-                                                 int gy, int k, int nx, int ny, float q[4], float dg[4]) {
+template <int V, typename Op>
+__device__ __forceinline__ void applyv_pointwise(const Op &op, const float c[V], float xl, float xr, const float ym[V],
+                                                 const float yp[V], const float zm[V], const float zp[V], int gx,
+                                                 int gy, int k, int nx, int ny, float q[V], float dg[V]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < V; ++i) {
         const float xm = i == 0 ? xl : c[i - 1];
-        const float xp = i == 3 ? xr : c[i + 1];
+        const float xp = i == V - 1 ? xr : c[i + 1];
         op.apply(c[i], xm, xp, ym[i], yp[i], zm[i], zp[i], min(gx + i, nx - 1), min(gy, ny - 1), k, q[i], dg[i]);
     }
 }
 
-template <typename Self>
-__device__ __forceinline__ void OpConst::apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
-                                                const float yp[4], const float zm[4], const float zp[4], int gx,
-                                                int gy, int k, int nx, int ny, float q[4], float dg[4]) const {
-    apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx, ny, q, dg);
+template <int V>
+__device__ __forceinline__ void OpConst::applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
+                                                const float yp[V], const float zm[V], const float zp[V], int gx,
+                                                int gy, int k, int nx, int ny, float q[V], float dg[V]) const {
+    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx, ny, q, dg);
 }
-template <typename Self>
-__device__ __forceinline__ void OpBlock::apply4(Cache &, const float c[4], float xl, float xr, const float ym[4],
-                                                const float yp[4], const float zm[4], const float zp[4], int gx,
-                                                int gy, int k, int nx_, int ny_, float q[4], float dg[4]) const {
-    apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+template <int V>
+__device__ __forceinline__ void OpBlock::applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
+                                                const float yp[V], const float zm[V], const float zp[V], int gx,
+                                                int gy, int k, int nx_, int ny_, float q[V], float dg[V]) const {
+    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
 }
 
 // Block-constant coefficient through a per-block face table built once per
@@ -167,7 +167,7 @@ struct OpTable {
     float inv_d;  // unused
     const float4 *tab;
     int nx, ny, nz, nbx, nby, kbx, kby, kbz;
-    int grouped;  // kbx % 4 == 0: a thread's four points share one block
+    int grouped4, grouped8;  // kbx % 4 == 0 / kbx % 8 == 0: a thread's 4 / 8 points share one block
     float cx, cy, cz;
     __device__ __forceinline__ void lookup(int bx, int by, int bz, float4 &t0, float4 &t1) const {
         const float4 *t = tab + 2 * (((size_t)bz * nby + by) * nbx + bx);
@@ -194,17 +194,18 @@ struct OpTable {
         int bz = -1, bx = 0, by = 0, ix0 = 0, iy = 0;
         float4 t0, t1;
     };
-    __device__ __forceinline__ void apply4(Cache &cc, const float c[4], float xl, float xr, const float ym[4],
-                                           const float yp[4], const float zm[4], const float zp[4], int gx, int gy,
-                                           int k, int nx_, int ny_, float q[4], float dg[4]) const {
-        if (!grouped) {
-            apply4_pointwise(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+    template <int V>
+    __device__ __forceinline__ void applyv(Cache &cc, const float c[V], float xl, float xr, const float ym[V],
+                                           const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
+                                           int k, int nx_, int ny_, float q[V], float dg[V]) const {
+        if (!(V == 4 ? grouped4 : grouped8)) {
+            applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
             return;
         }
         const int bz = k / kbz, iz = k - bz * kbz;
         if (bz != cc.bz) {
             if (cc.bz < 0) {
-                const int i0 = min(gx, (nx - 1) & ~3), j = min(gy, ny - 1);  // gx is a multiple of 4
+                const int i0 = min(gx, (nx - 1) & ~(V - 1)), j = min(gy, ny - 1);  // gx is a multiple of V
                 cc.bx = i0 / kbx;
                 cc.by = j / kby;
                 cc.ix0 = i0 - cc.bx * kbx;
@@ -219,10 +220,10 @@ struct OpTable {
         const float w4 = cz * (iz == 0 ? t1.y : kc), w5 = cz * (iz == kbz - 1 ? t1.z : kc);
         const float wyz = (w2 + w3) + (w4 + w5);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < V; ++i) {
             const int ix = cc.ix0 + i;
             const float xm = i == 0 ? xl : c[i - 1];
-            const float xp = i == 3 ? xr : c[i + 1];
+            const float xp = i == V - 1 ? xr : c[i + 1];
             const float w0 = cx * (ix == 0 ? t0.y : kc), w1 = cx * (ix == kbx - 1 ? t0.z : kc);
             q[i] = w0 * (c[i] - xm) + w1 * (c[i] - xp) + w2 * (c[i] - ym[i]) + w3 * (c[i] - yp[i]) +
                    w4 * (c[i] - zm[i]) + w5 * (c[i] - zp[i]);
@@ -269,7 +270,8 @@ using CenterT = typename std::conditional<KIND == K_PASSA, float, T>::type;
 
 template <typename T, int TX, int TY, int KIND>
 struct Geometry {
-    static constexpr int NT = TX / 4 * TY;
+    static constexpr int V = 16 / (int)sizeof(T);  // points per thread: one 16-byte vector of T
+    static constexpr int NT = TX / V * TY;
     static constexpr int XH = full_row<TX>() ? 0 : 16 / (int)sizeof(T);
     static constexpr int HX = TX + 2 * XH, HY = TY + 2;
     static constexpr int NH = KIND == K_PASSA ? 2 : 1;
@@ -302,11 +304,11 @@ __device__ __forceinline__ void manual_box(const T *src, T *dst, int nx, int ny,
 }
 
 template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
-__global__ void __launch_bounds__(TX / 4 * TY)
+__global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
     using G = Geometry<T, TX, TY, KIND>;
     using TC = CenterT<T, KIND>;
-    constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV;
+    constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV, V = G::V;
     constexpr uint32_t HB = G::HB, SB = G::SB;
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -345,11 +347,11 @@ __global__ void __launch_bounds__(TX / 4 * TY)
     const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
     const int k0 = blockIdx.y * a.zchunk, k1 = min(nz, k0 + a.zchunk);
-    const int lx = threadIdx.x % (TX / 4), ly = threadIdx.x / (TX / 4);
-    const int gx = x0 + 4 * lx, gy = y0 + ly;
-    bool ok[4];
+    const int lx = threadIdx.x % (TX / V), ly = threadIdx.x / (TX / V);
+    const int gx = x0 + V * lx, gy = y0 + ly;
+    bool ok[V];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) ok[i] = gy < ny && gx + i < nx;
+    for (int i = 0; i < V; ++i) ok[i] = gy < ny && gx + i < nx;
 
     const bool load_h1 = NH == 2 && !first;
     const bool load_c = G::NC == 1 && !(KIND == K_PASSA && !do_x);
@@ -408,14 +410,14 @@ __global__ void __launch_bounds__(TX / 4 * TY)
         }
         return v;
     };
-    auto in_val4 = [&](const unsigned char *base, int idx, float v[4]) {
-        ld4<T>(reinterpret_cast<const T *>(base) + idx, v);
+    auto in_valv = [&](const unsigned char *base, int idx, float v[V]) {
+        ldv<T, V>(reinterpret_cast<const T *>(base) + idx, v);
         if constexpr (KIND == K_PASSA) {
             if (!first) {
-                float p[4];
-                ld4<T>(reinterpret_cast<const T *>(base + HB) + idx, p);
+                float p[V];
+                ldv<T, V>(reinterpret_cast<const T *>(base + HB) + idx, p);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = fmaf(beta, p[i], v[i]);
+                for (int i = 0; i < V; ++i) v[i] = fmaf(beta, p[i], v[i]);
             }
         }
     };
@@ -427,9 +429,11 @@ __global__ void __launch_bounds__(TX / 4 * TY)
             issue(t);
             issued_hi = t;
         }
-        float qa[4] = {0.f, 0.f, 0.f, 0.f}, qb[4] = {0.f, 0.f, 0.f, 0.f}, qc[4] = {0.f, 0.f, 0.f, 0.f};
+        float qa[V], qb[V], qc[V];
+#pragma unroll
+        for (int i = 0; i < V; ++i) qa[i] = qb[i] = qc[i] = 0.f;
         typename Op::Cache opc;
-        const int cidx = (ly + 1) * HX + XH + 4 * lx;  // this thread's first point in a halo box
+        const int cidx = (ly + 1) * HX + XH + V * lx;  // this thread's first point in a halo box
         for (int t = 0; t <= tl; ++t) {
             const int s = t % S;
             const unsigned char *base = smem + (size_t)s * SB;
@@ -438,47 +442,48 @@ __global__ void __launch_bounds__(TX / 4 * TY)
             }
             consumed = t;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
-            in_val4(base, cidx, qc);
+            for (int i = 0; i < V; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
+            in_valv(base, cidx, qc);
             if (t >= 2) {
                 // ---- output plane k = pl(t-1) from its own stage ----
                 const int k = plane(t - 1);
                 const unsigned char *bk = smem + (size_t)((t - 1) % S) * SB;
-                float ym[4], yp[4];
-                in_val4(bk, cidx - HX, ym);
-                in_val4(bk, cidx + HX, yp);
+                float ym[V], yp[V];
+                in_valv(bk, cidx - HX, ym);
+                in_valv(bk, cidx + HX, yp);
                 // whole-row tiles: the x neighbours past either end of the row are
                 // boundary zeros (the box holds no x halo)
                 const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
-                const float xr = (full_row<TX>() && lx == TX / 4 - 1) ? 0.0f : in_val(bk, cidx + 4);
-                float q[4], dg[4];
-                op.apply4(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q, dg);
+                const float xr = (full_row<TX>() && lx == TX / V - 1) ? 0.0f : in_val(bk, cidx + V);
+                float q[V], dg[V];
+                op.template applyv<V>(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q,
+                                      dg);
                 const size_t g = ((size_t)k * ny + gy) * nx + gx;
-                const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + 4 * lx;
-                float out0[4], out1[4];
+                const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + V * lx;
+                float out0[V], out1[V];
                 bool st1 = false;
                 if constexpr (KIND == K_STENCIL) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) out0[i] = q[i] * a.scale;
+                    for (int i = 0; i < V; ++i) out0[i] = q[i] * a.scale;
                 } else if constexpr (KIND == K_PASSA) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < V; ++i) {
                         out0[i] = qb[i];
                         if (ok[i]) acc[0] = fmaf(qb[i], q[i], acc[0]);
                     }
                     if (do_x) {
-                        float xv[4], po[4];
-                        ld4<TC>(cen, xv);
-                        ld4<T>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
+                        float xv[V], po[V];
+                        ldv<TC, V>(cen, xv);
+                        ldv<T, V>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
+                        for (int i = 0; i < V; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
                         st1 = true;
                     }
                 } else {  // K_PASSB
-                    float zv[4];
-                    ld4<TC>(cen, zv);
+                    float zv[V];
+                    ldv<TC, V>(cen, zv);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < V; ++i) {
                         const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
                         const float z = Op::kConst ? r * op.inv_d : r / dg[i];
                         out0[i] = z;
@@ -488,12 +493,12 @@ __global__ void __launch_bounds__(TX / 4 * TY)
                         }
                     }
                 }
-                if (ok[0] && ok[3] && TMA) {
-                    st4<T>(O0 + g, out0);
-                    if (st1) st4<TC>(O1 + g, out1);
+                if (ok[0] && ok[V - 1] && TMA) {
+                    stv<T, V>(O0 + g, out0);
+                    if (st1) stv<TC, V>(O1 + g, out1);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < V; ++i)
                         if (ok[i]) {
                             O0[g + i] = from_f<T>(out0[i]);
                             if (st1) O1[g + i] = from_f<TC>(out1[i]);

@@ -98,7 +98,7 @@ inline bool tma_ok(size_t esize, int nx, std::initializer_list<const void *> ptr
 template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
 struct PassKernel {
     static constexpr size_t smem = zmarch_smem_bytes<T, TX, TY, S, KIND>();
-    static constexpr int threads = TX / 4 * TY;
+    static constexpr int threads = TX / (16 / (int)sizeof(T)) * TY;
     static void *fn() { return reinterpret_cast<void *>(&zmarch_kernel<T, TX, TY, S, KIND, TMA, Op>); }
     static cudaError_t prepare() {
         return cudaFuncSetAttribute(zmarch_kernel<T, TX, TY, S, KIND, TMA, Op>,
@@ -177,7 +177,8 @@ inline OpTable make_op_table(const gbpcg_grid &g, float scale, const float4 *tab
     o.kbx = g.kbx; o.kby = g.kby; o.kbz = g.kbz;
     o.nbx = (g.nx + g.kbx - 1) / g.kbx;
     o.nby = (g.ny + g.kby - 1) / g.kby;
-    o.grouped = g.kbx % 4 == 0;
+    o.grouped4 = g.kbx % 4 == 0;
+    o.grouped8 = g.kbx % 8 == 0;
     o.cx = (float)(c(g.nx) * scale); o.cy = (float)(c(g.ny) * scale); o.cz = (float)(c(g.nz) * scale);
     return o;
 }
