@@ -1,0 +1,216 @@
+"""FP64 oracle of the learned preconditioner and of flexible CG.
+
+TEST INFRASTRUCTURE ONLY (test suite, smoke, benchmark CPU leg).  Plain
+numpy, float64, channels-last arrays of shape (Z, Y, X, C); no code shared
+with the CUDA path.  Neither the paper nor its comparison systems contain a
+learned preconditioner: this follows the design the project states for it.
+
+Conventions
+  conv3   out[v, o] = sum_{t, i} W[o, t, i] * in[v + off(t), i], 3x3x3 taps
+          t = (dz+1)*9 + (dy+1)*3 + (dx+1), zero padding, stride 1, no bias.
+  pool2   2x2x2 average (even sizes).
+  up2     nearest-neighbour doubling.
+  U-net   (levels L0 full, L1 half, L2 quarter resolution; ReLU after every
+          conv but the last):
+            c1 (2->16), c2 (16->16) = e0
+            pool, c3 (16->32), c4 (32->32) = e1
+            pool, c5 (32->64), c6 (64->64)
+            up, concat [up(64), e1] -> c7 (96->32)
+            up, concat [up(32), e0] -> c8 (48->16)
+            c9 (16->1) = output
+          input channels [r / rms(r), log k]; the output is scaled by
+          rms(r) * h^2 (the network predicts in normalised units).
+  loss    L(z) = 1/2 z.Az - z.r: the A-norm error 1/2 ||z - A^{-1}r||_A^2 up to
+          the constant -1/2 r.A^{-1}r; dL/dz = A z - r.
+  FCG     flexible CG with truncation 1 (Notay, SIAM J. Sci. Comput. 22, 2000):
+          beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+TAPS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+LAYERS = [("c1", 2, 16), ("c2", 16, 16), ("c3", 16, 32), ("c4", 32, 32), ("c5", 32, 64), ("c6", 64, 64),
+          ("c7", 96, 32), ("c8", 48, 16), ("c9", 16, 1)]
+
+
+def shift(x, dz, dy, dx):
+    """y[z, y, x] = x[z + dz, y + dy, x + dx], zero outside."""
+    Z, Y, X = x.shape[:3]
+    out = np.zeros_like(x)
+    zs, zd = (slice(dz, Z), slice(0, Z - dz)) if dz >= 0 else (slice(0, Z + dz), slice(-dz, Z))
+    ys, yd = (slice(dy, Y), slice(0, Y - dy)) if dy >= 0 else (slice(0, Y + dy), slice(-dy, Y))
+    xs, xd = (slice(dx, X), slice(0, X - dx)) if dx >= 0 else (slice(0, X + dx), slice(-dx, X))
+    out[zd, yd, xd] = x[zs, ys, xs]
+    return out
+
+
+def conv3(x, W):
+    """x: (Z, Y, X, Ci); W: (Co, 27, Ci) -> (Z, Y, X, Co)."""
+    out = np.zeros(x.shape[:3] + (W.shape[0],))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        out += shift(x, dz, dy, dx) @ W[:, t, :].T
+    return out
+
+
+def conv3_adjoint(gy, W):
+    """The adjoint of conv3 in its input: sum_t shift(gy, -off(t)) @ W_t."""
+    out = np.zeros(gy.shape[:3] + (W.shape[2],))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        out += shift(gy, -dz, -dy, -dx) @ W[:, t, :]
+    return out
+
+
+def conv3_weight_grad(x, gy):
+    """dL/dW for L depending on y = conv3(x, W) through gy = dL/dy."""
+    Co, Ci = gy.shape[3], x.shape[3]
+    g = np.zeros((Co, 27, Ci))
+    gy2 = gy.reshape(-1, Co)
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        g[:, t, :] = gy2.T @ shift(x, dz, dy, dx).reshape(-1, Ci)
+    return g
+
+
+def pool2(x):
+    Z, Y, X, C = x.shape
+    return x.reshape(Z // 2, 2, Y // 2, 2, X // 2, 2, C).mean(axis=(1, 3, 5))
+
+
+def pool2_adjoint(g):
+    return up2(g) / 8.0
+
+
+def up2(x):
+    return x.repeat(2, axis=0).repeat(2, axis=1).repeat(2, axis=2)
+
+
+def up2_adjoint(g):
+    Z, Y, X, C = g.shape
+    return g.reshape(Z // 2, 2, Y // 2, 2, X // 2, 2, C).sum(axis=(1, 3, 5))
+
+
+def relu(x):
+    return np.maximum(x, 0.0)
+
+
+def init_weights(seed: int = 0):
+    """He-style initialisation from SplitMix64 normals (one stream per layer)."""
+    from paper_2603_23343_gb300 import inputs
+    ws = {}
+    for li, (name, ci, co) in enumerate(LAYERS):
+        n = co * 27 * ci
+        std = np.sqrt(2.0 / (27 * ci)) * (0.5 if name == "c9" else 1.0)
+        ws[name] = inputs.standard_normal(seed * 1000 + li, 0, n).reshape(co, 27, ci) * std
+    return ws
+
+
+def net_forward(x, ws, round_fn=None):
+    """U-net on input x (Z, Y, X, 2); returns (output (Z,Y,X,1), cache).
+
+    round_fn (optional) is applied to every stored activation, to mirror a
+    reduced-precision implementation layer by layer."""
+    R = round_fn if round_fn is not None else (lambda a: a)
+    c = {"x": x}
+    a1 = R(relu(conv3(x, ws["c1"])))
+    e0 = R(relu(conv3(a1, ws["c2"])))
+    p1 = R(pool2(e0))
+    a3 = R(relu(conv3(p1, ws["c3"])))
+    e1 = R(relu(conv3(a3, ws["c4"])))
+    p2 = R(pool2(e1))
+    a5 = R(relu(conv3(p2, ws["c5"])))
+    a6 = R(relu(conv3(a5, ws["c6"])))
+    k7 = np.concatenate([R(up2(a6)), e1], axis=3)
+    a7 = R(relu(conv3(k7, ws["c7"])))
+    k8 = np.concatenate([R(up2(a7)), e0], axis=3)
+    a8 = R(relu(conv3(k8, ws["c8"])))
+    out = conv3(a8, ws["c9"])
+    c.update(a1=a1, e0=e0, p1=p1, a3=a3, e1=e1, p2=p2, a5=a5, a6=a6, k7=k7, a7=a7, k8=k8, a8=a8)
+    return out, c
+
+
+def net_backward(gout, ws, c):
+    """Gradients of a loss w.r.t. every weight and the input, given gout = dL/d(output)."""
+    g = {}
+    g["c9"] = conv3_weight_grad(c["a8"], gout)
+    ga8 = conv3_adjoint(gout, ws["c9"]) * (c["a8"] > 0)
+    g["c8"] = conv3_weight_grad(c["k8"], ga8)
+    gk8 = conv3_adjoint(ga8, ws["c8"])
+    ga7 = up2_adjoint(gk8[..., :32]) * (c["a7"] > 0)
+    ge0 = gk8[..., 32:].copy()
+    g["c7"] = conv3_weight_grad(c["k7"], ga7)
+    gk7 = conv3_adjoint(ga7, ws["c7"])
+    ga6 = up2_adjoint(gk7[..., :64]) * (c["a6"] > 0)
+    ge1 = gk7[..., 64:].copy()
+    g["c6"] = conv3_weight_grad(c["a5"], ga6)
+    ga5 = conv3_adjoint(ga6, ws["c6"]) * (c["a5"] > 0)
+    g["c5"] = conv3_weight_grad(c["p2"], ga5)
+    ge1 += pool2_adjoint(conv3_adjoint(ga5, ws["c5"]))
+    ge1 *= (c["e1"] > 0)
+    g["c4"] = conv3_weight_grad(c["a3"], ge1)
+    ga3 = conv3_adjoint(ge1, ws["c4"]) * (c["a3"] > 0)
+    g["c3"] = conv3_weight_grad(c["p1"], ga3)
+    ge0 += pool2_adjoint(conv3_adjoint(ga3, ws["c3"]))
+    ge0 *= (c["e0"] > 0)
+    g["c2"] = conv3_weight_grad(c["a1"], ge0)
+    ga1 = conv3_adjoint(ge0, ws["c2"]) * (c["a1"] > 0)
+    g["c1"] = conv3_weight_grad(c["x"], ga1)
+    g["x"] = conv3_adjoint(ga1, ws["c1"])
+    return g
+
+
+def net_input(r, logk):
+    """Channels [r / rms(r), log k] and the output scale rms(r) * h^2."""
+    rms = float(np.sqrt(np.mean(r * r)))
+    nz, ny, nx = r.shape
+    h2 = (1.0 / (max(nx, ny, nz) + 1)) ** 2
+    x = np.stack([r / rms if rms > 0 else r, logk], axis=3)
+    return x, rms * h2
+
+
+def precond_apply(r, logk, ws):
+    """z = N(r): the preconditioner the learned FCG applies."""
+    x, scale = net_input(r, logk)
+    out, _ = net_forward(x, ws)
+    return out[..., 0] * scale
+
+
+def loss(z, r, k=None, kb=8):
+    """1/2 z.Az - z.r with A the solver's operator."""
+    az = oracle.apply(z, k, kb)
+    return 0.5 * float(np.sum(z * az)) - float(np.sum(z * r))
+
+
+def loss_grad_z(z, r, k=None, kb=8):
+    return oracle.apply(z, k, kb) - r
+
+
+def fcg(b, precond, tol=1e-6, maxit=500, k=None, kb=8, x0=None):
+    """Flexible CG, truncation 1: r = b - A x; z = M(r); p = z;
+    repeat q = A p; alpha = r.z / p.q; x += alpha p; r_new = r - alpha q;
+    stop on ||r_new||/||b||; z_new = M(r_new);
+    beta = z_new.(r_new - r) / (z.r); p = z_new + beta p."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - oracle.apply(x, k, kb)
+    bn = np.linalg.norm(b)
+    z = precond(r)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    it = 0
+    hist = [np.linalg.norm(r) / bn]
+    while it < maxit and hist[-1] > tol:
+        q = oracle.apply(p, k, kb)
+        alpha = rz / float(np.sum(p * q))
+        x += alpha * p
+        r_new = r - alpha * q
+        it += 1
+        hist.append(np.linalg.norm(r_new) / bn)
+        if hist[-1] <= tol:
+            break
+        z_new = precond(r_new)
+        beta = float(np.sum(z_new * (r_new - r))) / rz
+        p = z_new + beta * p
+        rz = float(np.sum(r_new * z_new))
+        r, z = r_new, z_new
+    return dict(x=x, iters=it, hist=np.array(hist))

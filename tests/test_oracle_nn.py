@@ -1,0 +1,133 @@
+"""Pins of the learned-preconditioner oracle (oracle/nn.py), CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.nn as nn
+from paper_2603_23343_gb300 import inputs
+
+
+def rnd(shape, seed):
+    n = int(np.prod(shape))
+    return inputs.uniform_pm1(seed, 0, n, np.float64).reshape(shape)
+
+
+def test_weight_tap_order():
+    """Weights are laid out (Co, 27, Ci) with tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)."""
+    for t, (dz, dy, dx) in enumerate(nn.TAPS):
+        assert t == (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)
+    x = rnd((4, 5, 6, 1), 21)
+    W = np.zeros((1, 27, 1))
+    W[0, 14, 0] = 1.0  # t = 14: (dz, dy, dx) = (0, 0, +1)
+    np.testing.assert_array_equal(nn.conv3(x, W)[:, :, :-1], x[:, :, 1:])
+
+
+def test_conv_tap_convention():
+    """Tap (dz, dy, dx) = (0, 0, +1) reads the +x neighbour: out[..., x] = in[..., x + 1]."""
+    x = rnd((4, 5, 6, 1), 1)
+    W = np.zeros((1, 27, 1))
+    W[0, nn.TAPS.index((0, 0, 1)), 0] = 1.0
+    y = nn.conv3(x, W)
+    np.testing.assert_array_equal(y[:, :, :-1], x[:, :, 1:])
+    assert not np.any(y[:, :, -1])
+    W2 = np.zeros((1, 27, 1))
+    W2[0, nn.TAPS.index((-1, 0, 0)), 0] = 1.0  # reads the -z neighbour
+    y2 = nn.conv3(x, W2)
+    np.testing.assert_array_equal(y2[1:], x[:-1])
+    assert not np.any(y2[0])
+
+
+def test_conv_delta_kernel_is_identity_and_constant_input():
+    x = rnd((5, 6, 7, 3), 2)
+    W = np.zeros((3, 27, 3))
+    W[:, 13, :] = np.eye(3)
+    np.testing.assert_array_equal(nn.conv3(x, W), x)
+    Wr = rnd((2, 27, 3), 3)
+    c = np.ones((6, 6, 6, 3)) * 0.5
+    y = nn.conv3(c, Wr)
+    np.testing.assert_allclose(y[2, 2, 2], 0.5 * Wr.sum(axis=(1, 2)), rtol=1e-13)
+    # a corner point sees only the 8 in-range taps
+    in_corner = [t for t, (dz, dy, dx) in enumerate(nn.TAPS) if dz >= 0 and dy >= 0 and dx >= 0]
+    np.testing.assert_allclose(y[0, 0, 0], 0.5 * Wr[:, in_corner, :].sum(axis=(1, 2)), rtol=1e-13)
+
+
+def test_conv_adjoints_exact():
+    x = rnd((4, 6, 5, 3), 4)
+    y = rnd((4, 6, 5, 2), 5)
+    W = rnd((2, 27, 3), 6)
+    lhs = float(np.sum(nn.conv3(x, W) * y))
+    assert abs(lhs - float(np.sum(x * nn.conv3_adjoint(y, W)))) <= 1e-12 * abs(lhs) + 1e-12
+    E = rnd((2, 27, 3), 7)
+    lhs_w = float(np.sum(nn.conv3(x, E) * y))  # conv is linear in W
+    assert abs(lhs_w - float(np.sum(E * nn.conv3_weight_grad(x, y)))) <= 1e-12 * abs(lhs_w) + 1e-12
+
+
+def test_pool_and_upsample_adjoints():
+    a = rnd((4, 6, 8, 2), 8)
+    b = rnd((2, 3, 4, 2), 9)
+    assert abs(np.sum(nn.pool2(a) * b) - np.sum(a * nn.pool2_adjoint(b))) <= 1e-12
+    assert abs(np.sum(nn.up2(b) * a) - np.sum(b * nn.up2_adjoint(a))) <= 1e-12
+    np.testing.assert_allclose(nn.pool2(np.ones((4, 4, 4, 1))), np.ones((2, 2, 2, 1)))
+
+
+def test_unet_backward_matches_finite_differences():
+    shape = (8, 8, 8)
+    r = rnd(shape, 10)
+    k = inputs.lognormal_blocks(2, 2, 2, 11).astype(np.float64)
+    logk = np.log(np.repeat(np.repeat(np.repeat(k, 4, 0), 4, 1), 4, 2))
+    ws = nn.init_weights(3)
+    x, scale = nn.net_input(r, logk)
+
+    def L(wset, xin):
+        out, _ = nn.net_forward(xin, wset)
+        z = out[..., 0] * scale
+        return nn.loss(z, r, k, 4)
+
+    out, cache = nn.net_forward(x, ws)
+    z = out[..., 0] * scale
+    gout = (nn.loss_grad_z(z, r, k, 4) * scale)[..., None]
+    g = nn.net_backward(gout, ws, cache)
+    h = 1e-6
+    checks = [("c1", (3, 13, 0)), ("c2", (5, 0, 7)), ("c4", (1, 20, 3)), ("c5", (10, 13, 4)), ("c6", (63, 26, 63)),
+              ("c7", (7, 5, 90)), ("c8", (15, 13, 40)), ("c9", (0, 13, 9))]
+    for name, idx in checks:
+        wp = {k2: v.copy() for k2, v in ws.items()}
+        wm = {k2: v.copy() for k2, v in ws.items()}
+        wp[name][idx] += h
+        wm[name][idx] -= h
+        fd = (L(wp, x) - L(wm, x)) / (2 * h)
+        assert abs(fd - g[name][idx]) <= 1e-5 * max(1e-8, abs(fd)) + 1e-9, (name, fd, g[name][idx])
+    for idx in [(1, 2, 3, 0), (7, 7, 0, 1), (4, 5, 6, 0)]:
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (L(ws, xp) - L(ws, xm)) / (2 * h)
+        assert abs(fd - g["x"][idx]) <= 1e-5 * max(1e-8, abs(fd)) + 1e-9
+
+
+def test_loss_is_minimised_by_the_solution():
+    shape = (5, 4, 6)
+    r = rnd(shape, 12)
+    zstar = oracle.pcg(r, tol=1e-14, maxit=500)["x"]
+    assert np.max(np.abs(nn.loss_grad_z(zstar, r))) <= 1e-9 * np.max(np.abs(r))
+    pert = rnd(shape, 13) * 1e-3
+    assert nn.loss(zstar + pert, r) > nn.loss(zstar, r)
+    np.testing.assert_allclose(nn.loss(zstar, r), -0.5 * float(np.sum(r * zstar)), rtol=1e-10)
+
+
+@pytest.mark.parametrize("varcoeff", [False, True])
+def test_fcg_reduces_to_pcg_for_linear_preconditioners(varcoeff):
+    shape = (10, 12, 9)
+    b = rnd(shape, 14)
+    k = None
+    if varcoeff:
+        nbx, nby, nbz = inputs.block_counts(9, 12, 10, 4)
+        k = inputs.lognormal_blocks(nbx, nby, nbz, 15).astype(np.float64)
+    d = oracle.diag(shape, k, 4)
+    ref = oracle.pcg(b, tol=1e-8, maxit=500, k=k, kb=4)
+    f = nn.fcg(b, lambda r: r / d, tol=1e-8, maxit=500, k=k, kb=4)
+    assert abs(f["iters"] - ref["iters"]) <= 1
+    np.testing.assert_allclose(f["x"], ref["x"], rtol=0, atol=1e-7 * np.max(np.abs(ref["x"])))
+    plain = oracle.pcg(b, tol=1e-8, maxit=500, k=k, kb=4, precond=None)
+    f2 = nn.fcg(b, lambda r: r.copy(), tol=1e-8, maxit=500, k=k, kb=4)
+    assert abs(f2["iters"] - plain["iters"]) <= 1
