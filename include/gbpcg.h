@@ -63,7 +63,8 @@ typedef enum {
 } gbpcg_dtype;
 
 typedef enum {
-    GBPCG_PRECOND_JACOBI = 0
+    GBPCG_PRECOND_JACOBI = 0,
+    GBPCG_PRECOND_LEARNED = 1 /* gbpcg_fcg_solve only */
 } gbpcg_precond;
 
 /* Grid and operator.  k_block == NULL selects the constant-coefficient
@@ -237,6 +238,152 @@ int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *
 int gbpcg_autotune(const gbpcg_grid *grid, const gbpcg_opts *opts, const void *b, int32_t *tile_cfg,
                    double *us_per_iter, gbpcg_stream stream);
 int gbpcg_autotune_record(const gbpcg_grid *grid, const gbpcg_opts *opts, int32_t tile_cfg);
+
+/* ------------------------------------------------------------------------
+ * Learned preconditioner (no counterpart in the paper, which preconditions
+ * with Jacobi only): z = N(r), a three-level 3D U-net of 3x3x3
+ * convolutions without bias, used inside flexible CG.
+ *
+ *   c1 (2->16), c2 (16->16) = e0                       full resolution
+ *   2x2x2 average pool, c3 (16->32), c4 (32->32) = e1  half
+ *   2x2x2 average pool, c5 (32->64), c6 (64->64)       quarter
+ *   nearest upsample, concat [up, e1] -> c7 (96->32)   half
+ *   nearest upsample, concat [up, e0] -> c8 (48->16)   full
+ *   c9 (16->1)
+ * ReLU after every convolution but c9.  Input channels: r / rms(r) and
+ * log k of the voxel's coefficient block (0 for the Poisson operator); the
+ * output is multiplied by rms(r) h^2, h = 1/(max(nx, ny, nz) + 1), so N is
+ * positively homogeneous: N(a r) = a N(r) for a > 0.
+ *
+ * Layouts: activations channels-last, (nz, ny, nx, C), BF16; a layer's
+ * weights (Co, 27, Ci) with tap t = (dz+1)*9 + (dy+1)*3 + (dx+1) reading
+ * in[z+dz, y+dy, x+dx]; zero padding.  The FP32 master weights of the whole
+ * network are one array of GBPCG_NN_NUM_WEIGHTS floats, layers c1..c9 in
+ * order.  Convolutions with 16 or more input and output channels run on the
+ * tensor cores (tcgen05, BF16 operands, FP32 accumulation).
+ *
+ * Grids: each size a multiple of 4 such that every level's voxels split
+ * into 128-voxel tiles of whole x-rows or whole planes (any multiple of 512,
+ * or powers of two >= 32).  Workspaces: DEVICE, 256-byte aligned, from the
+ * matching *_workspace_size; a bounded wait that gives up inside a
+ * convolution zeroes that tile's output and sets an error word in the
+ * workspace (see gbpcg_nn_status).
+ * ---------------------------------------------------------------------- */
+
+#define GBPCG_NN_NUM_WEIGHTS 319248
+
+/* Workspace bytes of the gbpcg_conv3_* calls for one shape. */
+int gbpcg_conv3_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, size_t *bytes);
+
+/*
+ * y[v, o] = sum_{t, i} w[o, t, i] x[v + off(t), i]  (then max(y, 0) when
+ * relu != 0).  x: DEVICE BF16 (nz, ny, nx, ci); w: DEVICE BF16 (co, 27, ci);
+ * y: DEVICE FP32 (nz, ny, nx, co).  Supported: ci a multiple of 16 with co
+ * in {16, 32, 48, 64, 96} (tensor cores), or (ci, co) in {(2, 16), (16, 1),
+ * (1, 16)} (CUDA cores).  Arrays 16-byte aligned.
+ */
+int gbpcg_conv3_forward(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x, const void *w,
+                        float *y, int32_t relu, void *workspace, size_t workspace_bytes, gbpcg_stream stream);
+
+/*
+ * gx[v, i] = sum_{t, o} w[o, t, i] gy[v - off(t), o]: the adjoint of
+ * gbpcg_conv3_forward in x (computed as a forward convolution with mirrored
+ * taps and transposed channels).  gy: DEVICE BF16 (.., co); w: DEVICE BF16
+ * (co, 27, ci); gx: DEVICE FP32 (.., ci).  Supported when the forward shape
+ * with ci and co exchanged is.
+ */
+int gbpcg_conv3_backward_data(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *gy,
+                              const void *w, float *gx, void *workspace, size_t workspace_bytes,
+                              gbpcg_stream stream);
+
+/*
+ * gw[o, t, i] = sum_v gy[v, o] x[v + off(t), i]: the gradient in w of a loss
+ * that depends on y = conv(x, w) through gy = dL/dy.  x: DEVICE BF16
+ * (.., ci); gy: DEVICE BF16 (.., co); gw: DEVICE FP32 (co, 27, ci),
+ * overwritten.  ci in {1, 2} or a multiple of 8, co = 1 or a multiple of 8;
+ * the sum is taken in a fixed order (bitwise reproducible).
+ */
+int gbpcg_conv3_backward_weight(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x,
+                                const void *gy, float *gw, void *workspace, size_t workspace_bytes,
+                                gbpcg_stream stream);
+
+/* Workspace bytes of the network for a grid: inference (training = 0) or
+ * forward + backward (training != 0).  A training workspace serves every
+ * gbpcg_nn_* call. */
+int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t training, size_t *bytes);
+
+/*
+ * z = N(r).  w: DEVICE FP32 master weights (GBPCG_NN_NUM_WEIGHTS); r, z:
+ * DEVICE FP32 (nz, ny, nx); grid->k_block supplies the log k channel.  The
+ * activations stay in the workspace for gbpcg_nn_backward.
+ */
+int gbpcg_nn_forward(const gbpcg_grid *grid, const float *w, const float *r, float *z, void *workspace,
+                     size_t workspace_bytes, gbpcg_stream stream);
+
+/*
+ * gw = dL/dw for every weight (DEVICE FP32, GBPCG_NN_NUM_WEIGHTS,
+ * overwritten), given gz = dL/dz (DEVICE FP32) at the z of the last
+ * gbpcg_nn_forward on this (training) workspace.  The normalisation by
+ * rms(r) is treated as a constant.
+ */
+int gbpcg_nn_backward(const gbpcg_grid *grid, const float *gz, float *gw, void *workspace, size_t workspace_bytes,
+                      gbpcg_stream stream);
+
+/*
+ * Loss of one training pair (r, e = A^{-1} r): for z.Ae >= 0 the relative
+ * A-norm error of the best multiple of z (a preconditioned step's line
+ * search chooses that multiple, so only the direction of z matters), mirrored
+ * for z.Ae < 0 so that only positive multiples of e reach the minimum 0.
+ * With a = z.Ae, c = z.Az, E = e.Ae and A the grid's operator:
+ *   loss = 1/2 (1 - a |a| / (c E))   (= 1/2 ||(a/c) z - e||_A^2 / E, a >= 0),
+ *   gz = dloss/dz = (|a| / (c E)) ((a/c) A z - A e).
+ * z, e, gz: DEVICE FP32; loss: DEVICE double (may be NULL).  Training
+ * workspace.
+ */
+int gbpcg_nn_loss(const gbpcg_grid *grid, const float *z, const float *e, float *gz, double *loss,
+                  void *workspace, size_t workspace_bytes, gbpcg_stream stream);
+
+/* Adam with bias correction on n FP32 weights (DEVICE w, g, m, v; step >= 1
+ * counts from 1). */
+int gbpcg_nn_adam(int64_t n, float *w, const float *g, float *m, float *v, int32_t step, double lr, double beta1,
+                  double beta2, double eps, gbpcg_stream stream);
+
+/*
+ * One training step on one pair: z = N(r); loss and gz as gbpcg_nn_loss;
+ * gw = dL/dw; Adam (beta 0.9 / 0.999, eps 1e-8) updates w, m, v in place.
+ * z, gz, gw: DEVICE scratch that receives those values; loss: DEVICE double.
+ */
+int gbpcg_nn_train_step(const gbpcg_grid *grid, float *w, float *m, float *v, int32_t step, double lr,
+                        const float *r, const float *e, float *z, float *gz, float *gw, double *loss,
+                        void *workspace, size_t workspace_bytes, gbpcg_stream stream);
+
+/* Workspace bytes of gbpcg_fcg_solve (opts as for the solve). */
+int gbpcg_fcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t *bytes);
+
+/*
+ * Flexible CG (truncation 1: beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k),
+ * Notay 2000) for A x = b with the learned preconditioner z = N(r), N given
+ * by the DEVICE FP32 weights w.  opts: precond = GBPCG_PRECOND_LEARNED,
+ * io_dtype = F64 (b read, x initial guess in / solution out, DEVICE,
+ * 16-byte aligned), storage = F32, no flags; tol and maxit as in
+ * gbpcg_pcg_solve (maxit counts every A.p product, fallback included).
+ * Vectors are FP32, x and the scalars FP64; at recursive convergence the
+ * true residual is recomputed in FP64 and, if it misses tol, replaces r
+ * (FCG restarts).  Descent check: if p.Ap <= 0, r.z <= 0, a scalar is not
+ * finite, the residual grows 10x over 5 iterations, or a convolution timed
+ * out, the solve continues from the current x with Jacobi PCG and returns
+ * GBPCG_FALLBACK_USED on convergence.  The host reads the scalars once per
+ * iteration.  result: iters (all), pass_launches[0] = FCG iterations,
+ * pass_launches[1] = Jacobi fallback iterations, pass_ms[0] = time in the
+ * network, pass_ms[1] = the rest, replacements.
+ */
+int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const void *b, void *x, const gbpcg_opts *opts,
+                    gbpcg_result *result, gbpcg_stream stream);
+
+/* Synchronises `stream`, then returns GBPCG_TIMEOUT (and clears the word) if
+ * a convolution in this workspace gave up a bounded wait since the last
+ * check, else GBPCG_OK. */
+int gbpcg_nn_status(void *workspace, gbpcg_stream stream);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,14 @@ Conventions
           rms(r) * h^2 (the network predicts in normalised units).
   loss    L(z) = 1/2 z.Az - z.r: the A-norm error 1/2 ||z - A^{-1}r||_A^2 up to
           the constant -1/2 r.A^{-1}r; dL/dz = A z - r.
+  training loss (scale-free, sign-aware): with target e = A^{-1} r,
+          a = z.Ae, c = z.Az, E = e.Ae, L(z) = 1/2 (1 - a |a| / (c E)).  For
+          a >= 0 that is 1/2 ||s z - e||_A^2 / ||e||_A^2 with the best multiple
+          s = a / c (a preconditioned step's line search picks it, so only the
+          direction of z matters); for a < 0 it rises to 1, so the minimum
+          (0) is reached only by positive multiples of e and the trained
+          preconditioner keeps r.z > 0.
+  Adam    Kingma & Ba, ICLR 2015, Algorithm 1 (bias-corrected moments).
   FCG     flexible CG with truncation 1 (Notay, SIAM J. Sci. Comput. 22, 2000):
           beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
 """
@@ -96,14 +104,9 @@ def relu(x):
 
 
 def init_weights(seed: int = 0):
-    """He-style initialisation from SplitMix64 normals (one stream per layer)."""
+    """He-style initialisation from SplitMix64 normals (the shared input generator)."""
     from paper_2603_23343_gb300 import inputs
-    ws = {}
-    for li, (name, ci, co) in enumerate(LAYERS):
-        n = co * 27 * ci
-        std = np.sqrt(2.0 / (27 * ci)) * (0.5 if name == "c9" else 1.0)
-        ws[name] = inputs.standard_normal(seed * 1000 + li, 0, n).reshape(co, 27, ci) * std
-    return ws
+    return inputs.unet_init_weights(seed, LAYERS)
 
 
 def net_forward(x, ws, round_fn=None):
@@ -130,34 +133,54 @@ def net_forward(x, ws, round_fn=None):
     return out, c
 
 
-def net_backward(gout, ws, c):
-    """Gradients of a loss w.r.t. every weight and the input, given gout = dL/d(output)."""
+def net_backward(gout, ws, c, round_fn=None, trace=None):
+    """Gradients of a loss w.r.t. every weight and the input, given gout = dL/d(output).
+
+    round_fn (optional) is applied to every propagated gradient that feeds a
+    convolution (after its ReLU mask), mirroring an implementation that
+    stores those in reduced precision; sums and skip gradients are not
+    rounded.  trace (optional dict) receives, per layer, the (input,
+    output gradient) pair its weight gradient is formed from."""
+    R = round_fn if round_fn is not None else (lambda a: a)
     g = {}
-    g["c9"] = conv3_weight_grad(c["a8"], gout)
-    ga8 = conv3_adjoint(gout, ws["c9"]) * (c["a8"] > 0)
-    g["c8"] = conv3_weight_grad(c["k8"], ga8)
+
+    def wg(name, x, gy):
+        if trace is not None:
+            trace[name] = (x, gy)
+        return conv3_weight_grad(x, gy)
+
+    g["c9"] = wg("c9", c["a8"], gout)
+    ga8 = R(conv3_adjoint(gout, ws["c9"]) * (c["a8"] > 0))
+    g["c8"] = wg("c8", c["k8"], ga8)
     gk8 = conv3_adjoint(ga8, ws["c8"])
-    ga7 = up2_adjoint(gk8[..., :32]) * (c["a7"] > 0)
+    ga7 = R(up2_adjoint(gk8[..., :32]) * (c["a7"] > 0))
     ge0 = gk8[..., 32:].copy()
-    g["c7"] = conv3_weight_grad(c["k7"], ga7)
+    g["c7"] = wg("c7", c["k7"], ga7)
     gk7 = conv3_adjoint(ga7, ws["c7"])
-    ga6 = up2_adjoint(gk7[..., :64]) * (c["a6"] > 0)
+    ga6 = R(up2_adjoint(gk7[..., :64]) * (c["a6"] > 0))
     ge1 = gk7[..., 64:].copy()
-    g["c6"] = conv3_weight_grad(c["a5"], ga6)
-    ga5 = conv3_adjoint(ga6, ws["c6"]) * (c["a5"] > 0)
-    g["c5"] = conv3_weight_grad(c["p2"], ga5)
-    ge1 += pool2_adjoint(conv3_adjoint(ga5, ws["c5"]))
-    ge1 *= (c["e1"] > 0)
-    g["c4"] = conv3_weight_grad(c["a3"], ge1)
-    ga3 = conv3_adjoint(ge1, ws["c4"]) * (c["a3"] > 0)
-    g["c3"] = conv3_weight_grad(c["p1"], ga3)
-    ge0 += pool2_adjoint(conv3_adjoint(ga3, ws["c3"]))
-    ge0 *= (c["e0"] > 0)
-    g["c2"] = conv3_weight_grad(c["a1"], ge0)
-    ga1 = conv3_adjoint(ge0, ws["c2"]) * (c["a1"] > 0)
-    g["c1"] = conv3_weight_grad(c["x"], ga1)
+    g["c6"] = wg("c6", c["a5"], ga6)
+    ga5 = R(conv3_adjoint(ga6, ws["c6"]) * (c["a5"] > 0))
+    g["c5"] = wg("c5", c["p2"], ga5)
+    ge1 = R((ge1 + pool2_adjoint(conv3_adjoint(ga5, ws["c5"]))) * (c["e1"] > 0))
+    g["c4"] = wg("c4", c["a3"], ge1)
+    ga3 = R(conv3_adjoint(ge1, ws["c4"]) * (c["a3"] > 0))
+    g["c3"] = wg("c3", c["p1"], ga3)
+    ge0 = R((ge0 + pool2_adjoint(conv3_adjoint(ga3, ws["c3"]))) * (c["e0"] > 0))
+    g["c2"] = wg("c2", c["a1"], ge0)
+    ga1 = R(conv3_adjoint(ge0, ws["c2"]) * (c["a1"] > 0))
+    g["c1"] = wg("c1", c["x"], ga1)
     g["x"] = conv3_adjoint(ga1, ws["c1"])
     return g
+
+
+def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update at step t >= 1; returns (w, m, v) as new arrays."""
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** t)
+    vhat = v / (1.0 - b2 ** t)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
 def net_input(r, logk):
@@ -184,6 +207,31 @@ def loss(z, r, k=None, kb=8):
 
 def loss_grad_z(z, r, k=None, kb=8):
     return oracle.apply(z, k, kb) - r
+
+
+def loss_scaled(z, e, k=None, kb=8):
+    """Sign-aware scale-free loss; for z.Ae >= 0 written out as 1/2 ||s z - e||_A^2 / ||e||_A^2."""
+    az = oracle.apply(z, k, kb)
+    ae = oracle.apply(e, k, kb)
+    a = float(np.sum(z * ae))
+    c = float(np.sum(z * az))
+    E = float(np.sum(e * ae))
+    if a >= 0.0:
+        s = a / c
+        d = s * z - e
+        return 0.5 * float(np.sum(d * oracle.apply(d, k, kb))) / E
+    return 0.5 * (1.0 + a * a / (c * E))
+
+
+def loss_scaled_grad(z, e, k=None, kb=8):
+    """dL/dz of loss_scaled: with a = z.Ae, c = z.Az, E = e.Ae, L = 1/2 (1 - a |a| / (c E)) and
+    dL/dz = (|a| / (c E)) ((a / c) A z - A e)."""
+    az = oracle.apply(z, k, kb)
+    ae = oracle.apply(e, k, kb)
+    a = float(np.sum(z * ae))
+    c = float(np.sum(z * az))
+    E = float(np.sum(e * ae))
+    return (abs(a) / (c * E)) * ((a / c) * az - ae)
 
 
 def fcg(b, precond, tol=1e-6, maxit=500, k=None, kb=8, x0=None):

@@ -31,7 +31,17 @@ _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.f
 
 EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbpcg_stencil_apply", "gbpcg_dot",
            "gbpcg_dot_noalloc", "gbpcg_axpy", "gbpcg_tile_config", "gbpcg_workspace_size", "gbpcg_pcg_solve",
-           "gbpcg_workspace_size_batched", "gbpcg_pcg_solve_batched", "gbpcg_autotune", "gbpcg_autotune_record"]
+           "gbpcg_workspace_size_batched", "gbpcg_pcg_solve_batched", "gbpcg_autotune", "gbpcg_autotune_record",
+           "gbpcg_conv3_workspace_size", "gbpcg_conv3_forward", "gbpcg_conv3_backward_data",
+           "gbpcg_conv3_backward_weight", "gbpcg_nn_workspace_size", "gbpcg_nn_forward", "gbpcg_nn_backward",
+           "gbpcg_nn_loss", "gbpcg_nn_adam", "gbpcg_nn_train_step", "gbpcg_nn_status", "gbpcg_fcg_workspace_size",
+           "gbpcg_fcg_solve"]
+PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
+
+NN_NUM_WEIGHTS = 319248
+# (name, input channels, output channels) of the U-net's layers, in weight-array order
+NN_LAYERS = [("c1", 2, 16), ("c2", 16, 16), ("c3", 16, 32), ("c4", 32, 32), ("c5", 32, 64), ("c6", 64, 64),
+             ("c7", 96, 32), ("c8", 48, 16), ("c9", 16, 1)]
 
 
 class Grid(ctypes.Structure):
@@ -110,6 +120,31 @@ def load(path: str = LIB_PATH):
                                        ctypes.POINTER(D), P]
         lib.gbpcg_autotune_record.restype = ctypes.c_int
         lib.gbpcg_autotune_record.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), I32]
+        lib.gbpcg_conv3_workspace_size.restype = ctypes.c_int
+        lib.gbpcg_conv3_workspace_size.argtypes = [I32, I32, I32, I32, I32, ctypes.POINTER(SZ)]
+        for name in ("gbpcg_conv3_backward_data", "gbpcg_conv3_backward_weight"):
+            getattr(lib, name).restype = ctypes.c_int
+            getattr(lib, name).argtypes = [I32, I32, I32, I32, I32, P, P, P, P, SZ, P]
+        lib.gbpcg_conv3_forward.restype = ctypes.c_int
+        lib.gbpcg_conv3_forward.argtypes = [I32, I32, I32, I32, I32, P, P, P, I32, P, SZ, P]
+        lib.gbpcg_nn_workspace_size.restype = ctypes.c_int
+        lib.gbpcg_nn_workspace_size.argtypes = [I32, I32, I32, I32, ctypes.POINTER(SZ)]
+        lib.gbpcg_nn_forward.restype = ctypes.c_int
+        lib.gbpcg_nn_forward.argtypes = [ctypes.POINTER(Grid), P, P, P, P, SZ, P]
+        lib.gbpcg_nn_backward.restype = ctypes.c_int
+        lib.gbpcg_nn_backward.argtypes = [ctypes.POINTER(Grid), P, P, P, SZ, P]
+        lib.gbpcg_nn_loss.restype = ctypes.c_int
+        lib.gbpcg_nn_loss.argtypes = [ctypes.POINTER(Grid), P, P, P, P, P, SZ, P]
+        lib.gbpcg_nn_adam.restype = ctypes.c_int
+        lib.gbpcg_nn_adam.argtypes = [I64, P, P, P, P, I32, D, D, D, D, P]
+        lib.gbpcg_nn_train_step.restype = ctypes.c_int
+        lib.gbpcg_nn_train_step.argtypes = [ctypes.POINTER(Grid), P, P, P, I32, D, P, P, P, P, P, P, P, SZ, P]
+        lib.gbpcg_nn_status.restype = ctypes.c_int
+        lib.gbpcg_nn_status.argtypes = [P, P]
+        lib.gbpcg_fcg_workspace_size.restype = ctypes.c_int
+        lib.gbpcg_fcg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), ctypes.POINTER(SZ)]
+        lib.gbpcg_fcg_solve.restype = ctypes.c_int
+        lib.gbpcg_fcg_solve.argtypes = [ctypes.POINTER(Grid), P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
         _lib = lib
         return lib
 
@@ -359,3 +394,180 @@ def load_autotune(path):
         nx, ny, nz, io = (int(v) for v in key.split(","))
         autotune_record((nz, ny, nx), code, io)
     return entries
+
+
+# --------------------------------------------------- learned preconditioner --
+
+def conv3_workspace(shape, ci, co, device="cuda") -> torch.Tensor:
+    nz, ny, nx = (int(v) for v in shape)
+    n = ctypes.c_size_t(0)
+    _check(load().gbpcg_conv3_workspace_size(nx, ny, nz, int(ci), int(co), ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=device)
+
+
+def _conv_check(a: torch.Tensor, name: str):
+    if a.dim() != 4 or not a.is_cuda or not a.is_contiguous() or a.dtype != torch.bfloat16:
+        raise GbpcgError(ERR_ARG, f"{name} must be a contiguous bfloat16 CUDA tensor (nz, ny, nx, C)")
+
+
+def conv3_forward(x: torch.Tensor, w: torch.Tensor, relu=False, workspace=None, stream=None) -> torch.Tensor:
+    """y = conv3(x, w) in FP32 (gbpcg_conv3_forward); x (nz, ny, nx, ci) and w (co, 27, ci) bfloat16."""
+    _conv_check(x, "x")
+    co, _, ci = w.shape
+    nz, ny, nx, _ = x.shape
+    y = torch.empty((nz, ny, nx, co), dtype=torch.float32, device=x.device)
+    ws = workspace if workspace is not None else conv3_workspace(x.shape[:3], ci, co, x.device)
+    _check(load().gbpcg_conv3_forward(nx, ny, nz, ci, co, _ptr(x), _ptr(w.contiguous()), _ptr(y), int(bool(relu)),
+                                      _ptr(ws), ws.numel(), _stream(stream)))
+    return y
+
+
+def conv3_backward_data(gy: torch.Tensor, w: torch.Tensor, workspace=None, stream=None) -> torch.Tensor:
+    """gx = conv3 adjoint of gy (gbpcg_conv3_backward_data); gy (.., co), w (co, 27, ci) bfloat16."""
+    _conv_check(gy, "gy")
+    co, _, ci = w.shape
+    nz, ny, nx, _ = gy.shape
+    gx = torch.empty((nz, ny, nx, ci), dtype=torch.float32, device=gy.device)
+    ws = workspace if workspace is not None else conv3_workspace(gy.shape[:3], ci, co, gy.device)
+    _check(load().gbpcg_conv3_backward_data(nx, ny, nz, ci, co, _ptr(gy), _ptr(w.contiguous()), _ptr(gx), _ptr(ws),
+                                            ws.numel(), _stream(stream)))
+    return gx
+
+
+def conv3_backward_weight(x: torch.Tensor, gy: torch.Tensor, workspace=None, stream=None) -> torch.Tensor:
+    """gw (co, 27, ci) FP32 = sum_v gy[v, o] x[v + off(t), i] (gbpcg_conv3_backward_weight)."""
+    _conv_check(x, "x")
+    _conv_check(gy, "gy")
+    nz, ny, nx, ci = x.shape
+    co = gy.shape[3]
+    gw = torch.empty((co, 27, ci), dtype=torch.float32, device=x.device)
+    ws = workspace if workspace is not None else conv3_workspace(x.shape[:3], ci, co, x.device)
+    _check(load().gbpcg_conv3_backward_weight(nx, ny, nz, ci, co, _ptr(x), _ptr(gy), _ptr(gw), _ptr(ws), ws.numel(),
+                                              _stream(stream)))
+    return gw
+
+
+def nn_workspace(shape, training=False, device="cuda") -> torch.Tensor:
+    nz, ny, nx = (int(v) for v in shape)
+    n = ctypes.c_size_t(0)
+    _check(load().gbpcg_nn_workspace_size(nx, ny, nz, int(bool(training)), ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=device)
+
+
+def nn_pack_weights(ws: dict) -> torch.Tensor:
+    """One flat float32 array of the layers' (co, 27, ci) weights, c1..c9 in order (CPU tensor)."""
+    parts = [torch.as_tensor(ws[name], dtype=torch.float32).reshape(-1) for name, _, _ in NN_LAYERS]
+    return torch.cat(parts)
+
+
+def nn_unpack_weights(flat: torch.Tensor) -> dict:
+    out, o = {}, 0
+    for name, ci, co in NN_LAYERS:
+        n = co * 27 * ci
+        out[name] = flat[o:o + n].reshape(co, 27, ci)
+        o += n
+    return out
+
+
+def nn_forward(w: torch.Tensor, r: torch.Tensor, z=None, k_block=None, kb=8, workspace=None, stream=None):
+    """z = N(r) (gbpcg_nn_forward); w: float32 CUDA master weights, r (nz, ny, nx) float32."""
+    if z is None:
+        z = torch.empty_like(r)
+    ws = workspace if workspace is not None else nn_workspace(r.shape, False, r.device)
+    g = make_grid(r.shape, k_block, kb)
+    _check(load().gbpcg_nn_forward(ctypes.byref(g), _ptr(w), _ptr(r), _ptr(z), _ptr(ws), ws.numel(),
+                                   _stream(stream)))
+    return z
+
+
+def nn_backward(gz: torch.Tensor, workspace: torch.Tensor, gw=None, k_block=None, kb=8, stream=None):
+    """dL/dw from dL/dz after nn_forward on the same training workspace (gbpcg_nn_backward)."""
+    if gw is None:
+        gw = torch.empty(NN_NUM_WEIGHTS, dtype=torch.float32, device=gz.device)
+    g = make_grid(gz.shape, k_block, kb)
+    _check(load().gbpcg_nn_backward(ctypes.byref(g), _ptr(gz), _ptr(gw), _ptr(workspace), workspace.numel(),
+                                    _stream(stream)))
+    return gw
+
+
+def nn_loss(z: torch.Tensor, e: torch.Tensor, workspace: torch.Tensor, k_block=None, kb=8, stream=None):
+    """(loss device scalar, gz) of the scale-free A-norm loss (gbpcg_nn_loss)."""
+    gz = torch.empty_like(z)
+    loss = torch.empty((), dtype=torch.float64, device=z.device)
+    g = make_grid(z.shape, k_block, kb)
+    _check(load().gbpcg_nn_loss(ctypes.byref(g), _ptr(z), _ptr(e), _ptr(gz), _ptr(loss), _ptr(workspace),
+                                workspace.numel(), _stream(stream)))
+    return loss, gz
+
+
+def nn_adam(w, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Adam update of w, m, v in place (gbpcg_nn_adam)."""
+    _check(load().gbpcg_nn_adam(w.numel(), _ptr(w), _ptr(g), _ptr(m), _ptr(v), int(step), float(lr), float(beta1),
+                                float(beta2), float(eps), _stream(stream)))
+
+
+class NnTrainer:
+    """Device state of training (weights, Adam moments, scratch) for one grid
+    shape; ``step`` runs gbpcg_nn_train_step on one (r, e) pair."""
+
+    def __init__(self, w: torch.Tensor, shape, k_block=None, kb=8, device="cuda"):
+        self.w = w.to(device=device, dtype=torch.float32).contiguous().clone()
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.gw = torch.zeros_like(self.w)
+        self.shape = tuple(int(s) for s in shape)
+        self.z = torch.empty(self.shape, dtype=torch.float32, device=device)
+        self.gz = torch.empty_like(self.z)
+        self.loss = torch.zeros((), dtype=torch.float64, device=device)
+        self.ws = nn_workspace(self.shape, True, device)
+        self.k_block, self.kb = k_block, kb
+        self.t = 0
+
+    def set_coefficients(self, k_block, kb=8):
+        self.k_block, self.kb = k_block, kb
+
+    def step(self, r: torch.Tensor, e: torch.Tensor, lr=1e-3, stream=None) -> torch.Tensor:
+        self.t += 1
+        g = make_grid(self.shape, self.k_block, self.kb)
+        _check(load().gbpcg_nn_train_step(ctypes.byref(g), _ptr(self.w), _ptr(self.m), _ptr(self.v), self.t,
+                                          float(lr), _ptr(r), _ptr(e), _ptr(self.z), _ptr(self.gz), _ptr(self.gw),
+                                          _ptr(self.loss), _ptr(self.ws), self.ws.numel(), _stream(stream)))
+        return self.loss
+
+    def status(self, stream=None) -> int:
+        return _check(load().gbpcg_nn_status(_ptr(self.ws), _stream(stream)))
+
+
+def nn_status(workspace: torch.Tensor, stream=None) -> int:
+    return _check(load().gbpcg_nn_status(_ptr(workspace), _stream(stream)))
+
+
+def _fcg_opts(tol, maxit, workspace=None):
+    o = make_opts(tol=tol, maxit=maxit, io_dtype=F64, workspace=workspace)
+    o.precond = PRECOND_LEARNED
+    return o
+
+
+def fcg_workspace(shape, k_block=None, kb=8, tol=1e-6, maxit=2000, device="cuda") -> torch.Tensor:
+    g = make_grid(shape, k_block, kb)
+    o = _fcg_opts(tol, maxit)
+    n = ctypes.c_size_t(0)
+    _check(load().gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)))
+    return torch.empty(int(n.value), dtype=torch.uint8, device=device)
+
+
+def fcg_solve(w: torch.Tensor, b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None,
+              kb=8, workspace=None, stream=None):
+    """Flexible CG with the learned preconditioner N_w (gbpcg_fcg_solve); b, x float64 CUDA (nz, ny, nx).
+    Returns (x, result dict); FALLBACK_USED, NOT_CONVERGED and BREAKDOWN are reported, not raised."""
+    if b.dtype != torch.float64 or not b.is_cuda:
+        raise GbpcgError(ERR_ARG, "b must be a float64 CUDA tensor")
+    if x is None:
+        x = torch.zeros_like(b)
+    ws = workspace if workspace is not None else fcg_workspace(b.shape, k_block, kb, tol, maxit, b.device)
+    g = make_grid(b.shape, k_block, kb)
+    o = _fcg_opts(tol, maxit, ws)
+    res = Result()
+    _check(load().gbpcg_fcg_solve(ctypes.byref(g), _ptr(w), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(res),
+                                  _stream(stream)), allowed=(OK, NOT_CONVERGED, BREAKDOWN, FALLBACK_USED))
+    return x, res.as_dict()

@@ -70,6 +70,32 @@ int make_map_3d(CUtensorMap *map, CUtensorMapDataType dt, size_t esize, const vo
     return GBPCG_OK;
 }
 
+int make_map_nd(CUtensorMap *map, CUtensorMapDataType dt, const void *base, int rank, const uint64_t *dims,
+                const uint64_t *strides, const uint32_t *box) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        set_error("cuTensorMapEncodeTiled is unavailable");
+        return GBPCG_ERR_CUDA;
+    }
+    if (rank < 1 || rank > 5) return fail_arg("tensor map rank");
+    cuuint64_t d[5], st[4];
+    cuuint32_t bx[5], estr[5];
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+        estr[i] = 1;
+        if (i + 1 < rank) st[i] = strides[i];
+    }
+    CUresult r = fn(map, dt, rank, const_cast<void *>(base), d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+        return GBPCG_ERR_CUDA;
+    }
+    return GBPCG_OK;
+}
+
 int check_grid(const gbpcg_grid *g) {
     if (!g) return fail_arg("grid is NULL");
     if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return fail_arg("grid sizes must be positive");

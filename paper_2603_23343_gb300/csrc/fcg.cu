@@ -1,0 +1,433 @@
+// Flexible CG with the learned preconditioner z = N(r) (no counterpart in
+// the paper).  N is nonlinear (ReLU), so the Hestenes-Stiefel beta of plain
+// PCG loses conjugacy; FCG with truncation 1 (Notay, SIAM J. Sci. Comput.
+// 22, 2000) uses beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k) instead, which
+// equals the plain beta whenever N is linear and symmetric.
+//
+// One iteration: q = A p; p.q; fused update (alpha = r.z / p.q on the
+// device; x += alpha p in FP64; r_old = r; r -= alpha q; r.r); z = N(r);
+// fused r.z and z.r_old (beta on the device); p = z + beta p.  The update
+// kernels leave x and p untouched when p.q or r.z fail the descent check,
+// and the host, which reads the scalars once per iteration, switches to
+// Jacobi PCG from the current x (GBPCG_FALLBACK_USED).  At recursive
+// convergence the true residual is recomputed in FP64; if it misses the
+// tolerance, r is replaced by it and FCG restarts (p = z).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "launch.cuh"
+
+namespace gb {
+
+int launch_stencil_f64(const gbpcg_grid &g, const double *p, double *q, cudaStream_t s);
+
+// from nn.cu
+size_t nn_layout_total(int X, int Y, int Z, bool training);
+size_t nn_layout_err_offset();
+bool nn_shape_ok_ext(int X, int Y, int Z);
+int nn_prep_ext(const float *w, void *ws, int X, int Y, int Z, cudaStream_t s);
+int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s);
+
+struct FcgState {
+    double bb, rz, pq, rr, zr, alpha, beta, rr64;
+    int bad;  // 1: p.Ap <= 0 or not finite; 2: r.z <= 0 or not finite
+    int pad;
+    unsigned ticket[4];
+};
+
+constexpr int kFcgThreads = 256;
+constexpr unsigned kFcgMaxBlocks = 2048;
+
+// d (FP64, in place of A x) = b - A x, and its FP32 copy r (optional)
+__global__ void __launch_bounds__(256)
+    fcg_residual_kernel(int64_t n, const double *__restrict__ b, double *__restrict__ ax, float *__restrict__ r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = b[i] - ax[i];
+        ax[i] = d;
+        if (r) r[i] = (float)d;
+    }
+}
+
+__global__ void __launch_bounds__(kFcgThreads)
+    fcg_update_kernel(int64_t n4, FcgState *st, double *partials, double *__restrict__ x, const float *__restrict__ p,
+                      const float *__restrict__ q, float *__restrict__ r, float *__restrict__ rold) {
+    const double pq = st->pq, rz = st->rz;
+    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->bad = 1;
+        return;  // uniform over the grid: no block reaches the reduction
+    }
+    const double alpha = rz / pq;
+    const float af = (float)alpha;
+    double accd = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
+        const float4 pv = reinterpret_cast<const float4 *>(p)[i];
+        const float4 qv = reinterpret_cast<const float4 *>(q)[i];
+        float4 rv = reinterpret_cast<float4 *>(r)[i];
+        reinterpret_cast<float4 *>(rold)[i] = rv;
+        double2 *x2 = reinterpret_cast<double2 *>(x) + 2 * i;
+        double2 xa = x2[0], xb = x2[1];
+        xa.x = fma(alpha, (double)pv.x, xa.x);
+        xa.y = fma(alpha, (double)pv.y, xa.y);
+        xb.x = fma(alpha, (double)pv.z, xb.x);
+        xb.y = fma(alpha, (double)pv.w, xb.y);
+        x2[0] = xa;
+        x2[1] = xb;
+        rv.x = fmaf(-af, qv.x, rv.x);
+        rv.y = fmaf(-af, qv.y, rv.y);
+        rv.z = fmaf(-af, qv.z, rv.z);
+        rv.w = fmaf(-af, qv.w, rv.w);
+        reinterpret_cast<float4 *>(r)[i] = rv;
+        accd += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+    }
+    __shared__ double red[kFcgThreads / 32];
+    const double s = warp_sum(accd);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double part[1] = {0.0}, tot[1];
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kFcgThreads / 32; ++w) part[0] += red[w];
+    if (grid_sum_last<1, kFcgThreads>(part, partials, &st->ticket[0], tot) && threadIdx.x == 0) {
+        st->rr = tot[0];
+        st->alpha = alpha;
+    }
+}
+
+// r.z and z.r_old; beta = (r.z - z.r_old) / (previous r.z); r.z replaces it
+__global__ void __launch_bounds__(kFcgThreads)
+    fcg_dual_dot_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ r,
+                        const float *__restrict__ z, const float *__restrict__ rold) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
+        const float4 rv = reinterpret_cast<const float4 *>(r)[i];
+        const float4 zv = reinterpret_cast<const float4 *>(z)[i];
+        const float4 ov = reinterpret_cast<const float4 *>(rold)[i];
+        a0 += (double)(rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w);
+        a1 += (double)(ov.x * zv.x + ov.y * zv.y + ov.z * zv.z + ov.w * zv.w);
+    }
+    __shared__ double red[kFcgThreads / 32][2];
+    const double s0 = warp_sum(a0), s1 = warp_sum(a1);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][0] = s0, red[threadIdx.x >> 5][1] = s1;
+    __syncthreads();
+    double part[2] = {0.0, 0.0}, tot[2];
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kFcgThreads / 32; ++w) part[0] += red[w][0], part[1] += red[w][1];
+    if (grid_sum_last<2, kFcgThreads>(part, partials, &st->ticket[1], tot) && threadIdx.x == 0) {
+        const double rz_new = tot[0];
+        if (!(rz_new > 0.0) || !isfinite(rz_new) || !isfinite(tot[1])) {
+            st->bad = 2;
+        } else {
+            st->zr = tot[1];
+            st->beta = (rz_new - tot[1]) / st->rz;
+            st->rz = rz_new;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    fcg_p_kernel(int64_t n4, const FcgState *st, const float *__restrict__ z, float *__restrict__ p) {
+    if (st->bad) return;
+    const float b = (float)st->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 zv = reinterpret_cast<const float4 *>(z)[i];
+        float4 pv = reinterpret_cast<float4 *>(p)[i];
+        pv.x = fmaf(b, pv.x, zv.x);
+        pv.y = fmaf(b, pv.y, zv.y);
+        pv.z = fmaf(b, pv.z, zv.z);
+        pv.w = fmaf(b, pv.w, zv.w);
+        reinterpret_cast<float4 *>(p)[i] = pv;
+    }
+}
+
+struct FcgLayout {
+    size_t state, partials, dotws, r, rold, z, p, q, d64, nn, pcg, total;
+};
+
+static gbpcg_opts fallback_opts(const gbpcg_opts &o) {
+    gbpcg_opts f;
+    memset(&f, 0, sizeof(f));
+    f.tol = o.tol;
+    f.maxit = o.maxit;
+    f.precond = GBPCG_PRECOND_JACOBI;
+    f.storage = GBPCG_F32;
+    f.io_dtype = GBPCG_F64;
+    return f;
+}
+
+static int fcg_layout(const gbpcg_grid &g, const gbpcg_opts &o, FcgLayout *L) {
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return at;
+    };
+    L->state = take(sizeof(FcgState));
+    L->partials = take(sizeof(double) * 2 * kFcgMaxBlocks);
+    L->dotws = take(gbpcg_dot_workspace_size());
+    L->r = take(n * 4);
+    L->rold = take(n * 4);
+    L->z = take(n * 4);
+    L->p = take(n * 4);
+    L->q = take(n * 4);
+    L->d64 = take(n * 8);
+    L->nn = take(nn_layout_total(g.nx, g.ny, g.nz, false));
+    gbpcg_opts f = fallback_opts(o);
+    size_t pcg_bytes = 0;
+    int rc = gbpcg_workspace_size(&g, &f, &pcg_bytes);
+    if (rc) return rc;
+    L->pcg = take(pcg_bytes);
+    L->total = off;
+    return GBPCG_OK;
+}
+
+static int fcg_check(const gbpcg_grid *g, const gbpcg_opts *o) {
+    int rc = check_grid(g);
+    if (rc) return rc;
+    if (!o) return fail_arg("opts is NULL");
+    if (o->precond != GBPCG_PRECOND_LEARNED) return fail_arg("gbpcg_fcg_solve needs opts->precond = LEARNED");
+    if (o->io_dtype != GBPCG_F64) return fail_arg("gbpcg_fcg_solve needs FP64 b and x (io_dtype F64)");
+    if (o->storage != GBPCG_F32) return fail_arg("gbpcg_fcg_solve iterates in FP32 (storage F32)");
+    if (o->flags & GBPCG_FLAG_HOST_IO) return fail_arg("gbpcg_fcg_solve takes device b and x");
+    if (!(o->tol > 0.0) || o->maxit < 0) return fail_arg("tol must be > 0 and maxit >= 0");
+    if (!nn_shape_ok_ext(g->nx, g->ny, g->nz))
+        return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels");
+    return GBPCG_OK;
+}
+
+static unsigned red_blocks(int64_t n4) {
+    const int64_t want = (n4 + kFcgThreads * 8 - 1) / (kFcgThreads * 8);
+    return (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>({want, (int64_t)device_sm_count() * 4, (int64_t)kFcgMaxBlocks}));
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+extern "C" int gbpcg_fcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t *bytes) {
+    clear_error();
+    if (!bytes) return fail_arg("bytes is NULL");
+    int rc = fcg_check(grid, opts);
+    if (rc) return rc;
+    FcgLayout L;
+    rc = fcg_layout(*grid, *opts, &L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return GBPCG_OK;
+}
+
+extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const void *b_, void *x_,
+                               const gbpcg_opts *opts, gbpcg_result *result, gbpcg_stream stream) {
+    clear_error();
+    int rc = fcg_check(grid, opts);
+    if (rc) return rc;
+    if (!w || !b_ || !x_ || !result) return fail_arg("NULL argument");
+    if ((reinterpret_cast<uintptr_t>(b_) | reinterpret_cast<uintptr_t>(x_)) & 15u)
+        return fail_arg("b and x must be 16-byte aligned");
+    FcgLayout L;
+    rc = fcg_layout(*grid, *opts, &L);
+    if (rc) return rc;
+    if (!opts->workspace || opts->workspace_bytes < L.total) return fail_arg("workspace too small");
+    if (reinterpret_cast<uintptr_t>(opts->workspace) & 255u) return fail_arg("workspace must be 256-byte aligned");
+    const gbpcg_grid &g = *grid;
+    const double *b = static_cast<const double *>(b_);
+    double *x = static_cast<double *>(x_);
+    cudaStream_t s = (cudaStream_t)stream;
+    char *base = static_cast<char *>(opts->workspace);
+    FcgState *st = reinterpret_cast<FcgState *>(base + L.state);
+    double *partials = reinterpret_cast<double *>(base + L.partials);
+    void *dotws = base + L.dotws;
+    float *r = reinterpret_cast<float *>(base + L.r), *rold = reinterpret_cast<float *>(base + L.rold),
+          *z = reinterpret_cast<float *>(base + L.z), *p = reinterpret_cast<float *>(base + L.p),
+          *q = reinterpret_cast<float *>(base + L.q);
+    double *d64 = reinterpret_cast<double *>(base + L.d64);
+    void *nnws = base + L.nn;
+    const int64_t n = (int64_t)g.nx * g.ny * g.nz, n4 = n / 4;
+    const size_t dws = gbpcg_dot_workspace_size();
+    const unsigned rb = red_blocks(n4);
+    const unsigned eb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count() * 16));
+
+    memset(result, 0, sizeof(*result));
+    cudaEvent_t e0, e1, n0, n1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    GB_CUDA(cudaEventCreate(&n0));
+    GB_CUDA(cudaEventCreate(&n1));
+    struct EvGuard {
+        cudaEvent_t a, b, c, d;
+        ~EvGuard() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            cudaEventDestroy(c);
+            cudaEventDestroy(d);
+        }
+    } guard{e0, e1, n0, n1};
+
+    FcgState hs;
+    memset(&hs, 0, sizeof(hs));
+    int herr = 0;
+    auto pull = [&]() -> int {
+        GB_CUDA(cudaMemcpyAsync(&hs, st, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaMemcpyAsync(&herr, static_cast<char *>(nnws) + nn_layout_err_offset(), sizeof(int),
+                                cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        return GBPCG_OK;
+    };
+    // r = b - A x in FP64 (d64), its FP32 copy in r, ||r||^2 into st->rr64
+    auto true_residual = [&](bool to_r) -> int {
+        int rc2 = launch_stencil_f64(g, x, d64, s);
+        if (rc2) return rc2;
+        fcg_residual_kernel<<<eb, 256, 0, s>>>(n, b, d64, to_r ? r : nullptr);
+        GB_CUDA(cudaGetLastError());
+        return gbpcg_dot(n, GBPCG_F64, d64, d64, &st->rr64, dotws, dws, stream);
+    };
+    auto precondition = [&]() -> int {
+        GB_CUDA(cudaEventRecord(n0, s));
+        int rc2 = nn_forward_ext(g, r, z, nnws, s);
+        if (rc2) return rc2;
+        GB_CUDA(cudaEventRecord(n1, s));
+        return GBPCG_OK;
+    };
+    double nn_ms = 0.0;
+    auto add_nn_time = [&]() {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, n0, n1) == cudaSuccess) nn_ms += ms;
+    };
+    // restart: z = N(r), r.z, p = z
+    auto restart = [&]() -> int {
+        GB_CUDA(cudaMemsetAsync(&st->bad, 0, sizeof(int), s));
+        int rc2 = precondition();
+        if (rc2) return rc2;
+        rc2 = gbpcg_dot(n, GBPCG_F32, r, z, &st->rz, dotws, dws, stream);
+        if (rc2) return rc2;
+        GB_CUDA(cudaMemcpyAsync(p, z, n * 4, cudaMemcpyDeviceToDevice, s));
+        rc2 = pull();
+        if (rc2) return rc2;
+        add_nn_time();
+        return GBPCG_OK;
+    };
+
+    GB_CUDA(cudaEventRecord(e0, s));
+    GB_CUDA(cudaMemsetAsync(st, 0, sizeof(FcgState), s));
+    GB_CUDA(cudaMemsetAsync(static_cast<char *>(nnws) + nn_layout_err_offset(), 0, sizeof(int), s));
+    rc = nn_prep_ext(w, nnws, g.nx, g.ny, g.nz, s);
+    if (rc) return rc;
+    rc = gbpcg_dot(n, GBPCG_F64, b, b, &st->bb, dotws, dws, stream);
+    if (rc) return rc;
+    rc = true_residual(true);
+    if (rc) return rc;
+    rc = pull();
+    if (rc) return rc;
+    const double bb = hs.bb;
+    int status = GBPCG_NOT_CONVERGED, iters = 0, fcg_iters = 0, replacements = 0;
+    double rel = bb > 0.0 ? std::sqrt(hs.rr64 / bb) : 0.0, rel_true = rel;
+    bool fallback = false;
+    if (bb == 0.0) {
+        GB_CUDA(cudaMemsetAsync(x, 0, n * 8, s));
+        rel = rel_true = 0.0;
+        status = GBPCG_OK;
+    } else if (rel <= opts->tol) {
+        status = GBPCG_OK;
+    } else {
+        rc = restart();
+        if (rc) return rc;
+        if (!(hs.rz > 0.0) || !std::isfinite(hs.rz) || herr) fallback = true;
+        std::vector<double> hist{rel};
+        while (!fallback && iters < opts->maxit) {
+            rc = gbpcg_stencil_apply(&g, GBPCG_F32, p, q, stream);
+            if (rc) return rc;
+            rc = gbpcg_dot(n, GBPCG_F32, p, q, &st->pq, dotws, dws, stream);
+            if (rc) return rc;
+            fcg_update_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, x, p, q, r, rold);
+            GB_CUDA(cudaGetLastError());
+            rc = precondition();
+            if (rc) return rc;
+            fcg_dual_dot_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, r, z, rold);
+            GB_CUDA(cudaGetLastError());
+            fcg_p_kernel<<<eb, 256, 0, s>>>(n4, st, z, p);
+            GB_CUDA(cudaGetLastError());
+            rc = pull();
+            if (rc) return rc;
+            add_nn_time();
+            if (hs.bad == 1 || herr) {  // x untouched: this iteration did not happen
+                fallback = true;
+                break;
+            }
+            ++iters;
+            ++fcg_iters;
+            rel = std::sqrt(hs.rr / bb);
+            hist.push_back(rel);
+            if (!std::isfinite(rel)) {
+                fallback = true;
+                break;
+            }
+            if (rel <= opts->tol) {
+                rc = true_residual(true);
+                if (rc) return rc;
+                rc = pull();
+                if (rc) return rc;
+                rel_true = std::sqrt(hs.rr64 / bb);
+                if (rel_true <= opts->tol) {
+                    status = GBPCG_OK;
+                    break;
+                }
+                ++replacements;
+                rc = restart();
+                if (rc) return rc;
+                if (!(hs.rz > 0.0) || !std::isfinite(hs.rz) || herr) {
+                    fallback = true;
+                    break;
+                }
+                continue;
+            }
+            if (hs.bad == 2) {  // r.z <= 0: N(r) is no descent direction
+                fallback = true;
+                break;
+            }
+            if (hist.size() > 5 && rel > 10.0 * hist[hist.size() - 6]) {
+                fallback = true;
+                break;
+            }
+        }
+    }
+    int fb_iters = 0;
+    if (fallback) {
+        gbpcg_opts f = fallback_opts(*opts);
+        f.maxit = std::max(0, opts->maxit - iters);
+        f.workspace = base + L.pcg;
+        f.workspace_bytes = opts->workspace_bytes - L.pcg;
+        gbpcg_result fr;
+        rc = gbpcg_pcg_solve(&g, b, x, &f, &fr, stream);
+        if (rc == GBPCG_ERR_ARG || rc == GBPCG_ERR_CUDA) return rc;
+        fb_iters = fr.iters;
+        iters += fr.iters;
+        rel = fr.rel_res_recursive;
+        rel_true = fr.rel_res_true;
+        replacements += fr.replacements;
+        status = fr.status == GBPCG_OK ? GBPCG_FALLBACK_USED : fr.status;
+    } else if (status != GBPCG_OK) {
+        rc = true_residual(false);
+        if (rc) return rc;
+        rc = pull();
+        if (rc) return rc;
+        rel_true = std::sqrt(hs.rr64 / bb);
+    }
+    GB_CUDA(cudaEventRecord(e1, s));
+    GB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    result->iters = iters;
+    result->status = status;
+    result->rel_res_recursive = rel;
+    result->rel_res_true = rel_true;
+    result->time_ms = ms;
+    result->pass_ms[0] = nn_ms;
+    result->pass_ms[1] = ms - nn_ms;
+    result->pass_launches[0] = fcg_iters;
+    result->pass_launches[1] = fb_iters;
+    result->replacements = replacements;
+    result->refine_steps = 0;
+    return status;
+}

@@ -1,0 +1,1018 @@
+// Learned preconditioner z = N(r) (no counterpart in the paper, which keeps
+// Jacobi): a three-level 3D U-net of 3x3x3 convolutions without bias,
+// channels-last BF16 activations and weights with FP32 accumulation.
+//
+//   c1 (2->16), c2 (16->16) = e0          level 0 (full resolution)
+//   pool, c3 (16->32), c4 (32->32) = e1   level 1
+//   pool, c5 (32->64), c6 (64->64)        level 2
+//   up, [up(c6), e1] -> c7 (96->32)       level 1
+//   up, [up(c7), e0] -> c8 (48->16)       level 0
+//   c9 (16->1)                            output, no ReLU
+// Input channels: r / rms(r) and log k; output scaled by rms(r) h^2.  pool is
+// a 2x2x2 average, up nearest-neighbour doubling.
+//
+// Convolutions with 16+ input and output channels (c2..c8 and their
+// data-gradient convolutions) run on the tensor cores (conv_tc.cuh); the
+// 2- and 1-channel ends (c1, c9), the weight gradients and the glue run on
+// CUDA cores.  Concatenations are free: c2 and c4 write e0 / e1 straight
+// into the upper channels of the concatenated buffers, the upsampling
+// kernels fill the lower ones.
+#include <algorithm>
+#include <mutex>
+#include <type_traits>
+
+#include "conv_tc.cuh"
+#include "launch.cuh"
+
+namespace gb {
+
+// ------------------------------------------------------------ the network --
+
+struct LayerDesc {
+    int ci, co, level;
+};
+constexpr int kNumLayers = 9;
+constexpr LayerDesc kLayers[kNumLayers] = {{2, 16, 0},  {16, 16, 0}, {16, 32, 1}, {32, 32, 1}, {32, 64, 2},
+                                           {64, 64, 2}, {96, 32, 1}, {48, 16, 0}, {16, 1, 0}};
+constexpr int64_t layer_size(int l) { return (int64_t)kLayers[l].co * 27 * kLayers[l].ci; }
+constexpr int64_t layer_offset(int l) { return l == 0 ? 0 : layer_offset(l - 1) + layer_size(l - 1); }
+constexpr int64_t kNumWeights = layer_offset(kNumLayers);
+static_assert(kNumWeights == GBPCG_NN_NUM_WEIGHTS, "weight count");
+
+// ------------------------------------------------------ small helpers ------
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline unsigned blocks_for(int64_t n, int threads) {
+    return (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((n + threads - 1) / threads, (int64_t)device_sm_count() * 16));
+}
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Tile of the tensor-core convolution for a grid, if it has one.
+inline bool conv_tile(int X, int Y, int Z, ConvTile *t) {
+    if (X % 128 == 0) {
+        *t = {128, 1, 1};
+        return true;
+    }
+    if (128 % X) return false;
+    const int ty = 128 / X;
+    if (Y % ty == 0) {
+        *t = {X, ty, 1};
+        return true;
+    }
+    if (ty % Y) return false;
+    const int tz = ty / Y;
+    if (Z % tz) return false;
+    *t = {X, Y, tz};
+    return true;
+}
+
+// ----------------------------------------------- tensor-core convolution --
+
+template <int CO, typename OUT>
+static int conv_tc_launch(int X, int Y, int Z, int ci, const __nv_bfloat16 *in, const __nv_bfloat16 *w, OUT *out,
+                          int cstride, int coff, int relu, const __nv_bfloat16 *mask, int mstride, int moff, int *err,
+                          cudaStream_t s) {
+    ConvArgs a;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    a.ci = ci;
+    a.co = CO;
+    if (!conv_tile(X, Y, Z, &a.tile)) return fail_arg("grid has no 128-voxel convolution tile");
+    a.out = out;
+    a.cstride = cstride;
+    a.coff = coff;
+    a.relu = relu;
+    a.mask = mask;
+    a.mstride = mstride;
+    a.moff = moff;
+    a.err = err;
+    ConvMaps maps;
+    const uint64_t dims[4] = {(uint64_t)ci, (uint64_t)X, (uint64_t)Y, (uint64_t)Z};
+    const uint64_t strides[3] = {(uint64_t)ci * 2, (uint64_t)ci * 2 * X, (uint64_t)ci * 2 * X * Y};
+    const uint32_t box[4] = {8, (uint32_t)a.tile.tx, (uint32_t)a.tile.ty, (uint32_t)a.tile.tz};
+    int rc = make_map_nd(&maps.act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, in, 4, dims, strides, box);
+    if (rc) return rc;
+    const uint64_t wd[2] = {(uint64_t)27 * ci, (uint64_t)CO};
+    const uint64_t wst[1] = {(uint64_t)27 * ci * 2};
+    const uint32_t wb[2] = {8, (uint32_t)CO};
+    rc = make_map_nd(&maps.wgt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, wd, wst, wb);
+    if (rc) return rc;
+    constexpr uint32_t smem = conv_smem_bytes<CO>();
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(conv3_tc_kernel<CO, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    const int64_t tiles = (int64_t)X * Y * Z / 128;
+    conv3_tc_kernel<CO, OUT><<<(unsigned)tiles, 128, smem, s>>>(maps, a);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_tc launch");
+}
+
+template <typename OUT>
+static int conv_tc(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *in, const __nv_bfloat16 *w, OUT *out,
+                   int cstride, int coff, int relu, const __nv_bfloat16 *mask, int mstride, int moff, int *err,
+                   cudaStream_t s) {
+    switch (co) {
+        case 16: return conv_tc_launch<16, OUT>(X, Y, Z, ci, in, w, out, cstride, coff, relu, mask, mstride, moff, err, s);
+        case 32: return conv_tc_launch<32, OUT>(X, Y, Z, ci, in, w, out, cstride, coff, relu, mask, mstride, moff, err, s);
+        case 48: return conv_tc_launch<48, OUT>(X, Y, Z, ci, in, w, out, cstride, coff, relu, mask, mstride, moff, err, s);
+        case 64: return conv_tc_launch<64, OUT>(X, Y, Z, ci, in, w, out, cstride, coff, relu, mask, mstride, moff, err, s);
+        case 96: return conv_tc_launch<96, OUT>(X, Y, Z, ci, in, w, out, cstride, coff, relu, mask, mstride, moff, err, s);
+        default: return fail_arg("tensor-core convolution output channels must be 16, 32, 48, 64 or 96");
+    }
+}
+
+inline bool conv_tc_ok(int X, int Y, int Z, int ci, int co) {
+    ConvTile t;
+    return ci % 16 == 0 && ci <= 256 && (co == 16 || co == 32 || co == 48 || co == 64 || co == 96) &&
+           conv_tile(X, Y, Z, &t);
+}
+
+// ------------------------------------------------ CUDA-core convolution ----
+// One thread per voxel computes all CO outputs; weights (CO, 27, CI) sit in
+// shared memory as FP32, ordered so that every thread reads the same word.
+
+template <int C, typename T>
+__device__ __forceinline__ void load_ch(const T *p, float v[C]) {
+    if constexpr (C % 8 == 0 && std::is_same<T, __nv_bfloat16>::value) {
+#pragma unroll
+        for (int i = 0; i < C; i += 8) ld8(p + i, v + i);
+    } else {
+#pragma unroll
+        for (int i = 0; i < C; ++i) v[i] = to_f(p[i]);
+    }
+}
+
+template <int CI, int CO, typename TO>
+__global__ void __launch_bounds__(256)
+    conv3_simt_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
+                      TO *__restrict__ out, int relu, const __nv_bfloat16 *__restrict__ mask, int mstride, int moff,
+                      const double *scale) {
+    __shared__ float ws[27 * CI * CO];
+    for (int e = threadIdx.x; e < 27 * CI * CO; e += blockDim.x) {
+        const int o = e / (27 * CI), r = e - o * 27 * CI;  // r = t * CI + i
+        ws[r * CO + o] = __bfloat162float(w[e]);
+    }
+    __syncthreads();
+    const float sc = scale ? (float)*scale : 1.0f;
+    const int64_t n = (int64_t)X * Y * Z;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
+        float acc[CO];
+#pragma unroll
+        for (int o = 0; o < CO; ++o) acc[o] = 0.0f;
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
+            if (xx < 0 || xx >= X || yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
+            float iv[CI];
+            load_ch<CI>(in + (((int64_t)zz * Y + yy) * X + xx) * CI, iv);
+#pragma unroll
+            for (int i = 0; i < CI; ++i)
+#pragma unroll
+                for (int o = 0; o < CO; ++o) acc[o] = fmaf(iv[i], ws[(t * CI + i) * CO + o], acc[o]);
+        }
+        TO *po = out + v * CO;
+#pragma unroll
+        for (int o = 0; o < CO; ++o) {
+            float f = acc[o] * sc;
+            if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
+            if (mask && !(__bfloat162float(mask[v * mstride + moff + o]) > 0.0f)) f = 0.0f;
+            acc[o] = f;
+        }
+        if constexpr (CO % 8 == 0 && std::is_same<TO, __nv_bfloat16>::value) {
+#pragma unroll
+            for (int o = 0; o < CO; o += 8) st8(po + o, acc + o);
+        } else {
+#pragma unroll
+            for (int o = 0; o < CO; ++o) po[o] = from_f<TO>(acc[o]);
+        }
+    }
+}
+
+template <int CI, int CO, typename TO>
+static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out, int relu,
+                            const __nv_bfloat16 *mask, int mstride, int moff, const double *scale, cudaStream_t s) {
+    const int64_t n = (int64_t)X * Y * Z;
+    conv3_simt_kernel<CI, CO, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride, moff,
+                                                                      scale);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_simt launch");
+}
+
+inline bool conv_simt_ok(int ci, int co) { return (ci == 2 && co == 16) || (ci == 16 && co == 1) || (ci == 1 && co == 16); }
+
+template <typename TO>
+static int conv_simt(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out,
+                     int relu, const __nv_bfloat16 *mask, int mstride, int moff, const double *scale, cudaStream_t s) {
+    if (ci == 2 && co == 16) return conv_simt_launch<2, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
+    if (ci == 16 && co == 1) return conv_simt_launch<16, 1, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
+    if (ci == 1 && co == 16) return conv_simt_launch<1, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
+    return fail_arg("no CUDA-core convolution for these channel counts");
+}
+
+// ------------------------------------------------------ weight gradients --
+// gW[o, t, i] = sum_v gy[v, o] x[v + off(t), i].  A block owns up to 256
+// (tap, 4-output, 4-input) register blocks and a range of grid rows; it
+// stages one row segment of W voxels at a time (the 9 input rows it touches,
+// with a one-voxel halo, and the matching gy) in shared memory as FP32 and
+// accumulates outer products.  Each block writes its sums to its own slot of
+// a partial buffer; a second kernel adds the slots in a fixed order.
+
+constexpr int kWgThreads = 256;
+constexpr int kWgTargetBlocks = 608;
+
+__host__ __device__ constexpr int wg_xs_floats(int W, int ci) { return (9 * (W + 2) * ci + 3) & ~3; }
+
+template <int BO, int BI>
+__global__ void __launch_bounds__(kWgThreads)
+    wgrad_kernel(int X, int Y, int Z, int ci, int co, int W, int rows_per_block, const __nv_bfloat16 *__restrict__ x,
+                 const __nv_bfloat16 *__restrict__ gy, float *__restrict__ partials) {
+    extern __shared__ __align__(16) float wsm[];
+    float *xs = wsm;                         // [9][W + 2][ci]
+    float *gs = wsm + wg_xs_floats(W, ci);   // [W][co], 16-byte aligned
+    const int nob = co / BO, nib = ci / BI;
+    const int ncombo = 27 * nob * nib;
+    const int c = blockIdx.y * kWgThreads + threadIdx.x;
+    const bool active = c < ncombo;
+    const int t = active ? c / (nob * nib) : 0;
+    const int ob = active ? (c / nib) % nob : 0;
+    const int ib = active ? c % nib : 0;
+    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const int rk = (dz + 1) * 3 + (dy + 1);
+    float acc[BO][BI];
+#pragma unroll
+    for (int o = 0; o < BO; ++o)
+#pragma unroll
+        for (int i = 0; i < BI; ++i) acc[o][i] = 0.0f;
+
+    const int nrows = Y * Z;
+    const int r0 = blockIdx.x * rows_per_block, r1 = min(nrows, r0 + rows_per_block);
+    const int W2 = W + 2;
+    for (int row = r0; row < r1; ++row) {
+        const int y = row % Y, z = row / Y;
+        for (int x0 = 0; x0 < X; x0 += W) {
+            __syncthreads();
+            // stage x: 9 rows x (W + 2) voxels x ci channels
+            if (ci % 8 == 0) {
+                const int nch = ci / 8, tot = 9 * W2 * nch;
+                for (int e = threadIdx.x; e < tot; e += kWgThreads) {
+                    const int ch = e % nch, j = (e / nch) % W2, rr = e / (nch * W2);
+                    const int xx = x0 - 1 + j, yy = y + rr % 3 - 1, zz = z + rr / 3 - 1;
+                    float v8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    if (xx >= 0 && xx < X && yy >= 0 && yy < Y && zz >= 0 && zz < Z)
+                        ld8(x + (((int64_t)zz * Y + yy) * X + xx) * ci + ch * 8, v8);
+                    float *d = xs + (rr * W2 + j) * ci + ch * 8;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) d[q] = v8[q];
+                }
+            } else {
+                const int tot = 9 * W2 * ci;
+                for (int e = threadIdx.x; e < tot; e += kWgThreads) {
+                    const int ch = e % ci, j = (e / ci) % W2, rr = e / (ci * W2);
+                    const int xx = x0 - 1 + j, yy = y + rr % 3 - 1, zz = z + rr / 3 - 1;
+                    float v = 0.0f;
+                    if (xx >= 0 && xx < X && yy >= 0 && yy < Y && zz >= 0 && zz < Z)
+                        v = __bfloat162float(x[(((int64_t)zz * Y + yy) * X + xx) * ci + ch]);
+                    xs[(rr * W2 + j) * ci + ch] = v;
+                }
+            }
+            // stage gy: W voxels x co channels
+            {
+                const int64_t base = (((int64_t)z * Y + y) * X + x0) * co;
+                for (int e = threadIdx.x; e < W * co; e += kWgThreads) gs[e] = __bfloat162float(gy[base + e]);
+            }
+            __syncthreads();
+            if (active) {
+                const float *xp = xs + (rk * W2 + 1 + dx) * ci + ib * BI;
+                const float *gp = gs + ob * BO;
+#pragma unroll 4
+                for (int v = 0; v < W; ++v) {
+                    float g[BO], xv[BI];
+                    if constexpr (BO == 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(gp + v * co);
+                        g[0] = q.x, g[1] = q.y, g[2] = q.z, g[3] = q.w;
+                    } else {
+#pragma unroll
+                        for (int o = 0; o < BO; ++o) g[o] = gp[v * co + o];
+                    }
+                    if constexpr (BI == 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(xp + v * ci);
+                        xv[0] = q.x, xv[1] = q.y, xv[2] = q.z, xv[3] = q.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < BI; ++i) xv[i] = xp[v * ci + i];
+                    }
+#pragma unroll
+                    for (int o = 0; o < BO; ++o)
+#pragma unroll
+                        for (int i = 0; i < BI; ++i) acc[o][i] = fmaf(g[o], xv[i], acc[o][i]);
+                }
+            }
+        }
+    }
+    if (active) {
+        float *dst = partials + (int64_t)blockIdx.x * (27 * co * ci);
+#pragma unroll
+        for (int o = 0; o < BO; ++o)
+#pragma unroll
+            for (int i = 0; i < BI; ++i) dst[((ob * BO + o) * 27 + t) * ci + ib * BI + i] = acc[o][i];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    sum_slots_kernel(int64_t n, int nslots, const float *__restrict__ partials, float *__restrict__ out) {
+    for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256) {
+        float s = 0.0f;
+        for (int k = 0; k < nslots; ++k) s += partials[(int64_t)k * n + e];
+        out[e] = s;
+    }
+}
+
+struct WgradPlan {
+    int bo, bi, W, ngroups, S, rows_per_block;
+    size_t smem;
+};
+
+inline WgradPlan wgrad_plan(int X, int Y, int Z, int ci, int co) {
+    WgradPlan p;
+    p.bo = co % 4 == 0 ? 4 : 1;
+    p.bi = ci % 4 == 0 ? 4 : ci % 2 == 0 ? 2 : 1;
+    const int ncombo = 27 * (co / p.bo) * (ci / p.bi);
+    p.ngroups = (ncombo + kWgThreads - 1) / kWgThreads;
+    p.W = std::min(X, ci <= 48 ? 32 : 16);
+    const int rows = Y * Z;
+    // about four blocks per SM of a 152-SM part; fixed so that workspace sizes
+    // do not depend on the device that asks
+    const int want = std::max(1, (kWgTargetBlocks + p.ngroups - 1) / p.ngroups);
+    const int S0 = std::min(rows, want);
+    p.rows_per_block = (rows + S0 - 1) / S0;
+    p.S = (rows + p.rows_per_block - 1) / p.rows_per_block;
+    p.smem = (size_t)(wg_xs_floats(p.W, ci) + p.W * co) * sizeof(float);
+    return p;
+}
+
+inline bool wgrad_ok(int X, int ci, int co) {
+    const int W = std::min(X, ci <= 48 ? 32 : 16);
+    return X % W == 0 && (wg_xs_floats(W, ci) + W * co) * 4 <= 200 * 1024;
+}
+
+inline size_t wgrad_partial_bytes(int X, int Y, int Z, int ci, int co) {
+    WgradPlan p = wgrad_plan(X, Y, Z, ci, co);
+    return (size_t)p.S * 27 * ci * co * sizeof(float);
+}
+
+template <int BO, int BI>
+static cudaError_t wgrad_launch(const WgradPlan &p, int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x,
+                                const __nv_bfloat16 *gy, float *partials, cudaStream_t s) {
+    cudaFuncSetAttribute(wgrad_kernel<BO, BI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    wgrad_kernel<BO, BI><<<dim3(p.S, p.ngroups), kWgThreads, p.smem, s>>>(X, Y, Z, ci, co, p.W, p.rows_per_block, x,
+                                                                        gy, partials);
+    return cudaGetLastError();
+}
+
+static int wgrad(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, const __nv_bfloat16 *gy, float *gw,
+                 float *partials, cudaStream_t s) {
+    if (!wgrad_ok(X, ci, co)) return fail_arg("weight gradient: unsupported width or channel count");
+    WgradPlan p = wgrad_plan(X, Y, Z, ci, co);
+    cudaError_t e;
+    if (p.bo == 4 && p.bi == 4) e = wgrad_launch<4, 4>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    else if (p.bo == 4 && p.bi == 2) e = wgrad_launch<4, 2>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    else if (p.bo == 4) e = wgrad_launch<4, 1>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    else if (p.bi == 4) e = wgrad_launch<1, 4>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    else if (p.bi == 2) e = wgrad_launch<1, 2>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    else e = wgrad_launch<1, 1>(p, X, Y, Z, ci, co, x, gy, partials, s);
+    if (e != cudaSuccess) return fail_cuda(e, "wgrad launch");
+    const int64_t n = (int64_t)27 * ci * co;
+    sum_slots_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p.S, partials, gw);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "sum_slots launch");
+}
+
+// --------------------------------------------------------- glue kernels ----
+
+// Network input: channels (r / rms(r), log k); also the output scale rms h^2.
+__global__ void __launch_bounds__(256)
+    nn_input_kernel(int X, int Y, int Z, const float *__restrict__ r, const double *rr, const float *__restrict__ kb,
+                    int kbx, int kby, int kbz, double h2, __nv_bfloat16 *__restrict__ xin, double *scale) {
+    const int64_t n = (int64_t)X * Y * Z;
+    const double rms = sqrt(*rr / (double)n);
+    const float inv = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = rms * h2;
+    const int nbx = (X + kbx - 1) / kbx, nby = (Y + kby - 1) / kby;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        float lk = 0.0f;
+        if (kb) {
+            const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
+            lk = logf(kb[((int64_t)(z / kbz) * nby + y / kby) * nbx + x / kbx]);
+        }
+        __nv_bfloat162 p;
+        p.x = __float2bfloat16_rn(r[v] * inv);
+        p.y = __float2bfloat16_rn(lk);
+        reinterpret_cast<__nv_bfloat162 *>(xin)[v] = p;
+    }
+}
+
+// dst (coarse, C channels) = mean of the 2x2x2 children of src (channels
+// [soff, soff + C) of sstride).  One thread per (coarse voxel, 8 channels).
+__global__ void __launch_bounds__(256)
+    pool2_kernel(int Xc, int Yc, int Zc, int C, const __nv_bfloat16 *__restrict__ src, int sstride, int soff,
+                 __nv_bfloat16 *__restrict__ dst) {
+    const int nc8 = C / 8;
+    const int64_t n = (int64_t)Xc * Yc * Zc * nc8;
+    const int Xf = 2 * Xc, Yf = 2 * Yc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nc8);
+        const int64_t v = e / nc8;
+        const int x = (int)(v % Xc), y = (int)((v / Xc) % Yc), z = (int)(v / ((int64_t)Xc * Yc));
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t f = (((int64_t)(2 * z + (c >> 2)) * Yf + 2 * y + ((c >> 1) & 1)) * Xf + 2 * x + (c & 1));
+            float q[8];
+            ld8(src + f * sstride + soff + ch * 8, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += q[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s[i] *= 0.125f;
+        st8(dst + v * C + ch * 8, s);
+    }
+}
+
+// dst (fine, channels [doff, doff + C) of dstride) = src (coarse, C channels)
+// of the parent voxel.
+__global__ void __launch_bounds__(256)
+    up2_kernel(int Xf, int Yf, int Zf, int C, const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
+               int dstride, int doff) {
+    const int nc8 = C / 8;
+    const int64_t n = (int64_t)Xf * Yf * Zf * nc8;
+    const int Xc = Xf / 2, Yc = Yf / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nc8);
+        const int64_t v = e / nc8;
+        const int x = (int)(v % Xf), y = (int)((v / Xf) % Yf), z = (int)(v / ((int64_t)Xf * Yf));
+        const int64_t pv = ((int64_t)(z / 2) * Yc + y / 2) * Xc + x / 2;
+        *reinterpret_cast<uint4 *>(dst + v * dstride + doff + ch * 8) =
+            *reinterpret_cast<const uint4 *>(src + pv * C + ch * 8);
+    }
+}
+
+// dst (coarse, C channels, BF16) = (sum of the 8 fine children of g, FP32
+// channels [goff, goff + C) of gstride) * (mask > 0): the adjoint of
+// nearest upsampling followed by the ReLU derivative.
+__global__ void __launch_bounds__(256)
+    up2_adjoint_mask_kernel(int Xc, int Yc, int Zc, int C, const float *__restrict__ g, int gstride, int goff,
+                            const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ dst) {
+    const int nc8 = C / 8;
+    const int64_t n = (int64_t)Xc * Yc * Zc * nc8;
+    const int Xf = 2 * Xc, Yf = 2 * Yc;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nc8);
+        const int64_t v = e / nc8;
+        const int x = (int)(v % Xc), y = (int)((v / Xc) % Yc), z = (int)(v / ((int64_t)Xc * Yc));
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int64_t f = (((int64_t)(2 * z + (c >> 2)) * Yf + 2 * y + ((c >> 1) & 1)) * Xf + 2 * x + (c & 1));
+            float q[8];
+            ld8(g + f * gstride + goff + ch * 8, q);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += q[i];
+        }
+        float m[8];
+        ld8(mask + v * C + ch * 8, m);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s[i] = m[i] > 0.0f ? s[i] : 0.0f;
+        st8(dst + v * C + ch * 8, s);
+    }
+}
+
+// dst (fine, C channels, BF16) = (skip + t(parent) / 8) * (mask > 0): the
+// gradient reaching a skip connection, plus the adjoint of average pooling
+// of the coarse gradient t, times the ReLU derivative.
+__global__ void __launch_bounds__(256)
+    pool_adjoint_skip_mask_kernel(int Xf, int Yf, int Zf, int C, const float *__restrict__ skip, int sstride, int soff,
+                                  const float *__restrict__ t, const __nv_bfloat16 *__restrict__ mask, int mstride,
+                                  int moff, __nv_bfloat16 *__restrict__ dst) {
+    const int nc8 = C / 8;
+    const int64_t n = (int64_t)Xf * Yf * Zf * nc8;
+    const int Xc = Xf / 2, Yc = Yf / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)(e % nc8);
+        const int64_t v = e / nc8;
+        const int x = (int)(v % Xf), y = (int)((v / Xf) % Yf), z = (int)(v / ((int64_t)Xf * Yf));
+        const int64_t pv = ((int64_t)(z / 2) * Yc + y / 2) * Xc + x / 2;
+        float a[8], b[8], m[8];
+        ld8(skip + v * sstride + soff + ch * 8, a);
+        ld8(t + pv * C + ch * 8, b);
+        ld8(mask + v * mstride + moff + ch * 8, m);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = m[i] > 0.0f ? fmaf(b[i], 0.125f, a[i]) : 0.0f;
+        st8(dst + v * C + ch * 8, a);
+    }
+}
+
+// g_out = dL/d(network output) = dL/dz * scale, rounded to BF16.
+__global__ void __launch_bounds__(256)
+    scale_to_bf16_kernel(int64_t n, const float *__restrict__ gz, const double *scale, __nv_bfloat16 *__restrict__ out) {
+    const float sc = (float)*scale;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = __float2bfloat16_rn(gz[v] * sc);
+}
+
+struct WeightTable {
+    int64_t off[kNumLayers + 1];
+    int ci[kNumLayers], co[kNumLayers];
+};
+
+inline WeightTable weight_table() {
+    WeightTable t;
+    for (int l = 0; l <= kNumLayers; ++l) t.off[l] = layer_offset(l);
+    for (int l = 0; l < kNumLayers; ++l) t.ci[l] = kLayers[l].ci, t.co[l] = kLayers[l].co;
+    return t;
+}
+
+// BF16 copies of the FP32 master weights: wf in the forward layout (Co, 27,
+// Ci) and wflip[i, t, o] = W[o, 26 - t, i], the weights of the adjoint
+// convolution (taps mirrored, channel roles swapped).
+__global__ void __launch_bounds__(256)
+    weight_prep_kernel(const WeightTable tab, const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf,
+                       __nv_bfloat16 *__restrict__ wflip) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tab.off[kNumLayers];
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (e >= tab.off[l + 1]) ++l;
+        const int64_t r = e - tab.off[l];
+        const int ci = tab.ci[l], co = tab.co[l];
+        const int i = (int)(r % ci), t = (int)((r / ci) % 27), o = (int)(r / (27 * ci));
+        const __nv_bfloat16 b = __float2bfloat16_rn(w[e]);
+        wf[e] = b;
+        if (wflip) wflip[tab.off[l] + ((int64_t)i * 27 + (26 - t)) * co + o] = b;
+    }
+}
+
+// Adam (Kingma & Ba 2015) with bias correction, FP32 state; omb1 = 1 - b1
+// and omb2 = 1 - b2 come from the host in double (1 - (float)0.999 is 1.3e-5
+// off 1e-3).
+__global__ void __launch_bounds__(256)
+    adam_kernel(int64_t n, float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
+                float *__restrict__ v, float lr, float b1, float omb1, float b2, float omb2, float eps, float bc1,
+                float bc2) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float ge = g[e];
+        const float me = b1 * m[e] + omb1 * ge;
+        const float ve = b2 * v[e] + omb2 * ge * ge;
+        m[e] = me;
+        v[e] = ve;
+        w[e] -= lr * (me / bc1) / (sqrtf(ve / bc2) + eps);
+    }
+}
+
+// Scale-free, sign-aware A-norm loss of one pair: with a = z.Ae, c = z.Az,
+// E = e.Ae,
+//   loss = 1/2 (1 - a |a| / (c E))  (= 1/2 ||s z - e||_A^2 / E, s = a / c,
+//          for a >= 0; rising to 1 for negative multiples of e),
+//   gz = dloss/dz = (|a| / (c E)) (s A z - A e).
+// gz holds A z on entry.  z = 0 (c = 0) gives loss 1/2 and the gradient
+// -A e / E of the unscaled loss there.
+__global__ void __launch_bounds__(256)
+    loss_finish_kernel(int64_t n, const double *sc, float *__restrict__ gz, const float *__restrict__ ae, double *loss) {
+    const double a = sc[0], c = sc[1], E = sc[2];
+    double coef = 0.0, sdir = 0.0, l = 0.0;
+    if (c > 0.0 && E > 0.0) {
+        coef = fabs(a) / (c * E);
+        sdir = a / c;
+        l = 0.5 * (1.0 - a * fabs(a) / (c * E));
+    } else if (E > 0.0) {
+        coef = 1.0 / E;
+        sdir = 0.0;
+        l = 0.5;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && loss) *loss = l;
+    const float fc = (float)coef, fs = (float)sdir;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        gz[v] = fc * fmaf(fs, gz[v], -ae[v]);
+}
+
+// ------------------------------------------------------ workspace layout --
+
+struct NnLayout {
+    int X[3], Y[3], Z[3];
+    int64_t V[3];
+    size_t wf, wflip, scal, err, dotws;
+    size_t xin, a1, k8, p1, a3, k7, p2, a5, a6, a7, a8;
+    size_t gout, ga8, gk8, ga7, gk7, ga6, ga5, t5, ge1b, ga3, t3, ge0b, ga1, part;
+    size_t lae;  // loss scratch: A e
+    size_t total;
+};
+// device scalars at layout.scal (doubles); S_LA..S_LE: z.Ae, z.Az, e.Ae
+enum { S_RR = 0, S_SCALE, S_LA, S_LC, S_LE, S_LOSS, S_COUNT };
+
+inline bool nn_shape_ok(int X, int Y, int Z) {
+    if (X % 4 || Y % 4 || Z % 4) return false;
+    for (int l = 0; l < 3; ++l) {
+        ConvTile t;
+        if (!conv_tile(X >> l, Y >> l, Z >> l, &t)) return false;
+    }
+    return true;
+}
+
+inline NnLayout nn_layout(int X, int Y, int Z, bool training) {
+    NnLayout L;
+    for (int l = 0; l < 3; ++l) {
+        L.X[l] = X >> l, L.Y[l] = Y >> l, L.Z[l] = Z >> l;
+        L.V[l] = (int64_t)L.X[l] * L.Y[l] * L.Z[l];
+    }
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    const size_t B = 2, F = 4;
+    L.wf = take(kNumWeights * B);
+    L.wflip = take(kNumWeights * B);
+    L.scal = take(S_COUNT * sizeof(double));
+    L.err = take(sizeof(int));
+    L.dotws = take(gbpcg_dot_workspace_size());
+    L.xin = take(L.V[0] * 2 * B);
+    L.a1 = take(L.V[0] * 16 * B);
+    L.k8 = take(L.V[0] * 48 * B);
+    L.p1 = take(L.V[1] * 16 * B);
+    L.a3 = take(L.V[1] * 32 * B);
+    L.k7 = take(L.V[1] * 96 * B);
+    L.p2 = take(L.V[2] * 32 * B);
+    L.a5 = take(L.V[2] * 64 * B);
+    L.a6 = take(L.V[2] * 64 * B);
+    L.a7 = take(L.V[1] * 32 * B);
+    L.a8 = take(L.V[0] * 16 * B);
+    if (training) {
+        L.gout = take(L.V[0] * B);
+        L.ga8 = take(L.V[0] * 16 * B);
+        L.gk8 = take(L.V[0] * 48 * F);
+        L.ga7 = take(L.V[1] * 32 * B);
+        L.gk7 = take(L.V[1] * 96 * F);
+        L.ga6 = take(L.V[2] * 64 * B);
+        L.ga5 = take(L.V[2] * 64 * B);
+        L.t5 = take(L.V[2] * 32 * F);
+        L.ge1b = take(L.V[1] * 32 * B);
+        L.ga3 = take(L.V[1] * 32 * B);
+        L.t3 = take(L.V[1] * 16 * F);
+        L.ge0b = take(L.V[0] * 16 * B);
+        L.ga1 = take(L.V[0] * 16 * B);
+        size_t pb = 0;
+        for (int l = 0; l < kNumLayers; ++l) {
+            const int lv = kLayers[l].level;
+            pb = std::max(pb, wgrad_partial_bytes(L.X[lv], L.Y[lv], L.Z[lv], kLayers[l].ci, kLayers[l].co));
+        }
+        L.part = take(pb);
+        L.lae = take(L.V[0] * F);
+    } else {
+        L.gout = L.ga8 = L.gk8 = L.ga7 = L.gk7 = L.ga6 = L.ga5 = L.t5 = L.ge1b = L.ga3 = L.t3 = L.ge0b = L.ga1 =
+            L.part = L.lae = 0;
+    }
+    L.total = o;
+    return L;
+}
+
+struct NnPtrs {
+    char *base;
+    template <typename T>
+    T *at(size_t off) const {
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+using bf16 = __nv_bfloat16;
+
+#define GB_TRY(expr)                     \
+    do {                                 \
+        int _rc = (expr);                \
+        if (_rc != GBPCG_OK) return _rc; \
+    } while (0)
+
+// ----------------------------------------------------------- forward -------
+
+int nn_weight_prep(const float *w, void *ws, const NnLayout &L, cudaStream_t s) {
+    NnPtrs P{static_cast<char *>(ws)};
+    weight_prep_kernel<<<blocks_for(kNumWeights, 256), 256, 0, s>>>(weight_table(), w, P.at<bf16>(L.wf),
+                                                                     P.at<bf16>(L.wflip));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "weight_prep launch");
+}
+
+// z = N(r) with the BF16 weights already in the workspace.
+int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, const NnLayout &L, cudaStream_t s) {
+    NnPtrs P{static_cast<char *>(ws)};
+    const int X0 = L.X[0], Y0 = L.Y[0], Z0 = L.Z[0], X1 = L.X[1], Y1 = L.Y[1], Z1 = L.Z[1], X2 = L.X[2], Y2 = L.Y[2],
+              Z2 = L.Z[2];
+    const bf16 *wf = P.at<bf16>(L.wf);
+    auto W = [&](int l) { return wf + layer_offset(l); };
+    double *sc = P.at<double>(L.scal);
+    int *err = P.at<int>(L.err);
+    GB_TRY(gbpcg_dot(L.V[0], GBPCG_F32, r, r, sc + S_RR, P.base + L.dotws, gbpcg_dot_workspace_size(),
+                     (gbpcg_stream)s));
+    const int nmax = std::max(X0, std::max(Y0, Z0));
+    const double h = 1.0 / (nmax + 1);
+    nn_input_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, r, sc + S_RR, g.k_block, g.kbx, g.kby, g.kbz,
+                                                            h * h, P.at<bf16>(L.xin), sc + S_SCALE);
+    GB_CUDA(cudaGetLastError());
+    bf16 *a1 = P.at<bf16>(L.a1), *k8 = P.at<bf16>(L.k8), *p1 = P.at<bf16>(L.p1), *a3 = P.at<bf16>(L.a3),
+         *k7 = P.at<bf16>(L.k7), *p2 = P.at<bf16>(L.p2), *a5 = P.at<bf16>(L.a5), *a6 = P.at<bf16>(L.a6),
+         *a7 = P.at<bf16>(L.a7), *a8 = P.at<bf16>(L.a8);
+    GB_TRY(conv_simt<bf16>(X0, Y0, Z0, 2, 16, P.at<bf16>(L.xin), W(0), a1, 1, nullptr, 0, 0, nullptr, s));
+    GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 16, 16, a1, W(1), k8, 48, 32, 1, nullptr, 0, 0, err, s));
+    pool2_kernel<<<blocks_for(L.V[1] * 2, 256), 256, 0, s>>>(X1, Y1, Z1, 16, k8, 48, 32, p1);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 16, 32, p1, W(2), a3, 32, 0, 1, nullptr, 0, 0, err, s));
+    GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 32, 32, a3, W(3), k7, 96, 64, 1, nullptr, 0, 0, err, s));
+    pool2_kernel<<<blocks_for(L.V[2] * 4, 256), 256, 0, s>>>(X2, Y2, Z2, 32, k7, 96, 64, p2);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 32, 64, p2, W(4), a5, 64, 0, 1, nullptr, 0, 0, err, s));
+    GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 64, 64, a5, W(5), a6, 64, 0, 1, nullptr, 0, 0, err, s));
+    up2_kernel<<<blocks_for(L.V[1] * 8, 256), 256, 0, s>>>(X1, Y1, Z1, 64, a6, k7, 96, 0);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 96, 32, k7, W(6), a7, 32, 0, 1, nullptr, 0, 0, err, s));
+    up2_kernel<<<blocks_for(L.V[0] * 4, 256), 256, 0, s>>>(X0, Y0, Z0, 32, a7, k8, 48, 0);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 48, 16, k8, W(7), a8, 16, 0, 1, nullptr, 0, 0, err, s));
+    GB_TRY(conv_simt<float>(X0, Y0, Z0, 16, 1, a8, W(8), z, 0, nullptr, 0, 0, sc + S_SCALE, s));
+    return GBPCG_OK;
+}
+
+// Gradients of every weight given gz = dL/dz, from the activations the last
+// forward left in the workspace.
+int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cudaStream_t s) {
+    NnPtrs P{static_cast<char *>(ws)};
+    const int X0 = L.X[0], Y0 = L.Y[0], Z0 = L.Z[0], X1 = L.X[1], Y1 = L.Y[1], Z1 = L.Z[1], X2 = L.X[2], Y2 = L.Y[2],
+              Z2 = L.Z[2];
+    const bf16 *wflip = P.at<bf16>(L.wflip);
+    auto WT = [&](int l) { return wflip + layer_offset(l); };
+    auto G = [&](int l) { return gw + layer_offset(l); };
+    double *sc = P.at<double>(L.scal);
+    int *err = P.at<int>(L.err);
+    float *part = P.at<float>(L.part);
+    const bf16 *xin = P.at<bf16>(L.xin), *a1 = P.at<bf16>(L.a1), *k8 = P.at<bf16>(L.k8), *p1 = P.at<bf16>(L.p1),
+               *a3 = P.at<bf16>(L.a3), *k7 = P.at<bf16>(L.k7), *p2 = P.at<bf16>(L.p2), *a5 = P.at<bf16>(L.a5),
+               *a6 = P.at<bf16>(L.a6), *a7 = P.at<bf16>(L.a7), *a8 = P.at<bf16>(L.a8);
+    bf16 *gout = P.at<bf16>(L.gout), *ga8 = P.at<bf16>(L.ga8), *ga7 = P.at<bf16>(L.ga7), *ga6 = P.at<bf16>(L.ga6),
+         *ga5 = P.at<bf16>(L.ga5), *ge1b = P.at<bf16>(L.ge1b), *ga3 = P.at<bf16>(L.ga3), *ge0b = P.at<bf16>(L.ge0b),
+         *ga1 = P.at<bf16>(L.ga1);
+    float *gk8 = P.at<float>(L.gk8), *gk7 = P.at<float>(L.gk7), *t5 = P.at<float>(L.t5), *t3 = P.at<float>(L.t3);
+
+    scale_to_bf16_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.V[0], gz, sc + S_SCALE, gout);
+    GB_CUDA(cudaGetLastError());
+    // c9 (16 -> 1)
+    GB_TRY(wgrad(X0, Y0, Z0, 16, 1, a8, gout, G(8), part, s));
+    GB_TRY(conv_simt<bf16>(X0, Y0, Z0, 1, 16, gout, WT(8), ga8, 0, a8, 16, 0, nullptr, s));
+    // c8 (48 -> 16) on k8 = [up(a7), e0]
+    GB_TRY(wgrad(X0, Y0, Z0, 48, 16, k8, ga8, G(7), part, s));
+    GB_TRY(conv_tc<float>(X0, Y0, Z0, 16, 48, ga8, WT(7), gk8, 48, 0, 0, nullptr, 0, 0, err, s));
+    up2_adjoint_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk8, 48, 0, a7, ga7);
+    GB_CUDA(cudaGetLastError());
+    // c7 (96 -> 32) on k7 = [up(a6), e1]
+    GB_TRY(wgrad(X1, Y1, Z1, 96, 32, k7, ga7, G(6), part, s));
+    GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 96, ga7, WT(6), gk7, 96, 0, 0, nullptr, 0, 0, err, s));
+    up2_adjoint_mask_kernel<<<blocks_for(L.V[2] * 8, 256), 256, 0, s>>>(X2, Y2, Z2, 64, gk7, 96, 0, a6, ga6);
+    GB_CUDA(cudaGetLastError());
+    // c6 (64 -> 64), c5 (32 -> 64)
+    GB_TRY(wgrad(X2, Y2, Z2, 64, 64, a5, ga6, G(5), part, s));
+    GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 64, 64, ga6, WT(5), ga5, 64, 0, 0, a5, 64, 0, err, s));
+    GB_TRY(wgrad(X2, Y2, Z2, 32, 64, p2, ga5, G(4), part, s));
+    GB_TRY(conv_tc<float>(X2, Y2, Z2, 64, 32, ga5, WT(4), t5, 32, 0, 0, nullptr, 0, 0, err, s));
+    // e1: skip gradient (gk7 channels 64..95) + pooled-path gradient, ReLU mask
+    pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk7, 96, 64, t5, k7, 96,
+                                                                              64, ge1b);
+    GB_CUDA(cudaGetLastError());
+    // c4 (32 -> 32), c3 (16 -> 32)
+    GB_TRY(wgrad(X1, Y1, Z1, 32, 32, a3, ge1b, G(3), part, s));
+    GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 32, 32, ge1b, WT(3), ga3, 32, 0, 0, a3, 32, 0, err, s));
+    GB_TRY(wgrad(X1, Y1, Z1, 16, 32, p1, ga3, G(2), part, s));
+    GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 16, ga3, WT(2), t3, 16, 0, 0, nullptr, 0, 0, err, s));
+    // e0: skip gradient (gk8 channels 32..47) + pooled-path gradient, ReLU mask
+    pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[0] * 2, 256), 256, 0, s>>>(X0, Y0, Z0, 16, gk8, 48, 32, t3, k8, 48,
+                                                                              32, ge0b);
+    GB_CUDA(cudaGetLastError());
+    // c2 (16 -> 16), c1 (2 -> 16)
+    GB_TRY(wgrad(X0, Y0, Z0, 16, 16, a1, ge0b, G(1), part, s));
+    GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 16, 16, ge0b, WT(1), ga1, 16, 0, 0, a1, 16, 0, err, s));
+    GB_TRY(wgrad(X0, Y0, Z0, 2, 16, xin, ga1, G(0), part, s));
+    return GBPCG_OK;
+}
+
+int nn_check(const gbpcg_grid *g, const void *ws, size_t ws_bytes, bool training, NnLayout *L) {
+    GB_TRY(check_grid(g));
+    if (!nn_shape_ok(g->nx, g->ny, g->nz))
+        return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels "
+                        "(e.g. powers of two >= 32)");
+    *L = nn_layout(g->nx, g->ny, g->nz, training);
+    if (!ws || ws_bytes < L->total) return fail_arg("learned preconditioner: workspace too small");
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return fail_arg("workspace must be 256-byte aligned");
+    return GBPCG_OK;
+}
+
+// scale-free A-norm loss and its gradient (loss_finish_kernel)
+static int nn_loss_ws(const gbpcg_grid &g, const float *z, const float *e, float *gz, double *loss, void *ws,
+                      const NnLayout &L, cudaStream_t s) {
+    NnPtrs P{static_cast<char *>(ws)};
+    double *sc = P.at<double>(L.scal);
+    float *ae = P.at<float>(L.lae);
+    const int64_t n = L.V[0];
+    void *dws = P.base + L.dotws;
+    const size_t dwb = gbpcg_dot_workspace_size();
+    gbpcg_stream st = (gbpcg_stream)s;
+    GB_TRY(gbpcg_stencil_apply(&g, GBPCG_F32, z, gz, st));
+    GB_TRY(gbpcg_stencil_apply(&g, GBPCG_F32, e, ae, st));
+    GB_TRY(gbpcg_dot(n, GBPCG_F32, z, ae, sc + S_LA, dws, dwb, st));
+    GB_TRY(gbpcg_dot(n, GBPCG_F32, z, gz, sc + S_LC, dws, dwb, st));
+    GB_TRY(gbpcg_dot(n, GBPCG_F32, e, ae, sc + S_LE, dws, dwb, st));
+    loss_finish_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, sc + S_LA, gz, ae, loss ? loss : sc + S_LOSS);
+    GB_CUDA(cudaGetLastError());
+    return GBPCG_OK;
+}
+
+// entry points of the flexible-CG solver (fcg.cu)
+size_t nn_layout_total(int X, int Y, int Z, bool training) { return nn_layout(X, Y, Z, training).total; }
+size_t nn_layout_err_offset() { return nn_layout(128, 128, 128, false).err; }
+bool nn_shape_ok_ext(int X, int Y, int Z) { return nn_shape_ok(X, Y, Z); }
+int nn_prep_ext(const float *w, void *ws, int X, int Y, int Z, cudaStream_t s) {
+    return nn_weight_prep(w, ws, nn_layout(X, Y, Z, false), s);
+}
+int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s) {
+    return nn_forward_prepped(g, r, z, ws, nn_layout(g.nx, g.ny, g.nz, false), s);
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+// ------------------------------------------------------------------ C ABI --
+
+extern "C" int gbpcg_conv3_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, size_t *bytes) {
+    clear_error();
+    if (!bytes) return fail_arg("bytes is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0 || ci <= 0 || co <= 0) return fail_arg("sizes must be positive");
+    size_t b = 256 + align_up((size_t)27 * ci * co * 2, 256);
+    if (wgrad_ok(nx, ci, co)) b += wgrad_partial_bytes(nx, ny, nz, ci, co);
+    *bytes = b;
+    return GBPCG_OK;
+}
+
+static int conv_args(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *a, const void *b,
+                     const void *c, const void *ws, size_t ws_bytes) {
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail_arg("grid sizes must be positive");
+    if ((int64_t)nx * ny * nz > ((int64_t)1 << 34)) return fail_arg("grid too large");
+    if (!a || !b || !c) return fail_arg("NULL array");
+    if (!aligned16(a) || !aligned16(b) || !aligned16(c)) return fail_arg("arrays must be 16-byte aligned");
+    size_t need = 0;
+    int rc = gbpcg_conv3_workspace_size(nx, ny, nz, ci, co, &need);
+    if (rc) return rc;
+    if (!ws || ws_bytes < need) return fail_arg("workspace too small");
+    if (reinterpret_cast<uintptr_t>(ws) & 255u) return fail_arg("workspace must be 256-byte aligned");
+    return GBPCG_OK;
+}
+
+extern "C" int gbpcg_conv3_forward(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x,
+                                   const void *w, float *y, int32_t relu, void *workspace, size_t workspace_bytes,
+                                   gbpcg_stream stream) {
+    clear_error();
+    GB_TRY(conv_args(nx, ny, nz, ci, co, x, w, y, workspace, workspace_bytes));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bf16 *xi = static_cast<const bf16 *>(x), *wi = static_cast<const bf16 *>(w);
+    int *err = static_cast<int *>(workspace);
+    if (conv_tc_ok(nx, ny, nz, ci, co))
+        return conv_tc<float>(nx, ny, nz, ci, co, xi, wi, y, co, 0, relu, nullptr, 0, 0, err, s);
+    if (conv_simt_ok(ci, co)) return conv_simt<float>(nx, ny, nz, ci, co, xi, wi, y, relu, nullptr, 0, 0, nullptr, s);
+    return fail_arg("unsupported convolution shape or channel counts");
+}
+
+__global__ void flip_one_kernel(int ci, int co, const bf16 *__restrict__ w, bf16 *__restrict__ wflip) {
+    const int64_t n = (int64_t)27 * ci * co;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % ci), t = (int)((e / ci) % 27), o = (int)(e / (27 * ci));
+        wflip[((int64_t)i * 27 + (26 - t)) * co + o] = w[e];
+    }
+}
+
+extern "C" int gbpcg_conv3_backward_data(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *gy,
+                                         const void *w, float *gx, void *workspace, size_t workspace_bytes,
+                                         gbpcg_stream stream) {
+    clear_error();
+    GB_TRY(conv_args(nx, ny, nz, ci, co, gy, w, gx, workspace, workspace_bytes));
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tc = conv_tc_ok(nx, ny, nz, co, ci), simt = conv_simt_ok(co, ci);
+    if (!tc && !simt) return fail_arg("unsupported convolution shape or channel counts");
+    int *err = static_cast<int *>(workspace);
+    bf16 *wflip = reinterpret_cast<bf16 *>(static_cast<char *>(workspace) + 256);
+    flip_one_kernel<<<blocks_for((int64_t)27 * ci * co, 256), 256, 0, s>>>(ci, co, static_cast<const bf16 *>(w), wflip);
+    GB_CUDA(cudaGetLastError());
+    const bf16 *g = static_cast<const bf16 *>(gy);
+    if (tc) return conv_tc<float>(nx, ny, nz, co, ci, g, wflip, gx, ci, 0, 0, nullptr, 0, 0, err, s);
+    return conv_simt<float>(nx, ny, nz, co, ci, g, wflip, gx, 0, nullptr, 0, 0, nullptr, s);
+}
+
+extern "C" int gbpcg_conv3_backward_weight(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x,
+                                           const void *gy, float *gw, void *workspace, size_t workspace_bytes,
+                                           gbpcg_stream stream) {
+    clear_error();
+    GB_TRY(conv_args(nx, ny, nz, ci, co, x, gy, gw, workspace, workspace_bytes));
+    if (!wgrad_ok(nx, ci, co)) return fail_arg("weight gradient: unsupported width or channel count");
+    if (ci % 8 && ci > 2) return fail_arg("weight gradient: ci must be 1, 2 or a multiple of 8");
+    if (co % 8 && co != 1) return fail_arg("weight gradient: co must be 1 or a multiple of 8");
+    float *part =
+        reinterpret_cast<float *>(static_cast<char *>(workspace) + 256 + align_up((size_t)27 * ci * co * 2, 256));
+    return wgrad(nx, ny, nz, ci, co, static_cast<const bf16 *>(x), static_cast<const bf16 *>(gy), gw, part,
+                 (cudaStream_t)stream);
+}
+
+extern "C" int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t training, size_t *bytes) {
+    clear_error();
+    if (!bytes) return fail_arg("bytes is NULL");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail_arg("grid sizes must be positive");
+    if (!nn_shape_ok(nx, ny, nz))
+        return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels");
+    *bytes = nn_layout(nx, ny, nz, training != 0).total;
+    return GBPCG_OK;
+}
+
+extern "C" int gbpcg_nn_forward(const gbpcg_grid *grid, const float *w, const float *r, float *z, void *workspace,
+                                size_t workspace_bytes, gbpcg_stream stream) {
+    clear_error();
+    NnLayout L;
+    GB_TRY(nn_check(grid, workspace, workspace_bytes, false, &L));
+    if (!w || !r || !z) return fail_arg("NULL array");
+    if (!aligned16(r) || !aligned16(z)) return fail_arg("r and z must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    GB_CUDA(cudaMemsetAsync(static_cast<char *>(workspace) + L.err, 0, sizeof(int), s));
+    GB_TRY(nn_weight_prep(w, workspace, L, s));
+    return nn_forward_prepped(*grid, r, z, workspace, L, s);
+}
+
+extern "C" int gbpcg_nn_backward(const gbpcg_grid *grid, const float *gz, float *gw, void *workspace,
+                                 size_t workspace_bytes, gbpcg_stream stream) {
+    clear_error();
+    NnLayout L;
+    GB_TRY(nn_check(grid, workspace, workspace_bytes, true, &L));
+    if (!gz || !gw) return fail_arg("NULL array");
+    return nn_backward_ws(gz, gw, workspace, L, (cudaStream_t)stream);
+}
+
+extern "C" int gbpcg_nn_adam(int64_t n, float *w, const float *g, float *m, float *v, int32_t step, double lr,
+                             double beta1, double beta2, double eps, gbpcg_stream stream) {
+    clear_error();
+    if (n < 0 || step < 1) return fail_arg("n must be >= 0 and step >= 1");
+    if (n == 0) return GBPCG_OK;
+    if (!w || !g || !m || !v) return fail_arg("NULL array");
+    const float bc1 = (float)(1.0 - pow(beta1, step)), bc2 = (float)(1.0 - pow(beta2, step));
+    adam_kernel<<<blocks_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
+        n, w, g, m, v, (float)lr, (float)beta1, (float)(1.0 - beta1), (float)beta2, (float)(1.0 - beta2), (float)eps,
+        bc1, bc2);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "adam launch");
+}
+
+extern "C" int gbpcg_nn_loss(const gbpcg_grid *grid, const float *z, const float *e, float *gz, double *loss,
+                             void *workspace, size_t workspace_bytes, gbpcg_stream stream) {
+    clear_error();
+    NnLayout L;
+    GB_TRY(nn_check(grid, workspace, workspace_bytes, true, &L));
+    if (!z || !e || !gz) return fail_arg("NULL array");
+    return nn_loss_ws(*grid, z, e, gz, loss, workspace, L, (cudaStream_t)stream);
+}
+
+extern "C" int gbpcg_nn_train_step(const gbpcg_grid *grid, float *w, float *m, float *v, int32_t step, double lr,
+                                   const float *r, const float *e, float *z, float *gz, float *gw, double *loss,
+                                   void *workspace, size_t workspace_bytes, gbpcg_stream stream) {
+    clear_error();
+    NnLayout L;
+    GB_TRY(nn_check(grid, workspace, workspace_bytes, true, &L));
+    if (!w || !m || !v || !r || !e || !z || !gz || !gw) return fail_arg("NULL array");
+    if (!aligned16(r) || !aligned16(z) || !aligned16(e) || !aligned16(gz))
+        return fail_arg("vectors must be 16-byte aligned");
+    if (step < 1) return fail_arg("step must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    GB_CUDA(cudaMemsetAsync(static_cast<char *>(workspace) + L.err, 0, sizeof(int), s));
+    GB_TRY(nn_weight_prep(w, workspace, L, s));
+    GB_TRY(nn_forward_prepped(*grid, r, z, workspace, L, s));
+    GB_TRY(nn_loss_ws(*grid, z, e, gz, loss, workspace, L, s));
+    GB_TRY(nn_backward_ws(gz, gw, workspace, L, s));
+    return gbpcg_nn_adam(kNumWeights, w, gw, m, v, step, lr, 0.9, 0.999, 1e-8, stream);
+}
+
+extern "C" int gbpcg_nn_status(void *workspace, gbpcg_stream stream) {
+    clear_error();
+    if (!workspace) return fail_arg("workspace is NULL");
+    // the error word sits at the same offset in every learned-preconditioner workspace
+    const size_t off = nn_layout_err_offset();
+    int flag = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    GB_CUDA(cudaMemcpyAsync(&flag, static_cast<char *>(workspace) + off, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GB_CUDA(cudaStreamSynchronize(s));
+    if (!flag) return GBPCG_OK;
+    GB_CUDA(cudaMemsetAsync(static_cast<char *>(workspace) + off, 0, sizeof(int), s));
+    set_error("a bounded wait in a convolution kernel gave up");
+    return GBPCG_TIMEOUT;
+}

@@ -22,6 +22,9 @@ Workloads (the problem statements of the solver's configurations):
     0 .. 2*nblocks-1 (two per block for Box-Muller).
   * ``batch_shapes(nprob, seed, sizes)``: per-axis sizes drawn uniformly from
     ``sizes``; three draws per problem in (nx, ny, nz) order.
+  * ``unet_init_weights(seed, layers)``: initial weights of the learned
+    preconditioner's convolutions, He-style normals (std sqrt(2 / (27 ci)),
+    halved for the last layer), one stream per layer (seed * 1000 + index).
 """
 from __future__ import annotations
 
@@ -117,3 +120,13 @@ def varcoeff_problem(nx: int, ny: int, nz: int, seed: int = 1, kb: int = 8, dtyp
     k = lognormal_blocks(nbx, nby, nbz, seed)
     b = uniform_rhs((nz, ny, nx), seed, 2 * k.size, dtype)
     return k, b
+
+
+def unet_init_weights(seed: int, layers) -> dict:
+    """{name: (co, 27, ci) float64} for layers [(name, ci, co), ...]; the last layer's std is halved."""
+    ws = {}
+    for li, (name, ci, co) in enumerate(layers):
+        n = co * 27 * ci
+        std = np.sqrt(2.0 / (27 * ci)) * (0.5 if li == len(layers) - 1 else 1.0)
+        ws[name] = standard_normal(seed * 1000 + li, 0, n).reshape(co, 27, ci) * std
+    return ws

@@ -1,0 +1,71 @@
+"""Flexible CG with the learned preconditioner (gbpcg_fcg_solve), its descent
+check with the Jacobi fallback, and what a network trained on the GPU gains
+over Jacobi PCG.  Every solve is judged by the FP64 oracle's true residual
+||b - A x|| / ||b||, evaluated on the returned x."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2603_23343_gb300 import inputs, learned
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def true_relres(b, x, k=None, kb=8):
+    kk = None if k is None else k.cpu().numpy().astype(np.float64)
+    return oracle.true_relres(b.cpu().numpy(), x.cpu().numpy(), kk, kb)
+
+
+def test_identity_network_reproduces_cg(gpu_lib):
+    """N(r) = h^2 r (up to one BF16 rounding of r / rms) makes FCG plain CG, which for the
+    constant-coefficient operator is Jacobi PCG: the oracle's iteration count for the 32^3
+    Poisson problem (seed 0, tol 1e-6) is reproduced."""
+    with open(os.path.join(GOLDEN, "pcg_poisson32_seed0.json")) as f:
+        gold = json.load(f)
+    b = torch.from_numpy(inputs.poisson_problem(32, 0, np.float64)).cuda()
+    w = learned.identity_weights().cuda()
+    x, res = gpu_lib.fcg_solve(w, b, tol=1e-6, maxit=2000)
+    assert res["status"] == gpu_lib.OK, res
+    assert res["pass_launches"][1] == 0  # no fallback
+    assert abs(res["iters"] - gold["iters"]) <= 4, (res["iters"], gold["iters"])
+    assert true_relres(b, x) <= 1e-6
+    assert abs(res["rel_res_true"] - true_relres(b, x)) <= 1e-3 * res["rel_res_true"]
+
+
+@pytest.mark.parametrize("how", ["nan", "negated"])
+def test_descent_check_falls_back_to_jacobi(gpu_lib, how):
+    """A preconditioner that is no descent direction (NaN output, or N(r) = -h^2 r with
+    r.z < 0) is caught before it touches x; Jacobi PCG finishes the solve."""
+    shape = (32, 32, 32)
+    k, b = learned.problem(shape, 3)
+    w = learned.identity_weights()
+    if how == "nan":
+        w[-1] = float("nan")  # a weight of the last layer, after which no ReLU acts
+    else:
+        n9 = 16 * 27
+        w[-n9:] = -w[-n9:]
+    x, res = gpu_lib.fcg_solve(w.cuda(), b, tol=1e-6, maxit=3000, k_block=k)
+    assert res["status"] == gpu_lib.FALLBACK_USED, res
+    assert res["pass_launches"][0] == 0 and res["pass_launches"][1] == res["iters"]
+    _, ref = gpu_lib.pcg_solve(b.clone(), torch.zeros_like(b), tol=1e-6, maxit=3000, k_block=k)
+    assert res["iters"] == ref["iters"]
+    assert true_relres(b, x, k) <= 1e-6
+
+
+def test_zero_rhs_and_rejections(gpu_lib):
+    b = torch.zeros((32, 32, 32), dtype=torch.float64, device="cuda")
+    x = torch.ones_like(b)
+    w = learned.identity_weights().cuda()
+    x, res = gpu_lib.fcg_solve(w, b, x=x)
+    assert res["status"] == gpu_lib.OK and res["iters"] == 0
+    assert torch.count_nonzero(x).item() == 0
+    with pytest.raises(gpu_lib.GbpcgError):
+        gpu_lib.fcg_solve(w, torch.zeros((30, 30, 30), dtype=torch.float64, device="cuda"))
+    with pytest.raises(gpu_lib.GbpcgError):
+        gpu_lib.fcg_solve(w, torch.zeros((32, 32, 32), dtype=torch.float32, device="cuda"))

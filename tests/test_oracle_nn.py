@@ -131,3 +131,63 @@ def test_fcg_reduces_to_pcg_for_linear_preconditioners(varcoeff):
     plain = oracle.pcg(b, tol=1e-8, maxit=500, k=k, kb=4, precond=None)
     f2 = nn.fcg(b, lambda r: r.copy(), tol=1e-8, maxit=500, k=k, kb=4)
     assert abs(f2["iters"] - plain["iters"]) <= 1
+
+
+def test_adam_first_steps_closed_form():
+    """Step 1 moves every weight by lr * g / (|g| + eps), i.e. lr * sign(g) for |g| >> eps; a
+    constant gradient keeps that step size at every step (m_hat = g, v_hat = g^2 exactly)."""
+    g = rnd((50,), 16)
+    w0 = rnd((50,), 17)
+    w, m, v = nn.adam_step(w0, g, np.zeros(50), np.zeros(50), 1, lr=0.01)
+    np.testing.assert_allclose(w, w0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    for t in range(2, 6):
+        w_prev = w
+        w, m, v = nn.adam_step(w, g, m, v, t, lr=0.01)
+        np.testing.assert_allclose(w_prev - w, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+
+
+def test_rounded_backward_reduces_to_exact_and_traces_layers():
+    """With an identity round_fn the traced backward equals the plain one, and each traced
+    pair rebuilds that layer's weight gradient."""
+    shape = (8, 8, 8)
+    r = rnd(shape, 50)
+    ws = nn.init_weights(4)
+    x, scale = nn.net_input(r, np.zeros(shape))
+    out, cache = nn.net_forward(x, ws)
+    gout = rnd(shape + (1,), 51)
+    g0 = nn.net_backward(gout, ws, cache)
+    tr = {}
+    g1 = nn.net_backward(gout, ws, cache, round_fn=lambda a: a, trace=tr)
+    for name, _, _ in nn.LAYERS:
+        np.testing.assert_array_equal(g0[name], g1[name])
+        np.testing.assert_array_equal(nn.conv3_weight_grad(*tr[name]), g0[name])
+
+
+def test_scaled_loss_properties_and_gradient():
+    """Scale-free sign-aware A-norm loss: 0 at any positive multiple of the target, 1 at any
+    negative one, 1/2 for an A-orthogonal direction, invariant to positive scaling of z, and
+    its closed-form gradient matches central differences on both sides of z.Ae = 0."""
+    shape = (6, 5, 7)
+    nbx, nby, nbz = inputs.block_counts(7, 5, 6, 4)
+    k = inputs.lognormal_blocks(nbx, nby, nbz, 40).astype(np.float64)
+    e = rnd(shape, 41)
+    z = rnd(shape, 42)
+    assert abs(nn.loss_scaled(3.0 * e, e, k, 4)) <= 1e-14
+    assert abs(nn.loss_scaled(-0.5 * e, e, k, 4) - 1.0) <= 1e-14
+    ae = oracle.apply(e, k, 4)
+    zp = z - (float(np.sum(z * ae)) / float(np.sum(e * ae))) * e  # A-orthogonal to e
+    assert abs(nn.loss_scaled(zp, e, k, 4) - 0.5) <= 1e-12
+    for zz in (z + 0.3 * e, z - 0.3 * e):  # one with z.Ae > 0, one with z.Ae < 0
+        a = float(np.sum(zz * ae))
+        L = nn.loss_scaled(zz, e, k, 4)
+        assert (0.0 < L < 0.5) if a > 0 else (0.5 < L < 1.0)
+        assert abs(nn.loss_scaled(7.0 * zz, e, k, 4) - L) <= 1e-13
+        g = nn.loss_scaled_grad(zz, e, k, 4)
+        h = 1e-6
+        for idx in [(0, 0, 0), (3, 2, 4), (5, 4, 6), (2, 1, 3)]:
+            zp2, zm2 = zz.copy(), zz.copy()
+            zp2[idx] += h
+            zm2[idx] -= h
+            fd = (nn.loss_scaled(zp2, e, k, 4) - nn.loss_scaled(zm2, e, k, 4)) / (2 * h)
+            assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-11
+        assert abs(float(np.sum(g * zz))) <= 1e-12 * np.linalg.norm(g) * np.linalg.norm(zz)
