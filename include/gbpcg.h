@@ -98,7 +98,8 @@ typedef struct gbpcg_opts {
     size_t workspace_bytes;
     double inner_tol;      /* refinement (16-bit storage): relative tolerance of each inner solve */
     int32_t max_outer;     /* refinement: maximum outer FP64 steps */
-    int32_t reserved1;
+    int32_t fcg_m;         /* gbpcg_fcg_solve: each search direction is A-orthogonalised against the
+                              last fcg_m ones (1 .. 16; 0 selects 8); ignored elsewhere */
 } gbpcg_opts;
 
 typedef struct gbpcg_result {
@@ -361,9 +362,11 @@ int gbpcg_nn_train_step(const gbpcg_grid *grid, float *w, float *m, float *v, in
 int gbpcg_fcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t *bytes);
 
 /*
- * Flexible CG (truncation 1: beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k),
- * Notay 2000) for A x = b with the learned preconditioner z = N(r), N given
- * by the DEVICE FP32 weights w.  opts: precond = GBPCG_PRECOND_LEARNED,
+ * Flexible CG with truncation m = opts->fcg_m (Notay 2000: p_k = z_k minus
+ * its A-projections on the last m directions, alpha_k = p_k.r_k / p_k.Ap_k;
+ * m = 1 is the beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k) form) for A x = b
+ * with the learned preconditioner z = N(r), N given by the DEVICE FP32
+ * weights w.  opts: precond = GBPCG_PRECOND_LEARNED,
  * io_dtype = F64 (b read, x initial guess in / solution out, DEVICE,
  * 16-byte aligned), storage = F32, no flags; tol and maxit as in
  * gbpcg_pcg_solve (maxit counts every A.p product, fallback included).

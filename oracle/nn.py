@@ -18,8 +18,12 @@ Conventions
             up, concat [up(64), e1] -> c7 (96->32)
             up, concat [up(32), e0] -> c8 (48->16)
             c9 (16->1) = output
-          input channels [r / rms(r), log k]; the output is scaled by
-          rms(r) * h^2 (the network predicts in normalised units).
+          N acts on the Jacobi-scaled system D^{-1/2} A D^{-1/2} (D the
+          operator's diagonal): input channels [s / rms(s), log k] with
+          s = D^{-1/2} r; the output is multiplied by rms(s) D^{-1/2}.  A ReLU
+          network is piecewise linear in (r, log k) and cannot form the
+          product r / k that the coefficient contrast calls for; the scaling
+          supplies it, and N stays positively homogeneous in r.
   loss    L(z) = 1/2 z.Az - z.r: the A-norm error 1/2 ||z - A^{-1}r||_A^2 up to
           the constant -1/2 r.A^{-1}r; dL/dz = A z - r.
   training loss (scale-free, sign-aware): with target e = A^{-1} r,
@@ -30,7 +34,9 @@ Conventions
           (0) is reached only by positive multiples of e and the trained
           preconditioner keeps r.z > 0.
   Adam    Kingma & Ba, ICLR 2015, Algorithm 1 (bias-corrected moments).
-  FCG     flexible CG with truncation 1 (Notay, SIAM J. Sci. Comput. 22, 2000):
+  FCG     flexible CG (Notay, SIAM J. Sci. Comput. 22, 2000) with truncation m:
+          p_k = z_k - sum_{i=k-m}^{k-1} (z_k.Ap_i / p_i.Ap_i) p_i,
+          alpha_k = p_k.r_k / p_k.Ap_k; m = 1 is the beta form
           beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k).
 """
 from __future__ import annotations
@@ -183,18 +189,32 @@ def adam_step(w, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return w - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def net_input(r, logk):
-    """Channels [r / rms(r), log k] and the output scale rms(r) * h^2."""
-    rms = float(np.sqrt(np.mean(r * r)))
-    nz, ny, nx = r.shape
-    h2 = (1.0 / (max(nx, ny, nz) + 1)) ** 2
-    x = np.stack([r / rms if rms > 0 else r, logk], axis=3)
-    return x, rms * h2
+def logk_field(shape, k=None, kb=8):
+    """log k at every grid point (0 for the constant-coefficient operator)."""
+    if k is None:
+        return np.zeros(shape)
+    nz, ny, nx = shape
+    full = np.repeat(np.repeat(np.repeat(np.asarray(k, dtype=np.float64), kb, 0), kb, 1), kb, 2)
+    return np.log(full[:nz, :ny, :nx])
 
 
-def precond_apply(r, logk, ws):
+def jacobi_scale(shape, k=None, kb=8):
+    """D^{-1/2} of the operator's diagonal D."""
+    return 1.0 / np.sqrt(oracle.diag(shape, k, kb))
+
+
+def net_input(r, logk, dsc):
+    """Channels [s / rms(s), log k] with s = D^{-1/2} r (dsc = D^{-1/2}), and the output
+    scale field rms(s) D^{-1/2}."""
+    sr = r * dsc
+    rms = float(np.sqrt(np.mean(sr * sr)))
+    x = np.stack([sr / rms if rms > 0 else sr, logk], axis=3)
+    return x, rms * dsc
+
+
+def precond_apply(r, ws, k=None, kb=8):
     """z = N(r): the preconditioner the learned FCG applies."""
-    x, scale = net_input(r, logk)
+    x, scale = net_input(r, logk_field(r.shape, k, kb), jacobi_scale(r.shape, k, kb))
     out, _ = net_forward(x, ws)
     return out[..., 0] * scale
 
@@ -234,31 +254,31 @@ def loss_scaled_grad(z, e, k=None, kb=8):
     return (abs(a) / (c * E)) * ((a / c) * az - ae)
 
 
-def fcg(b, precond, tol=1e-6, maxit=500, k=None, kb=8, x0=None):
-    """Flexible CG, truncation 1: r = b - A x; z = M(r); p = z;
-    repeat q = A p; alpha = r.z / p.q; x += alpha p; r_new = r - alpha q;
-    stop on ||r_new||/||b||; z_new = M(r_new);
-    beta = z_new.(r_new - r) / (z.r); p = z_new + beta p."""
+def fcg(b, precond, tol=1e-6, maxit=500, k=None, kb=8, x0=None, m=1, directions=None):
+    """Flexible CG with truncation m: r = b - A x; repeat z = M(r);
+    p = z - sum over the last m directions p_i of (z.Ap_i / p_i.Ap_i) p_i;
+    alpha = p.r / p.Ap; x += alpha p; r -= alpha Ap; stop on ||r||/||b||.
+    directions (optional list) receives every (p, Ap)."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     r = b - oracle.apply(x, k, kb)
     bn = np.linalg.norm(b)
-    z = precond(r)
-    p = z.copy()
-    rz = float(np.sum(r * z))
-    it = 0
     hist = [np.linalg.norm(r) / bn]
+    window = []
+    it = 0
     while it < maxit and hist[-1] > tol:
+        z = precond(r)
+        p = z.copy()
+        for pi, qi in window:
+            p -= (float(np.sum(z * qi)) / float(np.sum(pi * qi))) * pi
         q = oracle.apply(p, k, kb)
-        alpha = rz / float(np.sum(p * q))
+        alpha = float(np.sum(p * r)) / float(np.sum(p * q))
         x += alpha * p
-        r_new = r - alpha * q
+        r = r - alpha * q
         it += 1
-        hist.append(np.linalg.norm(r_new) / bn)
-        if hist[-1] <= tol:
-            break
-        z_new = precond(r_new)
-        beta = float(np.sum(z_new * (r_new - r))) / rz
-        p = z_new + beta * p
-        rz = float(np.sum(r_new * z_new))
-        r, z = r_new, z_new
+        hist.append(np.linalg.norm(r) / bn)
+        window.append((p, q))
+        if directions is not None:
+            directions.append((p, q))
+        if len(window) > m:
+            window.pop(0)
     return dict(x=x, iters=it, hist=np.array(hist))

@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("io_dtype", ctypes.c_int32), ("flags", ctypes.c_uint32),
                 ("tile_cfg", ctypes.c_int32), ("workspace", ctypes.c_void_p),
                 ("workspace_bytes", ctypes.c_size_t), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("fcg_m", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -542,31 +542,33 @@ def nn_status(workspace: torch.Tensor, stream=None) -> int:
     return _check(load().gbpcg_nn_status(_ptr(workspace), _stream(stream)))
 
 
-def _fcg_opts(tol, maxit, workspace=None):
+def _fcg_opts(tol, maxit, workspace=None, m=0):
     o = make_opts(tol=tol, maxit=maxit, io_dtype=F64, workspace=workspace)
     o.precond = PRECOND_LEARNED
+    o.fcg_m = int(m)
     return o
 
 
-def fcg_workspace(shape, k_block=None, kb=8, tol=1e-6, maxit=2000, device="cuda") -> torch.Tensor:
+def fcg_workspace(shape, k_block=None, kb=8, tol=1e-6, maxit=2000, m=0, device="cuda") -> torch.Tensor:
     g = make_grid(shape, k_block, kb)
-    o = _fcg_opts(tol, maxit)
+    o = _fcg_opts(tol, maxit, None, m)
     n = ctypes.c_size_t(0)
     _check(load().gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)))
     return torch.empty(int(n.value), dtype=torch.uint8, device=device)
 
 
 def fcg_solve(w: torch.Tensor, b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None,
-              kb=8, workspace=None, stream=None):
-    """Flexible CG with the learned preconditioner N_w (gbpcg_fcg_solve); b, x float64 CUDA (nz, ny, nx).
-    Returns (x, result dict); FALLBACK_USED, NOT_CONVERGED and BREAKDOWN are reported, not raised."""
+              kb=8, m=0, workspace=None, stream=None):
+    """Flexible CG with truncation m (0: the library's default) and the learned preconditioner N_w
+    (gbpcg_fcg_solve); b, x float64 CUDA (nz, ny, nx).  Returns (x, result dict); FALLBACK_USED,
+    NOT_CONVERGED and BREAKDOWN are reported, not raised."""
     if b.dtype != torch.float64 or not b.is_cuda:
         raise GbpcgError(ERR_ARG, "b must be a float64 CUDA tensor")
     if x is None:
         x = torch.zeros_like(b)
-    ws = workspace if workspace is not None else fcg_workspace(b.shape, k_block, kb, tol, maxit, b.device)
+    ws = workspace if workspace is not None else fcg_workspace(b.shape, k_block, kb, tol, maxit, m, b.device)
     g = make_grid(b.shape, k_block, kb)
-    o = _fcg_opts(tol, maxit, ws)
+    o = _fcg_opts(tol, maxit, ws, m)
     res = Result()
     _check(load().gbpcg_fcg_solve(ctypes.byref(g), _ptr(w), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(res),
                                   _stream(stream)), allowed=(OK, NOT_CONVERGED, BREAKDOWN, FALLBACK_USED))

@@ -1,17 +1,22 @@
 // Flexible CG with the learned preconditioner z = N(r) (no counterpart in
-// the paper).  N is nonlinear (ReLU), so the Hestenes-Stiefel beta of plain
-// PCG loses conjugacy; FCG with truncation 1 (Notay, SIAM J. Sci. Comput.
-// 22, 2000) uses beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k) instead, which
-// equals the plain beta whenever N is linear and symmetric.
+// the paper).  N is nonlinear (ReLU), so plain PCG's short recurrence loses
+// conjugacy; FCG with truncation m (Notay, SIAM J. Sci. Comput. 22, 2000)
+// A-orthogonalises each new direction against the last m explicitly:
+//   p_k = z_k - sum_{i=k-m}^{k-1} (z_k.Ap_i / p_i.Ap_i) p_i,
+//   alpha_k = p_k.r_k / p_k.Ap_k.
+// m = 1 is the familiar beta = z_{k+1}.(r_{k+1} - r_k) / (z_k.r_k) form; a
+// larger m keeps a strongly nonlinear N from undoing earlier progress.
 //
-// One iteration: q = A p; p.q; fused update (alpha = r.z / p.q on the
-// device; x += alpha p in FP64; r_old = r; r -= alpha q; r.r); z = N(r);
-// fused r.z and z.r_old (beta on the device); p = z + beta p.  The update
-// kernels leave x and p untouched when p.q or r.z fail the descent check,
-// and the host, which reads the scalars once per iteration, switches to
-// Jacobi PCG from the current x (GBPCG_FALLBACK_USED).  At recursive
-// convergence the true residual is recomputed in FP64; if it misses the
-// tolerance, r is replaced by it and FCG restarts (p = z).
+// One iteration: z = N(r); one fused pass for r.z and every z.Ap_i (the
+// projection coefficients are formed on the device); p = z - sum c_i p_i;
+// Ap; one fused pass for p.Ap and r.p (alpha on the device); fused update
+// x += alpha p (FP64), r -= alpha Ap with r.r.  The directions and their
+// A-images live in a ring of m + 1 slots.  Every kernel after a failed
+// descent check (r.z <= 0, p.Ap <= 0, a non-finite scalar) leaves x, r and
+// p untouched, and the host, which reads the scalars once per iteration,
+// switches to Jacobi PCG from the current x (GBPCG_FALLBACK_USED).  At
+// recursive convergence the true residual is recomputed in FP64; if it
+// misses the tolerance, r is replaced by it and FCG restarts.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -30,11 +35,23 @@ bool nn_shape_ok_ext(int X, int Y, int Z);
 int nn_prep_ext(const float *w, void *ws, int X, int Y, int Z, cudaStream_t s);
 int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s);
 
+constexpr int kMaxDirs = 16;
+
 struct FcgState {
-    double bb, rz, pq, rr, zr, alpha, beta, rr64;
-    int bad;  // 1: p.Ap <= 0 or not finite; 2: r.z <= 0 or not finite
+    double bb, rz, rp, rr, rr64;
+    double pq[kMaxDirs + 1];  // p.Ap of every ring slot
+    double c[kMaxDirs];       // projection coefficients of the current step
+    int bad;                  // 1: p.Ap <= 0 or not finite; 2: r.z <= 0 or not finite
     int pad;
     unsigned ticket[4];
+};
+
+// The previous directions of one step: ring slots, oldest first.
+struct DirSet {
+    const float *p[kMaxDirs];
+    const float *q[kMaxDirs];
+    int slot[kMaxDirs];
+    int nd;
 };
 
 constexpr int kFcgThreads = 256;
@@ -50,22 +67,114 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+__device__ __forceinline__ float dot4f(const float4 a, const float4 b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
+}
+
+// Sums NV per-thread doubles over the block (result in thread 0), then over
+// the grid with the fixed-order last-block finish.
+template <int NV>
+__device__ __forceinline__ bool fcg_reduce(const double (&acc)[NV], double *partials, unsigned *ticket,
+                                           double (&tot)[NV]) {
+    __shared__ double red[kFcgThreads / 32][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double s = warp_sum(acc[v]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][v] = s;
+    }
+    __syncthreads();
+    double part[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        part[v] = 0.0;
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kFcgThreads / 32; ++w) part[v] += red[w][v];
+    }
+    return grid_sum_last<NV, kFcgThreads>(part, partials, ticket, tot);
+}
+
+// r.z and z.Ap_i of every previous direction; the last block forms the
+// projection coefficients c_i = z.Ap_i / p_i.Ap_i and checks r.z > 0.
+__global__ void __launch_bounds__(kFcgThreads)
+    fcg_mdot_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ r,
+                    const float *__restrict__ z, const DirSet d) {
+    double acc[kMaxDirs + 1];
+#pragma unroll
+    for (int v = 0; v <= kMaxDirs; ++v) acc[v] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
+        const float4 zv = reinterpret_cast<const float4 *>(z)[i];
+        acc[0] += (double)dot4f(reinterpret_cast<const float4 *>(r)[i], zv);
+#pragma unroll
+        for (int j = 0; j < kMaxDirs; ++j)
+            if (j < d.nd) acc[1 + j] += (double)dot4f(reinterpret_cast<const float4 *>(d.q[j])[i], zv);
+    }
+    double tot[kMaxDirs + 1];
+    if (fcg_reduce<kMaxDirs + 1>(acc, partials, &st->ticket[0], tot) && threadIdx.x == 0) {
+        const double rz = tot[0];
+        bool ok = rz > 0.0 && isfinite(rz);
+        for (int j = 0; j < d.nd; ++j) {
+            const double c = tot[1 + j] / st->pq[d.slot[j]];
+            ok = ok && isfinite(c);
+            st->c[j] = c;
+        }
+        st->rz = rz;
+        if (!ok) st->bad = 2;
+    }
+}
+
+// p = z - sum_j c_j p_j
+__global__ void __launch_bounds__(256)
+    fcg_combine_kernel(int64_t n4, const FcgState *st, const float *__restrict__ z, const DirSet d,
+                       float *__restrict__ p) {
+    if (st->bad) return;
+    float c[kMaxDirs];
+#pragma unroll
+    for (int j = 0; j < kMaxDirs; ++j) c[j] = j < d.nd ? (float)st->c[j] : 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = reinterpret_cast<const float4 *>(z)[i];
+#pragma unroll
+        for (int j = 0; j < kMaxDirs; ++j)
+            if (j < d.nd) {
+                const float4 pj = reinterpret_cast<const float4 *>(d.p[j])[i];
+                v.x = fmaf(-c[j], pj.x, v.x);
+                v.y = fmaf(-c[j], pj.y, v.y);
+                v.z = fmaf(-c[j], pj.z, v.z);
+                v.w = fmaf(-c[j], pj.w, v.w);
+            }
+        reinterpret_cast<float4 *>(p)[i] = v;
+    }
+}
+
+// p.Ap and r.p of the new direction; the last block checks p.Ap > 0
+__global__ void __launch_bounds__(kFcgThreads)
+    fcg_pdots_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ p,
+                     const float *__restrict__ q, const float *__restrict__ r, int slot) {
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
+        const float4 pv = reinterpret_cast<const float4 *>(p)[i];
+        acc[0] += (double)dot4f(pv, reinterpret_cast<const float4 *>(q)[i]);
+        acc[1] += (double)dot4f(pv, reinterpret_cast<const float4 *>(r)[i]);
+    }
+    double tot[2];
+    if (fcg_reduce<2>(acc, partials, &st->ticket[1], tot) && threadIdx.x == 0) {
+        st->pq[slot] = tot[0];
+        st->rp = tot[1];
+        if (!(tot[0] > 0.0) || !isfinite(tot[0]) || !isfinite(tot[1])) st->bad = st->bad ? st->bad : 1;
+    }
+}
+
+// alpha = r.p / p.Ap; x += alpha p (FP64); r -= alpha Ap; r.r
 __global__ void __launch_bounds__(kFcgThreads)
     fcg_update_kernel(int64_t n4, FcgState *st, double *partials, double *__restrict__ x, const float *__restrict__ p,
-                      const float *__restrict__ q, float *__restrict__ r, float *__restrict__ rold) {
-    const double pq = st->pq, rz = st->rz;
-    if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) st->bad = 1;
-        return;  // uniform over the grid: no block reaches the reduction
-    }
-    const double alpha = rz / pq;
+                      const float *__restrict__ q, float *__restrict__ r, int slot) {
+    if (st->bad) return;  // uniform over the grid: no block reaches the reduction
+    const double alpha = st->rp / st->pq[slot];
     const float af = (float)alpha;
-    double accd = 0.0;
+    double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
         const float4 pv = reinterpret_cast<const float4 *>(p)[i];
         const float4 qv = reinterpret_cast<const float4 *>(q)[i];
         float4 rv = reinterpret_cast<float4 *>(r)[i];
-        reinterpret_cast<float4 *>(rold)[i] = rv;
         double2 *x2 = reinterpret_cast<double2 *>(x) + 2 * i;
         double2 xa = x2[0], xb = x2[1];
         xa.x = fma(alpha, (double)pv.x, xa.x);
@@ -79,70 +188,21 @@ __global__ void __launch_bounds__(kFcgThreads)
         rv.z = fmaf(-af, qv.z, rv.z);
         rv.w = fmaf(-af, qv.w, rv.w);
         reinterpret_cast<float4 *>(r)[i] = rv;
-        accd += (double)(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        acc[0] += (double)dot4f(rv, rv);
     }
-    __shared__ double red[kFcgThreads / 32];
-    const double s = warp_sum(accd);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    double part[1] = {0.0}, tot[1];
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kFcgThreads / 32; ++w) part[0] += red[w];
-    if (grid_sum_last<1, kFcgThreads>(part, partials, &st->ticket[0], tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->alpha = alpha;
-    }
-}
-
-// r.z and z.r_old; beta = (r.z - z.r_old) / (previous r.z); r.z replaces it
-__global__ void __launch_bounds__(kFcgThreads)
-    fcg_dual_dot_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ r,
-                        const float *__restrict__ z, const float *__restrict__ rold) {
-    double a0 = 0.0, a1 = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
-        const float4 rv = reinterpret_cast<const float4 *>(r)[i];
-        const float4 zv = reinterpret_cast<const float4 *>(z)[i];
-        const float4 ov = reinterpret_cast<const float4 *>(rold)[i];
-        a0 += (double)(rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w);
-        a1 += (double)(ov.x * zv.x + ov.y * zv.y + ov.z * zv.z + ov.w * zv.w);
-    }
-    __shared__ double red[kFcgThreads / 32][2];
-    const double s0 = warp_sum(a0), s1 = warp_sum(a1);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][0] = s0, red[threadIdx.x >> 5][1] = s1;
-    __syncthreads();
-    double part[2] = {0.0, 0.0}, tot[2];
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kFcgThreads / 32; ++w) part[0] += red[w][0], part[1] += red[w][1];
-    if (grid_sum_last<2, kFcgThreads>(part, partials, &st->ticket[1], tot) && threadIdx.x == 0) {
-        const double rz_new = tot[0];
-        if (!(rz_new > 0.0) || !isfinite(rz_new) || !isfinite(tot[1])) {
-            st->bad = 2;
-        } else {
-            st->zr = tot[1];
-            st->beta = (rz_new - tot[1]) / st->rz;
-            st->rz = rz_new;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256)
-    fcg_p_kernel(int64_t n4, const FcgState *st, const float *__restrict__ z, float *__restrict__ p) {
-    if (st->bad) return;
-    const float b = (float)st->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 zv = reinterpret_cast<const float4 *>(z)[i];
-        float4 pv = reinterpret_cast<float4 *>(p)[i];
-        pv.x = fmaf(b, pv.x, zv.x);
-        pv.y = fmaf(b, pv.y, zv.y);
-        pv.z = fmaf(b, pv.z, zv.z);
-        pv.w = fmaf(b, pv.w, zv.w);
-        reinterpret_cast<float4 *>(p)[i] = pv;
-    }
+    double tot[1];
+    if (fcg_reduce<1>(acc, partials, &st->ticket[2], tot) && threadIdx.x == 0) st->rr = tot[0];
 }
 
 struct FcgLayout {
-    size_t state, partials, dotws, r, rold, z, p, q, d64, nn, pcg, total;
+    int m;  // truncation: directions kept
+    size_t state, partials, dotws, r, z, ring, d64, nn, pcg, total;  // ring: (m + 1) x (p, Ap)
 };
+
+inline int fcg_depth(const gbpcg_opts &o) { return o.fcg_m == 0 ? 8 : o.fcg_m; }
+
+// ring vector length, rounded so that every vector stays 256-byte aligned
+inline size_t align_n4(int64_t n) { return ((size_t)n + 63) / 64 * 64; }
 
 static gbpcg_opts fallback_opts(const gbpcg_opts &o) {
     gbpcg_opts f;
@@ -163,14 +223,13 @@ static int fcg_layout(const gbpcg_grid &g, const gbpcg_opts &o, FcgLayout *L) {
         off = (off + bytes + 255) / 256 * 256;
         return at;
     };
+    L->m = fcg_depth(o);
     L->state = take(sizeof(FcgState));
-    L->partials = take(sizeof(double) * 2 * kFcgMaxBlocks);
+    L->partials = take(sizeof(double) * (kMaxDirs + 1) * kFcgMaxBlocks);
     L->dotws = take(gbpcg_dot_workspace_size());
     L->r = take(n * 4);
-    L->rold = take(n * 4);
     L->z = take(n * 4);
-    L->p = take(n * 4);
-    L->q = take(n * 4);
+    L->ring = take((size_t)2 * (L->m + 1) * align_n4(n) * 4);
     L->d64 = take(n * 8);
     L->nn = take(nn_layout_total(g.nx, g.ny, g.nz, false));
     gbpcg_opts f = fallback_opts(o);
@@ -191,6 +250,7 @@ static int fcg_check(const gbpcg_grid *g, const gbpcg_opts *o) {
     if (o->storage != GBPCG_F32) return fail_arg("gbpcg_fcg_solve iterates in FP32 (storage F32)");
     if (o->flags & GBPCG_FLAG_HOST_IO) return fail_arg("gbpcg_fcg_solve takes device b and x");
     if (!(o->tol > 0.0) || o->maxit < 0) return fail_arg("tol must be > 0 and maxit >= 0");
+    if (o->fcg_m < 0 || o->fcg_m > kMaxDirs) return fail_arg("fcg_m must be 0 .. 16");
     if (!nn_shape_ok_ext(g->nx, g->ny, g->nz))
         return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels");
     return GBPCG_OK;
@@ -239,9 +299,11 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
     FcgState *st = reinterpret_cast<FcgState *>(base + L.state);
     double *partials = reinterpret_cast<double *>(base + L.partials);
     void *dotws = base + L.dotws;
-    float *r = reinterpret_cast<float *>(base + L.r), *rold = reinterpret_cast<float *>(base + L.rold),
-          *z = reinterpret_cast<float *>(base + L.z), *p = reinterpret_cast<float *>(base + L.p),
-          *q = reinterpret_cast<float *>(base + L.q);
+    float *r = reinterpret_cast<float *>(base + L.r), *z = reinterpret_cast<float *>(base + L.z);
+    const int m = L.m, nslots = m + 1;
+    const size_t vlen = align_n4((int64_t)g.nx * g.ny * g.nz);
+    auto ring_p = [&](int slot) { return reinterpret_cast<float *>(base + L.ring) + (size_t)(2 * slot) * vlen; };
+    auto ring_q = [&](int slot) { return reinterpret_cast<float *>(base + L.ring) + (size_t)(2 * slot + 1) * vlen; };
     double *d64 = reinterpret_cast<double *>(base + L.d64);
     void *nnws = base + L.nn;
     const int64_t n = (int64_t)g.nx * g.ny * g.nz, n4 = n / 4;
@@ -295,20 +357,6 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, n0, n1) == cudaSuccess) nn_ms += ms;
     };
-    // restart: z = N(r), r.z, p = z
-    auto restart = [&]() -> int {
-        GB_CUDA(cudaMemsetAsync(&st->bad, 0, sizeof(int), s));
-        int rc2 = precondition();
-        if (rc2) return rc2;
-        rc2 = gbpcg_dot(n, GBPCG_F32, r, z, &st->rz, dotws, dws, stream);
-        if (rc2) return rc2;
-        GB_CUDA(cudaMemcpyAsync(p, z, n * 4, cudaMemcpyDeviceToDevice, s));
-        rc2 = pull();
-        if (rc2) return rc2;
-        add_nn_time();
-        return GBPCG_OK;
-    };
-
     GB_CUDA(cudaEventRecord(e0, s));
     GB_CUDA(cudaMemsetAsync(st, 0, sizeof(FcgState), s));
     GB_CUDA(cudaMemsetAsync(static_cast<char *>(nnws) + nn_layout_err_offset(), 0, sizeof(int), s));
@@ -331,32 +379,42 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
     } else if (rel <= opts->tol) {
         status = GBPCG_OK;
     } else {
-        rc = restart();
-        if (rc) return rc;
-        if (!(hs.rz > 0.0) || !std::isfinite(hs.rz) || herr) fallback = true;
         std::vector<double> hist{rel};
-        while (!fallback && iters < opts->maxit) {
-            rc = gbpcg_stencil_apply(&g, GBPCG_F32, p, q, stream);
-            if (rc) return rc;
-            rc = gbpcg_dot(n, GBPCG_F32, p, q, &st->pq, dotws, dws, stream);
-            if (rc) return rc;
-            fcg_update_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, x, p, q, r, rold);
-            GB_CUDA(cudaGetLastError());
+        int nd = 0, cur = 0;  // directions in the window; ring slot of the next one
+        while (iters < opts->maxit) {
+            DirSet d;
+            memset(&d, 0, sizeof(d));
+            d.nd = nd;
+            for (int j = 0; j < nd; ++j) {  // oldest first
+                const int sl = ((cur - nd + j) % nslots + nslots) % nslots;
+                d.p[j] = ring_p(sl);
+                d.q[j] = ring_q(sl);
+                d.slot[j] = sl;
+            }
+            float *p = ring_p(cur), *q = ring_q(cur);
             rc = precondition();
             if (rc) return rc;
-            fcg_dual_dot_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, r, z, rold);
+            fcg_mdot_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, r, z, d);
             GB_CUDA(cudaGetLastError());
-            fcg_p_kernel<<<eb, 256, 0, s>>>(n4, st, z, p);
+            fcg_combine_kernel<<<eb, 256, 0, s>>>(n4, st, z, d, p);
+            GB_CUDA(cudaGetLastError());
+            rc = gbpcg_stencil_apply(&g, GBPCG_F32, p, q, stream);
+            if (rc) return rc;
+            fcg_pdots_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, p, q, r, cur);
+            GB_CUDA(cudaGetLastError());
+            fcg_update_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, x, p, q, r, cur);
             GB_CUDA(cudaGetLastError());
             rc = pull();
             if (rc) return rc;
             add_nn_time();
-            if (hs.bad == 1 || herr) {  // x untouched: this iteration did not happen
+            if (hs.bad || herr) {  // x and r untouched: this iteration did not happen
                 fallback = true;
                 break;
             }
             ++iters;
             ++fcg_iters;
+            nd = std::min(nd + 1, m);
+            cur = (cur + 1) % nslots;
             rel = std::sqrt(hs.rr / bb);
             hist.push_back(rel);
             if (!std::isfinite(rel)) {
@@ -374,17 +432,8 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
                     break;
                 }
                 ++replacements;
-                rc = restart();
-                if (rc) return rc;
-                if (!(hs.rz > 0.0) || !std::isfinite(hs.rz) || herr) {
-                    fallback = true;
-                    break;
-                }
+                nd = 0;  // restart from the replaced residual
                 continue;
-            }
-            if (hs.bad == 2) {  // r.z <= 0: N(r) is no descent direction
-                fallback = true;
-                break;
             }
             if (hist.size() > 5 && rel > 10.0 * hist[hist.size() - 6]) {
                 fallback = true;

@@ -8,8 +8,12 @@
 //   up, [up(c6), e1] -> c7 (96->32)       level 1
 //   up, [up(c7), e0] -> c8 (48->16)       level 0
 //   c9 (16->1)                            output, no ReLU
-// Input channels: r / rms(r) and log k; output scaled by rms(r) h^2.  pool is
-// a 2x2x2 average, up nearest-neighbour doubling.
+// N acts on the Jacobi-scaled system D^{-1/2} A D^{-1/2} (D the operator's
+// diagonal): input channels s / rms(s) with s = D^{-1/2} r, and log k; the
+// output is multiplied by rms(s) D^{-1/2}.  (A ReLU network is piecewise
+// linear in (r, log k) and cannot form the product r / k that the coefficient
+// contrast calls for; the scaling supplies it.)  pool is a 2x2x2 average, up
+// nearest-neighbour doubling.
 //
 // Convolutions with 16+ input and output channels (c2..c8 and their
 // data-gradient convolutions) run on the tensor cores (conv_tc.cuh); the
@@ -149,7 +153,7 @@ template <int CI, int CO, typename TO>
 __global__ void __launch_bounds__(256)
     conv3_simt_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
                       TO *__restrict__ out, int relu, const __nv_bfloat16 *__restrict__ mask, int mstride, int moff,
-                      const double *scale) {
+                      const double *scale, const float *__restrict__ vscale) {
     __shared__ float ws[27 * CI * CO];
     for (int e = threadIdx.x; e < 27 * CI * CO; e += blockDim.x) {
         const int o = e / (27 * CI), r = e - o * 27 * CI;  // r = t * CI + i
@@ -175,9 +179,10 @@ __global__ void __launch_bounds__(256)
                 for (int o = 0; o < CO; ++o) acc[o] = fmaf(iv[i], ws[(t * CI + i) * CO + o], acc[o]);
         }
         TO *po = out + v * CO;
+        const float vs = vscale ? sc * vscale[v] : sc;
 #pragma unroll
         for (int o = 0; o < CO; ++o) {
-            float f = acc[o] * sc;
+            float f = acc[o] * vs;
             if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
             if (mask && !(__bfloat162float(mask[v * mstride + moff + o]) > 0.0f)) f = 0.0f;
             acc[o] = f;
@@ -194,22 +199,28 @@ __global__ void __launch_bounds__(256)
 
 template <int CI, int CO, typename TO>
 static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out, int relu,
-                            const __nv_bfloat16 *mask, int mstride, int moff, const double *scale, cudaStream_t s) {
+                            const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
+                            const float *vscale, cudaStream_t s) {
     const int64_t n = (int64_t)X * Y * Z;
     conv3_simt_kernel<CI, CO, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride, moff,
-                                                                      scale);
+                                                                      scale, vscale);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_simt launch");
 }
 
 inline bool conv_simt_ok(int ci, int co) { return (ci == 2 && co == 16) || (ci == 16 && co == 1) || (ci == 1 && co == 16); }
 
+// out = conv(in) * (*scale) * vscale[v] (either factor optional)
 template <typename TO>
 static int conv_simt(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out,
-                     int relu, const __nv_bfloat16 *mask, int mstride, int moff, const double *scale, cudaStream_t s) {
-    if (ci == 2 && co == 16) return conv_simt_launch<2, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
-    if (ci == 16 && co == 1) return conv_simt_launch<16, 1, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
-    if (ci == 1 && co == 16) return conv_simt_launch<1, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, s);
+                     int relu, const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
+                     cudaStream_t s, const float *vscale = nullptr) {
+    if (ci == 2 && co == 16)
+        return conv_simt_launch<2, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, vscale, s);
+    if (ci == 16 && co == 1)
+        return conv_simt_launch<16, 1, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, vscale, s);
+    if (ci == 1 && co == 16)
+        return conv_simt_launch<1, 16, TO>(X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, vscale, s);
     return fail_arg("no CUDA-core convolution for these channel counts");
 }
 
@@ -393,14 +404,48 @@ static int wgrad(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, co
 
 // --------------------------------------------------------- glue kernels ----
 
-// Network input: channels (r / rms(r), log k); also the output scale rms h^2.
+// dsc = D^{-1/2} and s = D^{-1/2} r at every point.  D = sum over the six
+// faces of k_f / h_d^2, with k_f the harmonic mean of the two cells' block
+// coefficients on interior faces and the cell's own coefficient on boundary
+// faces (kb == NULL: k = 1).
 __global__ void __launch_bounds__(256)
-    nn_input_kernel(int X, int Y, int Z, const float *__restrict__ r, const double *rr, const float *__restrict__ kb,
-                    int kbx, int kby, int kbz, double h2, __nv_bfloat16 *__restrict__ xin, double *scale) {
+    jacobi_scale_kernel(int X, int Y, int Z, const float *__restrict__ r, const float *__restrict__ kb, int kbx,
+                        int kby, int kbz, float *__restrict__ dsc, float *__restrict__ sr) {
     const int64_t n = (int64_t)X * Y * Z;
-    const double rms = sqrt(*rr / (double)n);
+    const float cx = (float)(X + 1) * (float)(X + 1), cy = (float)(Y + 1) * (float)(Y + 1),
+                cz = (float)(Z + 1) * (float)(Z + 1);
+    const int nbx = (X + kbx - 1) / kbx, nby = (Y + kby - 1) / kby;
+    auto kat = [&](int x, int y, int z) { return kb[((int64_t)(z / kbz) * nby + y / kby) * nbx + x / kbx]; };
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        float d;
+        if (!kb) {
+            d = 2.0f * (cx + cy + cz);
+        } else {
+            const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
+            const float kc = kat(x, y, z);
+            auto face = [&](int xx, int yy, int zz) {
+                if (xx < 0 || xx >= X || yy < 0 || yy >= Y || zz < 0 || zz >= Z) return kc;
+                const float kn = kat(xx, yy, zz);
+                return 2.0f * kc * kn / (kc + kn);
+            };
+            d = cx * (face(x - 1, y, z) + face(x + 1, y, z)) + cy * (face(x, y - 1, z) + face(x, y + 1, z)) +
+                cz * (face(x, y, z - 1) + face(x, y, z + 1));
+        }
+        const float ds = 1.0f / sqrtf(d);
+        dsc[v] = ds;
+        sr[v] = r[v] * ds;
+    }
+}
+
+// Network input: channels (s / rms(s), log k) from the scaled residual s;
+// also the output scale rms(s).
+__global__ void __launch_bounds__(256)
+    nn_input_kernel(int X, int Y, int Z, const float *__restrict__ sr, const double *ss, const float *__restrict__ kb,
+                    int kbx, int kby, int kbz, __nv_bfloat16 *__restrict__ xin, double *scale) {
+    const int64_t n = (int64_t)X * Y * Z;
+    const double rms = sqrt(*ss / (double)n);
     const float inv = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = rms * h2;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = rms;
     const int nbx = (X + kbx - 1) / kbx, nby = (Y + kby - 1) / kby;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         float lk = 0.0f;
@@ -409,7 +454,7 @@ __global__ void __launch_bounds__(256)
             lk = logf(kb[((int64_t)(z / kbz) * nby + y / kby) * nbx + x / kbx]);
         }
         __nv_bfloat162 p;
-        p.x = __float2bfloat16_rn(r[v] * inv);
+        p.x = __float2bfloat16_rn(sr[v] * inv);
         p.y = __float2bfloat16_rn(lk);
         reinterpret_cast<__nv_bfloat162 *>(xin)[v] = p;
     }
@@ -515,12 +560,13 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// g_out = dL/d(network output) = dL/dz * scale, rounded to BF16.
+// g_out = dL/d(network output) = dL/dz * scale * dsc, rounded to BF16.
 __global__ void __launch_bounds__(256)
-    scale_to_bf16_kernel(int64_t n, const float *__restrict__ gz, const double *scale, __nv_bfloat16 *__restrict__ out) {
+    scale_to_bf16_kernel(int64_t n, const float *__restrict__ gz, const double *scale, const float *__restrict__ dsc,
+                         __nv_bfloat16 *__restrict__ out) {
     const float sc = (float)*scale;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-        out[v] = __float2bfloat16_rn(gz[v] * sc);
+        out[v] = __float2bfloat16_rn(gz[v] * sc * dsc[v]);
 }
 
 struct WeightTable {
@@ -603,6 +649,7 @@ struct NnLayout {
     int X[3], Y[3], Z[3];
     int64_t V[3];
     size_t wf, wflip, scal, err, dotws;
+    size_t dsc, sr;  // D^{-1/2} and the scaled residual (FP32)
     size_t xin, a1, k8, p1, a3, k7, p2, a5, a6, a7, a8;
     size_t gout, ga8, gk8, ga7, gk7, ga6, ga5, t5, ge1b, ga3, t3, ge0b, ga1, part;
     size_t lae;  // loss scratch: A e
@@ -638,6 +685,8 @@ inline NnLayout nn_layout(int X, int Y, int Z, bool training) {
     L.scal = take(S_COUNT * sizeof(double));
     L.err = take(sizeof(int));
     L.dotws = take(gbpcg_dot_workspace_size());
+    L.dsc = take(L.V[0] * F);
+    L.sr = take(L.V[0] * F);
     L.xin = take(L.V[0] * 2 * B);
     L.a1 = take(L.V[0] * 16 * B);
     L.k8 = take(L.V[0] * 48 * B);
@@ -713,12 +762,14 @@ int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, 
     auto W = [&](int l) { return wf + layer_offset(l); };
     double *sc = P.at<double>(L.scal);
     int *err = P.at<int>(L.err);
-    GB_TRY(gbpcg_dot(L.V[0], GBPCG_F32, r, r, sc + S_RR, P.base + L.dotws, gbpcg_dot_workspace_size(),
+    float *dsc = P.at<float>(L.dsc), *sr = P.at<float>(L.sr);
+    jacobi_scale_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, r, g.k_block, g.kbx, g.kby, g.kbz, dsc,
+                                                                sr);
+    GB_CUDA(cudaGetLastError());
+    GB_TRY(gbpcg_dot(L.V[0], GBPCG_F32, sr, sr, sc + S_RR, P.base + L.dotws, gbpcg_dot_workspace_size(),
                      (gbpcg_stream)s));
-    const int nmax = std::max(X0, std::max(Y0, Z0));
-    const double h = 1.0 / (nmax + 1);
-    nn_input_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, r, sc + S_RR, g.k_block, g.kbx, g.kby, g.kbz,
-                                                            h * h, P.at<bf16>(L.xin), sc + S_SCALE);
+    nn_input_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, sr, sc + S_RR, g.k_block, g.kbx, g.kby, g.kbz,
+                                                            P.at<bf16>(L.xin), sc + S_SCALE);
     GB_CUDA(cudaGetLastError());
     bf16 *a1 = P.at<bf16>(L.a1), *k8 = P.at<bf16>(L.k8), *p1 = P.at<bf16>(L.p1), *a3 = P.at<bf16>(L.a3),
          *k7 = P.at<bf16>(L.k7), *p2 = P.at<bf16>(L.p2), *a5 = P.at<bf16>(L.a5), *a6 = P.at<bf16>(L.a6),
@@ -739,7 +790,7 @@ int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, 
     up2_kernel<<<blocks_for(L.V[0] * 4, 256), 256, 0, s>>>(X0, Y0, Z0, 32, a7, k8, 48, 0);
     GB_CUDA(cudaGetLastError());
     GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 48, 16, k8, W(7), a8, 16, 0, 1, nullptr, 0, 0, err, s));
-    GB_TRY(conv_simt<float>(X0, Y0, Z0, 16, 1, a8, W(8), z, 0, nullptr, 0, 0, sc + S_SCALE, s));
+    GB_TRY(conv_simt<float>(X0, Y0, Z0, 16, 1, a8, W(8), z, 0, nullptr, 0, 0, sc + S_SCALE, s, dsc));
     return GBPCG_OK;
 }
 
@@ -763,7 +814,7 @@ int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cuda
          *ga1 = P.at<bf16>(L.ga1);
     float *gk8 = P.at<float>(L.gk8), *gk7 = P.at<float>(L.gk7), *t5 = P.at<float>(L.t5), *t3 = P.at<float>(L.t3);
 
-    scale_to_bf16_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.V[0], gz, sc + S_SCALE, gout);
+    scale_to_bf16_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.V[0], gz, sc + S_SCALE, P.at<float>(L.dsc), gout);
     GB_CUDA(cudaGetLastError());
     // c9 (16 -> 1)
     GB_TRY(wgrad(X0, Y0, Z0, 16, 1, a8, gout, G(8), part, s));

@@ -83,8 +83,9 @@ def initial_weights(seed: int = 0) -> torch.Tensor:
 
 
 def identity_weights() -> torch.Tensor:
-    """Weights for which N(r) = h^2 * r up to the BF16 rounding of r / rms(r):
-    c1 splits r into relu(r) and relu(-r), c2 and c8 carry them through the
+    """Weights that pass the scaled residual through, so that N(r) = D^{-1} r
+    (the Jacobi preconditioner) up to the BF16 rounding of D^{-1/2} r / rms:
+    c1 splits it into relu(s) and relu(-s), c2 and c8 carry them through the
     centre tap, the coarse path is zero and c9 recombines them."""
     ws = {name: np.zeros((co, 27, ci)) for name, ci, co in binding.NN_LAYERS}
     ws["c1"][0, 13, 0], ws["c1"][1, 13, 0] = 1.0, -1.0

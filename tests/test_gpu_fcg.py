@@ -22,10 +22,11 @@ def true_relres(b, x, k=None, kb=8):
     return oracle.true_relres(b.cpu().numpy(), x.cpu().numpy(), kk, kb)
 
 
-def test_identity_network_reproduces_cg(gpu_lib):
-    """N(r) = h^2 r (up to one BF16 rounding of r / rms) makes FCG plain CG, which for the
-    constant-coefficient operator is Jacobi PCG: the oracle's iteration count for the 32^3
-    Poisson problem (seed 0, tol 1e-6) is reproduced."""
+def test_identity_network_reproduces_jacobi_pcg(gpu_lib):
+    """The network acts on the Jacobi-scaled system, so weights that pass their input through
+    give N(r) = D^{-1} r (up to one BF16 rounding of the scaled residual): FCG becomes Jacobi
+    PCG, and the oracle's iteration count for the 32^3 Poisson problem (seed 0, tol 1e-6)
+    is reproduced."""
     with open(os.path.join(GOLDEN, "pcg_poisson32_seed0.json")) as f:
         gold = json.load(f)
     b = torch.from_numpy(inputs.poisson_problem(32, 0, np.float64)).cuda()
@@ -38,9 +39,21 @@ def test_identity_network_reproduces_cg(gpu_lib):
     assert abs(res["rel_res_true"] - true_relres(b, x)) <= 1e-3 * res["rel_res_true"]
 
 
+@pytest.mark.parametrize("seed", [3, 4])
+def test_identity_network_matches_jacobi_on_lognormal_coefficients(gpu_lib, seed):
+    """Same on the variable-coefficient operator: FCG with N(r) = D^{-1} r takes the iterations
+    of the library's Jacobi PCG (within a few: one BF16 rounding per application)."""
+    k, b = learned.problem((32, 32, 32), seed)
+    x, res = gpu_lib.fcg_solve(learned.identity_weights().cuda(), b, tol=1e-6, maxit=3000, k_block=k)
+    _, ref = gpu_lib.pcg_solve(b.clone(), torch.zeros_like(b), tol=1e-6, maxit=3000, k_block=k)
+    assert res["status"] == gpu_lib.OK and res["pass_launches"][1] == 0
+    assert abs(res["iters"] - ref["iters"]) <= max(3, ref["iters"] // 20), (res["iters"], ref["iters"])
+    assert true_relres(b, x, k) <= 1e-6
+
+
 @pytest.mark.parametrize("how", ["nan", "negated"])
 def test_descent_check_falls_back_to_jacobi(gpu_lib, how):
-    """A preconditioner that is no descent direction (NaN output, or N(r) = -h^2 r with
+    """A preconditioner that is no descent direction (NaN output, or N(r) = -D^{-1} r with
     r.z < 0) is caught before it touches x; Jacobi PCG finishes the solve."""
     shape = (32, 32, 32)
     k, b = learned.problem(shape, 3)

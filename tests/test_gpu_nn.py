@@ -132,18 +132,18 @@ def unet_case(n=32, seed=5, varcoeff=True, kb=8):
     if varcoeff:
         nb = (n + kb - 1) // kb
         k = inputs.lognormal_blocks(nb, nb, nb, seed + 1)
-        logk = np.log(np.repeat(np.repeat(np.repeat(k.astype(np.float64), kb, 0), kb, 1), kb, 2))[:n, :n, :n]
+        k64 = k.astype(np.float64)
         k_dev = torch.from_numpy(k).float().cuda()
     else:
-        k, logk, k_dev = None, np.zeros(shape), None
+        k64, k_dev = None, None
     ws = onn.init_weights(seed)
-    return r, k, logk, k_dev, ws
+    return r, k64, k_dev, ws
 
 
-def oracle_forward_bf16(r, logk, ws):
+def oracle_forward_bf16(r, k64, ws, kb=8):
     """The oracle U-net with the GPU's BF16 roundings of weights and activations."""
     wsb = {name: bf16_np(v) for name, v in ws.items()}
-    x, scale = onn.net_input(r, logk)
+    x, scale = onn.net_input(r, onn.logk_field(r.shape, k64, kb), onn.jacobi_scale(r.shape, k64, kb))
     x = bf16_np(x)
     out, cache = onn.net_forward(x, wsb, round_fn=bf16_np)
     return out[..., 0] * scale, cache, wsb, scale
@@ -152,21 +152,20 @@ def oracle_forward_bf16(r, logk, ws):
 @pytest.mark.parametrize("varcoeff", [False, True])
 @pytest.mark.parametrize("n", [32, 64])
 def test_unet_forward(gpu_lib, varcoeff, n):
-    r, k, logk, k_dev, ws = unet_case(n, 5 + n, varcoeff)
+    r, k64, k_dev, ws = unet_case(n, 5 + n, varcoeff)
     w = gpu_lib.nn_pack_weights(ws).cuda()
     z = gpu_lib.nn_forward(w, torch.from_numpy(r).float().cuda(), k_block=k_dev).cpu().double().numpy()
     # the oracle sees r as the FP32 numbers the GPU got
-    zr, _, _, _ = oracle_forward_bf16(r.astype(np.float32).astype(np.float64), logk, ws)
+    zr, _, _, _ = oracle_forward_bf16(r.astype(np.float32).astype(np.float64), k64, ws)
     err = np.linalg.norm(z - zr) / np.linalg.norm(zr)
     assert err <= 5e-3, err
     # and the unrounded FP64 network agrees to BF16 accuracy
-    x, scale = onn.net_input(r, logk)
-    z64 = onn.net_forward(x, ws)[0][..., 0] * scale
+    z64 = onn.precond_apply(r, ws, k64, 8)
     assert np.linalg.norm(z - z64) / np.linalg.norm(z64) <= 5e-2
 
 
 def test_unet_forward_is_positively_homogeneous(gpu_lib):
-    r, k, logk, k_dev, ws = unet_case(32, 9, True)
+    r, k64, k_dev, ws = unet_case(32, 9, True)
     w = gpu_lib.nn_pack_weights(ws).cuda()
     rd = torch.from_numpy(r).float().cuda()
     z1 = gpu_lib.nn_forward(w, rd, k_block=k_dev)
@@ -176,7 +175,7 @@ def test_unet_forward_is_positively_homogeneous(gpu_lib):
 
 def test_unet_backward(gpu_lib):
     n = 32
-    r, k, logk, k_dev, ws = unet_case(n, 11, True)
+    r, k64, k_dev, ws = unet_case(n, 11, True)
     w = gpu_lib.nn_pack_weights(ws).cuda()
     rd = torch.from_numpy(r).float().cuda()
     wsp = gpu_lib.nn_workspace(r.shape, training=True)
@@ -184,8 +183,8 @@ def test_unet_backward(gpu_lib):
     gz = rnd(r.shape, 12)
     gw = gpu_lib.nn_backward(torch.from_numpy(gz).float().cuda(), wsp, k_block=k_dev).cpu().double().numpy()
     assert gpu_lib.nn_status(wsp) == gpu_lib.OK
-    zr, cache, wsb, scale = oracle_forward_bf16(r.astype(np.float32).astype(np.float64), logk, ws)
-    gout = bf16_np(gz.astype(np.float32).astype(np.float64) * np.float32(scale))[..., None]
+    zr, cache, wsb, scale = oracle_forward_bf16(r.astype(np.float32).astype(np.float64), k64, ws)
+    gout = bf16_np(gz * scale)[..., None]
     trace = {}
     g = onn.net_backward(gout, wsb, cache, round_fn=bf16_np, trace=trace)
     gg = gpu_lib.nn_unpack_weights(torch.from_numpy(gw))

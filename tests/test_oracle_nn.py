@@ -76,7 +76,7 @@ def test_unet_backward_matches_finite_differences():
     k = inputs.lognormal_blocks(2, 2, 2, 11).astype(np.float64)
     logk = np.log(np.repeat(np.repeat(np.repeat(k, 4, 0), 4, 1), 4, 2))
     ws = nn.init_weights(3)
-    x, scale = nn.net_input(r, logk)
+    x, scale = nn.net_input(r, logk, nn.jacobi_scale(shape, k, 4))
 
     def L(wset, xin):
         out, _ = nn.net_forward(xin, wset)
@@ -131,6 +131,27 @@ def test_fcg_reduces_to_pcg_for_linear_preconditioners(varcoeff):
     plain = oracle.pcg(b, tol=1e-8, maxit=500, k=k, kb=4, precond=None)
     f2 = nn.fcg(b, lambda r: r.copy(), tol=1e-8, maxit=500, k=k, kb=4)
     assert abs(f2["iters"] - plain["iters"]) <= 1
+    f5 = nn.fcg(b, lambda r: r / d, tol=1e-8, maxit=500, k=k, kb=4, m=5)  # more memory changes nothing
+    assert abs(f5["iters"] - ref["iters"]) <= 1
+    np.testing.assert_allclose(f5["x"], ref["x"], rtol=0, atol=1e-7 * np.max(np.abs(ref["x"])))
+
+
+def test_fcg_full_memory_keeps_directions_a_orthogonal():
+    """With a nonlinear preconditioner and truncation m >= iterations, every search direction is
+    A-orthogonal to all earlier ones (Notay's FCG with full orthogonalisation)."""
+    shape = (6, 7, 5)
+    b = rnd(shape, 60)
+
+    def M(r):  # a small nonlinear, positively homogeneous map
+        return np.maximum(r, 0.0) * 2.0 + np.minimum(r, 0.0) * 0.5 + 0.1 * oracle.apply(r) / 100.0
+
+    dirs = []
+    nn.fcg(b, M, tol=1e-10, maxit=12, m=50, directions=dirs)
+    for i in range(len(dirs)):
+        for j in range(i):
+            pi, qi = dirs[i]
+            pj, qj = dirs[j]
+            assert abs(float(np.sum(pi * qj))) <= 1e-9 * np.sqrt(float(np.sum(pi * qi)) * float(np.sum(pj * qj)))
 
 
 def test_adam_first_steps_closed_form():
@@ -152,7 +173,7 @@ def test_rounded_backward_reduces_to_exact_and_traces_layers():
     shape = (8, 8, 8)
     r = rnd(shape, 50)
     ws = nn.init_weights(4)
-    x, scale = nn.net_input(r, np.zeros(shape))
+    x, scale = nn.net_input(r, np.zeros(shape), nn.jacobi_scale(shape))
     out, cache = nn.net_forward(x, ws)
     gout = rnd(shape + (1,), 51)
     g0 = nn.net_backward(gout, ws, cache)
@@ -191,3 +212,22 @@ def test_scaled_loss_properties_and_gradient():
             fd = (nn.loss_scaled(zp2, e, k, 4) - nn.loss_scaled(zm2, e, k, 4)) / (2 * h)
             assert abs(fd - g[idx]) <= 1e-6 * abs(fd) + 1e-11
         assert abs(float(np.sum(g * zz))) <= 1e-12 * np.linalg.norm(g) * np.linalg.norm(zz)
+
+
+def test_network_input_scaling():
+    """The input is the Jacobi-scaled residual at unit rms plus log k; the output scale undoes
+    both, so N is positively homogeneous in r, and a single block of constant k reduces the
+    scaling to the Poisson one times k^{-1/2}."""
+    shape = (8, 8, 8)
+    r = rnd(shape, 70)
+    k = np.full((1, 1, 1), 3.0)
+    dsc = nn.jacobi_scale(shape, k, 8)
+    np.testing.assert_allclose(dsc, nn.jacobi_scale(shape) / np.sqrt(3.0), rtol=1e-14)
+    x, scale = nn.net_input(r, nn.logk_field(shape, k, 8), dsc)
+    assert abs(float(np.mean(x[..., 0] ** 2)) - 1.0) <= 1e-12
+    np.testing.assert_allclose(x[..., 1], np.log(3.0), rtol=1e-15)
+    np.testing.assert_allclose(x[..., 0] * scale, r * dsc * dsc, rtol=1e-12)
+    ws = nn.init_weights(7)
+    z1 = nn.precond_apply(r, ws, k, 8)
+    z2 = nn.precond_apply(2.5 * r, ws, k, 8)
+    np.testing.assert_allclose(z2, 2.5 * z1, rtol=1e-12, atol=1e-300)
