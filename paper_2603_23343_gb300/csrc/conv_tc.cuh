@@ -93,7 +93,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // TMEM columns to allocate for an accumulator of N FP32 columns (a power
 // of two, at least 32).
 __host__ __device__ constexpr uint32_t tmem_cols(int N) {
-    return N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+    return N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : N <= 256 ? 256u : 512u;
 }
 
 struct __align__(128) ConvMaps {
@@ -253,6 +253,158 @@ __global__ void __launch_bounds__(128) conv3_tc_kernel(const __grid_constant__ C
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, NCOL);
+    if (!good && threadIdx.x == 0) atomicExch(a.err, 1);
+}
+
+// ------------------------------------------------------------------------
+// Halo-slab variant for X a multiple of 128: a CTA owns R = 4 rows of 128
+// voxels (four M tiles, 4 x CO TMEM columns) of one plane.  A pipeline step
+// is one 16-channel chunk of one source plane (dz): the (R + 2) rows x 130
+// voxels around the tile arrive in one TMA box per 8-channel half, together
+// with that plane's 9 taps of weights.  Every tap (dy, dx) of every M tile
+// then reads the slab in place: its A operand starts (rho + dy + 1) rows and
+// (dx + 1) voxels into it, a 16-byte multiple, with the same SBO (128 B) and
+// LBO (distance between the halves).  Input traffic per output voxel and
+// 16-channel chunk: 3 x 6 x 130 x 32 B / 512 = 146 B, against 27 x 32 B =
+// 864 B when each tap reloads its tile.
+
+constexpr int kHaloRows = 4;
+constexpr int kHaloX = 130;
+
+template <int CO>
+struct HaloCfg {
+    static constexpr uint32_t A_HALF = ((uint32_t)(16 * kHaloX * (kHaloRows + 2)) + 127) & ~127u;
+    static constexpr uint32_t B_HALF = 9u * CO * 16u;  // a multiple of 128 for CO % 16 == 0
+    static constexpr uint32_t A_TX = 2u * 16 * kHaloX * (kHaloRows + 2);
+    static constexpr uint32_t STAGE_TX = A_TX + 2 * B_HALF;
+    static constexpr uint32_t STAGE = (2 * A_HALF + 2 * B_HALF + 1023) & ~1023u;
+    static constexpr int STAGES = (int)(((220u * 1024u) / STAGE) < 6u ? ((220u * 1024u) / STAGE) : 6u);
+    static constexpr uint32_t SMEM = STAGES * STAGE;
+    static constexpr uint32_t NCOL = tmem_cols(kHaloRows * CO);
+    static_assert(STAGES >= 2, "halo stage too large");
+    static_assert(kHaloRows * CO <= 512, "TMEM columns");
+};
+
+template <int CO, typename OUT>
+__global__ void __launch_bounds__(128) conv3_tc_halo_kernel(const __grid_constant__ ConvMaps maps, const ConvArgs a) {
+    using H = HaloCfg<CO>;
+    constexpr int S = H::STAGES;
+    constexpr uint32_t IDESC = idesc_bf16(128, CO);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * 128, y0 = blockIdx.y * kHaloRows, z0 = blockIdx.z;
+    const int kc = a.ci / 16;
+    const int KT = 3 * kc;  // (chunk, plane) steps
+
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, H::NCOL);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t sbase = smem_u32(smem);
+
+    if (warp == 0 && lane == 0) {
+        int kk = 0;
+        for (; kk < KT; ++kk) {
+            const int s = kk % S;
+            if (kk >= S && !mbar_wait_bounded(&empty[s], ((kk / S) - 1) & 1)) {
+                s_err = 1;
+                break;
+            }
+            const int cc = kk / 3, pz = kk - cc * 3;  // chunk, plane (dz = pz - 1)
+            unsigned char *st = smem + (size_t)s * H::STAGE;
+            mbar_arrive_expect_tx(&full[s], H::STAGE_TX);
+            for (int h = 0; h < 2; ++h) {
+                tma_load_4d(st + h * H::A_HALF, &maps.act, &full[s], cc * 16 + h * 8, x0 - 1, y0 - 1, z0 + pz - 1);
+                for (int tau = 0; tau < 9; ++tau)
+                    tma_load_2d(st + 2 * H::A_HALF + h * H::B_HALF + tau * CO * 16, &maps.wgt, &full[s],
+                                (pz * 9 + tau) * a.ci + cc * 16 + h * 8, 0);
+            }
+        }
+        for (int s = 0; s < S; ++s) {
+            const int last = kk - 1 - ((kk - 1 - s) % S + S) % S;
+            if (last >= 0 && last < kk && !mbar_wait_bounded(&full[s], (last / S) & 1)) s_err = 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kk = 0; kk < KT; ++kk) {
+            const int s = kk % S;
+            if (!mbar_wait_bounded(&full[s], (kk / S) & 1)) {
+                s_err = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = sbase + (uint32_t)s * H::STAGE;
+            const uint32_t sb = sa + 2 * H::A_HALF;
+#pragma unroll 1
+            for (int rho = 0; rho < kHaloRows; ++rho)
+#pragma unroll
+                for (int tau = 0; tau < 9; ++tau) {
+                    const int dy = tau / 3 - 1, dx = tau % 3 - 1;
+                    const uint32_t aa = sa + (uint32_t)(((rho + dy + 1) * kHaloX + dx + 1) * 16);
+                    const uint64_t adesc = umma_desc_kmajor(aa, H::A_HALF, 128);
+                    const uint64_t bdesc = umma_desc_kmajor(sb + (uint32_t)(tau * CO * 16), H::B_HALF, 128);
+                    mma_bf16(tmem + (uint32_t)(rho * CO), adesc, bdesc, IDESC, (kk > 0 || tau > 0) ? 1u : 0u);
+                }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&done, 0);
+    __syncthreads();
+    const bool good = ok && !s_err;
+    tc_fence_after();
+
+    // epilogue: warp w reads lanes 32w .. 32w + 31 (voxels x0 + 32w + lane) of each M tile
+    const int x = x0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int rho = 0; rho < kHaloRows; ++rho) {
+        const int64_t v = ((int64_t)z0 * a.Y + y0 + rho) * a.X + x;
+        OUT *out = static_cast<OUT *>(a.out) + v * a.cstride + a.coff;
+        const __nv_bfloat16 *mk = a.mask ? a.mask + v * a.mstride + a.moff : nullptr;
+#pragma unroll
+        for (int c0 = 0; c0 < CO; c0 += 16) {
+            float f[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(rho * CO + c0), f);
+            float m[16];
+            if (mk) {
+                ld8(mk + c0, m);
+                ld8(mk + c0 + 8, m + 8);
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                f[i] = good ? f[i] : 0.0f;
+                if (a.relu) f[i] = f[i] < 0.0f ? 0.0f : f[i];
+                if (mk && !(m[i] > 0.0f)) f[i] = 0.0f;
+            }
+            if constexpr (std::is_same<OUT, float>::value) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) st4(out + c0 + i, f + i);
+            } else {
+                st8(out + c0, f);
+                st8(out + c0 + 8, f + 8);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, H::NCOL);
     if (!good && threadIdx.x == 0) atomicExch(a.err, 1);
 }
 

@@ -103,6 +103,21 @@ static int conv_tc_launch(int X, int Y, int Z, int ci, const __nv_bfloat16 *in, 
     const uint32_t wb[2] = {8, (uint32_t)CO};
     rc = make_map_nd(&maps.wgt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, wd, wst, wb);
     if (rc) return rc;
+    if (X % 128 == 0 && Y % kHaloRows == 0 && Z <= 65535) {
+        // rows of 128: the halo-slab kernel, whose A box is (8, 130, rows + 2, 1)
+        const uint32_t hbox[4] = {8, (uint32_t)kHaloX, (uint32_t)kHaloRows + 2, 1};
+        rc = make_map_nd(&maps.act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, in, 4, dims, strides, hbox);
+        if (rc) return rc;
+        constexpr uint32_t hsmem = HaloCfg<CO>::SMEM;
+        static std::once_flag honce;
+        std::call_once(honce, [] {
+            cudaFuncSetAttribute(conv3_tc_halo_kernel<CO, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)hsmem);
+        });
+        conv3_tc_halo_kernel<CO, OUT><<<dim3(X / 128, Y / kHaloRows, Z), 128, hsmem, s>>>(maps, a);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_tc_halo launch");
+    }
     constexpr uint32_t smem = conv_smem_bytes<CO>();
     static std::once_flag once;
     std::call_once(once, [] {
