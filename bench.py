@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N_GRID, help="grid points per axis (default 256)")
     ap.add_argument("--cpu-iters", type=int, default=200, help="oracle iterations in the CPU-baseline sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner leg")
+    ap.add_argument("--learned-full", action="store_true",
+                    help="learned leg at the full recipe: 128^3 training on seeds 10-99, evaluation on 100-109")
     return ap.parse_args()
 
 
@@ -60,6 +63,101 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def tensor_peak():
+    """Dense BF16 TFLOP/s: (burst, sustained, source)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+# U-net work per finest-level voxel (multiply-adds): level 0 c1 + c2 + c8 + c9, level 1 (1/8)
+# c3 + c4 + c7, level 2 (1/64) c5 + c6; 2 FLOP per multiply-add
+UNET_MACS_PER_VOXEL = (864 + 6912 + 20736 + 432) + (13824 + 27648 + 82944) / 8 + (55296 + 110592) / 64
+
+
+def learned_leg(B, learned, stream, full: bool):
+    """BASELINE config 4: train on the GPU at 128^3 on lognormal problems (pairs from the plain
+    solver), evaluate learned FCG against Jacobi PCG at 256^3 on held-out seeds, and time the
+    heaviest convolution (c8, 48 -> 16 channels at 256^3) against the tensor peak."""
+    import torch
+    train_seeds = range(10, 100) if full else range(10, 42)
+    eval_seeds = range(100, 110) if full else range(100, 102)
+    steps = 6000 if full else 2000
+    t0 = time.perf_counter()
+    pairs = learned.make_pairs((128, 128, 128), seeds=train_seeds)
+    torch.cuda.synchronize()
+    pair_s = time.perf_counter() - t0
+    w, losses, train_s = learned.train(pairs, learned.initial_weights(0).cuda(), steps, lr=1e-3, lr_final=1e-4)
+    del pairs
+    torch.cuda.empty_cache()
+    evals = []
+    for sd in eval_seeds:
+        k, bb = learned.problem((256, 256, 256), sd)
+        xj = torch.zeros_like(bb)
+        B.pcg_solve(bb, xj, tol=TOL, maxit=20000, k_block=k)  # graph build
+        xj.zero_()
+        _, rj = B.pcg_solve(bb, xj, tol=TOL, maxit=20000, k_block=k)
+        fws = B.fcg_workspace(bb.shape, k_block=k, tol=TOL, maxit=20000)
+        _, rl = B.fcg_solve(w, bb, tol=TOL, maxit=20000, k_block=k, workspace=fws)
+        evals.append({"seed": sd, "jacobi": {"iters": rj["iters"], "ms": rj["time_ms"],
+                                             "rel_res_true_fp64": rj["rel_res_true"]},
+                      "learned_fcg": {"iters": rl["iters"], "ms": rl["time_ms"], "network_ms": rl["pass_ms"][0],
+                                      "fcg_iters": rl["pass_launches"][0], "fallback_iters": rl["pass_launches"][1],
+                                      "status": rl["status_name"], "rel_res_true_fp64": rl["rel_res_true"]}})
+        del fws, xj
+        torch.cuda.empty_cache()
+    # one network application and the c8 convolution alone, CUDA events on the launching stream
+    n = 256
+    k, bb = learned.problem((n, n, n), eval_seeds[0])
+    r = bb.float()
+    z = torch.empty_like(r)
+    nws = B.nn_workspace(r.shape)
+    B.nn_forward(w, r, z, k_block=k, workspace=nws, stream=stream)
+    xin = torch.randn((n, n, n, 48), device="cuda").to(torch.bfloat16)
+    w8 = (torch.randn((16, 27, 48), device="cuda") * 0.03).to(torch.bfloat16)
+    cws = B.conv3_workspace((n, n, n), 48, 16)
+    B.conv3_forward(xin, w8, workspace=cws, stream=stream)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    for _ in range(reps):
+        B.nn_forward(w, r, z, k_block=k, workspace=nws, stream=stream)
+    e1.record(stream)
+    for _ in range(reps):
+        B.conv3_forward(xin, w8, workspace=cws, stream=stream)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    net_ms = e0.elapsed_time(e1) / reps
+    c8_ms = e1.elapsed_time(e2) / reps
+    burst, sustained, src = tensor_peak()
+    c8_flop = 2.0 * n ** 3 * 27 * 48 * 16
+    net_flop = 2.0 * n ** 3 * UNET_MACS_PER_VOXEL
+    c8_tf = c8_flop / (c8_ms * 1e-3) / 1e12
+    iters_j = [e["jacobi"]["iters"] for e in evals]
+    iters_l = [e["learned_fcg"]["iters"] for e in evals]
+    return {
+        "recipe": ("full" if full else "reduced") + f": train 128^3 lognormal seeds {train_seeds.start}-"
+                  f"{train_seeds.stop - 1} x snapshots (0,2,5,10,20,40,80), {steps} Adam steps; "
+                  f"evaluate 256^3 seeds {eval_seeds.start}-{eval_seeds.stop - 1}, tol {TOL}",
+        "pairs_s": pair_s, "train_s": train_s, "train_ms_per_step": 1e3 * train_s / steps,
+        "loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-200:]))],
+        "eval": evals,
+        "iters_ratio_learned_over_jacobi": float(np.mean(iters_l) / np.mean(iters_j)),
+        "ms_ratio_learned_over_jacobi": float(np.mean([e["learned_fcg"]["ms"] for e in evals]) /
+                                              np.mean([e["jacobi"]["ms"] for e in evals])),
+        "network_256": {"ms": net_ms, "tflops": net_flop / (net_ms * 1e-3) / 1e12,
+                        "flop": net_flop},
+        "roofline_conv_c8_256": {"bound": "tensor", "kernel": "conv3_tc_halo_kernel<16> (48->16 channels)",
+                                 "achieved": c8_tf, "peak": burst, "unit": "TFLOP/s", "frac": c8_tf / burst,
+                                 "peak_source": src + " bf16 burst", "flop_per_launch": c8_flop,
+                                 "avg_launch_us": c8_ms * 1e3, "traffic": None},
+    }
 
 
 class ClockSampler:
@@ -372,6 +470,11 @@ def main():
                "sequential_ms": seq_ms}
     del rhs, xb
 
+    learned_res = None
+    if not args.no_learned and n == 256:
+        from paper_2603_23343_gb300 import learned
+        learned_res = learned_leg(B, learned, stream, args.learned_full)
+
     iter_us = ms_step * 1e3 / max(1, iters)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -402,6 +505,7 @@ def main():
             },
             "mixed_precision": mixed,
             "batched_config3": batched,
+            "learned_config4": learned_res,
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,
                     "d2h_bytes_per_step": N * 8 + 256},
