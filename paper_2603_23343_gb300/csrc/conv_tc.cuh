@@ -278,7 +278,9 @@ struct HaloCfg {
     static constexpr uint32_t A_TX = 2u * 16 * kHaloX * (kHaloRows + 2);
     static constexpr uint32_t STAGE_TX = A_TX + 2 * B_HALF;
     static constexpr uint32_t STAGE = (2 * A_HALF + 2 * B_HALF + 1023) & ~1023u;
-    static constexpr int STAGES = (int)(((220u * 1024u) / STAGE) < 6u ? ((220u * 1024u) / STAGE) : 6u);
+    // two CTAs per SM (about 110 KB each), so that one CTA's prologue and
+    // epilogue overlap the other's loads and MMAs
+    static constexpr int STAGES = (int)(((110u * 1024u) / STAGE) < 6u ? ((110u * 1024u) / STAGE) : 6u);
     static constexpr uint32_t SMEM = STAGES * STAGE;
     static constexpr uint32_t NCOL = tmem_cols(kHaloRows * CO);
     static_assert(STAGES >= 2, "halo stage too large");

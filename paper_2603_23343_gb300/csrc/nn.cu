@@ -150,8 +150,11 @@ inline bool conv_tc_ok(int X, int Y, int Z, int ci, int co) {
 }
 
 // ------------------------------------------------ CUDA-core convolution ----
-// One thread per voxel computes all CO outputs; weights (CO, 27, CI) sit in
-// shared memory as FP32, ordered so that every thread reads the same word.
+// For the 1- and 2-channel ends of the network.  A thread computes VX
+// consecutive x voxels: for each of the 9 (dy, dz) source rows it loads the
+// VX + 2 input positions once and applies the 3 x-taps to all VX outputs, so
+// loads and shared-memory weight reads are shared by VX outputs.  Weights
+// (CO, 27, CI) sit in shared memory as FP32 [t][i][o].
 
 template <int C, typename T>
 __device__ __forceinline__ void load_ch(const T *p, float v[C]) {
@@ -164,50 +167,92 @@ __device__ __forceinline__ void load_ch(const T *p, float v[C]) {
     }
 }
 
-template <int CI, int CO, typename TO>
+template <int CI, int CO, int VX, typename TO>
 __global__ void __launch_bounds__(256)
     conv3_simt_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
                       TO *__restrict__ out, int relu, const __nv_bfloat16 *__restrict__ mask, int mstride, int moff,
                       const double *scale, const float *__restrict__ vscale) {
-    __shared__ float ws[27 * CI * CO];
+    __shared__ __align__(16) float ws[27 * CI * CO];
     for (int e = threadIdx.x; e < 27 * CI * CO; e += blockDim.x) {
         const int o = e / (27 * CI), r = e - o * 27 * CI;  // r = t * CI + i
         ws[r * CO + o] = __bfloat162float(w[e]);
     }
     __syncthreads();
     const float sc = scale ? (float)*scale : 1.0f;
-    const int64_t n = (int64_t)X * Y * Z;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
-        float acc[CO];
+    const int XQ = X / VX;
+    const int64_t n = (int64_t)XQ * Y * Z;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int xq = (int)(u % XQ), y = (int)((u / XQ) % Y), z = (int)(u / ((int64_t)XQ * Y));
+        const int x0 = xq * VX;
+        float acc[VX][CO];
 #pragma unroll
-        for (int o = 0; o < CO; ++o) acc[o] = 0.0f;
+        for (int j = 0; j < VX; ++j)
+#pragma unroll
+            for (int o = 0; o < CO; ++o) acc[j][o] = 0.0f;
 #pragma unroll 1
-        for (int t = 0; t < 27; ++t) {
-            const int xx = x + t % 3 - 1, yy = y + (t / 3) % 3 - 1, zz = z + t / 9 - 1;
-            if (xx < 0 || xx >= X || yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
-            float iv[CI];
-            load_ch<CI>(in + (((int64_t)zz * Y + yy) * X + xx) * CI, iv);
+        for (int r9 = 0; r9 < 9; ++r9) {
+            const int yy = y + r9 % 3 - 1, zz = z + r9 / 3 - 1;
+            if (yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
+            const __nv_bfloat16 *row = in + (((int64_t)zz * Y + yy) * X) * CI;
+            float iv[VX + 2][CI];
 #pragma unroll
-            for (int i = 0; i < CI; ++i)
+            for (int q = 0; q < VX + 2; ++q) {
+                const int xx = x0 - 1 + q;
+                if (xx >= 0 && xx < X) {
+                    load_ch<CI>(row + (int64_t)xx * CI, iv[q]);
+                } else {
 #pragma unroll
-                for (int o = 0; o < CO; ++o) acc[o] = fmaf(iv[i], ws[(t * CI + i) * CO + o], acc[o]);
+                    for (int i = 0; i < CI; ++i) iv[q][i] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const float *wt = ws + (r9 * 3 + dx) * CI * CO;  // tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)
+#pragma unroll
+                for (int i = 0; i < CI; ++i) {
+                    if constexpr (CO % 4 == 0) {
+#pragma unroll
+                        for (int o = 0; o < CO; o += 4) {
+                            const float4 wv = *reinterpret_cast<const float4 *>(wt + i * CO + o);
+#pragma unroll
+                            for (int j = 0; j < VX; ++j) {
+                                const float a = iv[j + dx][i];
+                                acc[j][o] = fmaf(a, wv.x, acc[j][o]);
+                                acc[j][o + 1] = fmaf(a, wv.y, acc[j][o + 1]);
+                                acc[j][o + 2] = fmaf(a, wv.z, acc[j][o + 2]);
+                                acc[j][o + 3] = fmaf(a, wv.w, acc[j][o + 3]);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int o = 0; o < CO; ++o) {
+                            const float wv = wt[i * CO + o];
+#pragma unroll
+                            for (int j = 0; j < VX; ++j) acc[j][o] = fmaf(iv[j + dx][i], wv, acc[j][o]);
+                        }
+                    }
+                }
+            }
         }
-        TO *po = out + v * CO;
-        const float vs = vscale ? sc * vscale[v] : sc;
 #pragma unroll
-        for (int o = 0; o < CO; ++o) {
-            float f = acc[o] * vs;
-            if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
-            if (mask && !(__bfloat162float(mask[v * mstride + moff + o]) > 0.0f)) f = 0.0f;
-            acc[o] = f;
-        }
-        if constexpr (CO % 8 == 0 && std::is_same<TO, __nv_bfloat16>::value) {
+        for (int j = 0; j < VX; ++j) {
+            const int64_t v = ((int64_t)z * Y + y) * X + x0 + j;
+            TO *po = out + v * CO;
+            const float vs = vscale ? sc * vscale[v] : sc;
 #pragma unroll
-            for (int o = 0; o < CO; o += 8) st8(po + o, acc + o);
-        } else {
+            for (int o = 0; o < CO; ++o) {
+                float f = acc[j][o] * vs;
+                if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
+                if (mask && !(__bfloat162float(mask[v * mstride + moff + o]) > 0.0f)) f = 0.0f;
+                acc[j][o] = f;
+            }
+            if constexpr (CO % 8 == 0 && std::is_same<TO, __nv_bfloat16>::value) {
 #pragma unroll
-            for (int o = 0; o < CO; ++o) po[o] = from_f<TO>(acc[o]);
+                for (int o = 0; o < CO; o += 8) st8(po + o, acc[j] + o);
+            } else {
+#pragma unroll
+                for (int o = 0; o < CO; ++o) po[o] = from_f<TO>(acc[j][o]);
+            }
         }
     }
 }
@@ -216,9 +261,15 @@ template <int CI, int CO, typename TO>
 static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out, int relu,
                             const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
                             const float *vscale, cudaStream_t s) {
-    const int64_t n = (int64_t)X * Y * Z;
-    conv3_simt_kernel<CI, CO, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride, moff,
-                                                                      scale, vscale);
+    if (X % 4 == 0) {
+        const int64_t n = (int64_t)(X / 4) * Y * Z;
+        conv3_simt_kernel<CI, CO, 4, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride,
+                                                                             moff, scale, vscale);
+    } else {
+        const int64_t n = (int64_t)X * Y * Z;
+        conv3_simt_kernel<CI, CO, 1, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride,
+                                                                             moff, scale, vscale);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_simt launch");
 }
