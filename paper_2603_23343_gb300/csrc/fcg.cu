@@ -32,7 +32,7 @@ int launch_stencil_f64(const gbpcg_grid &g, const double *p, double *q, cudaStre
 size_t nn_layout_total(int X, int Y, int Z, bool training);
 size_t nn_layout_err_offset();
 bool nn_shape_ok_ext(int X, int Y, int Z);
-int nn_prep_ext(const float *w, void *ws, int X, int Y, int Z, cudaStream_t s);
+int nn_prep_ext(const float *w, void *ws, const gbpcg_grid &g, cudaStream_t s);
 int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s);
 
 constexpr int kMaxDirs = 16;
@@ -360,7 +360,7 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
     GB_CUDA(cudaEventRecord(e0, s));
     GB_CUDA(cudaMemsetAsync(st, 0, sizeof(FcgState), s));
     GB_CUDA(cudaMemsetAsync(static_cast<char *>(nnws) + nn_layout_err_offset(), 0, sizeof(int), s));
-    rc = nn_prep_ext(w, nnws, g.nx, g.ny, g.nz, s);
+    rc = nn_prep_ext(w, nnws, g, s);
     if (rc) return rc;
     rc = gbpcg_dot(n, GBPCG_F64, b, b, &st->bb, dotws, dws, stream);
     if (rc) return rc;

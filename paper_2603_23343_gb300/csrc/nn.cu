@@ -470,13 +470,13 @@ static int wgrad(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, co
 
 // --------------------------------------------------------- glue kernels ----
 
-// dsc = D^{-1/2} and s = D^{-1/2} r at every point.  D = sum over the six
-// faces of k_f / h_d^2, with k_f the harmonic mean of the two cells' block
-// coefficients on interior faces and the cell's own coefficient on boundary
-// faces (kb == NULL: k = 1).
+// dsc = D^{-1/2} at every point.  D = sum over the six faces of k_f / h_d^2,
+// with k_f the harmonic mean of the two cells' block coefficients on interior
+// faces and the cell's own coefficient on boundary faces (kb == NULL: k = 1).
+// It depends on the operator only, so a solve computes it once.
 __global__ void __launch_bounds__(256)
-    jacobi_scale_kernel(int X, int Y, int Z, const float *__restrict__ r, const float *__restrict__ kb, int kbx,
-                        int kby, int kbz, float *__restrict__ dsc, float *__restrict__ sr) {
+    jacobi_scale_kernel(int X, int Y, int Z, const float *__restrict__ kb, int kbx, int kby, int kbz,
+                        float *__restrict__ dsc) {
     const int64_t n = (int64_t)X * Y * Z;
     const float cx = (float)(X + 1) * (float)(X + 1), cy = (float)(Y + 1) * (float)(Y + 1),
                 cz = (float)(Z + 1) * (float)(Z + 1);
@@ -497,9 +497,16 @@ __global__ void __launch_bounds__(256)
             d = cx * (face(x - 1, y, z) + face(x + 1, y, z)) + cy * (face(x, y - 1, z) + face(x, y + 1, z)) +
                 cz * (face(x, y, z - 1) + face(x, y, z + 1));
         }
-        const float ds = 1.0f / sqrtf(d);
-        dsc[v] = ds;
-        sr[v] = r[v] * ds;
+        dsc[v] = 1.0f / sqrtf(d);
+    }
+}
+
+// s = D^{-1/2} r (n a multiple of 4)
+__global__ void __launch_bounds__(256)
+    scale_residual_kernel(int64_t n4, const float *__restrict__ r, const float *__restrict__ dsc, float *__restrict__ sr) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = reinterpret_cast<const float4 *>(r)[i], d = reinterpret_cast<const float4 *>(dsc)[i];
+        reinterpret_cast<float4 *>(sr)[i] = make_float4(a.x * d.x, a.y * d.y, a.z * d.z, a.w * d.w);
     }
 }
 
@@ -819,8 +826,18 @@ int nn_weight_prep(const float *w, void *ws, const NnLayout &L, cudaStream_t s) 
     return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "weight_prep launch");
 }
 
-// z = N(r) with the BF16 weights already in the workspace.
-int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, const NnLayout &L, cudaStream_t s) {
+// D^{-1/2} of the grid's operator into the workspace.
+int nn_diag_prep(const gbpcg_grid &g, void *ws, const NnLayout &L, cudaStream_t s) {
+    NnPtrs P{static_cast<char *>(ws)};
+    jacobi_scale_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.X[0], L.Y[0], L.Z[0], g.k_block, g.kbx, g.kby, g.kbz,
+                                                                P.at<float>(L.dsc));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "jacobi_scale launch");
+}
+
+// z = N(r) with the BF16 weights (and, if dsc_ready, D^{-1/2}) already in the workspace.
+int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, const NnLayout &L, cudaStream_t s,
+                       bool dsc_ready = false) {
     NnPtrs P{static_cast<char *>(ws)};
     const int X0 = L.X[0], Y0 = L.Y[0], Z0 = L.Z[0], X1 = L.X[1], Y1 = L.Y[1], Z1 = L.Z[1], X2 = L.X[2], Y2 = L.Y[2],
               Z2 = L.Z[2];
@@ -829,8 +846,8 @@ int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, 
     double *sc = P.at<double>(L.scal);
     int *err = P.at<int>(L.err);
     float *dsc = P.at<float>(L.dsc), *sr = P.at<float>(L.sr);
-    jacobi_scale_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, r, g.k_block, g.kbx, g.kby, g.kbz, dsc,
-                                                                sr);
+    if (!dsc_ready) GB_TRY(nn_diag_prep(g, ws, L, s));
+    scale_residual_kernel<<<blocks_for(L.V[0] / 4, 256), 256, 0, s>>>(L.V[0] / 4, r, dsc, sr);
     GB_CUDA(cudaGetLastError());
     GB_TRY(gbpcg_dot(L.V[0], GBPCG_F32, sr, sr, sc + S_RR, P.base + L.dotws, gbpcg_dot_workspace_size(),
                      (gbpcg_stream)s));
@@ -955,11 +972,13 @@ static int nn_loss_ws(const gbpcg_grid &g, const float *z, const float *e, float
 size_t nn_layout_total(int X, int Y, int Z, bool training) { return nn_layout(X, Y, Z, training).total; }
 size_t nn_layout_err_offset() { return nn_layout(128, 128, 128, false).err; }
 bool nn_shape_ok_ext(int X, int Y, int Z) { return nn_shape_ok(X, Y, Z); }
-int nn_prep_ext(const float *w, void *ws, int X, int Y, int Z, cudaStream_t s) {
-    return nn_weight_prep(w, ws, nn_layout(X, Y, Z, false), s);
+int nn_prep_ext(const float *w, void *ws, const gbpcg_grid &g, cudaStream_t s) {
+    const NnLayout L = nn_layout(g.nx, g.ny, g.nz, false);
+    GB_TRY(nn_weight_prep(w, ws, L, s));
+    return nn_diag_prep(g, ws, L, s);
 }
 int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s) {
-    return nn_forward_prepped(g, r, z, ws, nn_layout(g.nx, g.ny, g.nz, false), s);
+    return nn_forward_prepped(g, r, z, ws, nn_layout(g.nx, g.ny, g.nz, false), s, true);
 }
 
 }  // namespace gb
