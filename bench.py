@@ -427,8 +427,7 @@ def main():
 
     mixed = {"poisson256_tol1e-6": {"fp32_plain": {"ms": ms_step, "iters": iters}}}
     for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
-        mixed["poisson256_tol1e-6"][name] = timed_solve(b, tol=TOL, maxit=MAXIT, storage=dt, inner_tol=1e-2,
-                                                        max_outer=10)
+        mixed["poisson256_tol1e-6"][name] = timed_solve(b, tol=TOL, maxit=MAXIT, storage=dt, max_outer=20)
     if N <= 256 ** 3:
         k512, b512 = inputs.varcoeff_problem(512, 512, 512, seed=1, kb=8)
         kd = torch.from_numpy(k512).cuda()
@@ -436,10 +435,8 @@ def main():
         del b512
         c2 = {}
         c2["fp32_plain"] = timed_solve(bd, tol=1e-8, maxit=20000, k_block=kd, kb=8)
-        c2["fp16"] = timed_solve(bd, tol=1e-8, maxit=8000, k_block=kd, kb=8, storage=torch.float16, inner_tol=1e-2,
-                                 max_outer=10)
-        c2["bf16"] = timed_solve(bd, tol=1e-8, maxit=6000, k_block=kd, kb=8, storage=torch.bfloat16,
-                                 inner_tol=1e-2, max_outer=4)
+        c2["fp16"] = timed_solve(bd, tol=1e-8, maxit=8000, k_block=kd, kb=8, storage=torch.float16, max_outer=20)
+        c2["bf16"] = timed_solve(bd, tol=1e-8, maxit=6000, k_block=kd, kb=8, storage=torch.bfloat16, max_outer=20)
         mixed["config2_512_lognormal_tol1e-8"] = c2
         del bd, kd
         torch.cuda.empty_cache()

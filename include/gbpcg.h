@@ -96,7 +96,8 @@ typedef struct gbpcg_opts {
                               configuration of pass A / pass B (see gbpcg_tile_config) */
     void *workspace;       /* device scratch owned by the caller */
     size_t workspace_bytes;
-    double inner_tol;      /* refinement (16-bit storage): relative tolerance of each inner solve */
+    double inner_tol;      /* refinement (16-bit storage): relative tolerance of each inner solve;
+                              0 selects the default, 0.1 for BF16 and 1e-2 for F16 */
     int32_t max_outer;     /* refinement: maximum outer FP64 steps */
     int32_t fcg_m;         /* gbpcg_fcg_solve: each search direction is A-orthogonalised against the
                               last fcg_m ones (1 .. 16; 0 selects 8); ignored elsewhere */

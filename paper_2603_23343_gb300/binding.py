@@ -259,7 +259,7 @@ def tile_cfg_code(cfg_a=None, cfg_b=None) -> int:
 
 
 def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
-              profile=False, tile_cfg=0, inner_tol=1e-2, max_outer=30, autotune=False) -> Opts:
+              profile=False, tile_cfg=0, inner_tol=0.0, max_outer=30, autotune=False) -> Opts:
     o = Opts()
     o.tol = float(tol)
     o.maxit = int(maxit)
@@ -291,7 +291,7 @@ def alloc_workspace(shape, k_block=None, kb=8, device="cuda", **opt_kw) -> torch
 
 def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
               workspace: torch.Tensor | None = None, host_io=False, profile=False, tile_cfg=0, storage=None,
-              inner_tol=1e-2, max_outer=30, stream=None):
+              inner_tol=0.0, max_outer=30, stream=None):
     """Jacobi-PCG solve of A x = b (gbpcg_pcg_solve).  Returns (x, result dict).
 
     b and x are float32 or float64 (the solution accumulates in that type; the
@@ -301,7 +301,8 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     iteration kernels one by one, each timed with CUDA events, and reports
     the summed pass times in result["pass_ms"].  storage=torch.bfloat16 or
     torch.float16 (with float64 b and x) selects mixed precision: FP64
-    iterative refinement around 16-bit inner solves to inner_tol.
+    iterative refinement around 16-bit inner solves to inner_tol (0: the library's default,
+    0.1 for BF16 and 1e-2 for FP16).
     """
     if b.dim() != 3 or not b.is_contiguous():
         raise GbpcgError(ERR_ARG, "b must be a contiguous (nz, ny, nx) tensor")

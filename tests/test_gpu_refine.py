@@ -82,10 +82,12 @@ def test_refinement_edge_cases(gpu_lib):
 
 @pytest.mark.slow
 def test_config2_512_lognormal_full_size(gpu_lib):
-    """512^3, k = exp(N(0,1)) per 8^3 block (seed 1), b ~ U[-1,1) after k; FP16
-    vectors refined in FP64 to 1e-8.  BF16 (8-bit mantissa) stalls in its first
-    inner solve on this grid: the solve must stop cleanly with NOT_CONVERGED and
-    a residual no worse than that of its last accepted step."""
+    """512^3, k = exp(N(0,1)) per 8^3 block (seed 1), b ~ U[-1,1) after k; FP16 and
+    BF16 vectors refined in FP64 to 1e-8 with the library's default inner tolerances
+    (BF16's 8-bit mantissa stalls short of 1e-2 per inner solve here; its default 0.1
+    takes more outer steps instead), and a BF16 solve held to 1e-2 per inner solve
+    must stop cleanly (NOT_CONVERGED or BREAKDOWN) at a residual no worse than its
+    last accepted step, reported truthfully."""
     k, b32 = inputs.varcoeff_problem(512, 512, 512, seed=1, kb=8)
     b = b32.astype(np.float64)
     del b32
@@ -95,8 +97,13 @@ def test_config2_512_lognormal_full_size(gpu_lib):
     true_rel = oracle.true_relres(b, x, k64, 8)
     assert true_rel <= 1e-8
     assert abs(res["rel_res_true"] - true_rel) <= 1e-3 * true_rel
-    xb, rb = refine(gpu_lib, b, torch.bfloat16, k=k, kb=8, maxit=6000, max_outer=4)
-    assert rb["status"] in (0, 3)
+    xb, rb = refine(gpu_lib, b, torch.bfloat16, k=k, kb=8, maxit=6000, max_outer=20)
+    assert rb["status"] == 0, rb
     tb = oracle.true_relres(b, xb, k64, 8)
+    assert tb <= 1e-8
     assert abs(rb["rel_res_true"] - tb) <= 1e-3 * tb
-    assert tb < 1.0
+    xs, rs = refine(gpu_lib, b, torch.bfloat16, k=k, kb=8, maxit=3000, max_outer=4, inner_tol=1e-2)
+    assert rs["status"] in (0, 3, 4)
+    ts = oracle.true_relres(b, xs, k64, 8)
+    assert abs(rs["rel_res_true"] - ts) <= 1e-3 * ts
+    assert ts < 1.0
