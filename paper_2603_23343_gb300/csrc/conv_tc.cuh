@@ -411,3 +411,164 @@ __global__ void __launch_bounds__(128) conv3_tc_halo_kernel(const __grid_constan
 }
 
 }  // namespace gb
+
+namespace gb {
+
+// ------------------------------------------------------------------------
+// Weight gradient on the tensor cores:
+//   gW[o, t, i] = sum_u gy[u - off(t), o] x[u, i]
+// as D[(t, o), i] = sum_u A[(t, o), u] B[i, u] with K = voxels.  An M tile
+// stacks tp = 128 / Co taps of Co output channels (8 taps of 16 channels,
+// 4 of 32, ...); rows past tp Co or past tap 26 are zero.  Both operands
+// are MN-major: a TMA box of 8 channels x 128 voxels puts each voxel's 8
+// channels in one 16-byte row, i.e. core matrices of 8 voxels (K) x 8
+// channels (M or N), K groups 128 B apart (LBO) and 8-channel groups one box
+// (2 KB) apart (SBO).  The tap shift is the box origin; TMA's zero fill
+// gives gy = 0 outside the grid.  A CTA owns a run of 128-voxel chunks (a
+// K slice) and a group of M tiles, accumulates in TMEM (group x Ci columns)
+// and writes its sums to its own slot; slots are added in a fixed order.
+
+struct __align__(128) WgMaps {
+    CUtensorMap gy;  // (Co, X, Y, Z) BF16, box (8, tx, ty, tz)
+    CUtensorMap x;   // (Ci, X, Y, Z) BF16, box (8, tx, ty, tz)
+};
+
+struct WgArgs {
+    int X, Y, Z, ci, co;
+    ConvTile tile;
+    int tp, mtiles, group;          // taps per M tile, M tiles, M tiles per CTA
+    int chunks, chunks_per_cta;     // 128-voxel chunks in the grid, per CTA
+    uint32_t stage_bytes, a_bytes;  // bytes per stage, of which A
+    int stages;
+    uint32_t ncol;                  // TMEM columns allocated
+    float *partials;                // [gridDim.x][co][27][ci]
+    int *err;
+};
+
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);  // A and B MN-major
+}
+
+__device__ __forceinline__ uint64_t umma_desc_mnmajor(uint32_t saddr, uint32_t lbo_k, uint32_t sbo_mn) {
+    return umma_desc_kmajor(saddr, lbo_k, sbo_mn);  // same fields: LBO between K groups, SBO between MN groups
+}
+
+constexpr int kWgMaxStages = 6;
+
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(const __grid_constant__ WgMaps maps, const WgArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kWgMaxStages], empty[kWgMaxStages], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = a.stages;
+    const int m0 = blockIdx.y * a.group;
+    const int gm = min(a.group, a.mtiles - m0);
+    const int c_begin = blockIdx.x * a.chunks_per_cta;
+    const int c_end = min(a.chunks, c_begin + a.chunks_per_cta);
+    const int KT = (c_end - c_begin) * gm;
+    const int gpt = a.co / 8;            // 8-channel groups per tap
+    const int nb = a.ci / 8;             // B groups
+    const uint32_t idesc = idesc_bf16_mn(128, a.ci);
+
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, a.ncol);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t sbase = smem_u32(smem);
+
+    if (warp == 0 && lane == 0) {
+        int kk = 0;
+        for (; kk < KT; ++kk) {
+            const int s = kk % S;
+            if (kk >= S && !mbar_wait_bounded(&empty[s], ((kk / S) - 1) & 1)) {
+                s_err = 1;
+                break;
+            }
+            const int c = c_begin + kk / gm, mt = m0 + kk % gm;
+            const int64_t v0 = (int64_t)c * 128;
+            const int x0 = (int)(v0 % a.X), y0 = (int)((v0 / a.X) % a.Y), z0 = (int)(v0 / ((int64_t)a.X * a.Y));
+            unsigned char *st = smem + (size_t)s * a.stage_bytes;
+            mbar_arrive_expect_tx(&full[s], a.stage_bytes);
+            for (int g = 0; g < 16; ++g) {
+                const int tau = g / gpt, h = g - tau * gpt, t = mt * a.tp + tau;
+                if (tau < a.tp && t < 27) {
+                    const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                    tma_load_4d(st + g * 2048, &maps.gy, &full[s], h * 8, x0 - dx, y0 - dy, z0 - dz);
+                } else {  // a row group past the taps: a box wholly outside the tensor reads as zeros
+                    tma_load_4d(st + g * 2048, &maps.gy, &full[s], a.co, x0, y0, z0);
+                }
+            }
+            for (int g = 0; g < nb; ++g) tma_load_4d(st + a.a_bytes + g * 2048, &maps.x, &full[s], g * 8, x0, y0, z0);
+        }
+        for (int s = 0; s < S; ++s) {
+            const int last = kk - 1 - ((kk - 1 - s) % S + S) % S;
+            if (last >= 0 && last < kk && !mbar_wait_bounded(&full[s], (last / S) & 1)) s_err = 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        for (int kk = 0; kk < KT; ++kk) {
+            const int s = kk % S;
+            if (!mbar_wait_bounded(&full[s], (kk / S) & 1)) {
+                s_err = 1;
+                break;
+            }
+            tc_fence_after();
+            const int first_chunk = (kk / gm) == 0, mt = kk % gm;
+            const uint32_t sa = sbase + (uint32_t)s * a.stage_bytes, sb = sa + a.a_bytes;
+#pragma unroll
+            for (int k16 = 0; k16 < 8; ++k16) {  // 16 voxels per MMA: two 8-voxel K groups
+                const uint64_t ad = umma_desc_mnmajor(sa + k16 * 256, 128, 2048);
+                const uint64_t bd = umma_desc_mnmajor(sb + k16 * 256, 128, 2048);
+                mma_bf16(tmem + (uint32_t)(mt * a.ci), ad, bd, idesc, (first_chunk && k16 == 0) ? 0u : 1u);
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(&done);
+    }
+    __syncwarp();
+    const bool ok = mbar_wait_bounded(&done, 0);
+    __syncthreads();
+    const bool good = ok && !s_err && KT > 0;
+    tc_fence_after();
+
+    // epilogue: TMEM lane = M row = (tau, o); columns = input channels of M tile mt
+    const int row = warp * 32 + lane;
+    const int tau = row / a.co, o = row - tau * a.co;
+    float *slot = a.partials + (int64_t)blockIdx.x * ((int64_t)a.co * 27 * a.ci);
+    for (int mt = 0; mt < gm; ++mt) {
+        const int t = (m0 + mt) * a.tp + tau;
+        const bool valid = tau < a.tp && t < 27;
+        for (int c0 = 0; c0 < a.ci; c0 += 16) {
+            float f[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(mt * a.ci + c0), f);
+            if (valid) {
+                float *dst = slot + ((int64_t)o * 27 + t) * a.ci + c0;
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) {
+                    float q[4] = {good ? f[i] : 0.f, good ? f[i + 1] : 0.f, good ? f[i + 2] : 0.f, good ? f[i + 3] : 0.f};
+                    st4(dst + i, q);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, a.ncol);
+    if (!good && KT > 0 && threadIdx.x == 0) atomicExch(a.err, 1);
+}
+
+}  // namespace gb

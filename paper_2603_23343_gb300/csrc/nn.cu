@@ -436,9 +436,86 @@ inline bool wgrad_ok(int X, int ci, int co) {
     return X % W == 0 && (wg_xs_floats(W, ci) + W * co) * 4 <= 200 * 1024;
 }
 
+// Tensor-core weight gradient (wgrad_tc_kernel): Ci a multiple of 16, Co with
+// 128 / Co taps per M tile, grids with 128-voxel tiles.
+inline bool wgrad_tc_ok(int X, int Y, int Z, int ci, int co) {
+    ConvTile t;
+    return ci % 16 == 0 && ci <= 128 && (co == 16 || co == 32 || co == 48 || co == 64 || co == 96) &&
+           conv_tile(X, Y, Z, &t) && ((int64_t)X * Y * Z) / 128 <= INT32_MAX;
+}
+
+struct WgTcPlan {
+    int tp, mtiles, group, ngroups, chunks, cpc, S, stages;
+    uint32_t a_bytes, stage_bytes, ncol;
+    size_t smem;
+};
+
+inline WgTcPlan wgrad_tc_plan(int X, int Y, int Z, int ci, int co) {
+    WgTcPlan p;
+    p.tp = 128 / co;
+    p.mtiles = (27 + p.tp - 1) / p.tp;
+    p.group = std::min(p.mtiles, 512 / ci);
+    p.ngroups = (p.mtiles + p.group - 1) / p.group;
+    p.chunks = (int)(((int64_t)X * Y * Z) / 128);
+    // about two CTAs per SM of a 152-SM part, fixed so that workspace sizes do
+    // not depend on the device that asks
+    const int S0 = std::max(1, std::min(p.chunks, (kWgTargetBlocks / 2 + p.ngroups - 1) / p.ngroups));
+    p.cpc = (p.chunks + S0 - 1) / S0;
+    p.S = (p.chunks + p.cpc - 1) / p.cpc;
+    p.a_bytes = 16u * 2048u;
+    p.stage_bytes = p.a_bytes + (uint32_t)(ci / 8) * 2048u;
+    p.stages = (int)std::max<uint32_t>(2, std::min<uint32_t>(kWgMaxStages, (200u * 1024u) / p.stage_bytes));
+    p.ncol = tmem_cols(p.group * ci);
+    p.smem = (size_t)p.stages * p.stage_bytes;
+    return p;
+}
+
 inline size_t wgrad_partial_bytes(int X, int Y, int Z, int ci, int co) {
     WgradPlan p = wgrad_plan(X, Y, Z, ci, co);
-    return (size_t)p.S * 27 * ci * co * sizeof(float);
+    size_t b = (size_t)p.S * 27 * ci * co * sizeof(float);
+    if (wgrad_tc_ok(X, Y, Z, ci, co)) b = std::max(b, (size_t)wgrad_tc_plan(X, Y, Z, ci, co).S * 27 * ci * co * 4);
+    return b;
+}
+
+static int wgrad_tc(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, const __nv_bfloat16 *gy, float *gw,
+                    float *partials, int *err, cudaStream_t s) {
+    const WgTcPlan p = wgrad_tc_plan(X, Y, Z, ci, co);
+    WgArgs a;
+    a.X = X;
+    a.Y = Y;
+    a.Z = Z;
+    a.ci = ci;
+    a.co = co;
+    conv_tile(X, Y, Z, &a.tile);
+    a.tp = p.tp;
+    a.mtiles = p.mtiles;
+    a.group = p.group;
+    a.chunks = p.chunks;
+    a.chunks_per_cta = p.cpc;
+    a.stage_bytes = p.stage_bytes;
+    a.a_bytes = p.a_bytes;
+    a.stages = p.stages;
+    a.ncol = p.ncol;
+    a.partials = partials;
+    a.err = err;
+    WgMaps maps;
+    const uint32_t box[4] = {8, (uint32_t)a.tile.tx, (uint32_t)a.tile.ty, (uint32_t)a.tile.tz};
+    const uint64_t gd[4] = {(uint64_t)co, (uint64_t)X, (uint64_t)Y, (uint64_t)Z};
+    const uint64_t gs[3] = {(uint64_t)co * 2, (uint64_t)co * 2 * X, (uint64_t)co * 2 * X * Y};
+    int rc = make_map_nd(&maps.gy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, gy, 4, gd, gs, box);
+    if (rc) return rc;
+    const uint64_t xd[4] = {(uint64_t)ci, (uint64_t)X, (uint64_t)Y, (uint64_t)Z};
+    const uint64_t xs[3] = {(uint64_t)ci * 2, (uint64_t)ci * 2 * X, (uint64_t)ci * 2 * X * Y};
+    rc = make_map_nd(&maps.x, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, x, 4, xd, xs, box);
+    if (rc) return rc;
+    cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+    wgrad_tc_kernel<<<dim3(p.S, p.ngroups), 128, p.smem, s>>>(maps, a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "wgrad_tc launch");
+    const int64_t n = (int64_t)27 * ci * co;
+    sum_slots_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p.S, partials, gw);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "sum_slots launch");
 }
 
 template <int BO, int BI>
@@ -451,7 +528,8 @@ static cudaError_t wgrad_launch(const WgradPlan &p, int X, int Y, int Z, int ci,
 }
 
 static int wgrad(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, const __nv_bfloat16 *gy, float *gw,
-                 float *partials, cudaStream_t s) {
+                 float *partials, cudaStream_t s, int *err = nullptr) {
+    if (err && wgrad_tc_ok(X, Y, Z, ci, co)) return wgrad_tc(X, Y, Z, ci, co, x, gy, gw, partials, err, s);
     if (!wgrad_ok(X, ci, co)) return fail_arg("weight gradient: unsupported width or channel count");
     WgradPlan p = wgrad_plan(X, Y, Z, ci, co);
     cudaError_t e;
@@ -900,40 +978,40 @@ int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cuda
     scale_to_bf16_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.V[0], gz, sc + S_SCALE, P.at<float>(L.dsc), gout);
     GB_CUDA(cudaGetLastError());
     // c9 (16 -> 1)
-    GB_TRY(wgrad(X0, Y0, Z0, 16, 1, a8, gout, G(8), part, s));
+    GB_TRY(wgrad(X0, Y0, Z0, 16, 1, a8, gout, G(8), part, s, err));
     GB_TRY(conv_simt<bf16>(X0, Y0, Z0, 1, 16, gout, WT(8), ga8, 0, a8, 16, 0, nullptr, s));
     // c8 (48 -> 16) on k8 = [up(a7), e0]
-    GB_TRY(wgrad(X0, Y0, Z0, 48, 16, k8, ga8, G(7), part, s));
+    GB_TRY(wgrad(X0, Y0, Z0, 48, 16, k8, ga8, G(7), part, s, err));
     GB_TRY(conv_tc<float>(X0, Y0, Z0, 16, 48, ga8, WT(7), gk8, 48, 0, 0, nullptr, 0, 0, err, s));
     up2_adjoint_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk8, 48, 0, a7, ga7);
     GB_CUDA(cudaGetLastError());
     // c7 (96 -> 32) on k7 = [up(a6), e1]
-    GB_TRY(wgrad(X1, Y1, Z1, 96, 32, k7, ga7, G(6), part, s));
+    GB_TRY(wgrad(X1, Y1, Z1, 96, 32, k7, ga7, G(6), part, s, err));
     GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 96, ga7, WT(6), gk7, 96, 0, 0, nullptr, 0, 0, err, s));
     up2_adjoint_mask_kernel<<<blocks_for(L.V[2] * 8, 256), 256, 0, s>>>(X2, Y2, Z2, 64, gk7, 96, 0, a6, ga6);
     GB_CUDA(cudaGetLastError());
     // c6 (64 -> 64), c5 (32 -> 64)
-    GB_TRY(wgrad(X2, Y2, Z2, 64, 64, a5, ga6, G(5), part, s));
+    GB_TRY(wgrad(X2, Y2, Z2, 64, 64, a5, ga6, G(5), part, s, err));
     GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 64, 64, ga6, WT(5), ga5, 64, 0, 0, a5, 64, 0, err, s));
-    GB_TRY(wgrad(X2, Y2, Z2, 32, 64, p2, ga5, G(4), part, s));
+    GB_TRY(wgrad(X2, Y2, Z2, 32, 64, p2, ga5, G(4), part, s, err));
     GB_TRY(conv_tc<float>(X2, Y2, Z2, 64, 32, ga5, WT(4), t5, 32, 0, 0, nullptr, 0, 0, err, s));
     // e1: skip gradient (gk7 channels 64..95) + pooled-path gradient, ReLU mask
     pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk7, 96, 64, t5, k7, 96,
                                                                               64, ge1b);
     GB_CUDA(cudaGetLastError());
     // c4 (32 -> 32), c3 (16 -> 32)
-    GB_TRY(wgrad(X1, Y1, Z1, 32, 32, a3, ge1b, G(3), part, s));
+    GB_TRY(wgrad(X1, Y1, Z1, 32, 32, a3, ge1b, G(3), part, s, err));
     GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 32, 32, ge1b, WT(3), ga3, 32, 0, 0, a3, 32, 0, err, s));
-    GB_TRY(wgrad(X1, Y1, Z1, 16, 32, p1, ga3, G(2), part, s));
+    GB_TRY(wgrad(X1, Y1, Z1, 16, 32, p1, ga3, G(2), part, s, err));
     GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 16, ga3, WT(2), t3, 16, 0, 0, nullptr, 0, 0, err, s));
     // e0: skip gradient (gk8 channels 32..47) + pooled-path gradient, ReLU mask
     pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[0] * 2, 256), 256, 0, s>>>(X0, Y0, Z0, 16, gk8, 48, 32, t3, k8, 48,
                                                                               32, ge0b);
     GB_CUDA(cudaGetLastError());
     // c2 (16 -> 16), c1 (2 -> 16)
-    GB_TRY(wgrad(X0, Y0, Z0, 16, 16, a1, ge0b, G(1), part, s));
+    GB_TRY(wgrad(X0, Y0, Z0, 16, 16, a1, ge0b, G(1), part, s, err));
     GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 16, 16, ge0b, WT(1), ga1, 16, 0, 0, a1, 16, 0, err, s));
-    GB_TRY(wgrad(X0, Y0, Z0, 2, 16, xin, ga1, G(0), part, s));
+    GB_TRY(wgrad(X0, Y0, Z0, 2, 16, xin, ga1, G(0), part, s, err));
     return GBPCG_OK;
 }
 
@@ -992,7 +1070,7 @@ extern "C" int gbpcg_conv3_workspace_size(int32_t nx, int32_t ny, int32_t nz, in
     if (!bytes) return fail_arg("bytes is NULL");
     if (nx <= 0 || ny <= 0 || nz <= 0 || ci <= 0 || co <= 0) return fail_arg("sizes must be positive");
     size_t b = 256 + align_up((size_t)27 * ci * co * 2, 256);
-    if (wgrad_ok(nx, ci, co)) b += wgrad_partial_bytes(nx, ny, nz, ci, co);
+    if (wgrad_ok(nx, ci, co) || wgrad_tc_ok(nx, ny, nz, ci, co)) b += wgrad_partial_bytes(nx, ny, nz, ci, co);
     *bytes = b;
     return GBPCG_OK;
 }
@@ -1055,13 +1133,14 @@ extern "C" int gbpcg_conv3_backward_weight(int32_t nx, int32_t ny, int32_t nz, i
                                            gbpcg_stream stream) {
     clear_error();
     GB_TRY(conv_args(nx, ny, nz, ci, co, x, gy, gw, workspace, workspace_bytes));
-    if (!wgrad_ok(nx, ci, co)) return fail_arg("weight gradient: unsupported width or channel count");
+    if (!wgrad_ok(nx, ci, co) && !wgrad_tc_ok(nx, ny, nz, ci, co))
+        return fail_arg("weight gradient: unsupported width or channel count");
     if (ci % 8 && ci > 2) return fail_arg("weight gradient: ci must be 1, 2 or a multiple of 8");
     if (co % 8 && co != 1) return fail_arg("weight gradient: co must be 1 or a multiple of 8");
     float *part =
         reinterpret_cast<float *>(static_cast<char *>(workspace) + 256 + align_up((size_t)27 * ci * co * 2, 256));
     return wgrad(nx, ny, nz, ci, co, static_cast<const bf16 *>(x), static_cast<const bf16 *>(gy), gw, part,
-                 (cudaStream_t)stream);
+                 (cudaStream_t)stream, static_cast<int *>(workspace));
 }
 
 extern "C" int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t training, size_t *bytes) {
