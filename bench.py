@@ -87,7 +87,7 @@ def learned_leg(B, learned, stream, full: bool):
     import torch
     train_seeds = range(10, 100) if full else range(10, 42)
     eval_seeds = range(100, 110) if full else range(100, 102)
-    steps = 6000 if full else 2000
+    steps = 4000
     t0 = time.perf_counter()
     pairs = learned.make_pairs((128, 128, 128), seeds=train_seeds)
     torch.cuda.synchronize()

@@ -100,7 +100,7 @@ typedef struct gbpcg_opts {
                               0 selects the default, 0.1 for BF16 and 1e-2 for F16 */
     int32_t max_outer;     /* refinement: maximum outer FP64 steps */
     int32_t fcg_m;         /* gbpcg_fcg_solve: each search direction is A-orthogonalised against the
-                              last fcg_m ones (1 .. 16; 0 selects 8); ignored elsewhere */
+                              last fcg_m ones (1 .. 32; 0 selects 24); ignored elsewhere */
 } gbpcg_opts;
 
 typedef struct gbpcg_result {

@@ -35,7 +35,7 @@ bool nn_shape_ok_ext(int X, int Y, int Z);
 int nn_prep_ext(const float *w, void *ws, const gbpcg_grid &g, cudaStream_t s);
 int nn_forward_ext(const gbpcg_grid &g, const float *r, float *z, void *ws, cudaStream_t s);
 
-constexpr int kMaxDirs = 16;
+constexpr int kMaxDirs = 32;
 
 struct FcgState {
     double bb, rz, rp, rr, rr64;
@@ -199,7 +199,7 @@ struct FcgLayout {
     size_t state, partials, dotws, r, z, ring, d64, nn, pcg, total;  // ring: (m + 1) x (p, Ap)
 };
 
-inline int fcg_depth(const gbpcg_opts &o) { return o.fcg_m == 0 ? 8 : o.fcg_m; }
+inline int fcg_depth(const gbpcg_opts &o) { return o.fcg_m == 0 ? 24 : o.fcg_m; }
 
 // ring vector length, rounded so that every vector stays 256-byte aligned
 inline size_t align_n4(int64_t n) { return ((size_t)n + 63) / 64 * 64; }
@@ -250,7 +250,7 @@ static int fcg_check(const gbpcg_grid *g, const gbpcg_opts *o) {
     if (o->storage != GBPCG_F32) return fail_arg("gbpcg_fcg_solve iterates in FP32 (storage F32)");
     if (o->flags & GBPCG_FLAG_HOST_IO) return fail_arg("gbpcg_fcg_solve takes device b and x");
     if (!(o->tol > 0.0) || o->maxit < 0) return fail_arg("tol must be > 0 and maxit >= 0");
-    if (o->fcg_m < 0 || o->fcg_m > kMaxDirs) return fail_arg("fcg_m must be 0 .. 16");
+    if (o->fcg_m < 0 || o->fcg_m > kMaxDirs) return fail_arg("fcg_m must be 0 .. 32");
     if (!nn_shape_ok_ext(g->nx, g->ny, g->nz))
         return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels");
     return GBPCG_OK;
