@@ -195,3 +195,63 @@ def test_last_error_is_cleared_on_success(lib):
     o = B.make_opts()
     assert lib.gbpcg_workspace_size(ctypes.byref(g2), ctypes.byref(o), ctypes.byref(n)) == B.OK
     assert B.last_error() == ""
+
+
+def test_learned_preconditioner_argument_checks(lib):
+    n = ctypes.c_size_t(0)
+    # every level must split into 128-voxel tiles of whole rows or planes
+    assert lib.gbpcg_nn_workspace_size(30, 30, 30, 0, ctypes.byref(n)) == B.ERR_ARG
+    assert lib.gbpcg_nn_workspace_size(32, 32, 32, 0, ctypes.byref(n)) == B.OK
+    inference = n.value
+    assert inference >= 32 ** 3 * (2 + 16 + 48 + 16) * 2  # finest-level BF16 activations
+    assert lib.gbpcg_nn_workspace_size(32, 32, 32, 1, ctypes.byref(n)) == B.OK
+    assert n.value > inference  # training adds the gradient buffers
+    assert lib.gbpcg_conv3_workspace_size(8, 8, 8, 16, 16, ctypes.byref(n)) == B.OK
+    ws_ok = n.value
+    P = ctypes.c_void_p
+    assert lib.gbpcg_conv3_forward(8, 8, 8, 16, 16, None, None, None, 0, None, 0, None) == B.ERR_ARG
+    # 16-byte alignment of the arrays, 256-byte alignment and size of the workspace
+    assert lib.gbpcg_conv3_forward(8, 8, 8, 16, 16, P(8), P(16), P(32), 0, P(256), ws_ok, None) == B.ERR_ARG
+    assert lib.gbpcg_conv3_forward(8, 8, 8, 16, 16, P(16), P(32), P(48), 0, P(256), 16, None) == B.ERR_ARG
+    assert lib.gbpcg_conv3_forward(8, 8, 8, 16, 16, P(16), P(32), P(48), 0, P(272), ws_ok, None) == B.ERR_ARG
+    # no kernel for 24 output channels, or for a 3-channel weight gradient
+    assert lib.gbpcg_conv3_workspace_size(8, 8, 8, 16, 24, ctypes.byref(n)) == B.OK
+    assert lib.gbpcg_conv3_forward(8, 8, 8, 16, 24, P(16), P(32), P(48), 0, P(256), n.value, None) == B.ERR_ARG
+    assert lib.gbpcg_conv3_workspace_size(8, 8, 8, 3, 16, ctypes.byref(n)) == B.OK
+    assert lib.gbpcg_conv3_backward_weight(8, 8, 8, 3, 16, P(16), P(32), P(48), P(256), n.value, None) == B.ERR_ARG
+    assert lib.gbpcg_nn_adam(-1, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, None) == B.ERR_ARG
+    assert lib.gbpcg_nn_adam(10, None, None, None, None, 0, 1e-3, 0.9, 0.999, 1e-8, None) == B.ERR_ARG
+    assert lib.gbpcg_nn_adam(0, None, None, None, None, 1, 1e-3, 0.9, 0.999, 1e-8, None) == B.OK
+    assert lib.gbpcg_nn_status(None, None) == B.ERR_ARG
+    g = _grid(32, 32, 32)
+    assert lib.gbpcg_nn_forward(ctypes.byref(g), None, None, None, P(256), inference, None) == B.ERR_ARG
+
+
+def test_fcg_argument_checks(lib):
+    g = _grid(32, 32, 32)
+    n = ctypes.c_size_t(0)
+    o = B._fcg_opts(1e-6, 100)
+    assert lib.gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    default = n.value
+    o.fcg_m = 1
+    assert lib.gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    # the default keeps 24 directions and their A-images: 46 more FP32 vectors than m = 1
+    assert default - n.value >= 46 * 32 ** 3 * 4
+    o.fcg_m = 33
+    assert lib.gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    bad = [B.make_opts(io_dtype=B.F64)]  # Jacobi preconditioner: not this entry point
+    for field, value in (("io_dtype", B.F32), ("storage", B.BF16), ("flags", B.FLAG_HOST_IO), ("tol", 0.0),
+                         ("maxit", -1)):
+        ob = B._fcg_opts(1e-6, 100)
+        setattr(ob, field, value)
+        bad.append(ob)
+    for ob in bad:
+        assert lib.gbpcg_fcg_workspace_size(ctypes.byref(g), ctypes.byref(ob), ctypes.byref(n)) == B.ERR_ARG
+    g30 = _grid(30, 30, 30)
+    assert lib.gbpcg_fcg_workspace_size(ctypes.byref(g30), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    r = B.Result()
+    o = B._fcg_opts(1e-6, 100)
+    assert lib.gbpcg_fcg_solve(ctypes.byref(g), None, ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.byref(o),
+                               ctypes.byref(r), None) == B.ERR_ARG
+    assert lib.gbpcg_fcg_solve(ctypes.byref(g), ctypes.c_void_p(256), ctypes.c_void_p(264), ctypes.c_void_p(512),
+                               ctypes.byref(o), ctypes.byref(r), None) == B.ERR_ARG  # b not 16-byte aligned

@@ -39,12 +39,14 @@ def test_identity_network_reproduces_jacobi_pcg(gpu_lib):
     assert abs(res["rel_res_true"] - true_relres(b, x)) <= 1e-3 * res["rel_res_true"]
 
 
-@pytest.mark.parametrize("seed", [3, 4])
-def test_identity_network_matches_jacobi_on_lognormal_coefficients(gpu_lib, seed):
+@pytest.mark.parametrize("seed,m", [(3, 0), (4, 0), (3, 1), (3, 32)])
+def test_identity_network_matches_jacobi_on_lognormal_coefficients(gpu_lib, seed, m):
     """Same on the variable-coefficient operator: FCG with N(r) = D^{-1} r takes the iterations
-    of the library's Jacobi PCG (within a few: one BF16 rounding per application)."""
+    of the library's Jacobi PCG (within a few: one BF16 rounding per application), whatever the
+    truncation depth m (0: the default) -- with a linear symmetric preconditioner every earlier
+    direction is already A-orthogonal."""
     k, b = learned.problem((32, 32, 32), seed)
-    x, res = gpu_lib.fcg_solve(learned.identity_weights().cuda(), b, tol=1e-6, maxit=3000, k_block=k)
+    x, res = gpu_lib.fcg_solve(learned.identity_weights().cuda(), b, tol=1e-6, maxit=3000, k_block=k, m=m)
     _, ref = gpu_lib.pcg_solve(b.clone(), torch.zeros_like(b), tol=1e-6, maxit=3000, k_block=k)
     assert res["status"] == gpu_lib.OK and res["pass_launches"][1] == 0
     assert abs(res["iters"] - ref["iters"]) <= max(3, ref["iters"] // 20), (res["iters"], ref["iters"])
@@ -69,6 +71,14 @@ def test_descent_check_falls_back_to_jacobi(gpu_lib, how):
     _, ref = gpu_lib.pcg_solve(b.clone(), torch.zeros_like(b), tol=1e-6, maxit=3000, k_block=k)
     assert res["iters"] == ref["iters"]
     assert true_relres(b, x, k) <= 1e-6
+
+
+def test_iteration_cap_reports_not_converged_truthfully(gpu_lib):
+    k, b = learned.problem((32, 32, 32), 5)
+    x, res = gpu_lib.fcg_solve(learned.identity_weights().cuda(), b, tol=1e-6, maxit=10, k_block=k)
+    assert res["status"] == gpu_lib.NOT_CONVERGED and res["iters"] == 10
+    t = true_relres(b, x, k)
+    assert t > 1e-6 and abs(res["rel_res_true"] - t) <= 1e-3 * t
 
 
 def test_zero_rhs_and_rejections(gpu_lib):
