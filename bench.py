@@ -412,26 +412,31 @@ def main():
         _, rc = B.pcg_solve(bc, xc, tol=TOL, maxit=MAXIT, workspace=wc, stream=stream)
 
     # mixed precision (16-bit iteration vectors, FP64 refinement) next to plain FP32
-    def timed_solve(bb, **kw):
+    def timed_solve(bb, reps=1, **kw):
+        """Best of `reps` timed solves after one warm-up (graphs built and cached)."""
         xx = torch.zeros_like(bb)
         wsx = B.alloc_workspace(bb.shape, io_dtype=B.F64, storage=B._DTYPES.get(kw.get("storage"), B.F32),
                                 k_block=kw.get("k_block"), kb=kw.get("kb", 8))
-        B.pcg_solve(bb, xx, workspace=wsx, **kw)  # warm-up: graphs built and cached
-        xx.zero_()
-        torch.cuda.synchronize()
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record(stream)
-        _, rr = B.pcg_solve(bb, xx, workspace=wsx, stream=stream, **kw)
-        t1.record(stream)
-        torch.cuda.synchronize()
+        B.pcg_solve(bb, xx, workspace=wsx, **kw)
+        best = None
+        for _ in range(reps):
+            xx.zero_()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            _, rr = B.pcg_solve(bb, xx, workspace=wsx, stream=stream, **kw)
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1)
+            best = ms if best is None else min(best, ms)
         del wsx, xx
-        return {"ms": t0.elapsed_time(t1), "iters": rr["iters"], "outer_steps": rr["refine_steps"],
+        return {"ms": best, "reps": reps, "iters": rr["iters"], "outer_steps": rr["refine_steps"],
                 "status": rr["status_name"], "rel_res_true_fp64": rr["rel_res_true"]}
 
     mixed = {"poisson256_tol1e-6": {"fp32_plain": {"ms": ms_step, "iters": iters}}}
     for name, dt in (("bf16", torch.bfloat16), ("fp16", torch.float16)):
-        mixed["poisson256_tol1e-6"][name] = timed_solve(b, tol=TOL, maxit=MAXIT, storage=dt, max_outer=20)
+        mixed["poisson256_tol1e-6"][name] = timed_solve(b, reps=3, tol=TOL, maxit=MAXIT, storage=dt, max_outer=20)
     if N <= 256 ** 3:
         k512, b512 = inputs.varcoeff_problem(512, 512, 512, seed=1, kb=8)
         kd = torch.from_numpy(k512).cuda()
