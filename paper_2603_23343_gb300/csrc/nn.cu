@@ -257,11 +257,91 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Strided variant for wide inputs (CI a multiple of 8, X a multiple of 128): a
+// warp owns 128 consecutive x voxels of a row and lane l computes x = l + 32 j
+// (j < 4), so every warp-wide load reads contiguous memory (one 16-byte vector
+// per lane, 512 B per instruction) while each shared-memory weight read still
+// feeds four outputs.  The x - 1 / x + 1 neighbours are loaded too (L1 hits).
+template <int CI, int CO, typename TO>
+__global__ void __launch_bounds__(256)
+    conv3_simt_strided_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in,
+                              const __nv_bfloat16 *__restrict__ w, TO *__restrict__ out, int relu,
+                              const __nv_bfloat16 *__restrict__ mask, int mstride, int moff, const double *scale,
+                              const float *__restrict__ vscale) {
+    constexpr int VX = 4;
+    __shared__ __align__(16) float ws[27 * CI * CO];
+    for (int e = threadIdx.x; e < 27 * CI * CO; e += blockDim.x) {
+        const int o = e / (27 * CI), r = e - o * 27 * CI;  // r = t * CI + i
+        ws[r * CO + o] = __bfloat162float(w[e]);
+    }
+    __syncthreads();
+    const float sc = scale ? (float)*scale : 1.0f;
+    const int lane = threadIdx.x & 31;
+    const int XS = X / 128;
+    const int64_t nseg = (int64_t)XS * Y * Z;
+    const int64_t wpb = blockDim.x / 32;
+    for (int64_t sg = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); sg < nseg; sg += (int64_t)gridDim.x * wpb) {
+        const int xs = (int)(sg % XS), y = (int)((sg / XS) % Y), z = (int)(sg / ((int64_t)XS * Y));
+        const int xb = xs * 128 + lane;
+        float acc[VX][CO];
+#pragma unroll
+        for (int j = 0; j < VX; ++j)
+#pragma unroll
+            for (int o = 0; o < CO; ++o) acc[j][o] = 0.0f;
+#pragma unroll 1
+        for (int r9 = 0; r9 < 9; ++r9) {
+            const int yy = y + r9 % 3 - 1, zz = z + r9 / 3 - 1;
+            if (yy < 0 || yy >= Y || zz < 0 || zz >= Z) continue;
+            const __nv_bfloat16 *row = in + (((int64_t)zz * Y + yy) * X) * CI;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                float iv[VX][CI];
+#pragma unroll
+                for (int j = 0; j < VX; ++j) {
+                    const int xx = xb + 32 * j + dx - 1;
+                    if (xx >= 0 && xx < X) {
+                        load_ch<CI>(row + (int64_t)xx * CI, iv[j]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < CI; ++i) iv[j][i] = 0.0f;
+                    }
+                }
+                const float *wt = ws + (r9 * 3 + dx) * CI * CO;
+#pragma unroll
+                for (int i = 0; i < CI; ++i)
+#pragma unroll
+                    for (int o = 0; o < CO; ++o) {
+                        const float wv = wt[i * CO + o];
+#pragma unroll
+                        for (int j = 0; j < VX; ++j) acc[j][o] = fmaf(iv[j][i], wv, acc[j][o]);
+                    }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+            const int64_t v = ((int64_t)z * Y + y) * X + xb + 32 * j;
+            TO *po = out + v * CO;
+            const float vs = vscale ? sc * vscale[v] : sc;
+#pragma unroll
+            for (int o = 0; o < CO; ++o) {
+                float f = acc[j][o] * vs;
+                if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
+                if (mask && !(__bfloat162float(mask[v * mstride + moff + o]) > 0.0f)) f = 0.0f;
+                po[o] = from_f<TO>(f);
+            }
+        }
+    }
+}
+
 template <int CI, int CO, typename TO>
 static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out, int relu,
                             const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
                             const float *vscale, cudaStream_t s) {
-    if (X % 4 == 0) {
+    if (CI % 8 == 0 && X % 128 == 0) {
+        const int64_t nseg = (int64_t)(X / 128) * Y * Z;  // one warp per 128-voxel row segment
+        conv3_simt_strided_kernel<CI, CO, TO><<<blocks_for(nseg * 32, 256), 256, 0, s>>>(
+            X, Y, Z, in, w, out, relu, mask, mstride, moff, scale, vscale);
+    } else if (X % 4 == 0) {
         const int64_t n = (int64_t)(X / 4) * Y * Z;
         conv3_simt_kernel<CI, CO, 4, TO><<<blocks_for(n, 256), 256, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride,
                                                                              moff, scale, vscale);

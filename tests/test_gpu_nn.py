@@ -81,7 +81,7 @@ def test_conv3_forward_relu(gpu_lib, ci, co):
     assert np.all(y >= 0)
 
 
-@pytest.mark.parametrize("shape", [(5, 7, 9), (4, 8, 32), (1, 1, 3), (3, 5, 16), (2, 3, 64)])
+@pytest.mark.parametrize("shape", [(5, 7, 9), (4, 8, 32), (1, 1, 3), (3, 5, 16), (2, 3, 64), (2, 3, 256)])
 @pytest.mark.parametrize("ci,co", [(2, 16), (16, 1), (1, 16)])
 def test_conv3_forward_cuda_cores(gpu_lib, shape, ci, co):
     x, w = conv_case(shape, ci, co, 200 + ci + co)
