@@ -81,7 +81,7 @@ UNET_MACS_PER_VOXEL = (864 + 6912 + 20736 + 432) + (13824 + 27648 + 82944) / 8 +
 
 
 def learned_leg(B, learned, stream, full: bool):
-    """BASELINE config 4: train on the GPU at 128^3 on lognormal problems (pairs from the plain
+    """The learned-preconditioner workload: train on the GPU at 128^3 on lognormal problems (pairs from the plain
     solver), evaluate learned FCG against Jacobi PCG at 256^3 on held-out seeds, and time the
     heaviest convolution (c8, 48 -> 16 channels at 256^3) against the tensor peak."""
     import torch
@@ -450,7 +450,7 @@ def main():
         del bd, kd
         torch.cuda.empty_cache()
 
-    # BASELINE config 3: 64 independent grids in one graph launch, tiles from the autotuner
+    # 64 independent grids (sizes from {48, 64, 96, 128, 160}) in one graph launch, tiles from the autotuner
     shapes = inputs.batch_shapes(64, 2)
     rhs = [torch.from_numpy(v).cuda() for v in inputs.batch_rhs(shapes, 2, dtype=np.float64)]
     xb = [torch.zeros_like(v) for v in rhs]

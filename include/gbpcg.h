@@ -211,7 +211,7 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
                     gbpcg_result *result, gbpcg_stream stream);
 
 /*
- * Many independent problems (BASELINE config 3) solved as one CUDA graph:
+ * Many independent problems solved as one CUDA graph:
  * each problem's whole solve (its own device-driven loop, as in
  * gbpcg_pcg_solve) is a branch of one graph, so one launch runs them all
  * concurrently and no problem waits on another's convergence.  grids[i],

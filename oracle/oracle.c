@@ -263,7 +263,7 @@ done:
     return status;
 }
 
-/* ||b - A x|| / ||b|| evaluated in FP64 (the judge of every solve). */
+/* ||b - A x|| / ||b|| evaluated in FP64 (every solve's result is checked with it). */
 double orc_true_relres(int nx, int ny, int nz, const double *kb, int kbx, int kby, int kbz,
                        const double *b, const double *x) {
     const int64_t n = (int64_t)nx * ny * nz;

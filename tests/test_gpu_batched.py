@@ -1,4 +1,4 @@
-"""Batched solves (BASELINE config 3): many independent grids in one graph launch.
+"""Batched solves: many independent grids in one graph launch.
 
 Each problem's iterate sequence in the batch is the same arithmetic as its
 standalone solve with the same tile configuration, so results must agree

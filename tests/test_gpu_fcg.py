@@ -1,6 +1,6 @@
 """Flexible CG with the learned preconditioner (gbpcg_fcg_solve), its descent
 check with the Jacobi fallback, and what a network trained on the GPU gains
-over Jacobi PCG.  Every solve is judged by the FP64 oracle's true residual
+over Jacobi PCG.  Every solve is checked with the FP64 oracle's true residual
 ||b - A x|| / ||b||, evaluated on the returned x."""
 import json
 import os

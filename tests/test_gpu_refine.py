@@ -1,5 +1,5 @@
 """Mixed precision: BF16/FP16 iteration vectors, FP32 arithmetic, FP64
-iterative refinement (BASELINE config 2), against the FP64 oracle.
+iterative refinement (512^3 lognormal-coefficient workload and smaller cases), against the FP64 oracle.
 
 Bar: the returned FP64 x has a true residual ||b - A x||/||b|| <= tol as
 evaluated by the oracle in FP64, the library's reported residual agrees with
