@@ -538,6 +538,18 @@ class NnTrainer:
     def status(self, stream=None) -> int:
         return _check(load().gbpcg_nn_status(_ptr(self.ws), _stream(stream)))
 
+    def state_dict(self) -> dict:
+        """Weights, Adam moments and step count (CPU copies), for torch.save."""
+        return {"w": self.w.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "t": self.t, "shape": self.shape}
+
+    def load_state_dict(self, state: dict):
+        """Resumes training from state_dict() output; the grid shape must match."""
+        if tuple(state["shape"]) != self.shape:
+            raise GbpcgError(ERR_ARG, f"checkpoint is for grid {tuple(state['shape'])}, not {self.shape}")
+        for name in ("w", "m", "v"):
+            getattr(self, name).copy_(state[name].to(self.w.device))
+        self.t = int(state["t"])
+
 
 def nn_status(workspace: torch.Tensor, stream=None) -> int:
     return _check(load().gbpcg_nn_status(_ptr(workspace), _stream(stream)))

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -26,6 +27,15 @@ int fail_cuda(cudaError_t e, const char *what);
         cudaError_t _e = (call);                               \
         if (_e != cudaSuccess) return ::gb::fail_cuda(_e, #call); \
     } while (0)
+
+// NVTX range over a host scope (visible in timeline profilers; a no-op when
+// no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *msg) { nvtxRangePushA(msg); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // ------------------------------------------------------------------ dtypes --
 

@@ -280,6 +280,7 @@ extern "C" int gbpcg_fcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts
 
 extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const void *b_, void *x_,
                                const gbpcg_opts *opts, gbpcg_result *result, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_fcg_solve");
     clear_error();
     int rc = fcg_check(grid, opts);
     if (rc) return rc;
@@ -346,6 +347,7 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
         return gbpcg_dot(n, GBPCG_F64, d64, d64, &st->rr64, dotws, dws, stream);
     };
     auto precondition = [&]() -> int {
+        NvtxRange net_range("learned preconditioner N(r)");
         GB_CUDA(cudaEventRecord(n0, s));
         int rc2 = nn_forward_ext(g, r, z, nnws, s);
         if (rc2) return rc2;
@@ -382,6 +384,7 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
         std::vector<double> hist{rel};
         int nd = 0, cur = 0;  // directions in the window; ring slot of the next one
         while (iters < opts->maxit) {
+            NvtxRange it_range("fcg iteration");
             DirSet d;
             memset(&d, 0, sizeof(d));
             d.nd = nd;

@@ -1172,6 +1172,7 @@ static int conv_args(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co,
 extern "C" int gbpcg_conv3_forward(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x,
                                    const void *w, float *y, int32_t relu, void *workspace, size_t workspace_bytes,
                                    gbpcg_stream stream) {
+    NvtxRange range("gbpcg_conv3_forward");
     clear_error();
     GB_TRY(conv_args(nx, ny, nz, ci, co, x, w, y, workspace, workspace_bytes));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1194,6 +1195,7 @@ __global__ void flip_one_kernel(int ci, int co, const bf16 *__restrict__ w, bf16
 extern "C" int gbpcg_conv3_backward_data(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *gy,
                                          const void *w, float *gx, void *workspace, size_t workspace_bytes,
                                          gbpcg_stream stream) {
+    NvtxRange range("gbpcg_conv3_backward_data");
     clear_error();
     GB_TRY(conv_args(nx, ny, nz, ci, co, gy, w, gx, workspace, workspace_bytes));
     cudaStream_t s = (cudaStream_t)stream;
@@ -1211,6 +1213,7 @@ extern "C" int gbpcg_conv3_backward_data(int32_t nx, int32_t ny, int32_t nz, int
 extern "C" int gbpcg_conv3_backward_weight(int32_t nx, int32_t ny, int32_t nz, int32_t ci, int32_t co, const void *x,
                                            const void *gy, float *gw, void *workspace, size_t workspace_bytes,
                                            gbpcg_stream stream) {
+    NvtxRange range("gbpcg_conv3_backward_weight");
     clear_error();
     GB_TRY(conv_args(nx, ny, nz, ci, co, x, gy, gw, workspace, workspace_bytes));
     if (!wgrad_ok(nx, ci, co) && !wgrad_tc_ok(nx, ny, nz, ci, co))
@@ -1235,6 +1238,7 @@ extern "C" int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32
 
 extern "C" int gbpcg_nn_forward(const gbpcg_grid *grid, const float *w, const float *r, float *z, void *workspace,
                                 size_t workspace_bytes, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_nn_forward");
     clear_error();
     NnLayout L;
     GB_TRY(nn_check(grid, workspace, workspace_bytes, false, &L));
@@ -1248,6 +1252,7 @@ extern "C" int gbpcg_nn_forward(const gbpcg_grid *grid, const float *w, const fl
 
 extern "C" int gbpcg_nn_backward(const gbpcg_grid *grid, const float *gz, float *gw, void *workspace,
                                  size_t workspace_bytes, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_nn_backward");
     clear_error();
     NnLayout L;
     GB_TRY(nn_check(grid, workspace, workspace_bytes, true, &L));
@@ -1281,6 +1286,7 @@ extern "C" int gbpcg_nn_loss(const gbpcg_grid *grid, const float *z, const float
 extern "C" int gbpcg_nn_train_step(const gbpcg_grid *grid, float *w, float *m, float *v, int32_t step, double lr,
                                    const float *r, const float *e, float *z, float *gz, float *gw, double *loss,
                                    void *workspace, size_t workspace_bytes, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_nn_train_step");
     clear_error();
     NnLayout L;
     GB_TRY(nn_check(grid, workspace, workspace_bytes, true, &L));

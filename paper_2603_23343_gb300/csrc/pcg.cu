@@ -305,6 +305,7 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
     double rel = 0.0, rel_prev = 0.0, corr_applied = 0.0;
     bool have_inner = false;
     for (;;) {
+        NvtxRange step_range("refinement outer step");
         OuterState ho;
         SolveState hi;
         GB_CUDA(cudaMemcpyAsync(&ho, os, sizeof(ho), cudaMemcpyDeviceToHost, s));
@@ -489,6 +490,7 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
 
 int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_opts *opts, gbpcg_result *result,
                     gbpcg_stream stream) {
+    NvtxRange range("gbpcg_pcg_solve");
     clear_error();
     if (int rc = check_grid(grid)) return rc;
     if (int rc = check_opts(opts)) return rc;
@@ -555,6 +557,7 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
 
 int gbpcg_autotune(const gbpcg_grid *grid, const gbpcg_opts *opts, const void *b, int32_t *tile_cfg,
                    double *us_per_iter, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_autotune");
     clear_error();
     if (int rc = check_grid(grid)) return rc;
     if (int rc = check_opts(opts)) return rc;
@@ -607,6 +610,7 @@ int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const g
 
 int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *const *b, void *const *x,
                             const gbpcg_opts *opts, gbpcg_result *results, gbpcg_stream stream) {
+    NvtxRange range("gbpcg_pcg_solve_batched");
     clear_error();
     if (int rc = check_batch(nprob, grids, opts)) return rc;
     if (!b || !x || !results) return fail_arg("b, x and results must be non-NULL");

@@ -232,3 +232,31 @@ def test_adam(gpu_lib):
         wr, mr, vr = onn.adam_step(wr, g.astype(np.float64), mr, vr, t, lr=1e-2)
     wg = w.cpu().double().numpy()
     assert np.all(np.abs(wg - wr) <= 3 * (6e-8 * np.abs(wr) + 1e-5 * 1e-2))
+
+
+def test_training_checkpoint_resumes_bitwise(gpu_lib, tmp_path):
+    """Five training steps equal three steps, a save and restore into a fresh trainer, and two
+    more steps, bit for bit (every training kernel sums in a fixed order)."""
+    from paper_2603_23343_gb300 import learned
+    shape = (32, 32, 32)
+    k, b = learned.problem(shape, 7)
+    e = torch.from_numpy(inputs.uniform_rhs(shape, 8, 0, np.float64)).cuda()
+    r = gpu_lib.stencil_apply(e, k_block=k).float()
+    e = e.float()
+    w0 = learned.initial_weights(1).cuda()
+    full = gpu_lib.NnTrainer(w0, shape, k_block=k)
+    for _ in range(5):
+        full.step(r, e, lr=1e-3)
+    part = gpu_lib.NnTrainer(w0, shape, k_block=k)
+    for _ in range(3):
+        part.step(r, e, lr=1e-3)
+    torch.save(part.state_dict(), tmp_path / "ckpt.pt")
+    resumed = gpu_lib.NnTrainer(learned.initial_weights(2).cuda(), shape, k_block=k)
+    resumed.load_state_dict(torch.load(tmp_path / "ckpt.pt"))
+    for _ in range(2):
+        resumed.step(r, e, lr=1e-3)
+    torch.testing.assert_close(resumed.w, full.w, rtol=0, atol=0)
+    torch.testing.assert_close(resumed.m, full.m, rtol=0, atol=0)
+    assert resumed.t == full.t == 5
+    with pytest.raises(gpu_lib.GbpcgError):
+        gpu_lib.NnTrainer(w0, (32, 32, 64), k_block=None).load_state_dict(part.state_dict())
