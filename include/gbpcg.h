@@ -389,6 +389,19 @@ int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const void *b, void 
  * check, else GBPCG_OK. */
 int gbpcg_nn_status(void *workspace, gbpcg_stream stream);
 
+/*
+ * Self-test of the bounded waits (no counterpart in the paper).  Every kernel
+ * of the library that waits on an asynchronous copy or MMA polls its mbarrier
+ * at most 2^18 times (about one second on GB300) and then reports
+ * GBPCG_TIMEOUT instead of hanging.  This call runs that wait in one CTA on a
+ * barrier that completes (arrive != 0) or never does (arrive == 0), with at
+ * most `polls` polls (1 .. 2^18), and
+ * returns GBPCG_OK or GBPCG_TIMEOUT as the device reported it; *ms (may be
+ * NULL) receives the kernel's duration.  scratch: 16 bytes of DEVICE memory,
+ * 16-byte aligned.  Synchronises `stream`.
+ */
+int gbpcg_wait_selftest(int32_t arrive, uint32_t polls, void *scratch, double *ms, gbpcg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

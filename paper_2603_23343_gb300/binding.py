@@ -35,7 +35,7 @@ EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbp
            "gbpcg_conv3_workspace_size", "gbpcg_conv3_forward", "gbpcg_conv3_backward_data",
            "gbpcg_conv3_backward_weight", "gbpcg_nn_workspace_size", "gbpcg_nn_forward", "gbpcg_nn_backward",
            "gbpcg_nn_loss", "gbpcg_nn_adam", "gbpcg_nn_train_step", "gbpcg_nn_status", "gbpcg_fcg_workspace_size",
-           "gbpcg_fcg_solve"]
+           "gbpcg_fcg_solve", "gbpcg_wait_selftest"]
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
 
 NN_NUM_WEIGHTS = 319248
@@ -143,6 +143,8 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_nn_status.argtypes = [P, P]
         lib.gbpcg_fcg_workspace_size.restype = ctypes.c_int
         lib.gbpcg_fcg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Opts), ctypes.POINTER(SZ)]
+        lib.gbpcg_wait_selftest.restype = ctypes.c_int
+        lib.gbpcg_wait_selftest.argtypes = [I32, ctypes.c_uint32, P, ctypes.POINTER(D), P]
         lib.gbpcg_fcg_solve.restype = ctypes.c_int
         lib.gbpcg_fcg_solve.argtypes = [ctypes.POINTER(Grid), P, P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
         _lib = lib
@@ -586,3 +588,12 @@ def fcg_solve(w: torch.Tensor, b: torch.Tensor, x: torch.Tensor | None = None, t
     _check(load().gbpcg_fcg_solve(ctypes.byref(g), _ptr(w), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(res),
                                   _stream(stream)), allowed=(OK, NOT_CONVERGED, BREAKDOWN, FALLBACK_USED))
     return x, res.as_dict()
+
+
+def wait_selftest(arrive: bool, polls: int, stream=None):
+    """(status, ms) of the bounded-wait self-test (gbpcg_wait_selftest); status is OK or TIMEOUT."""
+    ms = ctypes.c_double(0.0)
+    scratch = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    rc = _check(load().gbpcg_wait_selftest(int(bool(arrive)), int(polls), _ptr(scratch), ctypes.byref(ms),
+                                           _stream(stream)), allowed=(OK, TIMEOUT))
+    return rc, ms.value

@@ -223,3 +223,56 @@ int gbpcg_stencil_apply(const gbpcg_grid *grid, int32_t dtype, const void *p, vo
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------- self-test -----
+// One CTA initialises an mbarrier for one arrival and waits on it with the
+// library's bounded wait (at most `polls` polls); thread 0 arrives first only
+// when `arrive` is set.  Without the arrival the wait gives up and the CTA
+// writes GBPCG_TIMEOUT to *status instead of spinning on: the path every
+// kernel of the library takes when a copy or an MMA never completes.
+
+namespace gb {
+__global__ void wait_selftest_kernel(int arrive, uint32_t polls, int *status, long long *cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+        const long long t0 = clock64();
+        const bool ok = mbar_wait_bounded(&bar, 0, polls);
+        *cycles = clock64() - t0;
+        *status = ok ? GBPCG_OK : GBPCG_TIMEOUT;
+    }
+}
+}  // namespace gb
+
+extern "C" int gbpcg_wait_selftest(int32_t arrive, uint32_t polls, void *scratch, double *ms, gbpcg_stream stream) {
+    using namespace gb;
+    clear_error();
+    if (polls == 0 || polls > kWaitPolls) return fail_arg("polls must be 1 .. 2^18");
+    if (!scratch || (reinterpret_cast<uintptr_t>(scratch) & 15u)) return fail_arg("scratch must be 16-byte aligned");
+    int *d = static_cast<int *>(scratch);
+    long long *cyc = reinterpret_cast<long long *>(static_cast<char *>(scratch) + 8);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, s);
+    wait_selftest_kernel<<<1, 32, 0, s>>>(arrive, polls, d, cyc);
+    cudaEventRecord(e1, s);
+    int st = -1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (ms) *ms = t;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail_cuda(e, "wait self-test");
+    if (st == GBPCG_TIMEOUT) set_error("bounded wait gave up (self-test)");
+    return st;
+}

@@ -203,12 +203,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Every wait on a TMA completion is bounded: after this many polls the
-// caller records a timeout and stops instead of spinning forever.
-constexpr uint32_t kWaitPolls = 1u << 24;
+// Every wait on a TMA or MMA completion is bounded: after this many polls the
+// caller records a timeout and stops instead of spinning forever.  A failed
+// mbarrier.try_wait suspends about 3.8 us on GB300 (measured with
+// gbpcg_wait_selftest), so 2^18 polls give up after about one second -- far
+// beyond any legitimate wait (a stage's copy, a CTA's MMAs).
+constexpr uint32_t kWaitPolls = 1u << 18;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitPolls; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls = kWaitPolls) {
+    for (uint32_t i = 0; i < polls; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
