@@ -39,13 +39,14 @@ def test_identity_network_reproduces_jacobi_pcg(gpu_lib):
     assert abs(res["rel_res_true"] - true_relres(b, x)) <= 1e-3 * res["rel_res_true"]
 
 
-@pytest.mark.parametrize("seed,m", [(3, 0), (4, 0), (3, 1), (3, 32)])
-def test_identity_network_matches_jacobi_on_lognormal_coefficients(gpu_lib, seed, m):
+@pytest.mark.parametrize("seed,m,shape", [(3, 0, (32, 32, 32)), (4, 0, (32, 32, 32)), (3, 1, (32, 32, 32)),
+                                          (3, 32, (32, 32, 32)), (5, 0, (16, 32, 64))])
+def test_identity_network_matches_jacobi_on_lognormal_coefficients(gpu_lib, seed, m, shape):
     """Same on the variable-coefficient operator: FCG with N(r) = D^{-1} r takes the iterations
     of the library's Jacobi PCG (within a few: one BF16 rounding per application), whatever the
     truncation depth m (0: the default) -- with a linear symmetric preconditioner every earlier
     direction is already A-orthogonal."""
-    k, b = learned.problem((32, 32, 32), seed)
+    k, b = learned.problem(shape, seed)
     x, res = gpu_lib.fcg_solve(learned.identity_weights().cuda(), b, tol=1e-6, maxit=3000, k_block=k, m=m)
     _, ref = gpu_lib.pcg_solve(b.clone(), torch.zeros_like(b), tol=1e-6, maxit=3000, k_block=k)
     assert res["status"] == gpu_lib.OK and res["pass_launches"][1] == 0
