@@ -3,6 +3,7 @@
 #include <string>
 
 #include "launch.cuh"
+#include "stencil64.cuh"
 
 namespace gb {
 
@@ -112,31 +113,15 @@ __global__ void stencil_f64_kernel(int nx, int ny, int nz, const double *__restr
                                    double cx, double cy, double cz, const float *__restrict__ kb, int kbx, int kby,
                                    int kbz) {
     const int64_t n = (int64_t)nx * ny * nz;
-    const int nbx = BLOCK ? (nx + kbx - 1) / kbx : 0, nby = BLOCK ? (ny + kby - 1) / kby : 0;
+    const Coef64 cf{cx, cy, cz, kb, kbx, kby, kbz};
+    double w[6];
+    face_weights64<false>(w, 0, 0, 0, nx, ny, nz, cf);
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(g % nx);
         const int64_t t = g / nx;
         const int j = (int)(t % ny), k = (int)(t / ny);
-        const double c = p[g];
-        const double xm = i > 0 ? __ldg(p + g - 1) : 0.0, xp = i < nx - 1 ? __ldg(p + g + 1) : 0.0;
-        const double ym = j > 0 ? __ldg(p + g - nx) : 0.0, yp = j < ny - 1 ? __ldg(p + g + nx) : 0.0;
-        const int64_t pl = (int64_t)nx * ny;
-        const double zm = k > 0 ? __ldg(p + g - pl) : 0.0, zp = k < nz - 1 ? __ldg(p + g + pl) : 0.0;
-        double w[6] = {cx, cx, cy, cy, cz, cz};
-        if (BLOCK) {
-            auto K = [&](int a, int b, int cc) { return (double)__ldg(kb + ((int64_t)cc * nby + b) * nbx + a); };
-            auto hm = [](double a, double b) { return 2.0 * a * b / (a + b); };
-            const int bx = i / kbx, by = j / kby, bz = k / kbz;
-            const double kc = K(bx, by, bz);
-            w[0] = cx * ((i % kbx == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
-            w[1] = cx * ((i % kbx == kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
-            w[2] = cy * ((j % kby == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
-            w[3] = cy * ((j % kby == kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
-            w[4] = cz * ((k % kbz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
-            w[5] = cz * ((k % kbz == kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
-        }
-        q[g] = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) + w[4] * (c - zm) +
-               w[5] * (c - zp);
+        if (BLOCK) face_weights64<true>(w, i, j, k, nx, ny, nz, cf);
+        q[g] = apply64<BLOCK>(load_nbr64(p, g, i, j, k, nx, ny, nz), w);
     }
 }
 

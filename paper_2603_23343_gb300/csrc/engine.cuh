@@ -59,7 +59,7 @@ struct __align__(16) SolveState {
     double rr_rep;  // ||r||^2 at the last residual replacement
     double rr_conf; // ||b - A x||^2 at the last confirmation (recursive residual had met tol)
     int n_replace;  // residual replacements done
-    int pad1;
+    int true_known; // 1: rr_true, bb_true already hold b - A x of the final x
     unsigned int ticket[8];
 };
 
@@ -241,6 +241,7 @@ struct __align__(128) PassMaps {
 struct PassArgs {
     int nx, ny, nz;
     int tiles_x, zchunk;
+    int zparts;  // CTAs sharing one z chunk, each marching one part of it (0 or 1: whole chunks)
     const void *h0[2];
     const void *h1[2];
     const void *c0;
@@ -306,6 +307,7 @@ __device__ __forceinline__ void manual_box(const T *src, T *dst, int nx, int ny,
 template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
 __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
+    static_assert(S >= 2, "a stage is refilled only after the step that reads it as the output plane");
     using G = Geometry<T, TX, TY, KIND>;
     using TC = CenterT<T, KIND>;
     constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV, V = G::V;
@@ -346,7 +348,14 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
-    const int k0 = blockIdx.y * a.zchunk, k1 = min(nz, k0 + a.zchunk);
+    int k0, k1;  // this CTA's planes [k0, k1): part blockIdx.y % zparts of chunk blockIdx.y / zparts
+    {
+        const int parts = max(a.zparts, 1);
+        const int c = (int)blockIdx.y / parts, part = (int)blockIdx.y - c * parts;
+        const int c0 = c * a.zchunk, c1 = min(nz, c0 + a.zchunk), sub = (a.zchunk + parts - 1) / parts;
+        k0 = min(c1, c0 + part * sub);
+        k1 = min(c1, k0 + sub);
+    }
     const int lx = threadIdx.x % (TX / V), ly = threadIdx.x / (TX / V);
     const int gx = x0 + V * lx, gy = y0 + ly;
     bool ok[V];

@@ -19,7 +19,9 @@ enum TileCfg {
     CFG_128x8_S6 = 5,
     CFG_256x4 = 6,  // whole rows, nx <= 256
     CFG_256x8 = 7,  // whole rows, nx <= 256
-    NUM_CFG = 8
+    CFG_128x8_S3 = 8,
+    CFG_256x4_S3 = 9,  // whole rows, nx <= 256
+    NUM_CFG = 10
 };
 struct CfgDims { int tx, ty, s; };
 inline CfgDims cfg_dims(int c) {
@@ -31,6 +33,8 @@ inline CfgDims cfg_dims(int c) {
         case CFG_64x8_S6: return {64, 8, 6};
         case CFG_128x8_S6: return {128, 8, 6};
         case CFG_256x4: return {256, 4, 4};
+        case CFG_128x8_S3: return {128, 8, 3};
+        case CFG_256x4_S3: return {256, 4, 3};
         default: return {256, 8, 4};
     }
 }
@@ -41,6 +45,7 @@ inline bool cfg_fits(int c, int nx) { return cfg_dims(c).tx != 256 || nx <= 256;
 struct PassGeom {
     int cfg;
     int tiles_x, tiles_y, zchunk, zchunks;
+    int zparts;  // CTAs per z chunk (grid y = chunks x zparts)
     int threads;
     size_t smem;
     dim3 grid() const { return dim3((unsigned)(tiles_x * tiles_y), (unsigned)zchunks, 1); }
@@ -83,7 +88,26 @@ inline PassGeom make_geom(int cfg, int nx, int ny, int nz, int ctas_per_sm, size
     int zchunk = (int)((nz + best_zc - 1) / best_zc);
     g.zchunk = std::max(zchunk, 1);
     g.zchunks = (nz + g.zchunk - 1) / g.zchunk;
+    g.zparts = 1;
     return g;
+}
+
+// Gives a pass the z chunks of another pass (depth `zchunk`), each cut into
+// the most parts (at most 4, each at least 8 planes deep) whose CTAs still
+// fit the resident slots of the GPU in one wave; every part lies inside one
+// chunk of the other pass.
+inline void split_chunks(PassGeom &g, int zchunk, int nz, int ctas_per_sm) {
+    const long tiles = (long)g.tiles_x * g.tiles_y;
+    const long slots = std::min<long>((long)device_sm_count() * std::max(1, ctas_per_sm), kMaxPassBlocks);
+    g.zchunk = std::max(zchunk, 1);
+    const int chunks = (nz + g.zchunk - 1) / g.zchunk;
+    g.zparts = 1;
+    for (int parts = 4; parts >= 2; --parts)
+        if ((g.zchunk + parts - 1) / parts >= 8 && tiles * chunks * parts <= slots) {
+            g.zparts = parts;
+            break;
+        }
+    g.zchunks = chunks * g.zparts;
 }
 
 // True when every array meets TMA's rules: 16-byte aligned base and a row
@@ -130,6 +154,8 @@ struct PassKernel {
             case CFG_64x8_S6: { using K = PassKernel<T, 64, 8, 6, KIND, TMA, Op>; return CALL; } \
             case CFG_128x8_S6: { using K = PassKernel<T, 128, 8, 6, KIND, TMA, Op>; return CALL; } \
             case CFG_256x4: { using K = PassKernel<T, 256, 4, 4, KIND, TMA, Op>; return CALL; }  \
+            case CFG_128x8_S3: { using K = PassKernel<T, 128, 8, 3, KIND, TMA, Op>; return CALL; } \
+            case CFG_256x4_S3: { using K = PassKernel<T, 256, 4, 3, KIND, TMA, Op>; return CALL; } \
             default: { using K = PassKernel<T, 256, 8, 4, KIND, TMA, Op>; return CALL; }         \
         }                                                                      \
     }()

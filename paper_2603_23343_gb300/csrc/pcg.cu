@@ -85,9 +85,11 @@ template <bool BLOCK>
 __global__ void __launch_bounds__(256)
     outer_residual_kernel(int nx, int ny, int nz, const double *__restrict__ x, const double *__restrict__ b,
                           float *r32, double cx, double cy, double cz, const float *__restrict__ kb,
-                          int kbx, int kby, int kbz, OuterState *os, double *partials) {
-    const int64_t pl = (int64_t)nx * ny;
-    const int nbx = BLOCK ? (nx + kbx - 1) / kbx : 0, nby = BLOCK ? (ny + kby - 1) / kby : 0;
+                          int kbx, int kby, int kbz, const double *__restrict__ tab64, OuterState *os,
+                          double *partials) {
+    const Coef64 cf{cx, cy, cz, kb, kbx, kby, kbz};
+    double w[6];
+    face_weights64<false>(w, 0, 0, 0, nx, ny, nz, cf);
     double rr = 0.0, bb = 0.0, mx = 0.0;
     const int rows = ny * nz;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
@@ -95,26 +97,8 @@ __global__ void __launch_bounds__(256)
         const int64_t base = (int64_t)row * nx;
         for (int i = threadIdx.x; i < nx; i += 256) {
             const int64_t g = base + i;
-            const double c = x[g];
-            const double xm = i > 0 ? x[g - 1] : 0.0, xp = i < nx - 1 ? x[g + 1] : 0.0;
-            const double ym = j > 0 ? x[g - nx] : 0.0, yp = j < ny - 1 ? x[g + nx] : 0.0;
-            const double zm = k > 0 ? x[g - pl] : 0.0, zp = k < nz - 1 ? x[g + pl] : 0.0;
-            double w[6] = {cx, cx, cy, cy, cz, cz};
-            if (BLOCK) {
-                auto K = [&](int p, int q, int r) { return (double)__ldg(kb + ((int64_t)r * nby + q) * nbx + p); };
-                auto hm = [](double u, double v) { return 2.0 * u * v / (u + v); };
-                const int bx = i / kbx, by = j / kby, bz = k / kbz;
-                const int ix = i - bx * kbx, iy = j - by * kby, iz = k - bz * kbz;
-                const double kc = K(bx, by, bz);
-                w[0] = cx * ((ix == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
-                w[1] = cx * ((ix == kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
-                w[2] = cy * ((iy == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
-                w[3] = cy * ((iy == kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
-                w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
-                w[5] = cz * ((iz == kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
-            }
-            const double ax = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) +
-                              w[4] * (c - zm) + w[5] * (c - zp);
+            if (BLOCK) face_weights64_tab(w, i, j, k, nx, ny, tab64, cf);
+            const double ax = apply64<BLOCK>(load_nbr64(x, g, i, j, k, nx, ny, nz), w);
             const double bv = b[g];
             const double r = bv - ax;
             r32[g] = (float)r;
@@ -167,7 +151,7 @@ __global__ void zero_f64_kernel(double *x, int64_t n) {
 }
 
 struct RefineLayout {
-    size_t outer, partials, r32, din, inner, total;
+    size_t outer, partials, r32, din, tab64, inner, total;
     WsLayout in;
 };
 
@@ -179,6 +163,7 @@ static RefineLayout refine_layout(const gbpcg_grid &g, const gbpcg_opts &o) {
     r.partials = off; off += round256(sizeof(double) * 2 * 8192);
     r.r32 = off; off += round256(n * 4);
     r.din = off; off += round256(n * 4);
+    r.tab64 = off; off += round256((size_t)block_count(g) * kTab64 * sizeof(double));
     r.inner = off;
     r.in = ws_layout_n(n, o.storage, GBPCG_F32, false, block_count(g));
     off += r.in.total;
@@ -281,6 +266,17 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
                           &os->bscale};
     const unsigned rb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)g.ny * g.nz, device_sm_count() * 8));
     const unsigned eb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, device_sm_count() * 8));
+    // FP64 face weights of the unscaled operator for the outer residual (the
+    // inner solves keep their own table, of the scaled operator)
+    double *tab64 = reinterpret_cast<double *>(ws + R.tab64);
+    if (g.k_block) {
+        const int nbx = (g.nx + g.kbx - 1) / g.kbx, nby = (g.ny + g.kby - 1) / g.kby, nbz = (g.nz + g.kbz - 1) / g.kbz;
+        const int64_t nb = (int64_t)nbx * nby * nbz;
+        const Coef64 cf{cc(g.nx), cc(g.ny), cc(g.nz), g.k_block, g.kbx, g.kby, g.kbz};
+        build_face_table64<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096)), 256, 0, s>>>(
+            g.k_block, nbx, nby, nbz, cf, tab64);
+        GB_CUDA(cudaGetLastError());
+    }
     OuterState init;
     memset(&init, 0, sizeof(init));
     init.sigma = (double)sigma;
@@ -289,10 +285,11 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
         if (e) return e;
         if (g.k_block)
             outer_residual_kernel<true><<<rb, 256, 0, s>>>(g.nx, g.ny, g.nz, x, b, r32, cc(g.nx), cc(g.ny),
-                                                          cc(g.nz), g.k_block, g.kbx, g.kby, g.kbz, os, partials);
+                                                          cc(g.nz), g.k_block, g.kbx, g.kby, g.kbz, tab64, os,
+                                                          partials);
         else
             outer_residual_kernel<false><<<rb, 256, 0, s>>>(g.nx, g.ny, g.nz, x, b, r32, cc(g.nx), cc(g.ny),
-                                                           cc(g.nz), nullptr, 1, 1, 1, os, partials);
+                                                           cc(g.nz), nullptr, 1, 1, 1, nullptr, os, partials);
         return cudaGetLastError();
     };
 

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "launch.cuh"
+#include "stencil64.cuh"
 
 namespace gb {
 
@@ -63,6 +64,16 @@ static __global__ void build_face_table(const float *__restrict__ kb, int nbx, i
     }
 }
 
+// FP64 face-weight table of the residual kernels (stencil64.cuh), one
+// thread per block.
+static __global__ void build_face_table64(const float *kb, int nbx, int nby, int nbz, Coef64 cf, double *tab) {
+    const int64_t nb = (int64_t)nbx * nby * nbz;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += (int64_t)gridDim.x * blockDim.x) {
+        const int bx = (int)(t % nbx), by = (int)((t / nbx) % nby), bz = (int)(t / ((int64_t)nbx * nby));
+        face_table64_block(tab + kTab64 * t, kb, bx, by, bz, nbx, nby, nbz, cf);
+    }
+}
+
 enum ResMode { RES_INIT = 0, RES_REPLACE = 1, RES_TRUE = 2 };
 
 struct Res64Args {
@@ -73,6 +84,7 @@ struct Res64Args {
     double cx, cy, cz;
     const float *kb;
     int kbx, kby, kbz;
+    const double *tab64;   // FP64 face weights per coefficient block (build_face_table64)
     const double *bscale;  // NULL, or a device scalar multiplying b (inner refinement solves)
     SolveState *st;
     double *partials;
@@ -82,72 +94,105 @@ struct Res64Args {
 
 constexpr double kHuge = 1e300;
 
-// r = b - A x with FP64 arithmetic, one block per grid row (x fastest).
-//   RES_INIT     z = D^-1 r, d = 0; sums r.r, r.z, b.b  -> start state
-//   RES_REPLACE  z = D^-1 r;        sums r.r, r.z       -> replacement decisions
-//   RES_TRUE     sums r.r, b.b                          -> reported true residual
+// Compensated FP32 sum (Kahan): the running error of each addition is fed
+// back into the next, so the sum of a thread's terms is good to a few FP32
+// roundings however many there are.
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// r = b - A x with FP64 differences and sums of differences (stencil64.cuh),
+// one block per grid row (x fastest).
+//   RES_INIT     z = D^-1 r, d = 0; FP64 sums r.r, r.z, b.b -> start state
+//   RES_REPLACE  z = D^-1 r; sums r.r, r.z -> replacement decisions
+//   RES_TRUE     sum r.r -> reported true residual (b.b is the start
+//                state's).  Skipped when the solve ended on a replacement
+//                that already evaluated this x (it left x unchanged).
+// REPLACE and TRUE sum in compensated FP32 the values r 2^-e and z 2^-e,
+// with 2^e the power of two just above rms(b), so the squares stay
+// far from FP32 overflow and underflow; the products come back scaled by
+// 2^(2e) exactly.  GB300's FP64 rate is the reason: these kernels keep its
+// FP64 pipe busy (about 40 us per FP64 operation per point at 256^3,
+// measured), and the FP64 operations of a replacement drop from 16 (stencil,
+// b - A x, two FP64 dot products) to 11.
 template <int MODE, typename X, typename Bt, bool BLOCK, typename T>
 __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
     SolveState *st = a.st;
     if (MODE == RES_REPLACE && (!st->replace || st->done)) return;
+    if (MODE == RES_TRUE && st->true_known) return;
     const X *__restrict__ x = static_cast<const X *>(a.x);
     const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int64_t pl = (int64_t)nx * ny;
-    const int nbx = BLOCK ? (nx + a.kbx - 1) / a.kbx : 0, nby = BLOCK ? (ny + a.kby - 1) / a.kby : 0;
-    const double cx = a.cx, cy = a.cy, cz = a.cz;
-    const double bsc = a.bscale ? *a.bscale : 1.0;
+    const Coef64 cf{a.cx, a.cy, a.cz, a.kb, a.kbx, a.kby, a.kbz};
+    const bool bscaled = a.bscale != nullptr;
+    const double bsc = bscaled ? *a.bscale : 1.0;
+    // FP32 sums: scale 2^-e, unscale 2^(2e)
+    float fs = 1.0f;
+    double unscale = 1.0;
+    if (MODE != RES_INIT) {
+        const double bb = st->bb;
+        if (bb > 0.0 && isfinite(bb)) {
+            int e = 0;
+            frexp(sqrt(bb / ((double)nx * ny * nz)), &e);
+            e = max(-100, min(100, e));
+            fs = __int_as_float((127 - e) << 23);
+            unscale = ldexp(1.0, 2 * e);
+        }
+    }
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    KahanF k0, k1;
+    double w[6];
+    face_weights64<false>(w, 0, 0, 0, nx, ny, nz, cf);
+    const float dg_const = diag64(w);
     const int rows = ny * nz;
     for (int row = blockIdx.x; row < rows; row += gridDim.x) {
         const int j = row % ny, k = row / ny;
         const int64_t base = (int64_t)row * nx;
         for (int i = threadIdx.x; i < nx; i += 256) {
             const int64_t g = base + i;
-            auto L = [&](int64_t o) { return (double)__ldg(x + o); };
-            const double c = L(g);
-            const double xm = i > 0 ? L(g - 1) : 0.0, xp = i < nx - 1 ? L(g + 1) : 0.0;
-            const double ym = j > 0 ? L(g - nx) : 0.0, yp = j < ny - 1 ? L(g + nx) : 0.0;
-            const double zm = k > 0 ? L(g - pl) : 0.0, zp = k < nz - 1 ? L(g + pl) : 0.0;
-            double w[6] = {cx, cx, cy, cy, cz, cz};
-            if (BLOCK) {
-                const float *kb = a.kb;
-                auto K = [&](int p, int q, int r) { return (double)__ldg(kb + ((int64_t)r * nby + q) * nbx + p); };
-                auto hm = [](double u, double v) { return 2.0 * u * v / (u + v); };
-                const int bx = i / a.kbx, by = j / a.kby, bz = k / a.kbz;
-                const int ix = i - bx * a.kbx, iy = j - by * a.kby, iz = k - bz * a.kbz;
-                const double kc = K(bx, by, bz);
-                w[0] = cx * ((ix == 0 && i > 0) ? hm(kc, K(bx - 1, by, bz)) : kc);
-                w[1] = cx * ((ix == a.kbx - 1 && i < nx - 1) ? hm(kc, K(bx + 1, by, bz)) : kc);
-                w[2] = cy * ((iy == 0 && j > 0) ? hm(kc, K(bx, by - 1, bz)) : kc);
-                w[3] = cy * ((iy == a.kby - 1 && j < ny - 1) ? hm(kc, K(bx, by + 1, bz)) : kc);
-                w[4] = cz * ((iz == 0 && k > 0) ? hm(kc, K(bx, by, bz - 1)) : kc);
-                w[5] = cz * ((iz == a.kbz - 1 && k < nz - 1) ? hm(kc, K(bx, by, bz + 1)) : kc);
-            }
-            const double ax = w[0] * (c - xm) + w[1] * (c - xp) + w[2] * (c - ym) + w[3] * (c - yp) +
-                              w[4] * (c - zm) + w[5] * (c - zp);
-            const double bv = bsc * (double)__ldg(b + g);
+            const Nbr64 u = load_nbr64(x, g, i, j, k, nx, ny, nz);
+            if (BLOCK) face_weights64_tab(w, i, j, k, nx, ny, a.tab64, cf);
+            const double ax = apply64<BLOCK>(u, w);
+            const double bl = (double)__ldg(b + g);
+            const double bv = bscaled ? bsc * bl : bl;
             const double r = bv - ax;
-            s0 = fma(r, r, s0);
+            const float rf = (float)r;
             if (MODE == RES_TRUE) {
-                s1 = fma(bv, bv, s1);
+                const float rs = rf * fs;
+                k0.add(rs * rs);
             } else {
-                const float dg = (float)(((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]));
-                const T zt = from_f<T>((float)r / dg);
+                const float dg = BLOCK ? diag64(w) : dg_const;
+                const T zt = from_f<T>(rf / dg);
                 static_cast<T *>(a.z)[g] = zt;
-                s1 = fma(r, (double)to_f(zt), s1);
                 if (MODE == RES_INIT) {
-                    static_cast<float *>(a.d)[g] = 0.0f;
+                    s0 = fma(r, r, s0);
+                    s1 = fma(r, (double)to_f(zt), s1);
                     s2 = fma(bv, bv, s2);
+                    static_cast<float *>(a.d)[g] = 0.0f;
+                } else {
+                    const float rs = rf * fs;
+                    k0.add(rs * rs);
+                    k1.add(rs * (to_f(zt) * fs));
                 }
             }
         }
     }
-    constexpr int NV = MODE == RES_INIT ? 3 : 2;
+    if (MODE != RES_INIT) {
+        s0 = k0.value();
+        s1 = k1.value();
+    }
+    constexpr int NV = MODE == RES_INIT ? 3 : MODE == RES_REPLACE ? 2 : 1;
     __shared__ double red[8][3];
     s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
+    if (NV > 1) s1 = warp_sum(s1);
+    if (NV > 2) s2 = warp_sum(s2);
     if ((threadIdx.x & 31) == 0) {
         red[threadIdx.x >> 5][0] = s0;
         red[threadIdx.x >> 5][1] = s1;
@@ -158,26 +203,26 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) part[v] = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < 8; ++w)
+        for (int wi = 0; wi < 8; ++wi)
 #pragma unroll
-            for (int v = 0; v < NV; ++v) part[v] += red[w][v];
+            for (int v = 0; v < NV; ++v) part[v] += red[wi][v];
     if (!grid_sum_last<NV, 256>(part, a.partials, &st->ticket[4 + MODE], tot) || threadIdx.x != 0) return;
     if (MODE == RES_TRUE) {
-        st->rr_true = tot[0];
-        st->bb_true = tot[1];
+        st->rr_true = tot[0] * unscale;
+        st->bb_true = st->bb;
         return;
     }
     if (MODE == RES_INIT) {
         const double rr = tot[0], rz = tot[1], bb = tot[2];
         st->bb = bb; st->rr = rr; st->rz = rz; st->rr_rep = rr; st->rr_conf = kHuge;
-        st->it = 0; st->pending = 0; st->zero_x = 0; st->replace = 0;
+        st->it = 0; st->pending = 0; st->zero_x = 0; st->replace = 0; st->true_known = 0;
         if (bb == 0.0) { st->zero_x = 1; st->done = 1; st->status = GBPCG_OK; }
         else if (rr <= st->tol2 * bb) { st->done = 1; st->status = GBPCG_OK; }
         else if (!isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
         else if (st->maxit <= 0) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
         else { st->done = 0; st->status = GBPCG_NOT_CONVERGED; }
     } else {
-        const double rrt = tot[0], rzt = tot[1];
+        const double rrt = tot[0] * unscale, rzt = tot[1] * unscale;
         const int kind = st->replace;  // 1: decade of progress, 2: recursive residual met tol
         st->rr = rrt;
         st->rr_rep = rrt;
@@ -192,6 +237,13 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
             if (kind == 2) st->rr_conf = rrt;
             st->beta = rzt / st->rz;
             st->rz = rzt;
+        }
+        // converged here: the flush emptied d and cleared the pending update,
+        // so the finalize leaves x as this pass evaluated it
+        if (st->done && st->status == GBPCG_OK) {
+            st->true_known = 1;
+            st->rr_true = rrt;
+            st->bb_true = st->bb;
         }
     }
     if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
@@ -226,7 +278,7 @@ __global__ void finalize_kernel(const SolveState *st, X *x, const float *d, cons
 // ----------------------------------------------------------- workspace --
 
 struct WsLayout {
-    size_t state, partials, z, p0, p1, d, tab, bstage, xstage, total;
+    size_t state, partials, z, p0, p1, d, tab, tab64, bstage, xstage, total;
 };
 
 static inline size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -245,6 +297,7 @@ static inline WsLayout ws_layout_n(size_t n, int storage, int io_dtype, bool hos
     w.p1 = off; off += vs;
     w.d = off; off += round256(n * sizeof(float));  // d is FP32 for every storage type
     w.tab = off; off += round256((size_t)nblocks * 2 * sizeof(float4));  // face table (block coefficient)
+    w.tab64 = off; off += round256((size_t)nblocks * kTab64 * sizeof(double));  // FP64 face weights
     w.bstage = w.xstage = 0;
     if (host_io) {
         w.bstage = off; off += io;
@@ -284,6 +337,7 @@ struct SolvePlan {
     T *z, *p0, *p1;
     float *d;
     char *tab;
+    double *tab64;
     PassGeom ga, gb;
     PassMaps ma, mb;
     PassArgs aa, ab;
@@ -303,6 +357,7 @@ struct SolvePlan {
         p1 = reinterpret_cast<T *>(ws + L.p1);
         d = reinterpret_cast<float *>(ws + L.d);
         tab = ws + L.tab;
+        tab64 = reinterpret_cast<double *>(ws + L.tab64);
         const int nx = g.nx, ny = g.ny, nz = g.nz;
         // kernel attributes and occupancy (never during a capture)
         int occ_a = GB_CFG_DISPATCH(cfg_a, T, K_PASSA, TMA, Op, K::occupancy());
@@ -311,8 +366,7 @@ struct SolvePlan {
         // pass B uses pass A's z chunks (it marches them downwards), so each
         // of its CTAs starts on the planes pass A's CTAs finished with
         gb = make_geom(cfg_b, nx, ny, nz, occ_b, GB_CFG_DISPATCH(cfg_b, T, K_PASSB, TMA, Op, K::smem));
-        gb.zchunk = ga.zchunk;
-        gb.zchunks = ga.zchunks;
+        split_chunks(gb, ga.zchunk, nz, occ_b);
         memset(&ma, 0, sizeof(ma));
         memset(&mb, 0, sizeof(mb));
         if (TMA) {
@@ -336,9 +390,9 @@ struct SolvePlan {
             a->partials = partials;
             a->scale = 1.0f;
         }
-        aa.tiles_x = ga.tiles_x; aa.zchunk = ga.zchunk;
+        aa.tiles_x = ga.tiles_x; aa.zchunk = ga.zchunk; aa.zparts = ga.zparts;
         aa.h0[0] = aa.h0[1] = z; aa.h1[0] = p0; aa.h1[1] = p1; aa.c0 = d; aa.o0[0] = p0; aa.o0[1] = p1; aa.o1 = d;
-        ab.tiles_x = gb.tiles_x; ab.zchunk = gb.zchunk;
+        ab.tiles_x = gb.tiles_x; ab.zchunk = gb.zchunk; ab.zparts = gb.zparts;
         ab.h0[0] = p0; ab.h0[1] = p1; ab.h1[0] = ab.h1[1] = p0; ab.c0 = z; ab.o0[0] = ab.o0[1] = z; ab.o1 = z;
         auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
         memset(&ra, 0, sizeof(ra));
@@ -348,6 +402,7 @@ struct SolvePlan {
         ra.bscale = bscale;
         ra.kb = g.k_block;
         ra.kbx = g.k_block ? g.kbx : 1; ra.kby = g.k_block ? g.kby : 1; ra.kbz = g.k_block ? g.kbz : 1;
+        ra.tab64 = tab64;
         ra.st = st;
         ra.partials = partials;
         return GBPCG_OK;
@@ -384,8 +439,10 @@ struct SolvePlan {
         if (g.k_block) {
             const int nbx = (g.nx + g.kbx - 1) / g.kbx, nby = (g.ny + g.kby - 1) / g.kby, nbz = (g.nz + g.kbz - 1) / g.kbz;
             const int64_t nb = (int64_t)nbx * nby * nbz;
-            build_face_table<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096)), 256, 0, s>>>(
-                g.k_block, nbx, nby, nbz, reinterpret_cast<float4 *>(tab));
+            const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
+            build_face_table<<<blocks, 256, 0, s>>>(g.k_block, nbx, nby, nbz, reinterpret_cast<float4 *>(tab));
+            const Coef64 cf{ra.cx, ra.cy, ra.cz, g.k_block, g.kbx, g.kby, g.kbz};
+            build_face_table64<<<blocks, 256, 0, s>>>(g.k_block, nbx, nby, nbz, cf, tab64);
         }
         launch_res64<RES_INIT>(s);
         return cudaGetLastError();

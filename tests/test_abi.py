@@ -61,7 +61,7 @@ def test_struct_layout_matches_header(tmp_path):
 
 def test_tile_configs_enumerate(lib):
     cfgs = B.tile_configs()
-    assert len(cfgs) == 8 and cfgs[0] == (64, 16, 4) and cfgs[6] == (256, 4, 4)
+    assert len(cfgs) == 10 and cfgs[0] == (64, 16, 4) and cfgs[6] == (256, 4, 4) and cfgs[9] == (256, 4, 3)
     for tx, ty, st in cfgs:
         assert tx % 4 == 0 and ty >= 1 and st >= 2
     g = _grid(16, 16, 16)
