@@ -79,7 +79,8 @@ typedef struct gbpcg_grid {
 /* Flags of gbpcg_opts.flags */
 #define GBPCG_FLAG_HOST_IO 1u /* b and x may be host pointers; staged through the workspace */
 #define GBPCG_FLAG_PROFILE 2u /* launch the iteration kernels one by one (no graph), each
-                                 bracketed by CUDA events; fills gbpcg_result.pass_ms */
+                                 bracketed by CUDA events; fills gbpcg_result.pass_ms (BF16 /
+                                 F16 storage: the inner solves' passes, summed over the steps) */
 #define GBPCG_FLAG_AUTOTUNE 4u /* batched solves: pick each shape's tile configuration by timing
                                   (cached per shape in the process); the workspace grows by a
                                   scratch x per problem */

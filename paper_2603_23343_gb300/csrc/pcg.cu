@@ -352,8 +352,21 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
         // the inner solve starts from d = 0 (din keeps the last correction until
         // here, so a step can be undone)
         GB_CUDA(cudaMemsetAsync(din, 0, (size_t)n * sizeof(float), s));
-        int rc = o->storage == GBPCG_BF16 ? solve_launch<__nv_bfloat16>(inner, tma, s)
+        int rc;
+        if (o->flags & GBPCG_FLAG_PROFILE) {
+            // profile mode: the inner solve's kernels one by one, pass times summed over the steps
+            gbpcg_result ir;
+            memset(&ir, 0, sizeof(ir));
+            rc = o->storage == GBPCG_BF16 ? solve_profiled<__nv_bfloat16>(inner, tma, &ir, s)
+                                          : solve_profiled<__half>(inner, tma, &ir, s);
+            for (int p = 0; p < 2; ++p) {
+                result->pass_ms[p] += ir.pass_ms[p];
+                result->pass_launches[p] += ir.pass_launches[p];
+            }
+        } else {
+            rc = o->storage == GBPCG_BF16 ? solve_launch<__nv_bfloat16>(inner, tma, s)
                                           : solve_launch<__half>(inner, tma, s);
+        }
         if (rc) return rc;
         refine_update_kernel<<<eb, 256, 0, s>>>(x, din, os, n, 0);
         GB_CUDA(cudaGetLastError());

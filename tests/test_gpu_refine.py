@@ -107,3 +107,19 @@ def test_config2_512_lognormal_full_size(gpu_lib):
     ts = oracle.true_relres(b, xs, k64, 8)
     assert abs(rs["rel_res_true"] - ts) <= 1e-3 * ts
     assert ts < 1.0
+
+
+@pytest.mark.parametrize("storage", [torch.bfloat16, torch.float16])
+def test_refinement_profile_mode_matches_graph_mode(gpu_lib, storage):
+    """With the profile flag the inner solves launch their kernels one by one and time the
+    passes; the arithmetic is the same kernels in the same order, so iterations, steps and
+    the returned x equal the graph-mode solve's, bit for bit."""
+    b = inputs.uniform_rhs((40, 24, 100), 5, dtype=np.float64)
+    xg, rg = refine(gpu_lib, b, storage, maxit=4000)
+    xp, rp = refine(gpu_lib, b, storage, maxit=4000, profile=True)
+    assert rg["status"] == 0 and rp["status"] == 0
+    assert (rp["iters"], rp["refine_steps"]) == (rg["iters"], rg["refine_steps"])
+    assert np.array_equal(xp, xg)
+    assert rp["pass_launches"][0] == rp["iters"] and rp["pass_launches"][1] == rp["iters"]
+    assert rp["pass_ms"][0] > 0 and rp["pass_ms"][1] > 0
+    assert rg["pass_launches"] == [0, 0]
