@@ -114,6 +114,8 @@ typedef struct gbpcg_result {
     int32_t pass_launches[2];  /* GBPCG_FLAG_PROFILE: number of timed launches of each pass */
     int32_t replacements;      /* residual replacements (x flushed, r = b - A x in FP64) */
     int32_t refine_steps;      /* outer refinement steps (16-bit storage), else 0 */
+    int32_t pass_ctas[2];      /* GBPCG_FLAG_PROFILE: CTAs per launch of pass A / pass B (tiles x z
+                                  chunks, pass B's chunks possibly cut into parts) */
 } gbpcg_result;
 
 /* Library version string, e.g. "gbpcg 0.1 sm_103a". */

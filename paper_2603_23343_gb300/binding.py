@@ -62,13 +62,14 @@ class Result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("rel_res_recursive", ctypes.c_double),
                 ("rel_res_true", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("pass_ms", ctypes.c_double * 2), ("pass_launches", ctypes.c_int32 * 2),
-                ("replacements", ctypes.c_int32), ("refine_steps", ctypes.c_int32)]
+                ("replacements", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("pass_ctas", ctypes.c_int32 * 2)]
 
     def as_dict(self):
         return dict(iters=self.iters, status=self.status, status_name=STATUS_NAMES.get(self.status, "?"),
                     rel_res_recursive=self.rel_res_recursive, rel_res_true=self.rel_res_true,
-                    time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches), replacements=self.replacements,
-                    refine_steps=self.refine_steps)
+                    time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches),
+                    replacements=self.replacements, refine_steps=self.refine_steps, pass_ctas=list(self.pass_ctas))
 
 
 class GbpcgError(RuntimeError):

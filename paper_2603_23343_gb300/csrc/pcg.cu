@@ -362,6 +362,7 @@ static int refine_solve(const gbpcg_grid &g, const double *b, double *x, const g
             for (int p = 0; p < 2; ++p) {
                 result->pass_ms[p] += ir.pass_ms[p];
                 result->pass_launches[p] += ir.pass_launches[p];
+                result->pass_ctas[p] = ir.pass_ctas[p];
             }
         } else {
             rc = o->storage == GBPCG_BF16 ? solve_launch<__nv_bfloat16>(inner, tma, s)

@@ -581,7 +581,7 @@ struct SolvePlan {
     // Profile mode: the same kernels launched one by one on `s`, each pass
     // launch bracketed by CUDA events; the loop polls the device flag every
     // kChunk iterations.  Only launches of real iterations are summed.
-    int run_profiled(cudaStream_t s, double pass_ms[2], int launches[2]) {
+    int run_profiled(cudaStream_t s, double pass_ms[2], int launches[2], int ctas[2]) {
         constexpr int kChunk = 32;
         set_cond(0, 0, 0);
         GB_CUDA(launch_setup(s));
@@ -590,6 +590,8 @@ struct SolvePlan {
             for (int j = 0; j < 4; ++j) GB_CUDA(cudaEventCreate(&ev[i][j]));
         pass_ms[0] = pass_ms[1] = 0.0;
         launches[0] = launches[1] = 0;
+        ctas[0] = (int)ga.nblocks();
+        ctas[1] = (int)gb.nblocks();
         int flags_h[2] = {0, 0};
         int rc = GBPCG_OK;
         for (int base = 0; base < std::max(maxit, 1); base += kChunk) {
@@ -770,7 +772,7 @@ int solve_profiled(const SolveCall &c, bool tma, gbpcg_result *res, cudaStream_t
     return dispatch_plan<T>(c, tma, [&](auto op, auto tm, auto xt) {
         SolvePlan<decltype(op), decltype(tm)::value, decltype(xt), T> plan;
         if (int r = plan_init(plan, c, op)) return r;
-        return plan.run_profiled(s, res->pass_ms, res->pass_launches);
+        return plan.run_profiled(s, res->pass_ms, res->pass_launches, res->pass_ctas);
     });
 }
 

@@ -158,6 +158,29 @@ def test_every_tile_configuration(gpu_lib, cfg):
         check_against_oracle(gpu_lib, b, io=np.float64, tile_cfg=gpu_lib.tile_cfg_code(cfg, other))
 
 
+def test_pass_b_cuts_chunks_into_parts(gpu_lib):
+    """Pass B marches pass A's z chunks; where its occupancy leaves room it cuts each chunk
+    into parts, one CTA each.  Pass A on 6-stage 128x8 tiles (2 CTAs per SM) and pass B on
+    3-stage 128x8 tiles over a ragged 61 x 250 x 252 grid: pass B gets at least twice pass A's
+    CTAs (same tiles), and the last chunk's last part is shorter than the others.  The solve
+    takes the default partition's iterations (within one: partial sums are added in another
+    order) and meets the tolerance on the oracle's FP64 true residual."""
+    shape = (61, 250, 252)
+    b = inputs.uniform_rhs(shape, 31, dtype=np.float64)
+    bd = torch.from_numpy(b).cuda()
+    cfgs = gpu_lib.tile_configs()
+    code = gpu_lib.tile_cfg_code(cfgs.index((128, 8, 6)), cfgs.index((128, 8, 3)))
+    x, res = gpu_lib.pcg_solve(bd, tol=1e-6, maxit=3000, profile=True, tile_cfg=code)
+    ctas_a, ctas_b = res["pass_ctas"]
+    assert ctas_a > 0 and ctas_b % ctas_a == 0 and ctas_b // ctas_a >= 2, res["pass_ctas"]
+    _, ref = gpu_lib.pcg_solve(bd, tol=1e-6, maxit=3000)
+    assert res["status"] == gpu_lib.OK and ref["status"] == gpu_lib.OK
+    assert abs(res["iters"] - ref["iters"]) <= 1, (res["iters"], ref["iters"])
+    true_rel = oracle.true_relres(b, x.cpu().numpy())
+    assert true_rel <= 1e-6
+    assert abs(res["rel_res_true"] - true_rel) <= 1e-3 * true_rel
+
+
 def test_whole_row_configuration_rejects_wide_grids(gpu_lib):
     b = torch.zeros((4, 4, 260), dtype=torch.float32, device="cuda")
     with pytest.raises(gpu_lib.GbpcgError):
