@@ -93,6 +93,19 @@ def test_stencil_f64(gpu_lib, shape):
     assert np.all(np.abs(q - ref) <= 1e-13 * abs_op_bound(p))
 
 
+@pytest.mark.parametrize("shape,kb", [((10, 14, 22), 4), ((9, 17, 33), 3), ((16, 16, 16), 8)])
+def test_stencil_f64_block_coefficient(gpu_lib, shape, kb):
+    """FP64 operator with block coefficients (partial blocks at the far end of each axis where
+    the edge is not a multiple of kb): harmonic-mean faces in FP64, against the oracle."""
+    nz, ny, nx = shape
+    nbx, nby, nbz = inputs.block_counts(nx, ny, nz, kb)
+    k = inputs.lognormal_blocks(nbx, nby, nbz, 2)
+    p = inputs.uniform_rhs(shape, 8, dtype=np.float64)
+    q = gpu_lib.stencil_apply(to_dev(p, torch.float64), k_block=to_dev(k), kb=kb).cpu().numpy()
+    ref = oracle.apply(p, k.astype(np.float64), kb)
+    assert np.all(np.abs(q - ref) <= 1e-13 * abs_op_bound(p, k.astype(np.float64), kb))
+
+
 @pytest.mark.parametrize("n", [1, 7, 4096, 4097, 1_000_003, 1 << 22])
 def test_dot_f32(gpu_lib, n):
     x = inputs.uniform_pm1(10, 0, n)

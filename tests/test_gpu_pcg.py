@@ -57,9 +57,11 @@ def test_shapes_tma_and_plain_paths(gpu_lib, shape):
     check_against_oracle(gpu_lib, b)
 
 
-@pytest.mark.parametrize("shape,kb", [((48, 48, 48), 8), ((24, 20, 36), 4), ((13, 11, 9), 3)])
+@pytest.mark.parametrize("shape,kb", [((48, 48, 48), 8), ((24, 20, 36), 4), ((13, 11, 9), 3), ((10, 14, 22), 4)])
 @pytest.mark.parametrize("io", [np.float32, np.float64])
 def test_block_coefficient_lognormal(gpu_lib, shape, kb, io):
+    """Block coefficients, including partial blocks at the far end of every axis (10 x 14 x 22
+    with 4^3 blocks): the passes' FP32 face table and the residuals' FP64 face table."""
     nz, ny, nx = shape
     k, b = inputs.varcoeff_problem(nx, ny, nz, seed=1, kb=kb)
     check_against_oracle(gpu_lib, b, k=k, kb=kb, maxit=5000, io=io)
