@@ -60,8 +60,23 @@ struct __align__(16) SolveState {
     double rr_conf; // ||b - A x||^2 at the last confirmation (recursive residual had met tol)
     int n_replace;  // residual replacements done
     int true_known; // 1: rr_true, bb_true already hold b - A x of the final x
+    unsigned long long rhs_bits;  // max |b| as the bit pattern of a non-negative double
+    unsigned long long pad2;
     unsigned int ticket[8];
 };
+
+// Power of two s that brings max |b| into [0.5, 1) when it lies outside
+// [2^-21, 2^20), else 1.  The solver works on s b and s x (exact scalings):
+// the FP32 iteration vectors and their FP32 partial sums then stay far from
+// underflow and overflow whatever the scale of b.
+__device__ __forceinline__ double rhs_scale(unsigned long long bits) {
+    const double m = __longlong_as_double((long long)bits);
+    if (!(m > 0.0) || !isfinite(m)) return 1.0;
+    int e = 0;
+    frexp(m, &e);
+    if (e >= -20 && e <= 20) return 1.0;
+    return ldexp(1.0, -e);
+}
 
 // A residual replacement is triggered whenever ||r|| has dropped by this
 // factor squared since the last one (a decade of residual norm), and when

@@ -74,6 +74,31 @@ static __global__ void build_face_table64(const float *kb, int nbx, int nby, int
     }
 }
 
+// max |b| into st->rhs_bits (integer maxima of the bit patterns: no FP64 work).
+template <typename X>
+__global__ void __launch_bounds__(256) rhs_max_kernel(const X *__restrict__ b, int64_t n, SolveState *st) {
+    using U = typename std::conditional<sizeof(X) == 8, unsigned long long, unsigned int>::type;
+    constexpr U kAbs = (U)~((U)1 << (8 * sizeof(X) - 1));
+    U m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        X v = __ldg(b + i);
+        U u;
+        memcpy(&u, &v, sizeof(U));
+        u &= kAbs;
+        m = u > m ? u : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t > m ? t : m;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        X v;
+        memcpy(&v, &m, sizeof(U));
+        atomicMax(&st->rhs_bits, (unsigned long long)__double_as_longlong((double)v));
+    }
+}
+
 enum ResMode { RES_INIT = 0, RES_REPLACE = 1, RES_TRUE = 2 };
 
 struct Res64Args {
@@ -86,6 +111,7 @@ struct Res64Args {
     int kbx, kby, kbz;
     const double *tab64;   // FP64 face weights per coefficient block (build_face_table64)
     const double *bscale;  // NULL, or a device scalar multiplying b (inner refinement solves)
+    int rhs_auto;          // 1: b and x are scaled by rhs_scale(st->rhs_bits) (plain solves)
     SolveState *st;
     double *partials;
     cudaGraphConditionalHandle cond;
@@ -133,7 +159,8 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
     const Coef64 cf{a.cx, a.cy, a.cz, a.kb, a.kbx, a.kby, a.kbz};
     const bool bscaled = a.bscale != nullptr;
     const double bsc = bscaled ? *a.bscale : 1.0;
-    // FP32 sums: scale 2^-e, unscale 2^(2e)
+    // FP32 sums: scale 2^-e, unscale 2^(2e).  b arrives with max |b| within [2^-21, 2^20)
+    // (rhs_scale, or the refinement's own scaling), so r itself is far from FP32's limits.
     float fs = 1.0f;
     double unscale = 1.0;
     if (MODE != RES_INIT) {
@@ -152,38 +179,45 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
     face_weights64<false>(w, 0, 0, 0, nx, ny, nz, cf);
     const float dg_const = diag64(w);
     const int rows = ny * nz;
-    for (int row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int j = row % ny, k = row / ny;
-        const int64_t base = (int64_t)row * nx;
-        for (int i = threadIdx.x; i < nx; i += 256) {
-            const int64_t g = base + i;
-            const Nbr64 u = load_nbr64(x, g, i, j, k, nx, ny, nz);
-            if (BLOCK) face_weights64_tab(w, i, j, k, nx, ny, a.tab64, cf);
-            const double ax = apply64<BLOCK>(u, w);
-            const double bl = (double)__ldg(b + g);
-            const double bv = bscaled ? bsc * bl : bl;
-            const double r = bv - ax;
-            const float rf = (float)r;
-            if (MODE == RES_TRUE) {
+    // plain solves work on s b and s x: r = s (b - A x) (one more FP64 multiply, only when s != 1)
+    const double s_rhs = a.rhs_auto ? rhs_scale(st->rhs_bits) : 1.0;
+    auto sweep = [&](auto scaled_tag) {
+        constexpr bool SC = decltype(scaled_tag)::value;
+        for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+            const int j = row % ny, k = row / ny;
+            const int64_t base = (int64_t)row * nx;
+            for (int i = threadIdx.x; i < nx; i += 256) {
+                const int64_t g = base + i;
+                const Nbr64 u = load_nbr64(x, g, i, j, k, nx, ny, nz);
+                if (BLOCK) face_weights64_tab(w, i, j, k, nx, ny, a.tab64, cf);
+                const double ax = apply64<BLOCK>(u, w);
+                const double bl = (double)__ldg(b + g);
+                const double bv0 = bscaled ? bsc * bl : bl;
+                const double r = SC ? s_rhs * (bv0 - ax) : bv0 - ax;
+                const double bv = SC ? s_rhs * bv0 : bv0;
+                const float rf = (float)r;
                 const float rs = rf * fs;
-                k0.add(rs * rs);
-            } else {
-                const float dg = BLOCK ? diag64(w) : dg_const;
-                const T zt = from_f<T>(rf / dg);
-                static_cast<T *>(a.z)[g] = zt;
-                if (MODE == RES_INIT) {
-                    s0 = fma(r, r, s0);
-                    s1 = fma(r, (double)to_f(zt), s1);
-                    s2 = fma(bv, bv, s2);
-                    static_cast<float *>(a.d)[g] = 0.0f;
-                } else {
-                    const float rs = rf * fs;
+                if (MODE == RES_TRUE) {
                     k0.add(rs * rs);
-                    k1.add(rs * (to_f(zt) * fs));
+                } else {
+                    const float dg = BLOCK ? diag64(w) : dg_const;
+                    const T zt = from_f<T>(rf / dg);
+                    static_cast<T *>(a.z)[g] = zt;
+                    if (MODE == RES_INIT) {
+                        s0 = fma(r, r, s0);
+                        s1 = fma(r, (double)to_f(zt), s1);
+                        s2 = fma(bv, bv, s2);
+                        static_cast<float *>(a.d)[g] = 0.0f;
+                    } else {
+                        k0.add(rs * rs);
+                        k1.add(rs * (to_f(zt) * fs));
+                    }
                 }
             }
         }
-    }
+    };
+    if (s_rhs != 1.0) sweep(std::true_type{});
+    else sweep(std::false_type{});
     if (MODE != RES_INIT) {
         s0 = k0.value();
         s1 = k1.value();
@@ -249,22 +283,39 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
     if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
 }
 
+// x += (d + alpha_{it-1} p_{it-1}) / s: the increment is in the solver's scaled
+// units (s = rhs_scale, or 1), x in the caller's.
+template <typename X, typename T>
+__device__ __forceinline__ void add_increment(X *x, float *d, const T *p, float a, int64_t n, double inv_s,
+                                              bool clear_d) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+    if (inv_s == 1.0) {
+        for (int64_t i = tid; i < n; i += nth) {
+            x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]);
+            if (clear_d) d[i] = 0.0f;
+        }
+    } else {
+        const X is = (X)inv_s;  // a power of two: exact in X unless X's exponent range ends first
+        for (int64_t i = tid; i < n; i += nth) {
+            x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]) * is;
+            if (clear_d) d[i] = 0.0f;
+        }
+    }
+}
+
 // Residual replacement, step 1: x += d + alpha_{it-1} p_{it-1} (pending), d = 0.
 template <typename X, typename T>
-__global__ void flush_kernel(SolveState *st, X *x, float *d, const T *p0, const T *p1, int64_t n) {
+__global__ void flush_kernel(SolveState *st, X *x, float *d, const T *p0, const T *p1, int64_t n, int rhs_auto) {
     if (!st->replace || st->done) return;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
     const T *p = ((st->it - 1) & 1) ? p1 : p0;
     const float a = st->pending ? (float)st->alpha : 0.0f;
-    for (int64_t i = tid; i < n; i += nth) {
-        x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]);
-        d[i] = 0.0f;
-    }
+    add_increment<X, T>(x, d, p, a, n, rhs_auto ? 1.0 / rhs_scale(st->rhs_bits) : 1.0, true);
 }
 
 // x += d + alpha_{it-1} p_{it-1} (the pending update, if any); x = 0 when b = 0.
 template <typename X, typename T>
-__global__ void finalize_kernel(const SolveState *st, X *x, const float *d, const T *p0, const T *p1, int64_t n) {
+__global__ void finalize_kernel(const SolveState *st, X *x, const float *d, const T *p0, const T *p1, int64_t n,
+                                int rhs_auto) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
     if (st->zero_x) {
         for (int64_t i = tid; i < n; i += nth) x[i] = X(0);
@@ -272,7 +323,7 @@ __global__ void finalize_kernel(const SolveState *st, X *x, const float *d, cons
     }
     const T *p = ((st->it - 1) & 1) ? p1 : p0;
     const float a = st->pending ? (float)st->alpha : 0.0f;
-    for (int64_t i = tid; i < n; i += nth) x[i] = x[i] + (X)fmaf(a, to_f(p[i]), d[i]);
+    add_increment<X, T>(x, const_cast<float *>(d), p, a, n, rhs_auto ? 1.0 / rhs_scale(st->rhs_bits) : 1.0, false);
 }
 
 // ----------------------------------------------------------- workspace --
@@ -400,6 +451,7 @@ struct SolvePlan {
         ra.x = x; ra.b = b; ra.z = z; ra.d = d;
         ra.cx = cc(nx) * op_scale; ra.cy = cc(ny) * op_scale; ra.cz = cc(nz) * op_scale;
         ra.bscale = bscale;
+        ra.rhs_auto = bscale ? 0 : 1;  // inner refinement solves come scaled by the outer loop
         ra.kb = g.k_block;
         ra.kbx = g.k_block ? g.kbx : 1; ra.kby = g.k_block ? g.kby : 1; ra.kbz = g.k_block ? g.kbz : 1;
         ra.tab64 = tab64;
@@ -436,6 +488,10 @@ struct SolvePlan {
 
     cudaError_t launch_setup(cudaStream_t s) {
         reset_state_kernel<<<1, 32, 0, s>>>(st, tol, maxit);
+        if (ra.rhs_auto) {
+            const int64_t n = (int64_t)g.nx * g.ny * g.nz;
+            rhs_max_kernel<X><<<stream_blocks(n, 2048), 256, 0, s>>>(b, n, st);
+        }
         if (g.k_block) {
             const int nbx = (g.nx + g.kbx - 1) / g.kbx, nby = (g.ny + g.kby - 1) / g.kby, nbz = (g.nz + g.kbz - 1) / g.kbz;
             const int64_t nb = (int64_t)nbx * nby * nbz;
@@ -457,14 +513,14 @@ struct SolvePlan {
     // flush d into x, then r = b - A x in FP64 (both no-ops unless st->replace)
     cudaError_t launch_replace(cudaStream_t s) {
         const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-        flush_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
+        flush_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n, ra.rhs_auto);
         launch_res64<RES_REPLACE>(s);
         return cudaGetLastError();
     }
 
     cudaError_t launch_final(cudaStream_t s) {
         const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-        finalize_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n);
+        finalize_kernel<X, T><<<stream_blocks(n, 1024), 256, 0, s>>>(st, x, d, p0, p1, n, ra.rhs_auto);
         launch_res64<RES_TRUE>(s);
         return cudaGetLastError();
     }

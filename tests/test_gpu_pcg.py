@@ -183,6 +183,24 @@ def test_pass_b_cuts_chunks_into_parts(gpu_lib):
     assert abs(res["rel_res_true"] - true_rel) <= 1e-3 * true_rel
 
 
+@pytest.mark.parametrize("io,powers,tol", [(np.float64, (-300, -100, -40, 40, 100, 300), 1e-8),
+                                           (np.float32, (-60, -30, 30, 60), 1e-6)])
+def test_right_hand_side_scale_invariance(gpu_lib, io, powers, tol):
+    """Scaling b by 2^k scales the solution by 2^k and changes nothing else: the solver works on
+    s b with s a power of two that brings max |b| near 1 (when it is far from 1), so the FP32
+    iteration vectors and partial sums neither underflow nor overflow.  The iterations are the
+    same and x comes back as the unscaled solution times 2^k, bit for bit."""
+    b = inputs.uniform_rhs((24, 20, 36), 9, dtype=np.float64)
+    x0, r0 = solve(gpu_lib, b.astype(io), io=io, tol=tol, maxit=3000)
+    assert r0["status"] == gpu_lib.OK
+    for k in powers:
+        bk = (b * 2.0 ** k).astype(io)
+        xk, rk = solve(gpu_lib, bk, io=io, tol=tol, maxit=3000)
+        assert rk["status"] == gpu_lib.OK and rk["iters"] == r0["iters"], (k, rk)
+        assert np.array_equal(xk.astype(np.float64) * 2.0 ** -k, x0.astype(np.float64)), k
+        assert oracle.true_relres(bk.astype(np.float64), xk.astype(np.float64)) <= tol
+
+
 def test_whole_row_configuration_rejects_wide_grids(gpu_lib):
     b = torch.zeros((4, 4, 260), dtype=torch.float32, device="cuda")
     with pytest.raises(gpu_lib.GbpcgError):
