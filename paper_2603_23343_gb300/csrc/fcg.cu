@@ -57,13 +57,14 @@ struct DirSet {
 constexpr int kFcgThreads = 256;
 constexpr unsigned kFcgMaxBlocks = 2048;
 
-// d (FP64, in place of A x) = b - A x, and its FP32 copy r (optional)
+// d (FP64, in place of A x) = b - A x, and its FP32 copy r = s d (optional)
 __global__ void __launch_bounds__(256)
-    fcg_residual_kernel(int64_t n, const double *__restrict__ b, double *__restrict__ ax, float *__restrict__ r) {
+    fcg_residual_kernel(int64_t n, const double *__restrict__ b, double *__restrict__ ax, float *__restrict__ r,
+                        double s) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double d = b[i] - ax[i];
         ax[i] = d;
-        if (r) r[i] = (float)d;
+        if (r) r[i] = (float)(s == 1.0 ? d : d * s);
     }
 }
 
@@ -166,10 +167,11 @@ __global__ void __launch_bounds__(kFcgThreads)
 // alpha = r.p / p.Ap; x += alpha p (FP64); r -= alpha Ap; r.r
 __global__ void __launch_bounds__(kFcgThreads)
     fcg_update_kernel(int64_t n4, FcgState *st, double *partials, double *__restrict__ x, const float *__restrict__ p,
-                      const float *__restrict__ q, float *__restrict__ r, int slot) {
+                      const float *__restrict__ q, float *__restrict__ r, int slot, double inv_s) {
     if (st->bad) return;  // uniform over the grid: no block reaches the reduction
     const double alpha = st->rp / st->pq[slot];
     const float af = (float)alpha;
+    const double ax = alpha * inv_s;  // r, p, q are in the scaled units, x in the caller's
     double acc[1] = {0.0};
     for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
         const float4 pv = reinterpret_cast<const float4 *>(p)[i];
@@ -177,10 +179,10 @@ __global__ void __launch_bounds__(kFcgThreads)
         float4 rv = reinterpret_cast<float4 *>(r)[i];
         double2 *x2 = reinterpret_cast<double2 *>(x) + 2 * i;
         double2 xa = x2[0], xb = x2[1];
-        xa.x = fma(alpha, (double)pv.x, xa.x);
-        xa.y = fma(alpha, (double)pv.y, xa.y);
-        xb.x = fma(alpha, (double)pv.z, xb.x);
-        xb.y = fma(alpha, (double)pv.w, xb.y);
+        xa.x = fma(ax, (double)pv.x, xa.x);
+        xa.y = fma(ax, (double)pv.y, xa.y);
+        xb.x = fma(ax, (double)pv.z, xb.x);
+        xb.y = fma(ax, (double)pv.w, xb.y);
         x2[0] = xa;
         x2[1] = xb;
         rv.x = fmaf(-af, qv.x, rv.x);
@@ -338,11 +340,14 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
         GB_CUDA(cudaStreamSynchronize(s));
         return GBPCG_OK;
     };
-    // r = b - A x in FP64 (d64), its FP32 copy in r, ||r||^2 into st->rr64
+    // The FP32 vectors work on s b (s a power of two bringing rms(b) near 1 when it is far
+    // from it), so their products neither underflow nor overflow; x stays in the caller's units.
+    double s_rhs = 1.0;
+    // r = b - A x in FP64 (d64), its scaled FP32 copy in r, ||r||^2 into st->rr64
     auto true_residual = [&](bool to_r) -> int {
         int rc2 = launch_stencil_f64(g, x, d64, s);
         if (rc2) return rc2;
-        fcg_residual_kernel<<<eb, 256, 0, s>>>(n, b, d64, to_r ? r : nullptr);
+        fcg_residual_kernel<<<eb, 256, 0, s>>>(n, b, d64, to_r ? r : nullptr, s_rhs);
         GB_CUDA(cudaGetLastError());
         return gbpcg_dot(n, GBPCG_F64, d64, d64, &st->rr64, dotws, dws, stream);
     };
@@ -366,6 +371,13 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
     if (rc) return rc;
     rc = gbpcg_dot(n, GBPCG_F64, b, b, &st->bb, dotws, dws, stream);
     if (rc) return rc;
+    rc = pull();
+    if (rc) return rc;
+    if (hs.bb > 0.0 && std::isfinite(hs.bb)) {
+        int e = 0;
+        std::frexp(std::sqrt(hs.bb / (double)n), &e);
+        if (e < -20 || e > 20) s_rhs = std::ldexp(1.0, -e);
+    }
     rc = true_residual(true);
     if (rc) return rc;
     rc = pull();
@@ -405,7 +417,7 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
             if (rc) return rc;
             fcg_pdots_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, p, q, r, cur);
             GB_CUDA(cudaGetLastError());
-            fcg_update_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, x, p, q, r, cur);
+            fcg_update_kernel<<<rb, kFcgThreads, 0, s>>>(n4, st, partials, x, p, q, r, cur, 1.0 / s_rhs);
             GB_CUDA(cudaGetLastError());
             rc = pull();
             if (rc) return rc;
@@ -418,7 +430,7 @@ extern "C" int gbpcg_fcg_solve(const gbpcg_grid *grid, const float *w, const voi
             ++fcg_iters;
             nd = std::min(nd + 1, m);
             cur = (cur + 1) % nslots;
-            rel = std::sqrt(hs.rr / bb);
+            rel = std::sqrt(hs.rr / bb) / s_rhs;  // hs.rr is ||s r||^2
             hist.push_back(rel);
             if (!std::isfinite(rel)) {
                 fallback = true;

@@ -115,3 +115,18 @@ def test_trained_network_beats_jacobi(gpu_lib):
         assert res["status"] == gpu_lib.OK and res["pass_launches"][1] == 0, res
         assert res["iters"] < 0.3 * jac["iters"]
         assert true_relres(b, x, k) <= 1e-6
+
+
+def test_right_hand_side_scale(gpu_lib):
+    """Flexible CG keeps its FP32 vectors on s b (s a power of two bringing rms(b) near 1), so a
+    right-hand side scaled by 2^-100 or 2^100 converges like the unscaled one and x comes back
+    scaled; the network sees the residual divided by its rms either way."""
+    k, b = learned.problem((32, 32, 32), 3)
+    w = learned.identity_weights().cuda()
+    x0, r0 = gpu_lib.fcg_solve(w, b, tol=1e-6, maxit=3000, k_block=k)
+    assert r0["status"] == gpu_lib.OK
+    for p in (-100, 100):
+        bp = b * 2.0 ** p
+        xp, rp = gpu_lib.fcg_solve(w, bp, tol=1e-6, maxit=3000, k_block=k)
+        assert rp["status"] == gpu_lib.OK and abs(rp["iters"] - r0["iters"]) <= 1, (p, rp, r0)
+        assert true_relres(bp, xp, k) <= 1e-6
