@@ -192,6 +192,9 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
  * decade of residual reduction and at recursive convergence, flushed into x
  * while the residual is replaced by b - A x computed in FP64 (reliable
  * updates), so the returned x meets the tolerance in its true residual.
+ * The FP32 vectors work on s b and s x, s a power of two that brings max |b|
+ * near 1 when it is far from 1: any scale of b that FP64 can hold converges
+ * alike (a solve of 2^k b returns 2^k times the solution of b, bit for bit).
  *
  * Mixed precision (opts->storage BF16 or F16, FP64 b and x): iterative
  * refinement.  Each outer step computes r = b - A x in FP64 and stops when
