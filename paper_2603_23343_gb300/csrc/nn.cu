@@ -333,10 +333,106 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// One output channel (the network's last layer, 16 -> 1), marching in z: a thread owns four
+// consecutive x outputs of one row over a z range and keeps the partial sums of three output
+// planes in registers.  Input plane m is read once (three rows, six voxels, CI channels) and
+// added, tap by tap, into output planes m + 1, m and m - 1; plane m - 1 is then complete and
+// written.  Per output: 27 CI multiply-adds from CI / 8 x 4.5 sixteen-byte loads, against 27 x
+// CI / 8 loads when every output reads its own 27 neighbours.
+constexpr int kC1Rows = 8, kC1Chunk = 16;
+
+template <int CI, typename TO>
+__global__ void __launch_bounds__(32 * kC1Rows)
+    conv3_c1_march_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in,
+                          const __nv_bfloat16 *__restrict__ w, TO *__restrict__ out, int relu,
+                          const __nv_bfloat16 *__restrict__ mask, int mstride, int moff, const double *scale,
+                          const float *__restrict__ vscale) {
+    static_assert(CI % 8 == 0, "channels come in 16-byte groups");
+    __shared__ __align__(16) float ws[27 * CI];  // ws[t * CI + i], t = 9 (dz+1) + 3 (dy+1) + (dx+1)
+    for (int e = threadIdx.x; e < 27 * CI; e += blockDim.x) ws[e] = __bfloat162float(w[e]);
+    __syncthreads();
+    const float sc = scale ? (float)*scale : 1.0f;
+    const int x0 = (blockIdx.x * 32 + (threadIdx.x & 31)) * 4;
+    const int y = blockIdx.y * kC1Rows + (threadIdx.x >> 5);
+    const int zb = blockIdx.z * kC1Chunk, ze = min(Z, zb + kC1Chunk);
+    const bool active = x0 < X && y < Y;  // X % 4 == 0: a thread's four outputs are all inside or all out
+    float ap[4], ac[4], an[4];             // partial sums of output planes m - 1, m, m + 1
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ap[j] = ac[j] = an[j] = 0.0f;
+    for (int m = zb - 1; m <= ze; ++m) {
+        // which of the three output planes this input plane still feeds (uniform over the block)
+        const bool fn = m + 1 >= zb && m + 1 < ze, fc = m >= zb && m < ze, fp = m - 1 >= zb && m - 1 < ze;
+        if (active && m >= 0 && m < Z) {
+#pragma unroll 1
+            for (int r = 0; r < 3; ++r) {
+                const int yy = y + r - 1;
+                if (yy < 0 || yy >= Y) continue;
+                const __nv_bfloat16 *row = in + ((int64_t)m * Y + yy) * X * CI;
+#pragma unroll
+                for (int cb = 0; cb < CI; cb += 8) {
+                    float v[6][8];
+#pragma unroll
+                    for (int xi = 0; xi < 6; ++xi) {
+                        const int xx = x0 - 1 + xi;
+                        if (xx >= 0 && xx < X) {
+                            ld8(row + (int64_t)xx * CI + cb, v[xi]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) v[xi][c] = 0.0f;
+                        }
+                    }
+                    auto add = [&](float (&a)[4], int dzi) {
+#pragma unroll
+                        for (int dxi = 0; dxi < 3; ++dxi) {
+                            const float *wt = ws + (dzi * 9 + r * 3 + dxi) * CI + cb;
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                const float wv = wt[c];
+#pragma unroll
+                                for (int j = 0; j < 4; ++j) a[j] = fmaf(wv, v[j + dxi][c], a[j]);
+                            }
+                        }
+                    };
+                    if (fn) add(an, 0);  // dz = -1: output plane m + 1 reads input plane m
+                    if (fc) add(ac, 1);
+                    if (fp) add(ap, 2);  // dz = +1: output plane m - 1
+                }
+            }
+        }
+        if (fp && active) {  // output plane m - 1 has all three input planes
+            const int64_t v0 = ((int64_t)(m - 1) * Y + y) * X + x0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t v = v0 + j;
+                float f = ap[j] * (vscale ? sc * vscale[v] : sc);
+                if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
+                if (mask && !(__bfloat162float(mask[v * mstride + moff]) > 0.0f)) f = 0.0f;
+                out[v] = from_f<TO>(f);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ap[j] = ac[j];
+            ac[j] = an[j];
+            an[j] = 0.0f;
+        }
+    }
+}
+
 template <int CI, int CO, typename TO>
 static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const __nv_bfloat16 *w, TO *out, int relu,
                             const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
                             const float *vscale, cudaStream_t s) {
+    if constexpr (CO == 1 && CI % 8 == 0) {
+        if (X % 4 == 0) {
+            const dim3 grid((unsigned)((X / 4 + 31) / 32), (unsigned)((Y + kC1Rows - 1) / kC1Rows),
+                            (unsigned)((Z + kC1Chunk - 1) / kC1Chunk));
+            conv3_c1_march_kernel<CI, TO><<<grid, 32 * kC1Rows, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride,
+                                                                        moff, scale, vscale);
+            cudaError_t e = cudaGetLastError();
+            return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_c1_march launch");
+        }
+    }
     if (CI % 8 == 0 && X % 128 == 0) {
         const int64_t nseg = (int64_t)(X / 128) * Y * Z;  // one warp per 128-voxel row segment
         conv3_simt_strided_kernel<CI, CO, TO><<<blocks_for(nseg * 32, 256), 256, 0, s>>>(
