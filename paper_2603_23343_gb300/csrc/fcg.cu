@@ -99,16 +99,21 @@ __device__ __forceinline__ bool fcg_reduce(const double (&acc)[NV], double *part
 __global__ void __launch_bounds__(kFcgThreads)
     fcg_mdot_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ r,
                     const float *__restrict__ z, const DirSet d) {
-    double acc[kMaxDirs + 1];
+    // FP32 sums per thread (a handful of grid-stride steps), FP64 from the warp sums on:
+    // GB300's FP64 pipe would otherwise bound this kernel, not its loads
+    float facc[kMaxDirs + 1];
 #pragma unroll
-    for (int v = 0; v <= kMaxDirs; ++v) acc[v] = 0.0;
+    for (int v = 0; v <= kMaxDirs; ++v) facc[v] = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
         const float4 zv = reinterpret_cast<const float4 *>(z)[i];
-        acc[0] += (double)dot4f(reinterpret_cast<const float4 *>(r)[i], zv);
+        facc[0] += dot4f(reinterpret_cast<const float4 *>(r)[i], zv);
 #pragma unroll
         for (int j = 0; j < kMaxDirs; ++j)
-            if (j < d.nd) acc[1 + j] += (double)dot4f(reinterpret_cast<const float4 *>(d.q[j])[i], zv);
+            if (j < d.nd) facc[1 + j] += dot4f(reinterpret_cast<const float4 *>(d.q[j])[i], zv);
     }
+    double acc[kMaxDirs + 1];
+#pragma unroll
+    for (int v = 0; v <= kMaxDirs; ++v) acc[v] = (double)facc[v];
     double tot[kMaxDirs + 1];
     if (fcg_reduce<kMaxDirs + 1>(acc, partials, &st->ticket[0], tot) && threadIdx.x == 0) {
         const double rz = tot[0];
@@ -150,12 +155,13 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(kFcgThreads)
     fcg_pdots_kernel(int64_t n4, FcgState *st, double *partials, const float *__restrict__ p,
                      const float *__restrict__ q, const float *__restrict__ r, int slot) {
-    double acc[2] = {0.0, 0.0};
+    float facc[2] = {0.0f, 0.0f};
     for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
         const float4 pv = reinterpret_cast<const float4 *>(p)[i];
-        acc[0] += (double)dot4f(pv, reinterpret_cast<const float4 *>(q)[i]);
-        acc[1] += (double)dot4f(pv, reinterpret_cast<const float4 *>(r)[i]);
+        facc[0] += dot4f(pv, reinterpret_cast<const float4 *>(q)[i]);
+        facc[1] += dot4f(pv, reinterpret_cast<const float4 *>(r)[i]);
     }
+    double acc[2] = {(double)facc[0], (double)facc[1]};
     double tot[2];
     if (fcg_reduce<2>(acc, partials, &st->ticket[1], tot) && threadIdx.x == 0) {
         st->pq[slot] = tot[0];
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kFcgThreads)
     const double alpha = st->rp / st->pq[slot];
     const float af = (float)alpha;
     const double ax = alpha * inv_s;  // r, p, q are in the scaled units, x in the caller's
-    double acc[1] = {0.0};
+    float facc = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * kFcgThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kFcgThreads) {
         const float4 pv = reinterpret_cast<const float4 *>(p)[i];
         const float4 qv = reinterpret_cast<const float4 *>(q)[i];
@@ -190,8 +196,9 @@ __global__ void __launch_bounds__(kFcgThreads)
         rv.z = fmaf(-af, qv.z, rv.z);
         rv.w = fmaf(-af, qv.w, rv.w);
         reinterpret_cast<float4 *>(r)[i] = rv;
-        acc[0] += (double)dot4f(rv, rv);
+        facc += dot4f(rv, rv);
     }
+    double acc[1] = {(double)facc};
     double tot[1];
     if (fcg_reduce<1>(acc, partials, &st->ticket[2], tot) && threadIdx.x == 0) st->rr = tot[0];
 }
