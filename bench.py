@@ -476,6 +476,37 @@ def main():
                "sequential_ms": seq_ms}
     del rhs, xb
 
+    # a6: the dot and axpy kernels on 2^28 FP32 elements (1 GiB per vector, far above L2), best of 5
+    n28 = 1 << 28
+    gen = torch.Generator(device="cuda").manual_seed(28)
+    xa = torch.empty(n28, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=gen)
+    ya = torch.empty(n28, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=gen)
+    dout = torch.empty((), dtype=torch.float64, device="cuda")
+    dws = torch.empty(B.dot_workspace_size(), dtype=torch.uint8, device="cuda")
+
+    def best_us(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1) * 1e3)
+        return min(t)
+
+    t_dot = best_us(lambda: B.dot(xa, ya, dout, dws, stream=stream))
+    t_axpy = best_us(lambda: B.axpy(1e-3, xa, ya, stream=stream))
+    micro = {"n": n28, "dtype": "f32", "inputs": "U[-1,1) from a seeded device generator"}
+    for name, us, nbytes in (("dot", t_dot, 8 * n28), ("axpy", t_axpy, 12 * n28)):
+        micro[name] = {"us": us, "algorithmic_bytes": nbytes, "gbs": nbytes / (us * 1e-6) / 1e9,
+                       "frac": nbytes / (us * 1e-6) / 1e9 / peak}
+    del xa, ya, dws
+    torch.cuda.empty_cache()
+
     learned_res = None
     if not args.no_learned and n == 256:
         from paper_2603_23343_gb300 import learned
@@ -511,6 +542,7 @@ def main():
             },
             "mixed_precision": mixed,
             "batched_config3": batched,
+            "microkernels_2e28": micro,
             "learned_config4": learned_res,
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,
