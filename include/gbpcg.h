@@ -189,7 +189,7 @@ int gbpcg_workspace_size(const gbpcg_grid *grid, const gbpcg_opts *opts, size_t 
 /*
  * Jacobi-preconditioned CG (Sec. VII) for A x = b, with FP32 vectors and
  * FP64 scalars.  Updates are accumulated in a correction vector and, at every
- * decade of residual reduction and at recursive convergence, flushed into x
+ * two decades of residual reduction and at recursive convergence, flushed into x
  * while the residual is replaced by b - A x computed in FP64 (reliable
  * updates), so the returned x meets the tolerance in its true residual.
  * The FP32 vectors work on s b and s x, s a power of two that brings max |b|

@@ -14,7 +14,7 @@
 // Accuracy with FP32 vectors (reliable updates, van der Vorst & Ye, SIAM J.
 // Sci. Comput. 22, 2000): the updates alpha p go into a correction vector d
 // instead of x, so their rounding is relative to |d|, not |x|.  Whenever
-// ||r|| has dropped by a decade since the last time, and when the recursive
+// ||r|| has dropped by two decades since the last time, and when the recursive
 // residual meets the tolerance, d is flushed into x and the recursive
 // residual is replaced by b - A x evaluated in FP64; the iteration continues
 // from the replaced residual (p is kept).  Convergence is therefore decided
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
         else { st->done = 0; st->status = GBPCG_NOT_CONVERGED; }
     } else {
         const double rrt = tot[0] * unscale, rzt = tot[1] * unscale;
-        const int kind = st->replace;  // 1: decade of progress, 2: recursive residual met tol
+        const int kind = st->replace;  // 1: two decades of progress, 2: recursive residual met tol
         st->rr = rrt;
         st->rr_rep = rrt;
         st->replace = 0;
