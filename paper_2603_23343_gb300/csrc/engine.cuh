@@ -14,14 +14,14 @@
 // The seven-point operator at plane k needs the input at planes k-1, k, k+1
 // in the thread's own column (kept in registers as a 3-deep queue) and the
 // four in-plane neighbours (read from the plane-k box).  One thread computes
-// four consecutive x points of one row.
+// one 16-byte vector of a row: four FP32 or eight 16-bit x points.
 //
 // Pass kinds (Sec. VII's PCG split into two data passes plus setup):
 //   K_STENCIL  q = A p
 //   K_PASSA    p_k = z_k + beta_{k-1} p_{k-1} formed on the fly for every
 //              stencil input (no D needed: z, not r, is the stored vector);
 //              d += alpha_{k-1} p_{k-1} (deferred update of the previous
-//              iteration into the correction vector d, see pcg.cu); stores
+//              iteration into the correction vector d, see solver.cuh); stores
 //              p_k; sum p_k . A p_k -> alpha_k
 //   K_PASSB    q = A p_k recomputed (cheaper than storing it),
 //              r = D z - alpha_k q, z = D^-1 r; stores z; sums r.r, r.z
@@ -46,7 +46,7 @@ struct __align__(16) SolveState {
     double rr;      // ||r_k||^2 (recursive)
     double bb;      // ||b||^2
     double tol2;    // tol^2
-    double rr_true; // ||b - A x||^2, FP64
+    double rr_true; // ||b - A x||^2 (FP64 stencil, compensated FP32 sum of squares)
     double bb_true; // ||b||^2, FP64
     int it;         // completed iterations
     int maxit;
