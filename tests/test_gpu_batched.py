@@ -63,3 +63,18 @@ def test_config3_64_problems(gpu_lib):
     for b, x, r in zip(rhs, xs, res):
         assert r["status"] == 0, r
         assert oracle.true_relres(b, x.cpu().numpy()) <= 1e-6
+
+
+def test_batched_problems_keep_their_own_scale(gpu_lib):
+    """Each problem of a batch scales its own right-hand side: problems at 2^-200, 1 and 2^200
+    in one launch take the iterations of the unscaled problem and return its solution scaled,
+    bit for bit."""
+    b = inputs.uniform_rhs((24, 20, 36), 77, dtype=np.float64)
+    powers = (-200, 0, 200)
+    bs = [torch.from_numpy(b * 2.0 ** p).cuda() for p in powers]
+    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-8, maxit=3000)
+    x0 = xs[1].cpu().numpy()
+    for p, x, r in zip(powers, xs, res):
+        assert r["status"] == 0 and r["iters"] == res[1]["iters"], (p, r)
+        assert np.array_equal(x.cpu().numpy() * 2.0 ** -p, x0), p
+        assert oracle.true_relres(b * 2.0 ** p, x.cpu().numpy()) <= 1e-8
