@@ -547,7 +547,9 @@ def main():
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,
                     "d2h_bytes_per_step": N * 8 + 256},
-            "gpu_launches": args.steps * (2 * iters + 4 + 2 * res["replacements"]),
+            # per solve: reset, max |b|, initial residual, 2 per iteration, flush + residual per
+            # replacement, finalize, true residual
+            "gpu_launches": args.steps * (2 * iters + 5 + 2 * res["replacements"]),
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
