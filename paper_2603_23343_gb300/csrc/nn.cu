@@ -787,104 +787,112 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The resampling kernels below map threads to (x, 8-channel group) along a
+// row in blockIdx.x and threadIdx.x, and take y and z from blockIdx.y and
+// blockIdx.z: no 64-bit division per element (a grid-stride loop with
+// v % X, v / X per element made them issue-bound).
+struct RowIdx {
+    int x, ch, y, z;
+};
+template <int NC8>
+__device__ __forceinline__ bool row_idx(int X, RowIdx &r) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    r.x = e / NC8;
+    r.ch = e - r.x * NC8;
+    r.y = blockIdx.y;
+    r.z = blockIdx.z;
+    return r.x < X;
+}
+inline dim3 row_grid(int X, int nc8, int Y, int Z) {
+    return dim3((unsigned)((X * nc8 + 255) / 256), (unsigned)Y, (unsigned)Z);
+}
+
 // dst (coarse, C channels) = mean of the 2x2x2 children of src (channels
 // [soff, soff + C) of sstride).  One thread per (coarse voxel, 8 channels).
+template <int C>
 __global__ void __launch_bounds__(256)
-    pool2_kernel(int Xc, int Yc, int Zc, int C, const __nv_bfloat16 *__restrict__ src, int sstride, int soff,
+    pool2_kernel(int Xc, int Yc, int Zc, const __nv_bfloat16 *__restrict__ src, int sstride, int soff,
                  __nv_bfloat16 *__restrict__ dst) {
-    const int nc8 = C / 8;
-    const int64_t n = (int64_t)Xc * Yc * Zc * nc8;
+    RowIdx r;
+    if (!row_idx<C / 8>(Xc, r)) return;
     const int Xf = 2 * Xc, Yf = 2 * Yc;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % nc8);
-        const int64_t v = e / nc8;
-        const int x = (int)(v % Xc), y = (int)((v / Xc) % Yc), z = (int)(v / ((int64_t)Xc * Yc));
-        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t v = ((int64_t)r.z * Yc + r.y) * Xc + r.x;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int64_t f = (((int64_t)(2 * z + (c >> 2)) * Yf + 2 * y + ((c >> 1) & 1)) * Xf + 2 * x + (c & 1));
-            float q[8];
-            ld8(src + f * sstride + soff + ch * 8, q);
+    for (int c = 0; c < 8; ++c) {
+        const int64_t f = (((int64_t)(2 * r.z + (c >> 2)) * Yf + 2 * r.y + ((c >> 1) & 1)) * Xf + 2 * r.x + (c & 1));
+        float q[8];
+        ld8(src + f * sstride + soff + r.ch * 8, q);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s[i] += q[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) s[i] *= 0.125f;
-        st8(dst + v * C + ch * 8, s);
+        for (int i = 0; i < 8; ++i) s[i] += q[i];
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] *= 0.125f;
+    st8(dst + v * C + r.ch * 8, s);
 }
 
 // dst (fine, channels [doff, doff + C) of dstride) = src (coarse, C channels)
 // of the parent voxel.
+template <int C>
 __global__ void __launch_bounds__(256)
-    up2_kernel(int Xf, int Yf, int Zf, int C, const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
+    up2_kernel(int Xf, int Yf, int Zf, const __nv_bfloat16 *__restrict__ src, __nv_bfloat16 *__restrict__ dst,
                int dstride, int doff) {
-    const int nc8 = C / 8;
-    const int64_t n = (int64_t)Xf * Yf * Zf * nc8;
+    RowIdx r;
+    if (!row_idx<C / 8>(Xf, r)) return;
     const int Xc = Xf / 2, Yc = Yf / 2;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % nc8);
-        const int64_t v = e / nc8;
-        const int x = (int)(v % Xf), y = (int)((v / Xf) % Yf), z = (int)(v / ((int64_t)Xf * Yf));
-        const int64_t pv = ((int64_t)(z / 2) * Yc + y / 2) * Xc + x / 2;
-        *reinterpret_cast<uint4 *>(dst + v * dstride + doff + ch * 8) =
-            *reinterpret_cast<const uint4 *>(src + pv * C + ch * 8);
-    }
+    const int64_t v = ((int64_t)r.z * Yf + r.y) * Xf + r.x;
+    const int64_t pv = ((int64_t)(r.z / 2) * Yc + r.y / 2) * Xc + r.x / 2;
+    *reinterpret_cast<uint4 *>(dst + v * dstride + doff + r.ch * 8) =
+        *reinterpret_cast<const uint4 *>(src + pv * C + r.ch * 8);
 }
 
 // dst (coarse, C channels, BF16) = (sum of the 8 fine children of g, FP32
 // channels [goff, goff + C) of gstride) * (mask > 0): the adjoint of
 // nearest upsampling followed by the ReLU derivative.
+template <int C>
 __global__ void __launch_bounds__(256)
-    up2_adjoint_mask_kernel(int Xc, int Yc, int Zc, int C, const float *__restrict__ g, int gstride, int goff,
+    up2_adjoint_mask_kernel(int Xc, int Yc, int Zc, const float *__restrict__ g, int gstride, int goff,
                             const __nv_bfloat16 *__restrict__ mask, __nv_bfloat16 *__restrict__ dst) {
-    const int nc8 = C / 8;
-    const int64_t n = (int64_t)Xc * Yc * Zc * nc8;
+    RowIdx r;
+    if (!row_idx<C / 8>(Xc, r)) return;
     const int Xf = 2 * Xc, Yf = 2 * Yc;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % nc8);
-        const int64_t v = e / nc8;
-        const int x = (int)(v % Xc), y = (int)((v / Xc) % Yc), z = (int)(v / ((int64_t)Xc * Yc));
-        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t v = ((int64_t)r.z * Yc + r.y) * Xc + r.x;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int64_t f = (((int64_t)(2 * z + (c >> 2)) * Yf + 2 * y + ((c >> 1) & 1)) * Xf + 2 * x + (c & 1));
-            float q[8];
-            ld8(g + f * gstride + goff + ch * 8, q);
+    for (int c = 0; c < 8; ++c) {
+        const int64_t f = (((int64_t)(2 * r.z + (c >> 2)) * Yf + 2 * r.y + ((c >> 1) & 1)) * Xf + 2 * r.x + (c & 1));
+        float q[8];
+        ld8(g + f * gstride + goff + r.ch * 8, q);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) s[i] += q[i];
-        }
-        float m[8];
-        ld8(mask + v * C + ch * 8, m);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) s[i] = m[i] > 0.0f ? s[i] : 0.0f;
-        st8(dst + v * C + ch * 8, s);
+        for (int i = 0; i < 8; ++i) s[i] += q[i];
     }
+    float m[8];
+    ld8(mask + v * C + r.ch * 8, m);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s[i] = m[i] > 0.0f ? s[i] : 0.0f;
+    st8(dst + v * C + r.ch * 8, s);
 }
 
 // dst (fine, C channels, BF16) = (skip + t(parent) / 8) * (mask > 0): the
 // gradient reaching a skip connection, plus the adjoint of average pooling
 // of the coarse gradient t, times the ReLU derivative.
+template <int C>
 __global__ void __launch_bounds__(256)
-    pool_adjoint_skip_mask_kernel(int Xf, int Yf, int Zf, int C, const float *__restrict__ skip, int sstride, int soff,
+    pool_adjoint_skip_mask_kernel(int Xf, int Yf, int Zf, const float *__restrict__ skip, int sstride, int soff,
                                   const float *__restrict__ t, const __nv_bfloat16 *__restrict__ mask, int mstride,
                                   int moff, __nv_bfloat16 *__restrict__ dst) {
-    const int nc8 = C / 8;
-    const int64_t n = (int64_t)Xf * Yf * Zf * nc8;
+    RowIdx r;
+    if (!row_idx<C / 8>(Xf, r)) return;
     const int Xc = Xf / 2, Yc = Yf / 2;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)(e % nc8);
-        const int64_t v = e / nc8;
-        const int x = (int)(v % Xf), y = (int)((v / Xf) % Yf), z = (int)(v / ((int64_t)Xf * Yf));
-        const int64_t pv = ((int64_t)(z / 2) * Yc + y / 2) * Xc + x / 2;
-        float a[8], b[8], m[8];
-        ld8(skip + v * sstride + soff + ch * 8, a);
-        ld8(t + pv * C + ch * 8, b);
-        ld8(mask + v * mstride + moff + ch * 8, m);
+    const int64_t v = ((int64_t)r.z * Yf + r.y) * Xf + r.x;
+    const int64_t pv = ((int64_t)(r.z / 2) * Yc + r.y / 2) * Xc + r.x / 2;
+    float a[8], b[8], m[8];
+    ld8(skip + v * sstride + soff + r.ch * 8, a);
+    ld8(t + pv * C + r.ch * 8, b);
+    ld8(mask + v * mstride + moff + r.ch * 8, m);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = m[i] > 0.0f ? fmaf(b[i], 0.125f, a[i]) : 0.0f;
-        st8(dst + v * C + ch * 8, a);
-    }
+    for (int i = 0; i < 8; ++i) a[i] = m[i] > 0.0f ? fmaf(b[i], 0.125f, a[i]) : 0.0f;
+    st8(dst + v * C + r.ch * 8, a);
 }
 
 // g_out = dL/d(network output) = dL/dz * scale * dsc, rounded to BF16.
@@ -1113,18 +1121,18 @@ int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, 
          *a7 = P.at<bf16>(L.a7), *a8 = P.at<bf16>(L.a8);
     GB_TRY(conv_simt<bf16>(X0, Y0, Z0, 2, 16, P.at<bf16>(L.xin), W(0), a1, 1, nullptr, 0, 0, nullptr, s));
     GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 16, 16, a1, W(1), k8, 48, 32, 1, nullptr, 0, 0, err, s));
-    pool2_kernel<<<blocks_for(L.V[1] * 2, 256), 256, 0, s>>>(X1, Y1, Z1, 16, k8, 48, 32, p1);
+    pool2_kernel<16><<<row_grid(X1, 2, Y1, Z1), 256, 0, s>>>(X1, Y1, Z1, k8, 48, 32, p1);
     GB_CUDA(cudaGetLastError());
     GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 16, 32, p1, W(2), a3, 32, 0, 1, nullptr, 0, 0, err, s));
     GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 32, 32, a3, W(3), k7, 96, 64, 1, nullptr, 0, 0, err, s));
-    pool2_kernel<<<blocks_for(L.V[2] * 4, 256), 256, 0, s>>>(X2, Y2, Z2, 32, k7, 96, 64, p2);
+    pool2_kernel<32><<<row_grid(X2, 4, Y2, Z2), 256, 0, s>>>(X2, Y2, Z2, k7, 96, 64, p2);
     GB_CUDA(cudaGetLastError());
     GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 32, 64, p2, W(4), a5, 64, 0, 1, nullptr, 0, 0, err, s));
     GB_TRY(conv_tc<bf16>(X2, Y2, Z2, 64, 64, a5, W(5), a6, 64, 0, 1, nullptr, 0, 0, err, s));
-    up2_kernel<<<blocks_for(L.V[1] * 8, 256), 256, 0, s>>>(X1, Y1, Z1, 64, a6, k7, 96, 0);
+    up2_kernel<64><<<row_grid(X1, 8, Y1, Z1), 256, 0, s>>>(X1, Y1, Z1, a6, k7, 96, 0);
     GB_CUDA(cudaGetLastError());
     GB_TRY(conv_tc<bf16>(X1, Y1, Z1, 96, 32, k7, W(6), a7, 32, 0, 1, nullptr, 0, 0, err, s));
-    up2_kernel<<<blocks_for(L.V[0] * 4, 256), 256, 0, s>>>(X0, Y0, Z0, 32, a7, k8, 48, 0);
+    up2_kernel<32><<<row_grid(X0, 4, Y0, Z0), 256, 0, s>>>(X0, Y0, Z0, a7, k8, 48, 0);
     GB_CUDA(cudaGetLastError());
     GB_TRY(conv_tc<bf16>(X0, Y0, Z0, 48, 16, k8, W(7), a8, 16, 0, 1, nullptr, 0, 0, err, s));
     GB_TRY(conv_simt<float>(X0, Y0, Z0, 16, 1, a8, W(8), z, 0, nullptr, 0, 0, sc + S_SCALE, s, dsc));
@@ -1159,12 +1167,12 @@ int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cuda
     // c8 (48 -> 16) on k8 = [up(a7), e0]
     GB_TRY(wgrad(X0, Y0, Z0, 48, 16, k8, ga8, G(7), part, s, err));
     GB_TRY(conv_tc<float>(X0, Y0, Z0, 16, 48, ga8, WT(7), gk8, 48, 0, 0, nullptr, 0, 0, err, s));
-    up2_adjoint_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk8, 48, 0, a7, ga7);
+    up2_adjoint_mask_kernel<32><<<row_grid(X1, 4, Y1, Z1), 256, 0, s>>>(X1, Y1, Z1, gk8, 48, 0, a7, ga7);
     GB_CUDA(cudaGetLastError());
     // c7 (96 -> 32) on k7 = [up(a6), e1]
     GB_TRY(wgrad(X1, Y1, Z1, 96, 32, k7, ga7, G(6), part, s, err));
     GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 96, ga7, WT(6), gk7, 96, 0, 0, nullptr, 0, 0, err, s));
-    up2_adjoint_mask_kernel<<<blocks_for(L.V[2] * 8, 256), 256, 0, s>>>(X2, Y2, Z2, 64, gk7, 96, 0, a6, ga6);
+    up2_adjoint_mask_kernel<64><<<row_grid(X2, 8, Y2, Z2), 256, 0, s>>>(X2, Y2, Z2, gk7, 96, 0, a6, ga6);
     GB_CUDA(cudaGetLastError());
     // c6 (64 -> 64), c5 (32 -> 64)
     GB_TRY(wgrad(X2, Y2, Z2, 64, 64, a5, ga6, G(5), part, s, err));
@@ -1172,7 +1180,7 @@ int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cuda
     GB_TRY(wgrad(X2, Y2, Z2, 32, 64, p2, ga5, G(4), part, s, err));
     GB_TRY(conv_tc<float>(X2, Y2, Z2, 64, 32, ga5, WT(4), t5, 32, 0, 0, nullptr, 0, 0, err, s));
     // e1: skip gradient (gk7 channels 64..95) + pooled-path gradient, ReLU mask
-    pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[1] * 4, 256), 256, 0, s>>>(X1, Y1, Z1, 32, gk7, 96, 64, t5, k7, 96,
+    pool_adjoint_skip_mask_kernel<32><<<row_grid(X1, 4, Y1, Z1), 256, 0, s>>>(X1, Y1, Z1, gk7, 96, 64, t5, k7, 96,
                                                                               64, ge1b);
     GB_CUDA(cudaGetLastError());
     // c4 (32 -> 32), c3 (16 -> 32)
@@ -1181,7 +1189,7 @@ int nn_backward_ws(const float *gz, float *gw, void *ws, const NnLayout &L, cuda
     GB_TRY(wgrad(X1, Y1, Z1, 16, 32, p1, ga3, G(2), part, s, err));
     GB_TRY(conv_tc<float>(X1, Y1, Z1, 32, 16, ga3, WT(2), t3, 16, 0, 0, nullptr, 0, 0, err, s));
     // e0: skip gradient (gk8 channels 32..47) + pooled-path gradient, ReLU mask
-    pool_adjoint_skip_mask_kernel<<<blocks_for(L.V[0] * 2, 256), 256, 0, s>>>(X0, Y0, Z0, 16, gk8, 48, 32, t3, k8, 48,
+    pool_adjoint_skip_mask_kernel<16><<<row_grid(X0, 2, Y0, Z0), 256, 0, s>>>(X0, Y0, Z0, gk8, 48, 32, t3, k8, 48,
                                                                               32, ge0b);
     GB_CUDA(cudaGetLastError());
     // c2 (16 -> 16), c1 (2 -> 16)
