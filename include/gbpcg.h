@@ -160,8 +160,10 @@ int gbpcg_dot(int64_t n, int32_t dtype, const void *x, const void *y, double *re
  *
  * Its scratch is a static 128 KiB device array inside the library, present on
  * every GPU that loads it until the process exits.  The first call on a
- * device looks up that array's device address, so make that first call
- * outside any stream capture.  n is limited to 2^30 elements; larger n
+ * device looks up that array's device address and keeps it for the life of
+ * the process, so make that first call outside any stream capture; the kept
+ * address does not survive cudaDeviceReset on that device (do not call this
+ * function on a device after resetting it).  n is limited to 2^30 elements; larger n
  * returns GBPCG_ERR_ARG.  All calls share the one array: calls that may
  * overlap on the GPU (different streams, or different host threads without
  * ordering) race and must be serialised by the caller.  x, y: DEVICE arrays
@@ -258,10 +260,15 @@ int gbpcg_autotune_record(const gbpcg_grid *grid, const gbpcg_opts *opts, int32_
  *   nearest upsample, concat [up, e1] -> c7 (96->32)   half
  *   nearest upsample, concat [up, e0] -> c8 (48->16)   full
  *   c9 (16->1)
- * ReLU after every convolution but c9.  Input channels: r / rms(r) and
- * log k of the voxel's coefficient block (0 for the Poisson operator); the
- * output is multiplied by rms(r) h^2, h = 1/(max(nx, ny, nz) + 1), so N is
- * positively homogeneous: N(a r) = a N(r) for a > 0.
+ * ReLU after every convolution but c9.  The network works on the
+ * Jacobi-scaled system D^{-1/2} A D^{-1/2}, D the operator's diagonal (the
+ * sum of the six face weights k_f / h_d^2 at each point): with
+ * s = D^{-1/2} r and rms(s) = ||s|| / sqrt(nx ny nz), the input channels are
+ * s / rms(s) and log k of the voxel's coefficient block (0 for the Poisson
+ * operator), and the last layer's output u becomes
+ * z = rms(s) D^{-1/2} u.  N is therefore positively homogeneous:
+ * N(a r) = a N(r) for a > 0.  Weights that pass s / rms(s) through
+ * unchanged give z = D^{-1} r, the Jacobi preconditioner.
  *
  * Layouts: activations channels-last, (nz, ny, nx, C), BF16; a layer's
  * weights (Co, 27, Ci) with tap t = (dz+1)*9 + (dy+1)*3 + (dx+1) reading
@@ -319,6 +326,53 @@ int gbpcg_conv3_backward_weight(int32_t nx, int32_t ny, int32_t nz, int32_t ci, 
  * forward + backward (training != 0).  A training workspace serves every
  * gbpcg_nn_* call. */
 int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32_t training, size_t *bytes);
+
+/* Tensors that gbpcg_nn_forward and gbpcg_nn_backward leave in a workspace,
+ * for inspection (gbpcg_nn_tensor_info).  Level 0 is the grid, level 1 and
+ * 2 halve every size once and twice; a tensor of C channels is stored
+ * channels-last, (nz, ny, nx, C) of its level. */
+enum gbpcg_nn_tensor {
+    GBPCG_NN_T_XIN = 0,  /* BF16, 2: network input (s / rms(s), log k) */
+    GBPCG_NN_T_A1,       /* BF16, 16: relu(c1) */
+    GBPCG_NN_T_K8,       /* BF16, 48: c8 input, up(a7) in 0..31, e0 = relu(c2) in 32..47 */
+    GBPCG_NN_T_P1,       /* BF16, 16: pool(e0), level 1 */
+    GBPCG_NN_T_A3,       /* BF16, 32: relu(c3), level 1 */
+    GBPCG_NN_T_K7,       /* BF16, 96: c7 input, up(a6) in 0..63, e1 = relu(c4) in 64..95, level 1 */
+    GBPCG_NN_T_P2,       /* BF16, 32: pool(e1), level 2 */
+    GBPCG_NN_T_A5,       /* BF16, 64: relu(c5), level 2 */
+    GBPCG_NN_T_A6,       /* BF16, 64: relu(c6), level 2 */
+    GBPCG_NN_T_A7,       /* BF16, 32: relu(c7), level 1 */
+    GBPCG_NN_T_A8,       /* BF16, 16: relu(c8) */
+    GBPCG_NN_T_DSC,      /* F32, 1: D^{-1/2} */
+    GBPCG_NN_T_SR,       /* F32, 1: s = D^{-1/2} r */
+    GBPCG_NN_T_SCALE,    /* F64 scalar (level -1): rms(s) */
+    /* training workspaces only (gbpcg_nn_backward) */
+    GBPCG_NN_T_GOUT,     /* BF16, 1: dL/du of the last layer's output u (gz rms(s) D^{-1/2}) */
+    GBPCG_NN_T_GA8,      /* BF16, 16: dL/d(c8 output), ReLU mask applied */
+    GBPCG_NN_T_GK8,      /* F32, 48: dL/d(c8 input) */
+    GBPCG_NN_T_GA7,      /* BF16, 32: dL/d(c7 output), masked, level 1 */
+    GBPCG_NN_T_GK7,      /* F32, 96: dL/d(c7 input), level 1 */
+    GBPCG_NN_T_GA6,      /* BF16, 64: dL/d(c6 output), masked, level 2 */
+    GBPCG_NN_T_GA5,      /* BF16, 64: dL/d(c5 output), masked, level 2 */
+    GBPCG_NN_T_T5,       /* F32, 32: dL/d(c5 input), level 2 */
+    GBPCG_NN_T_GE1B,     /* BF16, 32: dL/d(c4 output) (skip + pooled path), masked, level 1 */
+    GBPCG_NN_T_GA3,      /* BF16, 32: dL/d(c3 output), masked, level 1 */
+    GBPCG_NN_T_T3,       /* F32, 16: dL/d(c3 input), level 1 */
+    GBPCG_NN_T_GE0B,     /* BF16, 16: dL/d(c2 output) (skip + pooled path), masked */
+    GBPCG_NN_T_GA1,      /* BF16, 16: dL/d(c1 output), masked */
+    GBPCG_NN_T_COUNT
+};
+
+/*
+ * Where tensor `index` (gbpcg_nn_tensor) lives in a network workspace of
+ * this grid (training != 0: a training workspace): byte offset from the
+ * workspace base, element type (gbpcg_dtype), channels per voxel and grid
+ * level.  Host-only; launches nothing.  Tensors marked "training" need
+ * training != 0 (else GBPCG_ERR_ARG).  A tensor holds what the last
+ * gbpcg_nn_forward / gbpcg_nn_backward on that workspace left there.
+ */
+int gbpcg_nn_tensor_info(int32_t nx, int32_t ny, int32_t nz, int32_t training, int32_t index, size_t *offset,
+                         int32_t *dtype, int32_t *channels, int32_t *level);
 
 /*
  * z = N(r).  w: DEVICE FP32 master weights (GBPCG_NN_NUM_WEIGHTS); r, z:

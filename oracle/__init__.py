@@ -72,6 +72,8 @@ def _load():
             lib.orc_pcg.argtypes = [I, I, I, P, I, I, I, P, P, D, I, I, P, P, P]
             lib.orc_true_relres.restype = D
             lib.orc_true_relres.argtypes = [I, I, I, P, I, I, I, P, P]
+            lib.orc_threads.restype = I
+            lib.orc_threads.argtypes = []
             lib.orc_refine.restype = I
             lib.orc_refine.argtypes = [I, I, I, P, I, I, I, P, P, D, I, D, I, P, P]
             _lib = lib
@@ -150,6 +152,11 @@ def true_relres(b, x, k=None, kb=8) -> float:
     nz, ny, nx = b.shape
     kp, kbx, kby, kbz, _keep = _kargs(k, kb)
     return float(_load().orc_true_relres(nx, ny, nz, kp, kbx, kby, kbz, _ptr(b), _ptr(x)))
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops run on."""
+    return int(_load().orc_threads())
 
 
 def pcg(b, x0=None, tol=1e-6, maxit=2000, k=None, kb=8, precond="jacobi", history=False):

@@ -47,6 +47,14 @@
 #define IDX(i, j, k) ((((int64_t)(k)) * ny + (j)) * nx + (i))
 #define SUM_CHUNK 4096
 
+/* Threads the parallel loops use (1 without OpenMP); reported beside timings. */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_threads(void) { return omp_get_max_threads(); }
+#else
+int orc_threads(void) { return 1; }
+#endif
+
 static double inv_h2(int n) {
     double h = 1.0 / (double)(n + 1);
     return 1.0 / (h * h);

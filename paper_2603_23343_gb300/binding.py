@@ -35,7 +35,7 @@ EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbp
            "gbpcg_conv3_workspace_size", "gbpcg_conv3_forward", "gbpcg_conv3_backward_data",
            "gbpcg_conv3_backward_weight", "gbpcg_nn_workspace_size", "gbpcg_nn_forward", "gbpcg_nn_backward",
            "gbpcg_nn_loss", "gbpcg_nn_adam", "gbpcg_nn_train_step", "gbpcg_nn_status", "gbpcg_fcg_workspace_size",
-           "gbpcg_fcg_solve", "gbpcg_wait_selftest"]
+           "gbpcg_fcg_solve", "gbpcg_wait_selftest", "gbpcg_nn_tensor_info"]
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
 
 NN_NUM_WEIGHTS = 319248
@@ -131,6 +131,9 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_nn_workspace_size.restype = ctypes.c_int
         lib.gbpcg_nn_workspace_size.argtypes = [I32, I32, I32, I32, ctypes.POINTER(SZ)]
         lib.gbpcg_nn_forward.restype = ctypes.c_int
+        lib.gbpcg_nn_tensor_info.argtypes = [I32, I32, I32, I32, I32, ctypes.POINTER(SZ), ctypes.POINTER(I32),
+                                             ctypes.POINTER(I32), ctypes.POINTER(I32)]
+        lib.gbpcg_nn_tensor_info.restype = ctypes.c_int
         lib.gbpcg_nn_forward.argtypes = [ctypes.POINTER(Grid), P, P, P, P, SZ, P]
         lib.gbpcg_nn_backward.restype = ctypes.c_int
         lib.gbpcg_nn_backward.argtypes = [ctypes.POINTER(Grid), P, P, P, SZ, P]
@@ -456,6 +459,26 @@ def nn_workspace(shape, training=False, device="cuda") -> torch.Tensor:
     n = ctypes.c_size_t(0)
     _check(load().gbpcg_nn_workspace_size(nx, ny, nz, int(bool(training)), ctypes.byref(n)))
     return torch.empty(int(n.value), dtype=torch.uint8, device=device)
+
+
+NN_TENSORS = ["xin", "a1", "k8", "p1", "a3", "k7", "p2", "a5", "a6", "a7", "a8", "dsc", "sr", "scale",
+              "gout", "ga8", "gk8", "ga7", "gk7", "ga6", "ga5", "t5", "ge1b", "ga3", "t3", "ge0b", "ga1"]
+
+
+def nn_tensor(workspace: torch.Tensor, shape, name: str, training=False) -> torch.Tensor:
+    """A view of tensor `name` (NN_TENSORS) inside a network workspace (gbpcg_nn_tensor_info):
+    (nz, ny, nx, C) of its level, channels-last; 'scale' is a 0-d float64."""
+    nz, ny, nx = (int(v) for v in shape)
+    off, dt, ch, lv = ctypes.c_size_t(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().gbpcg_nn_tensor_info(nx, ny, nz, int(bool(training)), NN_TENSORS.index(name), ctypes.byref(off),
+                                       ctypes.byref(dt), ctypes.byref(ch), ctypes.byref(lv)))
+    tdt = {F32: torch.float32, BF16: torch.bfloat16, F64: torch.float64}[dt.value]
+    esize = torch.tensor([], dtype=tdt).element_size()
+    if lv.value < 0:
+        return workspace[off.value:off.value + esize].view(tdt)[0]
+    dims = (nz >> lv.value, ny >> lv.value, nx >> lv.value, ch.value)
+    nbytes = dims[0] * dims[1] * dims[2] * dims[3] * esize
+    return workspace[off.value:off.value + nbytes].view(tdt).reshape(dims)
 
 
 def nn_pack_weights(ws: dict) -> torch.Tensor:

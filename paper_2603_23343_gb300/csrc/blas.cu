@@ -161,11 +161,11 @@ static int axpy_typed(int64_t n, double alpha, const void *x, void *y, cudaStrea
 // Scratch for gbpcg_dot_noalloc lives in this file-scope device array: a
 // ticket word (first 256 bytes) and one FP64 partial sum per block.  The
 // array exists once per GPU that loads the library and stays until the
-// process exits.  The launch uses one block per kNoAllocPerBlock elements,
-// so kNoAllocMaxBlocks partials bound n.
+// process exits.  The grid is sized like gbpcg_dot's (at most 8 blocks per
+// SM, each thread striding over the vector), and never beyond the
+// kNoAllocMaxBlocks partial slots the array holds.
 constexpr unsigned kNoAllocMaxBlocks = 16384;
-constexpr int64_t kNoAllocPerBlock = 65536;
-constexpr int64_t kNoAllocMaxN = (int64_t)kNoAllocMaxBlocks * kNoAllocPerBlock;  // 2^30
+constexpr int64_t kNoAllocMaxN = (int64_t)1 << 30;
 constexpr size_t kNoAllocScratchBytes = 256 + sizeof(double) * kNoAllocMaxBlocks;
 
 static __device__ __align__(256) unsigned char g_dot_scratch[kNoAllocScratchBytes];
@@ -190,11 +190,20 @@ static int noalloc_scratch(void **out) {
     return GBPCG_OK;
 }
 
+// Blocks of one allocation-free dot: per_block elements per block, at most
+// 8 per SM (the kernels stride over the rest) and never more than the
+// array's partial slots.
+static unsigned noalloc_blocks(int64_t n, int64_t per_block) {
+    const int64_t want = (n + per_block - 1) / per_block;
+    return (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>({want, (int64_t)device_sm_count() * 8, (int64_t)kNoAllocMaxBlocks}));
+}
+
 template <typename T>
 static int dot_noalloc_typed(int64_t n, const void *x, const void *y, double *out, void *scratch, cudaStream_t s) {
     unsigned *ticket = static_cast<unsigned *>(scratch);
     double *partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+    const unsigned blocks = noalloc_blocks(n, (int64_t)kDotThreads * 16);
     // the array keeps the previous call's contents: the ticket must restart at zero
     GB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
     const int vec = sizeof(T) == 4 ? (aligned16(x) && aligned16(y)) : (((uintptr_t)x | (uintptr_t)y) & 7u) == 0;
@@ -291,7 +300,7 @@ int gbpcg_dot_noalloc(int64_t n, int32_t dtype, const void *x, const void *y, do
         default: {
             unsigned *ticket = static_cast<unsigned *>(scratch);
             double *partials = reinterpret_cast<double *>(static_cast<char *>(scratch) + 256);
-            const unsigned blocks = (unsigned)std::max<int64_t>(1, (n + kNoAllocPerBlock - 1) / kNoAllocPerBlock);
+            const unsigned blocks = noalloc_blocks(n, (int64_t)kDotThreads * 8);
             GB_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
             dot_f64_kernel<<<blocks, kDotThreads, 0, s>>>(n, static_cast<const double *>(x),
                                                          static_cast<const double *>(y), partials, ticket, result);

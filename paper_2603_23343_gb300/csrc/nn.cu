@@ -1340,6 +1340,38 @@ extern "C" int gbpcg_nn_workspace_size(int32_t nx, int32_t ny, int32_t nz, int32
     return GBPCG_OK;
 }
 
+extern "C" int gbpcg_nn_tensor_info(int32_t nx, int32_t ny, int32_t nz, int32_t training, int32_t index,
+                                    size_t *offset, int32_t *dtype, int32_t *channels, int32_t *level) {
+    clear_error();
+    if (!offset || !dtype || !channels || !level) return fail_arg("NULL output pointer");
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail_arg("grid sizes must be positive");
+    if (!nn_shape_ok(nx, ny, nz))
+        return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels");
+    const NnLayout L = nn_layout(nx, ny, nz, training != 0);
+    struct Info { size_t off; int dt, ch, lv; bool train; };
+    const Info tab[] = {
+        {L.xin, GBPCG_BF16, 2, 0, false},   {L.a1, GBPCG_BF16, 16, 0, false},   {L.k8, GBPCG_BF16, 48, 0, false},
+        {L.p1, GBPCG_BF16, 16, 1, false},   {L.a3, GBPCG_BF16, 32, 1, false},   {L.k7, GBPCG_BF16, 96, 1, false},
+        {L.p2, GBPCG_BF16, 32, 2, false},   {L.a5, GBPCG_BF16, 64, 2, false},   {L.a6, GBPCG_BF16, 64, 2, false},
+        {L.a7, GBPCG_BF16, 32, 1, false},   {L.a8, GBPCG_BF16, 16, 0, false},   {L.dsc, GBPCG_F32, 1, 0, false},
+        {L.sr, GBPCG_F32, 1, 0, false},     {L.scal + S_SCALE * sizeof(double), GBPCG_F64, 1, -1, false},
+        {L.gout, GBPCG_BF16, 1, 0, true},   {L.ga8, GBPCG_BF16, 16, 0, true},   {L.gk8, GBPCG_F32, 48, 0, true},
+        {L.ga7, GBPCG_BF16, 32, 1, true},   {L.gk7, GBPCG_F32, 96, 1, true},    {L.ga6, GBPCG_BF16, 64, 2, true},
+        {L.ga5, GBPCG_BF16, 64, 2, true},   {L.t5, GBPCG_F32, 32, 2, true},     {L.ge1b, GBPCG_BF16, 32, 1, true},
+        {L.ga3, GBPCG_BF16, 32, 1, true},   {L.t3, GBPCG_F32, 16, 1, true},     {L.ge0b, GBPCG_BF16, 16, 0, true},
+        {L.ga1, GBPCG_BF16, 16, 0, true},
+    };
+    constexpr int kCount = (int)(sizeof(tab) / sizeof(tab[0]));
+    static_assert(kCount == GBPCG_NN_T_COUNT, "tensor table and enum disagree");
+    if (index < 0 || index >= kCount) return fail_arg("tensor index out of range");
+    if (tab[index].train && !training) return fail_arg("that tensor exists only in a training workspace");
+    *offset = tab[index].off;
+    *dtype = tab[index].dt;
+    *channels = tab[index].ch;
+    *level = tab[index].lv;
+    return GBPCG_OK;
+}
+
 extern "C" int gbpcg_nn_forward(const gbpcg_grid *grid, const float *w, const float *r, float *z, void *workspace,
                                 size_t workspace_bytes, gbpcg_stream stream) {
     NvtxRange range("gbpcg_nn_forward");

@@ -227,6 +227,39 @@ def test_learned_preconditioner_argument_checks(lib):
     assert lib.gbpcg_nn_forward(ctypes.byref(g), None, None, None, P(256), inference, None) == B.ERR_ARG
 
 
+def test_nn_tensor_info_is_host_logic(lib):
+    """Every tensor the network leaves in a workspace lies inside it, inference workspaces refuse
+    the training-only gradient tensors, and distinct tensors do not overlap."""
+    n = ctypes.c_size_t(0)
+    shape = (16, 16, 128)
+    spans = []
+    for training in (0, 1):
+        assert lib.gbpcg_nn_workspace_size(128, 16, 16, training, ctypes.byref(n)) == B.OK
+        total = n.value
+        for i, name in enumerate(B.NN_TENSORS):
+            off, dt, ch, lv = ctypes.c_size_t(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+            rc = lib.gbpcg_nn_tensor_info(128, 16, 16, training, i, ctypes.byref(off), ctypes.byref(dt),
+                                          ctypes.byref(ch), ctypes.byref(lv))
+            if i >= B.NN_TENSORS.index("gout") and not training:
+                assert rc == B.ERR_ARG, name
+                continue
+            assert rc == B.OK, name
+            esize = {B.F32: 4, B.BF16: 2, B.F64: 8}[dt.value]
+            vox = 1 if lv.value < 0 else (shape[0] >> lv.value) * (shape[1] >> lv.value) * (shape[2] >> lv.value)
+            assert off.value % 256 == 0 or lv.value < 0, name
+            assert off.value + vox * ch.value * esize <= total, name
+            if training:
+                spans.append((off.value, off.value + vox * ch.value * esize, name))
+    spans.sort()
+    for (a0, a1, na), (b0, b1, nb) in zip(spans, spans[1:]):
+        assert a1 <= b0, (na, nb)
+    off, dt, ch, lv = ctypes.c_size_t(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    assert lib.gbpcg_nn_tensor_info(128, 16, 16, 1, len(B.NN_TENSORS), ctypes.byref(off), ctypes.byref(dt),
+                                    ctypes.byref(ch), ctypes.byref(lv)) == B.ERR_ARG
+    assert lib.gbpcg_nn_tensor_info(30, 30, 30, 1, 0, ctypes.byref(off), ctypes.byref(dt), ctypes.byref(ch),
+                                    ctypes.byref(lv)) == B.ERR_ARG
+
+
 def test_fcg_argument_checks(lib):
     g = _grid(32, 32, 32)
     n = ctypes.c_size_t(0)

@@ -115,6 +115,23 @@ def test_dot_f32(gpu_lib, n):
     assert abs(d - ref) <= 1e-5 * float(np.sum(np.abs(x.astype(np.float64) * y))) + 1e-300
 
 
+def test_dot_and_axpy_at_bench_size_capped_grid(gpu_lib):
+    """2^26 + 3 elements: both kernels run their capped grid (8 blocks per SM) with every thread
+    striding over many vectors, the regime the 2^28 microbenchmark times, plus a ragged tail."""
+    n = (1 << 26) + 3
+    x = inputs.uniform_pm1(40, 0, n)
+    y = inputs.uniform_pm1(41, 0, n)
+    xd, yd = to_dev(x), to_dev(y)
+    d = float(gpu_lib.dot(xd, yd).item())
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    ref = oracle.dot(x64, y64)
+    assert abs(d - ref) <= 1e-5 * float(np.sum(np.abs(x64 * y64)))
+    alpha = 0.375
+    gpu_lib.axpy(alpha, xd, yd)
+    refa = oracle.axpy(alpha, x64, y64).astype(np.float32)
+    assert np.array_equal(yd.cpu().numpy(), refa)
+
+
 def test_dot_integer_exact_and_deterministic(gpu_lib):
     n = 3_000_001
     i = np.arange(n)

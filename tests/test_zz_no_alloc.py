@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2603_23343_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -27,13 +28,18 @@ def _pair(seed, n, dtype=torch.float32):
 
 
 def test_dot_noalloc_matches_dot_on_two_calls_in_a_row(gpu_lib):
-    cases = [(50, 3_000_001), (52, 1 << 22)]
+    # 2^24 + 5 runs the capped grid (8 blocks per SM, threads striding), 2^22 one pass per thread
+    cases = [(50, 3_000_001), (52, 1 << 22), (60, (1 << 24) + 5)]
     for seed, n in cases:
         x, y, scale = _pair(seed, n)
         ref = float(gpu_lib.dot(x, y).item())
         got = float(gpu_lib.dot_noalloc(x, y).item())
         # the tolerance the kernel tests use for FP32 dots: 1e-5 of sum |x_i y_i|
         assert abs(got - ref) <= 1e-5 * scale, (n, got, ref)
+        # and against the FP64 oracle on the same FP32 numbers
+        xo = x.cpu().double().numpy()
+        yo = y.cpu().double().numpy()
+        assert abs(got - oracle.dot(xo, yo)) <= 1e-5 * scale, (n, got)
     # the same input twice in a row: bit-identical results (the ticket restarts
     # at zero and the sum order is fixed); gbpcg_dot uses another grid size, so
     # it agrees within the tolerance rather than bit for bit
