@@ -159,6 +159,87 @@ def learned_leg(B, learned, stream, full: bool):
     }
 
 
+def ablation_leg(B, inputs, stream, b64, n):
+    """The paper's own experiments, repeated on GB300:
+    Sec. VII  device-resident loop (one CUDA graph) vs the fused kernels with the stop flag read
+              back to the host every iteration vs split kernels with host-side scalars (the
+              paper's FP32 variant, and its H100 comparator's structure), at n^3;
+    Sec. V    the dot product's reduction granularity and finish (gbpcg_dot_variant) from 2^16
+              to 2^28 elements;
+    Sec. VI-C TMA out-of-bounds zero fill vs bounds-checked plain loads vs TMA plus an
+              explicit zero fill, for the stencil apply from 32^3 to 256^3."""
+    import torch
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    # Sec. VII: how the loop is driven
+    b32 = b64.float()
+    sec7 = {}
+    for name, bb, mode in (("device_graph", b64, "graph"), ("host_readback_fused", b64, "host_loop"),
+                           ("split_kernels_host_scalars", b32, "split")):
+        xx = torch.zeros_like(bb)
+        ws = B.alloc_workspace(bb.shape, io_dtype=B.F64 if bb.dtype == torch.float64 else B.F32, mode=mode)
+        best = None
+        for _ in range(2):
+            xx.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r = B.pcg_solve(bb, xx, tol=TOL, maxit=MAXIT, workspace=ws, mode=mode, stream=stream)
+            wall = (time.perf_counter() - t0) * 1e3
+            best = wall if best is None else min(best, wall)
+        sec7[name] = {"ms": r["time_ms"], "wall_ms": best, "iters": r["iters"], "status": r["status_name"],
+                      "us_per_iter": 1e3 * r["time_ms"] / max(1, r["iters"]),
+                      "rel_res_recursive": r["rel_res_recursive"]}
+        del ws, xx
+    sec7["algorithmic_bytes_per_pt_iter"] = {"device_graph": ITER_BYTES, "host_readback_fused": ITER_BYTES,
+                                             "split_kernels_host_scalars": 76}
+    out[f"sec7_loop_driver_{n}"] = sec7
+    # Sec. V: reduction granularity and finish
+    names = ["cta_scalar_last_cta", "warp_partials_last_cta", "cta_scalar_second_kernel", "cta_scalar_fp64_atomics",
+             "cta_scalar_two_level_tree"]
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    xa = torch.empty(1 << 28, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=gen)
+    ya = torch.empty(1 << 28, dtype=torch.float32, device="cuda").uniform_(-1.0, 1.0, generator=gen)
+    res_d = torch.empty((), dtype=torch.float64, device="cuda")
+    wsv = torch.empty(B.load().gbpcg_dot_variant_workspace_size(), dtype=torch.uint8, device="cuda")
+    sec5 = {}
+    for lg in (16, 20, 24, 28):
+        m = 1 << lg
+        reps = 200 if lg <= 20 else 20 if lg <= 24 else 5
+        row = {}
+        for v, nm in enumerate(names):
+            us = 1e3 * timed(lambda: B.dot_variant(v, xa[:m], ya[:m], res_d, wsv, stream=stream), reps)
+            row[nm] = {"us": us, "gbs": 8 * m / (us * 1e-6) / 1e9}
+        sec5[f"2^{lg}"] = row
+    out["sec5_dot_reduction_variants"] = sec5
+    del xa, ya, wsv
+    # Sec. VI-C: boundary handling of the stencil apply
+    sec6 = {}
+    for m in (32, 64, 128, 256):
+        p = torch.from_numpy(inputs.uniform_rhs((m, m, m), 3)).cuda()
+        q = torch.empty_like(p)
+        reps = 200 if m <= 64 else 50 if m == 128 else 20
+        row = {}
+        for v, nm in enumerate(("tma_oob_zero_fill", "plain_loads_bounds_checked", "tma_plus_explicit_zero_fill")):
+            us = 1e3 * timed(lambda: B.stencil_apply_variant(v, p, q, stream=stream), reps)
+            row[nm] = {"us": us, "gbs": 8 * m ** 3 / (us * 1e-6) / 1e9}
+        sec6[f"{m}^3"] = row
+        del p, q
+    out["sec6c_stencil_boundary_variants"] = sec6
+    torch.cuda.empty_cache()
+    return out
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) while the timed region runs."""
 
@@ -547,6 +628,8 @@ def main():
     del xa, ya, dws
     torch.cuda.empty_cache()
 
+    ablations = ablation_leg(B, inputs, stream, b, n) if rank == 0 else None
+
     learned_res = None
     if not args.no_learned and n == 256:
         from paper_2603_23343_gb300 import learned
@@ -583,6 +666,7 @@ def main():
             "mixed_precision": mixed,
             "batched_config3": batched,
             "microkernels_2e28": micro,
+            "ablations": ablations,
             "learned_config4": learned_res,
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,

@@ -84,6 +84,17 @@ typedef struct gbpcg_grid {
 #define GBPCG_FLAG_AUTOTUNE 4u /* batched solves: pick each shape's tile configuration by timing
                                   (cached per shape in the process); the workspace grows by a
                                   scratch x per problem */
+#define GBPCG_FLAG_HOST_LOOP 8u /* the paper's FP32 variant reads the residual norm back to the
+                                   host every iteration (Sec. VII): the fused kernels launched one
+                                   iteration at a time, the host reading the device's stop flag
+                                   after each (FP32 storage; results equal the graph's bit for
+                                   bit) */
+#define GBPCG_FLAG_SPLIT 16u /* the paper's FP32 split-kernel solver (Sec. VII) and its H100
+                                comparator's structure: one kernel per operation (stencil, dot,
+                                axpy, element-wise Jacobi scaling, p update), alpha and beta formed
+                                on the host from dot products read back every iteration.  FP32
+                                device b and x, constant coefficient, no residual replacement;
+                                rel_res_true is not evaluated (0) */
 
 typedef struct gbpcg_opts {
     double tol;            /* stop when ||r_k||_2 / ||b||_2 <= tol (recursive residual) */
@@ -171,6 +182,43 @@ int gbpcg_dot(int64_t n, int32_t dtype, const void *x, const void *y, double *re
  */
 int gbpcg_dot_noalloc(int64_t n, int32_t dtype, const void *x, const void *y, double *result,
                       gbpcg_stream stream);
+
+/*
+ * Reduction variants of the dot product (Sec. V compares reducing each tile
+ * to a scalar before sending, Method 1, with sending whole tiles and reducing
+ * at the root, Method 2, and two routes of the partial sums through the
+ * network).  *result = sum_i x_i y_i with FP32 per-thread sums of four
+ * products added into FP64, then:
+ *   0  one partial per CTA, the last CTA to arrive adds them in block order
+ *      (gbpcg_dot's scheme; Method 1)
+ *   1  one partial per warp (8 per CTA), the last CTA adds them (Method 2)
+ *   2  one partial per CTA, added by a second kernel launch
+ *   3  one partial per CTA, FP64 atomicAdd into one accumulator (order not
+ *      fixed: the result may differ in the last bits from run to run)
+ *   4  one partial per CTA; the last CTA of each group of 32 adds its group,
+ *      the last group to finish adds the group totals (a two-level tree)
+ * x, y: DEVICE FP32, 16-byte aligned, n >= 1; result: DEVICE double;
+ * workspace: DEVICE, gbpcg_dot_variant_workspace_size() bytes, 256-byte
+ * aligned.  Variants 0, 1, 2 and 4 are bitwise reproducible.
+ */
+size_t gbpcg_dot_variant_workspace_size(void);
+int gbpcg_dot_variant(int32_t variant, int64_t n, const float *x, const float *y, double *result,
+                      void *workspace, size_t workspace_bytes, gbpcg_stream stream);
+
+/*
+ * Boundary-handling variants of q = A p (Sec. VI-C measures the cost of
+ * setting the boundary halo to zero by hand), constant coefficient, FP32
+ * DEVICE p and q:
+ *   0  TMA boxes, the out-of-grid part zero-filled by the TMA unit (the
+ *      library's stencil; needs 16-byte aligned arrays, nx a multiple of 4)
+ *   1  boxes copied with plain loads, each element bounds-checked and set to
+ *      zero outside the grid
+ *   2  TMA boxes, then the out-of-grid part of every box that touches the
+ *      boundary set to zero again by the threads (explicit zero fill)
+ * All three give the same q bit for bit.
+ */
+int gbpcg_stencil_apply_variant(const gbpcg_grid *grid, int32_t variant, const float *p, float *q,
+                                gbpcg_stream stream);
 
 /*
  * y = alpha x + y  (Sec. IV: element-wise arithmetic).  x, y: DEVICE arrays of

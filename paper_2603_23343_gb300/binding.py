@@ -26,6 +26,9 @@ F32, BF16, F16, F64 = 0, 1, 2, 3
 FLAG_HOST_IO = 1
 FLAG_PROFILE = 2
 FLAG_AUTOTUNE = 4
+FLAG_HOST_LOOP = 8
+FLAG_SPLIT = 16
+_MODES = {"graph": 0, "host_loop": FLAG_HOST_LOOP, "split": FLAG_SPLIT}
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
 
@@ -35,7 +38,8 @@ EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbp
            "gbpcg_conv3_workspace_size", "gbpcg_conv3_forward", "gbpcg_conv3_backward_data",
            "gbpcg_conv3_backward_weight", "gbpcg_nn_workspace_size", "gbpcg_nn_forward", "gbpcg_nn_backward",
            "gbpcg_nn_loss", "gbpcg_nn_adam", "gbpcg_nn_train_step", "gbpcg_nn_status", "gbpcg_fcg_workspace_size",
-           "gbpcg_fcg_solve", "gbpcg_wait_selftest", "gbpcg_nn_tensor_info"]
+           "gbpcg_fcg_solve", "gbpcg_wait_selftest", "gbpcg_nn_tensor_info", "gbpcg_dot_variant_workspace_size",
+           "gbpcg_dot_variant", "gbpcg_stencil_apply_variant"]
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
 
 NN_NUM_WEIGHTS = 319248
@@ -134,6 +138,12 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_nn_tensor_info.argtypes = [I32, I32, I32, I32, I32, ctypes.POINTER(SZ), ctypes.POINTER(I32),
                                              ctypes.POINTER(I32), ctypes.POINTER(I32)]
         lib.gbpcg_nn_tensor_info.restype = ctypes.c_int
+        lib.gbpcg_dot_variant_workspace_size.restype = SZ
+        lib.gbpcg_dot_variant_workspace_size.argtypes = []
+        lib.gbpcg_dot_variant.argtypes = [I32, I64, P, P, P, P, SZ, P]
+        lib.gbpcg_dot_variant.restype = ctypes.c_int
+        lib.gbpcg_stencil_apply_variant.argtypes = [ctypes.POINTER(Grid), I32, P, P, P]
+        lib.gbpcg_stencil_apply_variant.restype = ctypes.c_int
         lib.gbpcg_nn_forward.argtypes = [ctypes.POINTER(Grid), P, P, P, P, SZ, P]
         lib.gbpcg_nn_backward.restype = ctypes.c_int
         lib.gbpcg_nn_backward.argtypes = [ctypes.POINTER(Grid), P, P, P, SZ, P]
@@ -240,6 +250,27 @@ def dot_noalloc(x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = Non
     return out
 
 
+def dot_variant(variant: int, x: torch.Tensor, y: torch.Tensor, out: torch.Tensor | None = None,
+                workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """x.y (FP32, 16-byte aligned) with reduction variant 0..4 (gbpcg_dot_variant)."""
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=x.device)
+    if workspace is None:
+        workspace = torch.empty(load().gbpcg_dot_variant_workspace_size(), dtype=torch.uint8, device=x.device)
+    _check(load().gbpcg_dot_variant(int(variant), x.numel(), _ptr(x), _ptr(y), _ptr(out), _ptr(workspace),
+                                    workspace.numel(), _stream(stream)))
+    return out
+
+
+def stencil_apply_variant(variant: int, p: torch.Tensor, q: torch.Tensor | None = None, stream=None):
+    """q = A p (FP32, constant coefficient) with boundary variant 0..2 (gbpcg_stencil_apply_variant)."""
+    if q is None:
+        q = torch.empty_like(p)
+    g = make_grid(p.shape)
+    _check(load().gbpcg_stencil_apply_variant(ctypes.byref(g), int(variant), _ptr(p), _ptr(q), _stream(stream)))
+    return q
+
+
 def axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
     """y = alpha x + y in place (gbpcg_axpy)."""
     if x.numel() != y.numel() or x.dtype != y.dtype:
@@ -265,7 +296,9 @@ def tile_cfg_code(cfg_a=None, cfg_b=None) -> int:
 
 
 def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, workspace=None,
-              profile=False, tile_cfg=0, inner_tol=0.0, max_outer=30, autotune=False) -> Opts:
+              profile=False, tile_cfg=0, inner_tol=0.0, max_outer=30, autotune=False, mode="graph") -> Opts:
+    """gbpcg_opts; mode "graph" (the device-driven CUDA-graph loop), "host_loop" (GBPCG_FLAG_HOST_LOOP)
+    or "split" (GBPCG_FLAG_SPLIT)."""
     o = Opts()
     o.tol = float(tol)
     o.maxit = int(maxit)
@@ -273,6 +306,7 @@ def make_opts(tol=1e-6, maxit=2000, storage=F32, io_dtype=F32, host_io=False, wo
     o.storage = storage
     o.io_dtype = io_dtype
     o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0) | (FLAG_AUTOTUNE if autotune else 0)
+    o.flags |= _MODES[mode]
     o.tile_cfg = int(tile_cfg)
     o.inner_tol = float(inner_tol)
     o.max_outer = int(max_outer)
@@ -297,7 +331,7 @@ def alloc_workspace(shape, k_block=None, kb=8, device="cuda", **opt_kw) -> torch
 
 def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
               workspace: torch.Tensor | None = None, host_io=False, profile=False, tile_cfg=0, storage=None,
-              inner_tol=0.0, max_outer=30, stream=None):
+              inner_tol=0.0, max_outer=30, mode="graph", stream=None):
     """Jacobi-PCG solve of A x = b (gbpcg_pcg_solve).  Returns (x, result dict).
 
     b and x are float32 or float64 (the solution accumulates in that type; the
@@ -308,7 +342,8 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     the summed pass times in result["pass_ms"].  storage=torch.bfloat16 or
     torch.float16 (with float64 b and x) selects mixed precision: FP64
     iterative refinement around 16-bit inner solves to inner_tol (0: the library's default,
-    0.1 for BF16 and 1e-2 for FP16).
+    0.1 for BF16 and 1e-2 for FP16).  mode="host_loop" or "split" selects the paper's
+    host-readback variants (GBPCG_FLAG_HOST_LOOP, GBPCG_FLAG_SPLIT).
     """
     if b.dim() != 3 or not b.is_contiguous():
         raise GbpcgError(ERR_ARG, "b must be a contiguous (nz, ny, nx) tensor")
@@ -321,9 +356,9 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
     dev = b.device if b.is_cuda else torch.device("cuda", torch.cuda.current_device())
     if workspace is None:
         workspace = alloc_workspace(b.shape, k_block, kb, device=dev, io_dtype=io, host_io=host_io, storage=st,
-                                    inner_tol=inner_tol, max_outer=max_outer)
+                                    inner_tol=inner_tol, max_outer=max_outer, mode=mode)
     g = make_grid(b.shape, k_block, kb)
-    o = make_opts(tol, maxit, st, io, host_io, workspace, profile, tile_cfg, inner_tol, max_outer)
+    o = make_opts(tol, maxit, st, io, host_io, workspace, profile, tile_cfg, inner_tol, max_outer, mode=mode)
     r = Result()
     rc = load().gbpcg_pcg_solve(ctypes.byref(g), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
                                 _stream(stream))

@@ -321,7 +321,12 @@ __device__ __forceinline__ void manual_box(const T *src, T *dst, int nx, int ny,
     }
 }
 
-template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op>
+// ZFILL (an ablation of Sec. VI-C, off in every solver path): after each
+// TMA box lands, tiles that touch the domain boundary also zero the
+// out-of-grid part of the box explicitly, the work the paper's kernels do by
+// hand; here the TMA unit has already written those zeros, so the variant
+// measures what explicit zero filling would cost.
+template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op, bool ZFILL = false>
 __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
     static_assert(S >= 2, "a stage is refilled only after the step that reads it as the output plane");
@@ -467,6 +472,22 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
                 if (!mbar_wait_bounded(&full[s], (t / S) & 1)) s_timeout = 1;
             }
             consumed = t;
+            if constexpr (ZFILL) {
+                const int m = plane(t);
+                const bool edge = m < 0 || m >= nz || x0 - XH < 0 || x0 + TX + XH > nx || y0 - 1 < 0 ||
+                                  y0 + TY + 1 > ny;
+                if (edge) {
+                    T *hb = reinterpret_cast<T *>(smem + (size_t)s * SB);
+                    for (int e = threadIdx.x; e < HX * G::HY; e += NT) {
+                        const int r = e / HX, c = e - r * HX;
+                        const int bx = x0 - XH + c, by = y0 - 1 + r;
+                        if (m < 0 || m >= nz || bx < 0 || bx >= nx || by < 0 || by >= ny) hb[e] = from_f<T>(0.0f);
+                    }
+                    // generic-proxy writes before the TMA refills this stage
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                __syncthreads();
+            }
 #pragma unroll
             for (int i = 0; i < V; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
             in_valv(base, cidx, qc);

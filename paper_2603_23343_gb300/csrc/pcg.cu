@@ -176,6 +176,7 @@ static bool refine_mode(const gbpcg_opts &o) { return o.storage == GBPCG_BF16 ||
 
 static size_t workspace_total(const gbpcg_grid &g, const gbpcg_opts &o) {
     if (refine_mode(o)) return refine_layout(g, o).total;
+    if (o.flags & GBPCG_FLAG_SPLIT) return split_workspace_size(g);
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     size_t t = ws_layout_n(n, o.storage, o.io_dtype, o.flags & GBPCG_FLAG_HOST_IO, block_count(g)).total;
     if (o.flags & GBPCG_FLAG_AUTOTUNE) t += round256(n * dtype_size(o.io_dtype));  // tuner's scratch x
@@ -195,6 +196,12 @@ static int check_opts(const gbpcg_opts *o) {
     if (o->precond != GBPCG_PRECOND_JACOBI) return fail_arg("unknown preconditioner");
     if (!(o->tol >= 0.0)) return fail_arg("tol must be >= 0");
     if (o->maxit < 0) return fail_arg("maxit must be >= 0");
+    const uint32_t modes = o->flags & (GBPCG_FLAG_PROFILE | GBPCG_FLAG_HOST_LOOP | GBPCG_FLAG_SPLIT);
+    if (modes & (modes - 1)) return fail_arg("PROFILE, HOST_LOOP and SPLIT exclude one another");
+    if ((o->flags & (GBPCG_FLAG_HOST_LOOP | GBPCG_FLAG_SPLIT)) && refine_mode(*o))
+        return fail_arg("HOST_LOOP and SPLIT take FP32 storage");
+    if ((o->flags & GBPCG_FLAG_SPLIT) && (o->io_dtype != GBPCG_F32 || (o->flags & GBPCG_FLAG_HOST_IO)))
+        return fail_arg("SPLIT takes FP32 device b and x");
     if (o->tile_cfg < 0 || (o->tile_cfg & 0xff) > NUM_CFG || ((o->tile_cfg >> 8) & 0xff) > NUM_CFG ||
         (o->tile_cfg >> 16))
         return fail_arg("tile_cfg selects unknown tile configurations");
@@ -469,8 +476,8 @@ static int check_batch(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts 
         if (int rc = check_grid(&grids[i])) return rc;
     if (int rc = check_opts(opts)) return rc;
     if (opts->storage != GBPCG_F32) return fail_arg("batched solves use F32 storage");
-    if (opts->flags & (GBPCG_FLAG_HOST_IO | GBPCG_FLAG_PROFILE))
-        return fail_arg("batched solves take device buffers and no profile flag");
+    if (opts->flags & (GBPCG_FLAG_HOST_IO | GBPCG_FLAG_PROFILE | GBPCG_FLAG_HOST_LOOP | GBPCG_FLAG_SPLIT))
+        return fail_arg("batched solves take device buffers and no profile, host-loop or split flag");
     return GBPCG_OK;
 }
 
@@ -547,6 +554,11 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
         return rc;
     }
 
+    if (opts->flags & GBPCG_FLAG_SPLIT) {
+        if (g.k_block) return fail_arg("SPLIT takes the constant-coefficient operator");
+        return split_solve(g, static_cast<const float *>(b), static_cast<float *>(x), *opts, result, s);
+    }
+
     const WsLayout L = ws_layout_n((size_t)n, opts->storage, opts->io_dtype, false, block_count(g));
     const bool tma = tma_ok(sizeof(float), g.nx, {ws + L.z, ws + L.p0, ws + L.p1, ws + L.d});
     const SolveCall call{&g, cfg_a, cfg_b, bd, xd, ws, L, opts->tol, opts->maxit, opts->io_dtype, 1.0f, nullptr};
@@ -555,8 +567,9 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
     GB_CUDA(cudaEventCreate(&e0));
     GB_CUDA(cudaEventCreate(&e1));
     GB_CUDA(cudaEventRecord(e0, s));
-    const int rc = (opts->flags & GBPCG_FLAG_PROFILE) ? solve_profiled<float>(call, tma, result, s)
-                                                      : solve_launch<float>(call, tma, s);
+    const int rc = (opts->flags & GBPCG_FLAG_PROFILE)     ? solve_profiled<float>(call, tma, result, s)
+                   : (opts->flags & GBPCG_FLAG_HOST_LOOP) ? solve_host_loop<float>(call, tma, s)
+                                                          : solve_launch<float>(call, tma, s);
     if (rc) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

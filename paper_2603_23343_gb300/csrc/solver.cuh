@@ -634,6 +634,27 @@ struct SolvePlan {
         return GBPCG_OK;
     }
 
+    // Host-loop mode (the paper's FP32 variant reads the residual norm back
+    // every iteration, Sec. VII): the same kernels launched one iteration at
+    // a time, the host reading the device's stop flag after each iteration
+    // before it launches the next.
+    int run_host_loop(cudaStream_t s) {
+        set_cond(0, 0, 0);
+        GB_CUDA(launch_setup(s));
+        int done = 0;
+        GB_CUDA(cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GB_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < maxit && !done; ++i) {
+            GB_CUDA(launch_a(s));
+            GB_CUDA(launch_b(s));
+            GB_CUDA(launch_replace(s));
+            GB_CUDA(cudaMemcpyAsync(&done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            GB_CUDA(cudaStreamSynchronize(s));
+        }
+        GB_CUDA(launch_final(s));
+        return GBPCG_OK;
+    }
+
     // Profile mode: the same kernels launched one by one on `s`, each pass
     // launch bracketed by CUDA events; the loop polls the device flag every
     // kChunk iterations.  Only launches of real iterations are summed.
@@ -832,7 +853,23 @@ int solve_profiled(const SolveCall &c, bool tma, gbpcg_result *res, cudaStream_t
     });
 }
 
+// Host-loop mode (GBPCG_FLAG_HOST_LOOP): one iteration per host round trip.
+template <typename T>
+int solve_host_loop(const SolveCall &c, bool tma, cudaStream_t s) {
+    return dispatch_plan<T>(c, tma, [&](auto op, auto tm, auto xt) {
+        SolvePlan<decltype(op), decltype(tm)::value, decltype(xt), T> plan;
+        if (int r = plan_init(plan, c, op)) return r;
+        return plan.run_host_loop(s);
+    });
+}
+
+// The split-kernel FP32 solver with host-side scalars (ablation.cu).
+size_t split_workspace_size(const gbpcg_grid &g);
+int split_solve(const gbpcg_grid &g, const float *b, float *x, const gbpcg_opts &o, gbpcg_result *res,
+                cudaStream_t s);
+
 extern template int batched_capture<float>(const SolveCall *, const int *, int, cudaGraph_t *);
+extern template int solve_host_loop<float>(const SolveCall &, bool, cudaStream_t);
 extern template int solve_launch<float>(const SolveCall &, bool, cudaStream_t);
 extern template int solve_launch<__nv_bfloat16>(const SolveCall &, bool, cudaStream_t);
 extern template int solve_launch<__half>(const SolveCall &, bool, cudaStream_t);

@@ -227,6 +227,30 @@ def test_learned_preconditioner_argument_checks(lib):
     assert lib.gbpcg_nn_forward(ctypes.byref(g), None, None, None, P(256), inference, None) == B.ERR_ARG
 
 
+def test_mode_flags_and_variant_argument_checks(lib):
+    g = _grid(32, 32, 32)
+    n = ctypes.c_size_t(0)
+    o = B.make_opts(mode="split")
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.OK
+    assert n.value >= 4 * 32 ** 3 * 4  # r, z, p, q
+    for bad in (B.make_opts(mode="split", io_dtype=B.F64), B.make_opts(mode="host_loop", profile=True),
+                B.make_opts(mode="host_loop", storage=B.BF16, io_dtype=B.F64)):
+        assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(bad), ctypes.byref(n)) == B.ERR_ARG
+    o = B.make_opts(mode="split")
+    o.flags |= B.FLAG_HOST_LOOP
+    assert lib.gbpcg_workspace_size(ctypes.byref(g), ctypes.byref(o), ctypes.byref(n)) == B.ERR_ARG
+    P = ctypes.c_void_p
+    wsz = lib.gbpcg_dot_variant_workspace_size()
+    assert wsz > 0
+    assert lib.gbpcg_dot_variant(5, 16, P(256), P(512), P(768), P(1024), wsz, None) == B.ERR_ARG
+    assert lib.gbpcg_dot_variant(0, 0, P(256), P(512), P(768), P(1024), wsz, None) == B.ERR_ARG
+    assert lib.gbpcg_dot_variant(0, 16, P(260), P(512), P(768), P(1024), wsz, None) == B.ERR_ARG
+    assert lib.gbpcg_dot_variant(0, 16, P(256), P(512), P(768), P(1024), wsz - 1, None) == B.ERR_ARG
+    assert lib.gbpcg_stencil_apply_variant(ctypes.byref(g), 3, P(256), P(512), None) == B.ERR_ARG
+    assert lib.gbpcg_stencil_apply_variant(ctypes.byref(g), 0, P(256), P(256), None) == B.ERR_ARG
+    assert lib.gbpcg_stencil_apply_variant(ctypes.byref(g), 0, P(260), P(512), None) == B.ERR_ARG
+
+
 def test_nn_tensor_info_is_host_logic(lib):
     """Every tensor the network leaves in a workspace lies inside it, inference workspaces refuse
     the training-only gradient tensors, and distinct tensors do not overlap."""

@@ -50,7 +50,7 @@ def identity_precond(k64):
     def M(r):
         s = r * dsc
         rms = float(np.sqrt(np.mean(s * s)))
-        return bf16(s / rms) * rms * dsc
+        return bf16(s / rms) * (rms * dsc)
     return M
 
 
