@@ -89,6 +89,8 @@ typedef struct gbpcg_grid {
                                    iteration at a time, the host reading the device's stop flag
                                    after each (FP32 storage; results equal the graph's bit for
                                    bit) */
+#define GBPCG_FLAG_BATCH_GRAPH 32u /* batched solves: one CUDA graph with a branch per problem
+                                      instead of the single persistent kernel */
 #define GBPCG_FLAG_SPLIT 16u /* the paper's FP32 split-kernel solver (Sec. VII) and its H100
                                 comparator's structure: one kernel per operation (stencil, dot,
                                 axpy, element-wise Jacobi scaling, p update), alpha and beta formed
@@ -267,15 +269,27 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
                     gbpcg_result *result, gbpcg_stream stream);
 
 /*
- * Many independent problems solved as one CUDA graph:
- * each problem's whole solve (its own device-driven loop, as in
- * gbpcg_pcg_solve) is a branch of one graph, so one launch runs them all
- * concurrently and no problem waits on another's convergence.  grids[i],
- * b[i], x[i] (DEVICE pointers, opts->io_dtype) describe problem i; storage
- * is F32; results[i] receives problem i's outcome (time_ms is the batch's).
- * The workspace (gbpcg_workspace_size_batched) holds every problem's
- * scratch.  Returns GBPCG_OK when all problems converged, else the first
- * other status.  The instantiated graph is cached per argument set.
+ * Many independent problems, each the Jacobi-PCG solve of gbpcg_pcg_solve
+ * (Sec. VII), in one launch.  grids[i], b[i], x[i] (DEVICE pointers,
+ * opts->io_dtype) describe problem i; storage is F32; results[i] receives
+ * problem i's outcome (time_ms is the batch's).  The workspace
+ * (gbpcg_workspace_size_batched) holds every problem's scratch.  Returns
+ * GBPCG_OK when all problems converged, else the first other status.
+ *
+ * Constant-coefficient grids with nx a multiple of 4 run as ONE persistent
+ * kernel (a cooperative launch of as many CTAs as the GPU holds, inside a
+ * cached one-node CUDA graph): it walks the pass-A / pass-B tiles of every
+ * unfinished problem, one round per iteration, separated by grid-wide
+ * barriers; a problem drops out of the work when it converges; residual
+ * replacements, the setup and the finalize are phases of the same kernel.
+ * Each barrier wait is bounded: if one gives up, the unfinished problems
+ * report GBPCG_TIMEOUT.  result.pass_launches = {1, rounds run},
+ * pass_ctas[0] = the tile configuration (0: 64x16, 1: 128x8, 2: 32x32):
+ * opts->tile_cfg = c + 1 selects configuration c, else
+ * GBPCG_FLAG_AUTOTUNE times the three and keeps the fastest per set of
+ * shapes, else 64x16.  Otherwise (block coefficients, or GBPCG_FLAG_BATCH_GRAPH) each
+ * problem's whole solve is a branch of one CUDA graph with its own
+ * device-driven loop, tiles per shape from the autotuner.
  */
 int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts *opts,
                                  size_t *bytes);

@@ -28,6 +28,7 @@ FLAG_PROFILE = 2
 FLAG_AUTOTUNE = 4
 FLAG_HOST_LOOP = 8
 FLAG_SPLIT = 16
+FLAG_BATCH_GRAPH = 32
 _MODES = {"graph": 0, "host_loop": FLAG_HOST_LOOP, "split": FLAG_SPLIT}
 
 _DTYPES = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16, torch.float64: F64}
@@ -367,8 +368,10 @@ def pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=20
 
 
 def pcg_solve_batched(bs, xs=None, tol=1e-6, maxit=2000, tile_cfg=0, autotune=False, workspace=None,
-                      stream=None):
-    """Solves len(bs) independent problems as one graph launch (gbpcg_pcg_solve_batched).
+                      graph=False, stream=None):
+    """Solves len(bs) independent problems in one launch (gbpcg_pcg_solve_batched): one persistent
+    kernel for constant-coefficient grids (tile_cfg 1..3 picks its tiles), or with graph=True
+    (GBPCG_FLAG_BATCH_GRAPH) one CUDA graph with a branch per problem.
 
     bs, xs: lists of contiguous (nz, ny, nx) CUDA tensors (all float32 or all
     float64).  Returns (xs, [result dict per problem]).
@@ -382,6 +385,8 @@ def pcg_solve_batched(bs, xs=None, tol=1e-6, maxit=2000, tile_cfg=0, autotune=Fa
             raise GbpcgError(ERR_ARG, "b and x must be CUDA tensors of one dtype and matching shapes")
     grids = (Grid * n)(*[make_grid(b.shape) for b in bs])
     o = make_opts(tol, maxit, F32, io, False, None, False, tile_cfg, autotune=autotune)
+    if graph:
+        o.flags |= FLAG_BATCH_GRAPH
     lib = load()
     if workspace is None:
         nbytes = ctypes.c_size_t(0)

@@ -38,17 +38,26 @@ static_assert(sizeof(unsigned) * (kRvGroups + 1) <= kRvTicketBytes, "ticket area
 
 enum DotVariant { DV_CTA_LAST = 0, DV_WARP_LAST = 1, DV_CTA_KERNEL = 2, DV_CTA_ATOMIC = 3, DV_CTA_TREE = 4, DV_COUNT };
 
-// Per-thread part of x.y: FP32 sums of 4 products added into an FP64
-// accumulator (the production dot's arithmetic); x, y 16-byte aligned.
+// Per-thread part of x.y, streamed as gbpcg_dot streams it (four 16-byte
+// vectors of each input in flight per thread, FP32 sums of 8 products added
+// into an FP64 accumulator), so the variants differ only in the reduction.
+// x, y 16-byte aligned.
+__device__ __forceinline__ float dot4v(const float4 a, const float4 b, float s) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, s))));
+}
 __device__ __forceinline__ double thread_dot(int64_t n, const float *__restrict__ x, const float *__restrict__ y) {
     const int64_t tid = (int64_t)blockIdx.x * kRvThreads + threadIdx.x, nth = (int64_t)gridDim.x * kRvThreads;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x), *y4 = reinterpret_cast<const float4 *>(y);
     double acc = 0.0;
     const int64_t n4 = n / 4;
-    for (int64_t i = tid; i < n4; i += nth) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(x) + i);
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(y) + i);
-        acc += (double)fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+    int64_t i = tid;
+    for (; i + 3 * nth < n4; i += 4 * nth) {
+        const float4 a0 = x4[i], a1 = x4[i + nth], a2 = x4[i + 2 * nth], a3 = x4[i + 3 * nth];
+        const float4 b0 = y4[i], b1 = y4[i + nth], b2 = y4[i + 2 * nth], b3 = y4[i + 3 * nth];
+        acc += (double)dot4v(a1, b1, dot4v(a0, b0, 0.f));
+        acc += (double)dot4v(a3, b3, dot4v(a2, b2, 0.f));
     }
+    for (; i < n4; i += nth) acc += (double)dot4v(x4[i], y4[i], 0.f);
     for (int64_t j = 4 * n4 + tid; j < n; j += nth) acc += (double)(x[j] * y[j]);
     return acc;
 }

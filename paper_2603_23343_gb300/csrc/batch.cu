@@ -1,0 +1,646 @@
+// Many independent Jacobi-PCG problems (Sec. VII's solver, one per grid) in
+// ONE persistent kernel launch.
+//
+// The grid is as many CTAs as the GPU holds at once (a cooperative launch,
+// so every CTA is resident) and walks phases separated by grid-wide
+// barriers:
+//
+//   reset states | max |b| | r0 = b - A x0 (FP64)      once
+//   pass A | pass B | [flush | r = b - A x (FP64)]       every round, until all converge
+//   x += d + alpha p | true residual (FP64)              once
+//
+// A phase is a list of work items over all problems: a pass item is one
+// (x, y) tile of one problem marched through a chunk of z planes (the same
+// z-marching code as the single-problem passes, engine.cuh), a row item a
+// run of grid rows of one problem.  CTA c takes items c, c + G, c + 2G, ...
+// (G CTAs); items of problems that have converged are skipped, so a
+// problem drops out of the work as soon as it is done while the others go
+// on.  Each problem keeps its own scalars (SolveState), partial sums and
+// tickets: the CTA that finishes a problem's last item of a phase adds the
+// problem's partial sums in item order (bitwise reproducible) and takes the
+// scalar step (alpha; beta, convergence, the replacement trigger).
+//
+// The grid barrier is a counter and a generation word in device memory.
+// Every wait on it is bounded: after kBarrierPolls polls the waiting CTA
+// raises an abort flag and leaves, every other CTA leaves at its next
+// barrier, and the problems that had not finished report GBPCG_TIMEOUT.
+#include <algorithm>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <vector>
+
+#include "solver.cuh"
+
+namespace gb {
+
+namespace {
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchZDepth = 32;  // z planes per pass item
+constexpr int kRowPoints = 16384;  // grid points per row item (at least one row)
+constexpr uint32_t kBarrierPolls = 1u << 22;  // x ~64 ns of sleep: well under a second
+
+// Tile configurations of the persistent kernel (all 256 threads: the FP64
+// residual code strides rows by 256 threads).
+enum BatchCfg { BC_64x16 = 0, BC_128x8 = 1, BC_32x32 = 2, BC_COUNT = 3 };
+struct BcDims { int tx, ty; };
+inline BcDims bc_dims(int c) { return c == BC_64x16 ? BcDims{64, 16} : c == BC_128x8 ? BcDims{128, 8} : BcDims{32, 32}; }
+
+struct __align__(128) BatchProblem {
+    CUtensorMap hz, hp0, hp1;  // halo boxes of z, p0, p1
+    CUtensorMap cd, cz;        // centre boxes of d (pass A) and z (pass B)
+    OpConst op;
+    int nx, ny, nz, tiles_x, tiles, zdepth, zchunks;
+    int item0, nitems;          // pass items
+    int row0_item, nrow_items;  // row items
+    int rows_per_item;
+    float *z, *p0, *p1, *d;
+    SolveState *st;
+    double *partials;
+    Res64Args ra;
+};
+
+struct __align__(64) BatchHeader {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int abort;
+    int rounds;
+};
+
+struct BatchArgs {
+    BatchProblem *probs;
+    const int *item_prob;  // pass item -> problem
+    const int *row_prob;   // row item -> problem
+    BatchHeader *hdr;
+    int nprob, nitems, nrow_items;
+    double tol;
+    int maxit;
+};
+
+// Grid-wide barrier (bounded): false once any CTA has given up.
+__device__ __forceinline__ bool batch_barrier(BatchHeader *h) {
+    // writes of this phase (generic proxy) before the next phase's TMA loads (async proxy)
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __threadfence();
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &h->bar_gen;
+        volatile int *abort = &h->abort;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&h->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&h->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&h->bar_gen, 1u);
+        } else {
+            uint32_t polls = 0;
+            while (*gen == g) {
+                if (*abort) break;
+                if (++polls > kBarrierPolls) {
+                    atomicExch(&h->abort, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_ok = *abort == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The whole batch.  X: type of b and x (float or double).
+template <int TX, int TY, int S, typename X>
+__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchArgs A) {
+    using T = float;
+    using GA = Geometry<T, TX, TY, K_PASSA>;
+    using GB = Geometry<T, TX, TY, K_PASSB>;
+    static_assert(GA::NT == kBatchThreads, "persistent tiles have 256 threads");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ int s_timeout;
+    __shared__ int s_flag;
+    BatchHeader *hdr = A.hdr;
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t ring = 0;  // loads this CTA has issued into its ring (stage and phase of the next one)
+    const unsigned G = gridDim.x;
+
+    // ---- reset every problem's state ----
+    for (int p = blockIdx.x; p < A.nprob; p += G)
+        if (threadIdx.x == 0) {
+            SolveState *st = A.probs[p].st;
+            memset(st, 0, sizeof(SolveState));
+            st->tol2 = A.tol * A.tol;
+            st->maxit = A.maxit;
+            st->status = GBPCG_NOT_CONVERGED;
+        }
+    if (!batch_barrier(hdr)) return;
+
+    // ---- max |b| per problem (bit patterns: integer maxima) ----
+    for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+        const BatchProblem &P = A.probs[A.row_prob[item]];
+        const int local = item - P.row0_item;
+        const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+        using U = typename std::conditional<sizeof(X) == 8, unsigned long long, unsigned int>::type;
+        constexpr U kAbs = (U)~((U)1 << (8 * sizeof(X) - 1));
+        const X *b = static_cast<const X *>(P.ra.b);
+        U m = 0;
+        for (int row = r0; row < r1; ++row)
+            for (int i = threadIdx.x; i < P.nx; i += kBatchThreads) {
+                X v = __ldg(b + (int64_t)row * P.nx + i);
+                U u;
+                memcpy(&u, &v, sizeof(U));
+                u &= kAbs;
+                m = u > m ? u : m;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const U t = __shfl_xor_sync(0xffffffffu, m, o);
+            m = t > m ? t : m;
+        }
+        if ((threadIdx.x & 31) == 0 && m) {
+            X v;
+            memcpy(&v, &m, sizeof(U));
+            atomicMax(&P.st->rhs_bits, (unsigned long long)__double_as_longlong((double)v));
+        }
+    }
+    if (!batch_barrier(hdr)) return;
+
+    // ---- r0 = b - A x0 in FP64, z0 = D^-1 r0, d = 0 ----
+    for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+        const BatchProblem &P = A.probs[A.row_prob[item]];
+        const int local = item - P.row0_item;
+        const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+        double part[3], tot[3], unscale;
+        res64_rows<RES_INIT, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+        if (group_sum_last<3, kBatchThreads>(part, P.partials, &P.st->ticket[4 + RES_INIT], local, P.nrow_items,
+                                             tot) &&
+            threadIdx.x == 0)
+            res64_finish<RES_INIT>(P.st, tot, unscale);
+    }
+    if (!batch_barrier(hdr)) return;
+
+    // ---- the iteration rounds ----
+    for (int round = 0;; ++round) {
+        // continue while any problem is unfinished (the states are stable between barriers)
+        if (threadIdx.x < 32) {
+            int any = 0;
+            for (int p = threadIdx.x; p < A.nprob; p += 32) any |= !((volatile int *)&A.probs[p].st->done)[0];
+            any = __any_sync(0xffffffffu, any);
+            if (threadIdx.x == 0) s_flag = any;
+        }
+        __syncthreads();
+        const int active = s_flag;
+        __syncthreads();  // s_flag is written again before the next barrier
+        if (!active) break;
+
+        // pass A: p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap
+        for (int item = blockIdx.x; item < A.nitems; item += G) {
+            const BatchProblem &P = A.probs[A.item_prob[item]];
+            SolveState *st = P.st;
+            if (((volatile int *)&st->done)[0]) continue;
+            const int local = item - P.item0;
+            const int tile = local % P.tiles, chunk = local / P.tiles;
+            const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
+            const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+            const MarchScalars sc = read_scalars<K_PASSA>(st);
+            const bool odd = sc.it & 1;
+            MarchIO<T, K_PASSA> io;
+            io.H0 = P.z;
+            io.H1 = odd ? P.p0 : P.p1;  // p_{k-1}
+            io.C0 = P.d;
+            io.O0 = odd ? P.p1 : P.p0;  // p_k
+            io.O1 = P.d;
+            io.M0 = &P.hz;
+            io.M1 = odd ? &P.hp0 : &P.hp1;
+            io.MC = &P.cd;
+            float acc[GA::NV];
+            acc[0] = 0.f;
+            ring += march_tile<T, TX, TY, S, K_PASSA, true, OpConst, false>(smem, full, &s_timeout, ring, io, P.op,
+                                                                           P.nx, P.ny, P.nz, x0, y0, k0, k1, sc,
+                                                                           acc);
+            if (s_timeout) {
+                if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
+                return;
+            }
+            double part[1], tot[1];
+            block_sum<1, kBatchThreads>(acc, part);
+            if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, P.nitems, tot) &&
+                threadIdx.x == 0)
+                passa_finish(st, tot[0], false);
+        }
+        if (!batch_barrier(hdr)) return;
+
+        // pass B: q = A p_k, r = D z - alpha q, z = D^-1 r, r.r and r.z
+        for (int item = blockIdx.x; item < A.nitems; item += G) {
+            const BatchProblem &P = A.probs[A.item_prob[item]];
+            SolveState *st = P.st;
+            if (((volatile int *)&st->done)[0]) continue;
+            const int local = item - P.item0;
+            const int tile = local % P.tiles, chunk = local / P.tiles;
+            const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
+            const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+            const MarchScalars sc = read_scalars<K_PASSB>(st);
+            const bool odd = sc.it & 1;
+            MarchIO<T, K_PASSB> io;
+            io.H0 = odd ? P.p1 : P.p0;  // p_k
+            io.H1 = io.H0;
+            io.C0 = P.z;
+            io.O0 = P.z;
+            io.O1 = P.z;
+            io.M0 = odd ? &P.hp1 : &P.hp0;
+            io.M1 = io.M0;
+            io.MC = &P.cz;
+            float acc[GB::NV];
+            acc[0] = acc[1] = 0.f;
+            ring += march_tile<T, TX, TY, S, K_PASSB, true, OpConst, false>(smem, full, &s_timeout, ring, io, P.op,
+                                                                           P.nx, P.ny, P.nz, x0, y0, k0, k1, sc,
+                                                                           acc);
+            if (s_timeout) {
+                if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
+                return;
+            }
+            double part[2], tot[2];
+            block_sum<2, kBatchThreads>(acc, part);
+            if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, P.nitems, tot) &&
+                threadIdx.x == 0)
+                passb_finish(st, sc.it, tot[0], tot[1], false);
+        }
+        if (!batch_barrier(hdr)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) hdr->rounds = round + 1;
+
+        // residual replacement where a problem asked for one
+        if (threadIdx.x < 32) {
+            int any = 0;
+            for (int p = threadIdx.x; p < A.nprob; p += 32) {
+                const SolveState *st = A.probs[p].st;
+                any |= ((volatile const int *)&st->replace)[0] && !((volatile const int *)&st->done)[0];
+            }
+            any = __any_sync(0xffffffffu, any);
+            if (threadIdx.x == 0) s_flag = any;
+        }
+        __syncthreads();
+        const int replacing = s_flag;
+        __syncthreads();  // the next round writes s_flag before any barrier
+        if (!replacing) continue;
+        // flush: x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
+        for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+            const BatchProblem &P = A.probs[A.row_prob[item]];
+            const SolveState *st = P.st;
+            if (!st->replace || st->done) continue;
+            const int local = item - P.row0_item;
+            const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+            const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
+            const float a = st->pending ? (float)st->alpha : 0.0f;
+            const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
+            X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
+            const X is = (X)inv_s;
+            for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
+                const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
+                x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+                P.d[g] = 0.0f;
+            }
+        }
+        if (!batch_barrier(hdr)) return;
+        // r = b - A x in FP64, z = D^-1 r, the replacement's decisions
+        for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+            const BatchProblem &P = A.probs[A.row_prob[item]];
+            SolveState *st = P.st;
+            if (!((volatile int *)&st->replace)[0] || ((volatile int *)&st->done)[0]) continue;
+            const int local = item - P.row0_item;
+            const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+            double part[2], tot[2], unscale;
+            res64_rows<RES_REPLACE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+            if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local,
+                                                 P.nrow_items, tot) &&
+                threadIdx.x == 0)
+                res64_finish<RES_REPLACE>(st, tot, unscale);
+        }
+        if (!batch_barrier(hdr)) return;
+    }
+
+    // ---- x += (d + alpha_{k-1} p_{k-1}) / s (x = 0 when b = 0) ----
+    for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+        const BatchProblem &P = A.probs[A.row_prob[item]];
+        const SolveState *st = P.st;
+        const int local = item - P.row0_item;
+        const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+        X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
+        if (st->zero_x) {
+            for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) x[g] = X(0);
+            continue;
+        }
+        const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
+        const float a = st->pending ? (float)st->alpha : 0.0f;
+        const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
+        const X is = (X)inv_s;
+        for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
+            const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
+            x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+        }
+    }
+    if (!batch_barrier(hdr)) return;
+
+    // ---- true residual ||b - A x|| in FP64 (unless a replacement already evaluated this x) ----
+    for (int item = blockIdx.x; item < A.nrow_items; item += G) {
+        const BatchProblem &P = A.probs[A.row_prob[item]];
+        SolveState *st = P.st;
+        if (st->true_known) continue;
+        const int local = item - P.row0_item;
+        const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+        double part[1], tot[1], unscale;
+        res64_rows<RES_TRUE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+        if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_TRUE], local, P.nrow_items, tot) &&
+            threadIdx.x == 0)
+            res64_finish<RES_TRUE>(st, tot, unscale);
+    }
+}
+
+// Kernel, shared memory and occupancy of one configuration and io type.
+struct BatchKernel {
+    void *fn = nullptr;
+    size_t smem = 0;
+};
+
+template <int TX, int TY, typename X>
+BatchKernel batch_kernel_of() {
+    constexpr int S = 4;
+    BatchKernel k;
+    k.fn = reinterpret_cast<void *>(&batch_kernel<TX, TY, S, X>);
+    k.smem = zmarch_smem_bytes<float, TX, TY, S, K_PASSA>();
+    return k;
+}
+
+template <typename X>
+BatchKernel batch_kernel_for(int cfg) {
+    switch (cfg) {
+        case BC_64x16: return batch_kernel_of<64, 16, X>();
+        case BC_128x8: return batch_kernel_of<128, 8, X>();
+        default: return batch_kernel_of<32, 32, X>();
+    }
+}
+
+// Geometry of one problem under a configuration.
+struct ProbGeom {
+    int tiles_x, tiles, zdepth, zchunks, nitems, rows_per_item, nrow_items;
+};
+ProbGeom prob_geom(const gbpcg_grid &g, int cfg) {
+    const BcDims d = bc_dims(cfg);
+    ProbGeom p;
+    p.tiles_x = (g.nx + d.tx - 1) / d.tx;
+    p.tiles = p.tiles_x * ((g.ny + d.ty - 1) / d.ty);
+    p.zdepth = std::min(g.nz, kBatchZDepth);
+    p.zchunks = (g.nz + p.zdepth - 1) / p.zdepth;
+    p.nitems = p.tiles * p.zchunks;
+    // at least kRowPoints points per row item, and few enough items for the partial-sum slots
+    p.rows_per_item = std::max({1, kRowPoints / g.nx, (g.ny * g.nz + 4095) / 4096});
+    p.nrow_items = (g.ny * g.nz + p.rows_per_item - 1) / p.rows_per_item;
+    return p;
+}
+
+struct BatchLayout {
+    size_t hdr, probs, items, rows, total;
+    int nitems, nrow_items;
+};
+
+// The batch's own region at the front of the workspace: header, problem
+// table, item-to-problem maps (sized for the configuration with the most
+// items, so one workspace serves every configuration).
+BatchLayout batch_layout(int nprob, const gbpcg_grid *grids) {
+    BatchLayout L;
+    int items = 0, rows = 0;
+    for (int c = 0; c < BC_COUNT; ++c) {
+        int it = 0, rw = 0;
+        for (int i = 0; i < nprob; ++i) {
+            const ProbGeom p = prob_geom(grids[i], c);
+            it += p.nitems;
+            rw += p.nrow_items;
+        }
+        items = std::max(items, it);
+        rows = std::max(rows, rw);
+    }
+    size_t o = 0;
+    L.hdr = o; o += round256(sizeof(BatchHeader));
+    L.probs = o; o += round256(sizeof(BatchProblem) * (size_t)nprob);
+    L.items = o; o += round256(sizeof(int) * (size_t)items);
+    L.rows = o; o += round256(sizeof(int) * (size_t)rows);
+    L.total = o;
+    L.nitems = items;
+    L.nrow_items = rows;
+    return L;
+}
+
+// Instantiated single-kernel graphs, keyed by everything they bake in.
+struct PersistKey {
+    std::vector<SolveKey> keys;
+    int cfg;
+};
+struct PersistGraph {
+    PersistKey key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_persist_mu;
+std::list<PersistGraph> g_persist;
+constexpr size_t kPersistMax = 8;
+
+bool same_key(const PersistKey &a, const PersistKey &b) {
+    if (a.cfg != b.cfg || a.keys.size() != b.keys.size()) return false;
+    for (size_t i = 0; i < a.keys.size(); ++i)
+        if (!(a.keys[i] == b.keys[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+bool batch_persistent_ok(int nprob, const gbpcg_grid *grids) {
+    for (int i = 0; i < nprob; ++i) {
+        const gbpcg_grid &g = grids[i];
+        if (g.k_block || g.nx % 4) return false;  // Poisson operator, 16-byte rows for the TMA boxes
+        for (int c = 0; c < BC_COUNT; ++c)
+            if (prob_geom(g, c).nitems * 2 > 4 * (int)kMaxPassBlocks) return false;
+    }
+    return true;
+}
+
+size_t batch_persistent_bytes(int nprob, const gbpcg_grid *grids) { return batch_layout(nprob, grids).total; }
+
+int batch_persistent_cfgs() { return BC_COUNT; }
+
+// Sets up the problem table in the workspace's batch region and launches the
+// persistent kernel (inside a cached one-node CUDA graph when the cooperative
+// launch can be captured, else directly).  calls[i] describes problem i
+// (its workspace piece, b, x); maxit caps the rounds.
+int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall *calls, char *region, int cfg,
+                            double tol, int maxit, int io, cudaStream_t s) {
+    const BatchLayout BL = batch_layout(nprob, grids);
+    const BcDims dims = bc_dims(cfg);
+    std::vector<BatchProblem> probs(nprob);
+    std::vector<int> item_prob, row_prob;
+    int nitems = 0, nrow = 0;
+    for (int i = 0; i < nprob; ++i) {
+        const gbpcg_grid &g = grids[i];
+        const SolveCall &c = calls[i];
+        const ProbGeom pg = prob_geom(g, cfg);
+        BatchProblem &P = probs[i];
+        memset(&P, 0, sizeof(P));
+        char *w = c.ws;
+        P.z = reinterpret_cast<float *>(w + c.L.z);
+        P.p0 = reinterpret_cast<float *>(w + c.L.p0);
+        P.p1 = reinterpret_cast<float *>(w + c.L.p1);
+        P.d = reinterpret_cast<float *>(w + c.L.d);
+        P.st = reinterpret_cast<SolveState *>(w + c.L.state);
+        P.partials = reinterpret_cast<double *>(w + c.L.partials);
+        if (!tma_ok(sizeof(float), g.nx, {P.z, P.p0, P.p1, P.d}))
+            return fail_arg("persistent batch: every grid needs nx a multiple of 4 (16-byte rows)");
+        // halo boxes (TX + 2 XH) x (TY + 2), centre boxes TX x TY, as the single-problem passes use
+        const int xh = 4;
+        int rc = 0;
+        rc |= make_map_3d(&P.hz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.z, g.nx, g.ny, g.nz, dims.tx + 2 * xh,
+                          dims.ty + 2, 1);
+        rc |= make_map_3d(&P.hp0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.p0, g.nx, g.ny, g.nz, dims.tx + 2 * xh,
+                          dims.ty + 2, 1);
+        rc |= make_map_3d(&P.hp1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.p1, g.nx, g.ny, g.nz, dims.tx + 2 * xh,
+                          dims.ty + 2, 1);
+        rc |= make_map_3d(&P.cd, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.d, g.nx, g.ny, g.nz, dims.tx, dims.ty, 1);
+        rc |= make_map_3d(&P.cz, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, P.z, g.nx, g.ny, g.nz, dims.tx, dims.ty, 1);
+        if (rc) return GBPCG_ERR_CUDA;
+        P.op = make_op_const(g.nx, g.ny, g.nz);
+        P.nx = g.nx; P.ny = g.ny; P.nz = g.nz;
+        P.tiles_x = pg.tiles_x; P.tiles = pg.tiles; P.zdepth = pg.zdepth; P.zchunks = pg.zchunks;
+        P.item0 = nitems; P.nitems = pg.nitems;
+        P.row0_item = nrow; P.nrow_items = pg.nrow_items; P.rows_per_item = pg.rows_per_item;
+        if ((size_t)pg.nitems * 2 > 4 * kMaxPassBlocks || (size_t)pg.nrow_items * 3 > 4 * kMaxPassBlocks)
+            return fail_arg("persistent batch: a grid has more work items than its partial-sum slots");
+        for (int k = 0; k < pg.nitems; ++k) item_prob.push_back(i);
+        for (int k = 0; k < pg.nrow_items; ++k) row_prob.push_back(i);
+        nitems += pg.nitems;
+        nrow += pg.nrow_items;
+        auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
+        Res64Args &ra = P.ra;
+        memset(&ra, 0, sizeof(ra));
+        ra.nx = g.nx; ra.ny = g.ny; ra.nz = g.nz;
+        ra.x = c.x; ra.b = c.b; ra.z = P.z; ra.d = P.d;
+        ra.cx = cc(g.nx); ra.cy = cc(g.ny); ra.cz = cc(g.nz);
+        ra.kb = nullptr; ra.kbx = ra.kby = ra.kbz = 1;
+        ra.tab64 = nullptr;
+        ra.bscale = nullptr;
+        ra.rhs_auto = 1;
+        ra.st = P.st;
+        ra.partials = P.partials;
+    }
+    BatchHeader *hdr = reinterpret_cast<BatchHeader *>(region + BL.hdr);
+    BatchProblem *dprobs = reinterpret_cast<BatchProblem *>(region + BL.probs);
+    int *ditems = reinterpret_cast<int *>(region + BL.items);
+    int *drows = reinterpret_cast<int *>(region + BL.rows);
+
+    const BatchKernel K = io == GBPCG_F64 ? batch_kernel_for<double>(cfg) : batch_kernel_for<float>(cfg);
+    GB_CUDA(cudaFuncSetAttribute(K.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K.smem));
+    int occ = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, K.fn, kBatchThreads, K.smem));
+    if (occ < 1) return fail_arg("persistent batch kernel does not fit an SM");
+    const unsigned grid = (unsigned)(occ * device_sm_count());
+
+    BatchArgs A;
+    A.probs = dprobs;
+    A.item_prob = ditems;
+    A.row_prob = drows;
+    A.hdr = hdr;
+    A.nprob = nprob;
+    A.nitems = nitems;
+    A.nrow_items = nrow;
+    A.tol = tol;
+    A.maxit = maxit;
+
+    // the table is copied on every call (the stream orders it before the kernel); its contents
+    // depend only on the key, so a cached graph stays valid
+    GB_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(ditems, item_prob.data(), sizeof(int) * item_prob.size(), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemcpyAsync(drows, row_prob.data(), sizeof(int) * row_prob.size(), cudaMemcpyHostToDevice, s));
+    GB_CUDA(cudaMemsetAsync(hdr, 0, sizeof(BatchHeader), s));
+    // the host arrays must outlive the copies
+    GB_CUDA(cudaStreamSynchronize(s));
+
+    void *kargs[] = {&A};
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kBatchThreads);
+    lc.dynamicSmemBytes = K.smem;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+
+    PersistKey key;
+    key.cfg = cfg;
+    key.keys.resize(nprob);
+    for (int i = 0; i < nprob; ++i) key.keys[i] = make_key<float>(calls[i], true);
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_persist_mu);
+        for (auto it = g_persist.begin(); it != g_persist.end(); ++it)
+            if (same_key(it->key, key)) {
+                g_persist.splice(g_persist.begin(), g_persist, it);
+                exec = g_persist.front().exec;
+                break;
+            }
+        if (!exec) {
+            cudaStream_t cs = nullptr;
+            GB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            lc.stream = cs;
+            cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                cudaError_t e2 = cudaLaunchKernelExC(&lc, K.fn, kargs);
+                cudaError_t e3 = cudaStreamEndCapture(cs, &graph);
+                e = e2 ? e2 : e3;
+            }
+            cudaGraphExec_t ex = nullptr;
+            if (!e) e = cudaGraphInstantiate(&ex, graph, 0);
+            cudaStreamDestroy(cs);
+            lc.stream = s;
+            if (e) {
+                // cooperative launches that cannot be captured run directly
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+            } else {
+                PersistGraph pg;
+                pg.key = key;
+                pg.graph = graph;
+                pg.exec = ex;
+                g_persist.push_front(pg);
+                while (g_persist.size() > kPersistMax) {
+                    cudaGraphExecDestroy(g_persist.back().exec);
+                    cudaGraphDestroy(g_persist.back().graph);
+                    g_persist.pop_back();
+                }
+                exec = ex;
+            }
+        }
+    }
+    if (exec) GB_CUDA(cudaGraphLaunch(exec, s));
+    else GB_CUDA(cudaLaunchKernelExC(&lc, K.fn, kargs));
+    return GBPCG_OK;
+}
+
+// Rounds run and whether a bounded barrier wait gave up, from the batch
+// region (enqueued on s; valid after it synchronises).
+int batch_persistent_header(const char *region, int *rounds_abort, cudaStream_t s) {
+    GB_CUDA(cudaMemcpyAsync(rounds_abort, region + offsetof(BatchHeader, abort), 2 * sizeof(int),
+                            cudaMemcpyDeviceToHost, s));
+    return GBPCG_OK;
+}
+
+}  // namespace gb

@@ -284,11 +284,25 @@ __device__ __forceinline__ void block_sum(const float (&v)[NV], double (&out)[NV
 // added in block order by a fixed tree, so the result does not depend on
 // which block came last.  The ticket is reset for the next launch.
 template <int NV, int NT>
+__device__ __forceinline__ bool group_sum_last(const double (&part)[NV], double *partials, unsigned int *ticket,
+                                               unsigned bid, unsigned nblk, double (&total)[NV]);
+
+template <int NV, int NT>
 __device__ __forceinline__ bool grid_sum_last(const double (&part)[NV], double *partials,
                                               unsigned int *ticket, double (&total)[NV]) {
-    __shared__ bool s_last;
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    return group_sum_last<NV, NT>(part, partials, ticket, bid, nblk, total);
+}
+
+// The same finish over a group of nblk contributions numbered bid = 0 ..
+// nblk - 1 (a persistent CTA may contribute several, one per work item):
+// returns true in the CTA whose contribution arrived last, with the sums
+// taken in contribution order.
+template <int NV, int NT>
+__device__ __forceinline__ bool group_sum_last(const double (&part)[NV], double *partials, unsigned int *ticket,
+                                               unsigned bid, unsigned nblk, double (&total)[NV]) {
+    __shared__ bool s_last;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) partials[(size_t)bid * NV + i] = part[i];

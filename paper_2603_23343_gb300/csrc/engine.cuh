@@ -321,84 +321,78 @@ __device__ __forceinline__ void manual_box(const T *src, T *dst, int nx, int ny,
     }
 }
 
+// The pointers and tensor maps one pass reads and writes for one problem.
+template <typename T, int KIND>
+struct MarchIO {
+    using TC = CenterT<T, KIND>;
+    const T *H0, *H1;
+    const TC *C0;
+    T *O0;
+    TC *O1;
+    const CUtensorMap *M0, *M1, *MC;
+};
+
+// The solver scalars a pass reads when it starts (iteration k = it).
+struct MarchScalars {
+    int it;
+    float alpha;       // pass B: alpha_k
+    float beta;        // pass A: beta_{k-1}
+    float alpha_prev;  // pass A: alpha_{k-1}, for the deferred d update
+    bool first;        // pass A: k == 0 (p_0 = z_0, no p_{k-1} to load)
+    bool do_x;         // pass A: d still lacks alpha_{k-1} p_{k-1}
+};
+
+template <int KIND>
+__device__ __forceinline__ MarchScalars read_scalars(const SolveState *st) {
+    MarchScalars sc{};
+    if constexpr (KIND == K_PASSA || KIND == K_PASSB) sc.it = st->it;
+    if constexpr (KIND == K_PASSA) {
+        sc.first = (sc.it == 0);
+        sc.beta = (float)st->beta;
+        sc.alpha_prev = (float)st->alpha;
+        sc.do_x = st->pending != 0;
+    }
+    if constexpr (KIND == K_PASSB) sc.alpha = (float)st->alpha;
+    return sc;
+}
+
 // ZFILL (an ablation of Sec. VI-C, off in every solver path): after each
 // TMA box lands, tiles that touch the domain boundary also zero the
 // out-of-grid part of the box explicitly, the work the paper's kernels do by
 // hand; here the TMA unit has already written those zeros, so the variant
 // measures what explicit zero filling would cost.
-template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op, bool ZFILL = false>
-__global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
-    zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
+//
+// One CTA marches one tile (x0, y0) through planes [k0, k1) and adds its
+// points' partial sums into acc.  Loads go round an S-stage ring whose
+// stages and mbarrier phases continue from `ring` (the loads the CTA issued
+// before: a persistent CTA marches many tiles through one ring); the
+// function returns the number of loads this march issued.  A wait that runs
+// out sets *s_timeout; the march then stops, waits (bounded) for its copies
+// still in flight and returns.
+template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op, bool ZFILL>
+__device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *full, volatile int *s_timeout,
+                                               uint32_t ring, const MarchIO<T, KIND> &io, const Op &op, int nx,
+                                               int ny, int nz, int x0, int y0, int k0, int k1, const MarchScalars &sc,
+                                               float (&acc)[Geometry<T, TX, TY, KIND>::NV > 0
+                                                                ? Geometry<T, TX, TY, KIND>::NV
+                                                                : 1]) {
     static_assert(S >= 2, "a stage is refilled only after the step that reads it as the output plane");
     using G = Geometry<T, TX, TY, KIND>;
     using TC = CenterT<T, KIND>;
-    constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, NV = G::NV, V = G::V;
+    constexpr int NT = G::NT, XH = G::XH, HX = G::HX, NH = G::NH, V = G::V;
     constexpr uint32_t HB = G::HB, SB = G::SB;
+    if (k0 >= k1) return 0;
 
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[S];
-    __shared__ int s_timeout;
-
-    SolveState *st = a.st;
-    int it = 0;
-    float alpha = 0.f, beta = 0.f, alpha_prev = 0.f;
-    bool first = false, do_x = false;
-    if constexpr (KIND == K_PASSA || KIND == K_PASSB) {
-        if (st->done) return;  // uniform across the grid
-        it = st->it;
-    }
-    if constexpr (KIND == K_PASSA) {
-        first = (it == 0);
-        beta = (float)st->beta;
-        alpha_prev = (float)st->alpha;
-        do_x = st->pending != 0;
-    }
-    if constexpr (KIND == K_PASSB) alpha = (float)st->alpha;
-
-    int sh0 = 0, sh1 = 0, so0 = 0;
-    if constexpr (KIND == K_PASSA) { sh1 = (it + 1) & 1; so0 = it & 1; }
-    if constexpr (KIND == K_PASSB) sh0 = it & 1;
-    const T *H0 = static_cast<const T *>(a.h0[sh0]);
-    const T *H1 = static_cast<const T *>(a.h1[sh1]);
-    const TC *C0 = static_cast<const TC *>(a.c0);
-    T *O0 = static_cast<T *>(a.o0[so0]);
-    TC *O1 = static_cast<TC *>(a.o1);
-    const CUtensorMap *M0 = &maps.h0[sh0];
-    const CUtensorMap *M1 = &maps.h1[sh1];
-    const CUtensorMap *MC = &maps.c0;
-
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int tile = blockIdx.x;
-    const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
-    int k0, k1;  // this CTA's planes [k0, k1): part blockIdx.y % zparts of chunk blockIdx.y / zparts
-    {
-        const int parts = max(a.zparts, 1);
-        const int c = (int)blockIdx.y / parts, part = (int)blockIdx.y - c * parts;
-        const int c0 = c * a.zchunk, c1 = min(nz, c0 + a.zchunk), sub = (a.zchunk + parts - 1) / parts;
-        k0 = min(c1, c0 + part * sub);
-        k1 = min(c1, k0 + sub);
-    }
     const int lx = threadIdx.x % (TX / V), ly = threadIdx.x / (TX / V);
     const int gx = x0 + V * lx, gy = y0 + ly;
     bool ok[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) ok[i] = gy < ny && gx + i < nx;
 
+    const bool first = sc.first, do_x = sc.do_x;
+    const float alpha = sc.alpha, beta = sc.beta, alpha_prev = sc.alpha_prev;
     const bool load_h1 = NH == 2 && !first;
     const bool load_c = G::NC == 1 && !(KIND == K_PASSA && !do_x);
-
-    float acc[NV > 0 ? NV : 1];
-#pragma unroll
-    for (int i = 0; i < (NV > 0 ? NV : 1); ++i) acc[i] = 0.f;
-
-    if (threadIdx.x == 0) {
-        s_timeout = 0;
-        if constexpr (TMA) {
-            for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-            fence_mbar_init();
-        }
-    }
-    __syncthreads();
 
     // Planes are visited in march order: step t = 0..tl loads plane pl(t),
     // forward pl(t) = k0 - 1 + t, reverse pl(t) = k1 - t (the first and the
@@ -409,26 +403,28 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     constexpr bool REV = KIND == K_PASSB;
     const int tl = k1 - k0 + 1;
     auto plane = [&](int t) { return REV ? k1 - t : k0 - 1 + t; };
+    auto stage = [&](int t) { return (int)((ring + (uint32_t)t) % S); };
+    auto parity = [&](int t) { return (uint32_t)(((ring + (uint32_t)t) / S) & 1u); };
 
     auto issue = [&](int t) {
         const int m = plane(t);
-        const int s = t % S;
+        const int s = stage(t);
         unsigned char *base = smem + (size_t)s * SB;
         const bool cen = load_c && t >= 1 && t < tl;
         if constexpr (TMA) {
             if (threadIdx.x == 0) {
                 const uint32_t bytes = G::HBYTES + (load_h1 ? G::HBYTES : 0u) + (cen ? G::CBYTES : 0u);
                 mbar_arrive_expect_tx(&full[s], bytes);
-                tma_load_3d(base, M0, &full[s], x0 - XH, y0 - 1, m);
-                if (load_h1) tma_load_3d(base + HB, M1, &full[s], x0 - XH, y0 - 1, m);
-                if (cen) tma_load_3d(base + NH * HB, MC, &full[s], x0, y0, m);
+                tma_load_3d(base, io.M0, &full[s], x0 - XH, y0 - 1, m);
+                if (load_h1) tma_load_3d(base + HB, io.M1, &full[s], x0 - XH, y0 - 1, m);
+                if (cen) tma_load_3d(base + NH * HB, io.MC, &full[s], x0, y0, m);
             }
         } else {
-            manual_box<T, NT>(H0, reinterpret_cast<T *>(base), nx, ny, nz, x0 - XH, y0 - 1, m, HX, TY + 2);
+            manual_box<T, NT>(io.H0, reinterpret_cast<T *>(base), nx, ny, nz, x0 - XH, y0 - 1, m, HX, TY + 2);
             if (load_h1)
-                manual_box<T, NT>(H1, reinterpret_cast<T *>(base + HB), nx, ny, nz, x0 - XH, y0 - 1, m, HX,
+                manual_box<T, NT>(io.H1, reinterpret_cast<T *>(base + HB), nx, ny, nz, x0 - XH, y0 - 1, m, HX,
                                   TY + 2);
-            if (cen) manual_box<TC, NT>(C0, reinterpret_cast<TC *>(base + NH * HB), nx, ny, nz, x0, y0, m, TX, TY);
+            if (cen) manual_box<TC, NT>(io.C0, reinterpret_cast<TC *>(base + NH * HB), nx, ny, nz, x0, y0, m, TX, TY);
             __syncthreads();
         }
     };
@@ -455,117 +451,207 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
 
     int issued_hi = -1;
     int consumed = -1;
-    if (k0 < k1) {
-        for (int t = 0; t <= tl && t < S; ++t) {
-            issue(t);
-            issued_hi = t;
+    for (int t = 0; t <= tl && t < S; ++t) {
+        issue(t);
+        issued_hi = t;
+    }
+    float qa[V], qb[V], qc[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) qa[i] = qb[i] = qc[i] = 0.f;
+    typename Op::Cache opc;
+    const int cidx = (ly + 1) * HX + XH + V * lx;  // this thread's first point in a halo box
+    for (int t = 0; t <= tl; ++t) {
+        const int s = stage(t);
+        const unsigned char *base = smem + (size_t)s * SB;
+        if constexpr (TMA) {
+            if (!mbar_wait_bounded(&full[s], parity(t))) *s_timeout = 1;
         }
-        float qa[V], qb[V], qc[V];
-#pragma unroll
-        for (int i = 0; i < V; ++i) qa[i] = qb[i] = qc[i] = 0.f;
-        typename Op::Cache opc;
-        const int cidx = (ly + 1) * HX + XH + V * lx;  // this thread's first point in a halo box
-        for (int t = 0; t <= tl; ++t) {
-            const int s = t % S;
-            const unsigned char *base = smem + (size_t)s * SB;
-            if constexpr (TMA) {
-                if (!mbar_wait_bounded(&full[s], (t / S) & 1)) s_timeout = 1;
-            }
-            consumed = t;
-            if constexpr (ZFILL) {
-                const int m = plane(t);
-                const bool edge = m < 0 || m >= nz || x0 - XH < 0 || x0 + TX + XH > nx || y0 - 1 < 0 ||
-                                  y0 + TY + 1 > ny;
-                if (edge) {
-                    T *hb = reinterpret_cast<T *>(smem + (size_t)s * SB);
-                    for (int e = threadIdx.x; e < HX * G::HY; e += NT) {
-                        const int r = e / HX, c = e - r * HX;
-                        const int bx = x0 - XH + c, by = y0 - 1 + r;
-                        if (m < 0 || m >= nz || bx < 0 || bx >= nx || by < 0 || by >= ny) hb[e] = from_f<T>(0.0f);
-                    }
-                    // generic-proxy writes before the TMA refills this stage
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        consumed = t;
+        if constexpr (ZFILL) {
+            const int m = plane(t);
+            const bool edge = m < 0 || m >= nz || x0 - XH < 0 || x0 + TX + XH > nx || y0 - 1 < 0 ||
+                              y0 + TY + 1 > ny;
+            if (edge) {
+                T *hb = reinterpret_cast<T *>(smem + (size_t)s * SB);
+                for (int e = threadIdx.x; e < HX * G::HY; e += NT) {
+                    const int r = e / HX, c = e - r * HX;
+                    const int bx = x0 - XH + c, by = y0 - 1 + r;
+                    if (m < 0 || m >= nz || bx < 0 || bx >= nx || by < 0 || by >= ny) hb[e] = from_f<T>(0.0f);
                 }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int i = 0; i < V; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
-            in_valv(base, cidx, qc);
-            if (t >= 2) {
-                // ---- output plane k = pl(t-1) from its own stage ----
-                const int k = plane(t - 1);
-                const unsigned char *bk = smem + (size_t)((t - 1) % S) * SB;
-                float ym[V], yp[V];
-                in_valv(bk, cidx - HX, ym);
-                in_valv(bk, cidx + HX, yp);
-                // whole-row tiles: the x neighbours past either end of the row are
-                // boundary zeros (the box holds no x halo)
-                const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
-                const float xr = (full_row<TX>() && lx == TX / V - 1) ? 0.0f : in_val(bk, cidx + V);
-                float q[V], dg[V];
-                op.template applyv<V>(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q,
-                                      dg);
-                const size_t g = ((size_t)k * ny + gy) * nx + gx;
-                const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + V * lx;
-                float out0[V], out1[V];
-                bool st1 = false;
-                if constexpr (KIND == K_STENCIL) {
-#pragma unroll
-                    for (int i = 0; i < V; ++i) out0[i] = q[i] * a.scale;
-                } else if constexpr (KIND == K_PASSA) {
-#pragma unroll
-                    for (int i = 0; i < V; ++i) {
-                        out0[i] = qb[i];
-                        if (ok[i]) acc[0] = fmaf(qb[i], q[i], acc[0]);
-                    }
-                    if (do_x) {
-                        float xv[V], po[V];
-                        ldv<TC, V>(cen, xv);
-                        ldv<T, V>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
-#pragma unroll
-                        for (int i = 0; i < V; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
-                        st1 = true;
-                    }
-                } else {  // K_PASSB
-                    float zv[V];
-                    ldv<TC, V>(cen, zv);
-#pragma unroll
-                    for (int i = 0; i < V; ++i) {
-                        const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
-                        const float z = Op::kConst ? r * op.inv_d : r / dg[i];
-                        out0[i] = z;
-                        if (ok[i]) {
-                            acc[0] = fmaf(r, r, acc[0]);
-                            acc[1] = fmaf(r, z, acc[1]);
-                        }
-                    }
-                }
-                if (ok[0] && ok[V - 1] && TMA) {
-                    stv<T, V>(O0 + g, out0);
-                    if (st1) stv<TC, V>(O1 + g, out1);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < V; ++i)
-                        if (ok[i]) {
-                            O0[g + i] = from_f<T>(out0[i]);
-                            if (st1) O1[g + i] = from_f<TC>(out1[i]);
-                        }
-                }
+                // generic-proxy writes before the TMA refills this stage
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             }
             __syncthreads();
-            if (s_timeout) break;
-            if (t >= 1 && t - 1 + S <= tl) {
-                issue(t - 1 + S);
-                issued_hi = t - 1 + S;
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
+        in_valv(base, cidx, qc);
+        if (t >= 2) {
+            // ---- output plane k = pl(t-1) from its own stage ----
+            const int k = plane(t - 1);
+            const unsigned char *bk = smem + (size_t)stage(t - 1) * SB;
+            float ym[V], yp[V];
+            in_valv(bk, cidx - HX, ym);
+            in_valv(bk, cidx + HX, yp);
+            // whole-row tiles: the x neighbours past either end of the row are
+            // boundary zeros (the box holds no x halo)
+            const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
+            const float xr = (full_row<TX>() && lx == TX / V - 1) ? 0.0f : in_val(bk, cidx + V);
+            float q[V], dg[V];
+            op.template applyv<V>(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q,
+                                  dg);
+            const size_t g = ((size_t)k * ny + gy) * nx + gx;
+            const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + V * lx;
+            float out0[V], out1[V];
+            bool st1 = false;
+            if constexpr (KIND == K_STENCIL) {
+                (void)alpha;
+#pragma unroll
+                for (int i = 0; i < V; ++i) out0[i] = q[i] * sc.alpha;  // alpha carries the output scale
+            } else if constexpr (KIND == K_PASSA) {
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    out0[i] = qb[i];
+                    if (ok[i]) acc[0] = fmaf(qb[i], q[i], acc[0]);
+                }
+                if (do_x) {
+                    float xv[V], po[V];
+                    ldv<TC, V>(cen, xv);
+                    ldv<T, V>(reinterpret_cast<const T *>(bk + HB) + cidx, po);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
+                    st1 = true;
+                }
+            } else {  // K_PASSB
+                float zv[V];
+                ldv<TC, V>(cen, zv);
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
+                    const float z = Op::kConst ? r * op.inv_d : r / dg[i];
+                    out0[i] = z;
+                    if (ok[i]) {
+                        acc[0] = fmaf(r, r, acc[0]);
+                        acc[1] = fmaf(r, z, acc[1]);
+                    }
+                }
+            }
+            if (ok[0] && ok[V - 1] && TMA) {
+                stv<T, V>(io.O0 + g, out0);
+                if (st1) stv<TC, V>(io.O1 + g, out1);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (ok[i]) {
+                        io.O0[g + i] = from_f<T>(out0[i]);
+                        if (st1) io.O1[g + i] = from_f<TC>(out1[i]);
+                    }
             }
         }
+        __syncthreads();
+        if (*s_timeout) break;
+        if (t >= 1 && t - 1 + S <= tl) {
+            issue(t - 1 + S);
+            issued_hi = t - 1 + S;
+        }
+    }
+    if constexpr (TMA) {
+        if (*s_timeout) {
+            // give copies still in flight a bounded chance to land before exit
+            for (int t = consumed + 1; t <= issued_hi; ++t) mbar_wait_bounded(&full[stage(t)], parity(t));
+        }
+    }
+    return (uint32_t)(issued_hi + 1);
+}
+
+// Pass A's last-CTA step: alpha_k = rz / pq, or BREAKDOWN.
+__device__ __forceinline__ void passa_finish(SolveState *st, double pq, bool tmo) {
+    st->pq = pq;
+    st->pending = 0;
+    st->replace = 0;
+    if (!(pq > 0.0) || !isfinite(pq)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+    else st->alpha = st->rz / pq;
+    if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
+}
+
+// Pass B's last-CTA step: beta_k, the convergence test and the residual-
+// replacement trigger.
+__device__ __forceinline__ void passb_finish(SolveState *st, int it, double rr, double rz, bool tmo) {
+    st->it = it + 1;
+    st->rr = rr;
+    st->pending = 1;
+    if (!isfinite(rr) || !isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+    else if (rr <= st->tol2 * st->bb || rr <= kReplaceDrop2 * st->rr_rep) {
+        // flush d into x and recompute r = b - A x in FP64 before deciding
+        // (the replacement pass sets beta and the flags); 2 marks a
+        // confirmation of convergence
+        st->replace = rr <= st->tol2 * st->bb ? 2 : 1;
+    } else if (it + 1 >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+    else { st->beta = rz / st->rz; st->rz = rz; }
+    if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
+}
+
+template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op, bool ZFILL = false>
+__global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
+    zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
+    using G = Geometry<T, TX, TY, KIND>;
+    using TC = CenterT<T, KIND>;
+    constexpr int NT = G::NT, NV = G::NV;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ int s_timeout;
+
+    SolveState *st = a.st;
+    if constexpr (KIND == K_PASSA || KIND == K_PASSB) {
+        if (st->done) return;  // uniform across the grid
+    }
+    MarchScalars sc = read_scalars<KIND>(st);
+    if constexpr (KIND == K_STENCIL) sc.alpha = a.scale;
+    const int it = sc.it;
+
+    int sh0 = 0, sh1 = 0, so0 = 0;
+    if constexpr (KIND == K_PASSA) { sh1 = (it + 1) & 1; so0 = it & 1; }
+    if constexpr (KIND == K_PASSB) sh0 = it & 1;
+    MarchIO<T, KIND> io;
+    io.H0 = static_cast<const T *>(a.h0[sh0]);
+    io.H1 = static_cast<const T *>(a.h1[sh1]);
+    io.C0 = static_cast<const TC *>(a.c0);
+    io.O0 = static_cast<T *>(a.o0[so0]);
+    io.O1 = static_cast<TC *>(a.o1);
+    io.M0 = &maps.h0[sh0];
+    io.M1 = &maps.h1[sh1];
+    io.MC = &maps.c0;
+
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tiles_x) * TX, y0 = (tile / a.tiles_x) * TY;
+    int k0, k1;  // this CTA's planes [k0, k1): part blockIdx.y % zparts of chunk blockIdx.y / zparts
+    {
+        const int parts = max(a.zparts, 1);
+        const int c = (int)blockIdx.y / parts, part = (int)blockIdx.y - c * parts;
+        const int c0 = c * a.zchunk, c1 = min(nz, c0 + a.zchunk), sub = (a.zchunk + parts - 1) / parts;
+        k0 = min(c1, c0 + part * sub);
+        k1 = min(c1, k0 + sub);
+    }
+
+    float acc[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int i = 0; i < (NV > 0 ? NV : 1); ++i) acc[i] = 0.f;
+
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
         if constexpr (TMA) {
-            if (s_timeout) {
-                // give copies still in flight a bounded chance to land before exit
-                for (int t = consumed + 1; t <= issued_hi; ++t) mbar_wait_bounded(&full[t % S], (t / S) & 1);
-                if (threadIdx.x == 0) atomicExch(&st->timeout, 1);
-            }
+            for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+            fence_mbar_init();
         }
+    }
+    __syncthreads();
+
+    march_tile<T, TX, TY, S, KIND, TMA, Op, ZFILL>(smem, full, &s_timeout, 0u, io, op, nx, ny, nz, x0, y0, k0, k1,
+                                                   sc, acc);
+    if constexpr (TMA) {
+        if (s_timeout && threadIdx.x == 0) atomicExch(&st->timeout, 1);
     }
 
     if constexpr (NV > 0) {
@@ -574,28 +660,8 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
         if (grid_sum_last<NV, NT>(part, a.partials, &st->ticket[KIND], tot) && threadIdx.x == 0) {
             __threadfence();
             const bool tmo = atomicAdd(&st->timeout, 0) != 0;
-            if constexpr (KIND == K_PASSA) {
-                const double pq = tot[0];
-                st->pq = pq;
-                st->pending = 0;
-                st->replace = 0;
-                if (!(pq > 0.0) || !isfinite(pq)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
-                else st->alpha = st->rz / pq;
-            } else {
-                const double rr = tot[0], rz = tot[1];
-                st->it = it + 1;
-                st->rr = rr;
-                st->pending = 1;
-                if (!isfinite(rr) || !isfinite(rz) || !(rz > 0.0)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
-                else if (rr <= st->tol2 * st->bb || rr <= kReplaceDrop2 * st->rr_rep) {
-                    // flush d into x and recompute r = b - A x in FP64 before
-                    // deciding (the replacement pass sets beta and the flags);
-                    // 2 marks a confirmation of convergence
-                    st->replace = rr <= st->tol2 * st->bb ? 2 : 1;
-                } else if (it + 1 >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
-                else { st->beta = rz / st->rz; st->rz = rz; }
-            }
-            if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
+            if constexpr (KIND == K_PASSA) passa_finish(st, tot[0], tmo);
+            else passb_finish(st, it, tot[0], tot[1], tmo);
             if (a.use_cond) {
                 cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
                 cudaGraphSetConditional(a.cond_replace, st->replace ? 1u : 0u);

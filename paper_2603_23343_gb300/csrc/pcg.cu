@@ -469,6 +469,120 @@ static int autotune_one(const gbpcg_grid &g, const gbpcg_opts &o, const void *b,
     return GBPCG_OK;
 }
 
+namespace {
+// Persistent-kernel tile configuration per batch (device, io type, every problem's shape).
+std::mutex g_ptune_mu;
+std::map<std::vector<int>, int> g_ptune;
+}  // namespace
+
+// The batch as one persistent kernel (batch.cu); the workspace starts with
+// its tables, problem i's piece sits at off[i].  With GBPCG_FLAG_AUTOTUNE
+// each tile configuration is timed over 12 rounds into the pieces' scratch
+// x (b only read) and the fastest is kept for this set of shapes.
+static int persistent_batch(int nprob, const gbpcg_grid *grids, const void *const *b, void *const *x,
+                            const gbpcg_opts *opts, gbpcg_result *results, char *ws, const std::vector<WsLayout> &L,
+                            const std::vector<size_t> &off, cudaStream_t s) {
+    auto make_calls = [&](bool scratch) {
+        std::vector<SolveCall> calls(nprob);
+        for (int i = 0; i < nprob; ++i) {
+            char *w = ws + off[i];
+            void *xi = scratch ? static_cast<void *>(w + L[i].total) : x[i];
+            calls[i] = SolveCall{&grids[i], 0, 0, b[i], xi, w, L[i], opts->tol, opts->maxit, opts->io_dtype, 1.0f,
+                                 nullptr};
+        }
+        return calls;
+    };
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<int> tkey{dev, opts->io_dtype};
+    for (int i = 0; i < nprob; ++i) {
+        tkey.push_back(grids[i].nx);
+        tkey.push_back(grids[i].ny);
+        tkey.push_back(grids[i].nz);
+    }
+    int cfg = 0;
+    if (opts->tile_cfg) {
+        cfg = (opts->tile_cfg & 0xff) - 1;
+        if (cfg < 0 || cfg >= batch_persistent_cfgs() || (opts->tile_cfg >> 8))
+            return fail_arg("persistent batch: tile_cfg must be 1, 2 or 3 (64x16, 128x8, 32x32 tiles)");
+    } else if (opts->flags & GBPCG_FLAG_AUTOTUNE) {
+        int found = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_ptune_mu);
+            auto it = g_ptune.find(tkey);
+            if (it != g_ptune.end()) found = it->second;
+        }
+        if (found < 0) {
+            const std::vector<SolveCall> sc = make_calls(true);
+            double best = 1e300;
+            cudaEvent_t t0, t1;
+            GB_CUDA(cudaEventCreate(&t0));
+            GB_CUDA(cudaEventCreate(&t1));
+            for (int c = 0; c < batch_persistent_cfgs(); ++c) {
+                for (int i = 0; i < nprob; ++i)
+                    GB_CUDA(cudaMemsetAsync(sc[i].x, 0, (size_t)grids[i].nx * grids[i].ny * grids[i].nz *
+                                                            dtype_size(opts->io_dtype), s));
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {  // the first run builds the graph
+                    if (int rc = batch_persistent_launch(nprob, grids, sc.data(), ws, c, 0.0, 12, opts->io_dtype, s))
+                        return rc;
+                    GB_CUDA(cudaEventRecord(t0, s));
+                    if (int rc = batch_persistent_launch(nprob, grids, sc.data(), ws, c, 0.0, 12, opts->io_dtype, s))
+                        return rc;
+                    GB_CUDA(cudaEventRecord(t1, s));
+                    GB_CUDA(cudaEventSynchronize(t1));
+                    GB_CUDA(cudaEventElapsedTime(&ms, t0, t1));
+                }
+                if (ms < best) {
+                    best = ms;
+                    found = c;
+                }
+            }
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            std::lock_guard<std::mutex> lk(g_ptune_mu);
+            g_ptune[tkey] = found;
+        }
+        cfg = found;
+    }
+    const std::vector<SolveCall> calls = make_calls(false);
+    cudaEvent_t e0, e1;
+    GB_CUDA(cudaEventCreate(&e0));
+    GB_CUDA(cudaEventCreate(&e1));
+    struct Ev { cudaEvent_t a, b; ~Ev() { cudaEventDestroy(a); cudaEventDestroy(b); } } guard{e0, e1};
+    GB_CUDA(cudaEventRecord(e0, s));
+    if (int rc = batch_persistent_launch(nprob, grids, calls.data(), ws, cfg, opts->tol, opts->maxit, opts->io_dtype,
+                                         s))
+        return rc;
+    GB_CUDA(cudaEventRecord(e1, s));
+    std::vector<SolveState> hs(nprob);
+    for (int i = 0; i < nprob; ++i)
+        GB_CUDA(cudaMemcpyAsync(&hs[i], ws + off[i] + L[i].state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    int hdr[2] = {0, 0};  // abort, rounds
+    if (int rc = batch_persistent_header(ws, hdr, s)) return rc;
+    GB_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int worst = GBPCG_OK;
+    for (int i = 0; i < nprob; ++i) {
+        gbpcg_result &r = results[i];
+        memset(&r, 0, sizeof(r));
+        r.iters = hs[i].it;
+        r.status = hs[i].status;
+        if (hdr[0] && !(hs[i].done && hs[i].status == GBPCG_OK)) r.status = GBPCG_TIMEOUT;
+        r.rel_res_recursive = hs[i].bb > 0 ? sqrt(hs[i].rr / hs[i].bb) : 0.0;
+        r.rel_res_true = hs[i].bb_true > 0 ? sqrt(hs[i].rr_true / hs[i].bb_true) : 0.0;
+        r.time_ms = ms;
+        r.replacements = hs[i].n_replace;
+        r.pass_launches[0] = 1;        // kernel launches of the whole batch
+        r.pass_launches[1] = hdr[1];   // rounds the persistent kernel ran
+        r.pass_ctas[0] = cfg;          // persistent tile configuration used
+        if (r.status != GBPCG_OK && worst == GBPCG_OK) worst = r.status;
+    }
+    if (hdr[0]) set_error("a bounded grid-barrier wait of the persistent batch kernel timed out");
+    return worst;
+}
+
 static int check_batch(int32_t nprob, const gbpcg_grid *grids, const gbpcg_opts *opts) {
     if (nprob <= 0 || nprob > 4096) return fail_arg("nprob must be in 1..4096");
     if (!grids) return fail_arg("grids is NULL");
@@ -623,7 +737,7 @@ int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const g
     clear_error();
     if (int rc = check_batch(nprob, grids, opts)) return rc;
     if (!bytes) return fail_arg("bytes is NULL");
-    size_t total = 0;
+    size_t total = round256(batch_persistent_bytes(nprob, grids));  // the persistent kernel's tables
     for (int i = 0; i < nprob; ++i) {
         WsLayout L;
         total += batch_piece(grids[i], *opts, &L);
@@ -644,7 +758,8 @@ int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *
         if ((reinterpret_cast<uintptr_t>(b[i]) | reinterpret_cast<uintptr_t>(x[i])) & (esz - 1))
             return fail_arg("b[i] and x[i] must be aligned to their element size");
     }
-    size_t need = 0;
+    const size_t region = round256(batch_persistent_bytes(nprob, grids));
+    size_t need = region;
     std::vector<WsLayout> L(nprob);
     std::vector<size_t> off(nprob);
     for (int i = 0; i < nprob; ++i) {
@@ -656,6 +771,9 @@ int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *
     if (reinterpret_cast<uintptr_t>(opts->workspace) & 255u) return fail_arg("workspace must be 256-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(opts->workspace);
+
+    if (!(opts->flags & GBPCG_FLAG_BATCH_GRAPH) && batch_persistent_ok(nprob, grids))
+        return persistent_batch(nprob, grids, b, x, opts, results, ws, L, off, s);
 
     // tile configurations: explicit, autotuned (cached per shape), or the defaults
     std::vector<SolveCall> calls(nprob);

@@ -148,11 +148,17 @@ struct KahanF {
 // FP64 pipe busy (about 40 us per FP64 operation per point at 256^3,
 // measured), and the FP64 operations of a replacement drop from 16 (stencil,
 // b - A x, two FP64 dot products) to 11.
+template <int MODE>
+constexpr int res64_nv() { return MODE == RES_INIT ? 3 : MODE == RES_REPLACE ? 2 : 1; }
+
+// One CTA's part of the residual sums over rows row0, row0 + rstep, ...
+// below row1 (a row = nx consecutive points, row index j + ny k); the
+// block sums land in part[] (valid in thread 0) and *unscale receives the
+// factor that undoes the sums' power-of-two scaling.
 template <int MODE, typename X, typename Bt, bool BLOCK, typename T>
-__global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
-    SolveState *st = a.st;
-    if (MODE == RES_REPLACE && (!st->replace || st->done)) return;
-    if (MODE == RES_TRUE && st->true_known) return;
+__device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row1, int rstep,
+                                           double (&part)[res64_nv<MODE>()], double *unscale_out) {
+    const SolveState *st = a.st;
     const X *__restrict__ x = static_cast<const X *>(a.x);
     const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -173,17 +179,17 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
             unscale = ldexp(1.0, 2 * e);
         }
     }
+    *unscale_out = unscale;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     KahanF k0, k1;
     double w[6];
     face_weights64<false>(w, 0, 0, 0, nx, ny, nz, cf);
     const float dg_const = diag64(w);
-    const int rows = ny * nz;
     // plain solves work on s b and s x: r = s (b - A x) (one more FP64 multiply, only when s != 1)
     const double s_rhs = a.rhs_auto ? rhs_scale(st->rhs_bits) : 1.0;
     auto sweep = [&](auto scaled_tag) {
         constexpr bool SC = decltype(scaled_tag)::value;
-        for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+        for (int row = row0; row < row1; row += rstep) {
             const int j = row % ny, k = row / ny;
             const int64_t base = (int64_t)row * nx;
             for (int i = threadIdx.x; i < nx; i += 256) {
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
         s0 = k0.value();
         s1 = k1.value();
     }
-    constexpr int NV = MODE == RES_INIT ? 3 : MODE == RES_REPLACE ? 2 : 1;
+    constexpr int NV = res64_nv<MODE>();
     __shared__ double red[8][3];
     s0 = warp_sum(s0);
     if (NV > 1) s1 = warp_sum(s1);
@@ -233,21 +239,28 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
         red[threadIdx.x >> 5][2] = s2;
     }
     __syncthreads();
-    double part[NV], tot[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) part[v] = 0.0;
     if (threadIdx.x == 0)
         for (int wi = 0; wi < 8; ++wi)
 #pragma unroll
             for (int v = 0; v < NV; ++v) part[v] += red[wi][v];
-    if (!grid_sum_last<NV, 256>(part, a.partials, &st->ticket[4 + MODE], tot) || threadIdx.x != 0) return;
+    __syncthreads();  // red is reused by the next call
+}
+
+// The last contribution's step after the residual sums (thread 0):
+// RES_TRUE records the reported true residual, RES_INIT the start state,
+// RES_REPLACE the replacement's decisions.
+template <int MODE>
+__device__ __forceinline__ void res64_finish(SolveState *st, const double (&tot)[res64_nv<MODE>()],
+                                             double unscale) {
     if (MODE == RES_TRUE) {
         st->rr_true = tot[0] * unscale;
         st->bb_true = st->bb;
         return;
     }
     if (MODE == RES_INIT) {
-        const double rr = tot[0], rz = tot[1], bb = tot[2];
+        const double rr = tot[0], rz = tot[1], bb = tot[2 < res64_nv<MODE>() ? 2 : 0];
         st->bb = bb; st->rr = rr; st->rz = rz; st->rr_rep = rr; st->rr_conf = kHuge;
         st->it = 0; st->pending = 0; st->zero_x = 0; st->replace = 0; st->true_known = 0;
         if (bb == 0.0) { st->zero_x = 1; st->done = 1; st->status = GBPCG_OK; }
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
         else if (st->maxit <= 0) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
         else { st->done = 0; st->status = GBPCG_NOT_CONVERGED; }
     } else {
-        const double rrt = tot[0] * unscale, rzt = tot[1] * unscale;
+        const double rrt = tot[0] * unscale, rzt = tot[1 < res64_nv<MODE>() ? 1 : 0] * unscale;
         const int kind = st->replace;  // 1: two decades of progress, 2: recursive residual met tol
         st->rr = rrt;
         st->rr_rep = rrt;
@@ -280,6 +293,19 @@ __global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
             st->bb_true = st->bb;
         }
     }
+}
+
+template <int MODE, typename X, typename Bt, bool BLOCK, typename T>
+__global__ void __launch_bounds__(256) residual64_kernel(const Res64Args a) {
+    SolveState *st = a.st;
+    if (MODE == RES_REPLACE && (!st->replace || st->done)) return;
+    if (MODE == RES_TRUE && st->true_known) return;
+    constexpr int NV = res64_nv<MODE>();
+    double part[NV], tot[NV], unscale = 1.0;
+    res64_rows<MODE, X, Bt, BLOCK, T>(a, blockIdx.x, a.ny * a.nz, gridDim.x, part, &unscale);
+    if (!grid_sum_last<NV, 256>(part, a.partials, &st->ticket[4 + MODE], tot) || threadIdx.x != 0) return;
+    res64_finish<MODE>(st, tot, unscale);
+    if (MODE == RES_TRUE) return;
     if (a.use_cond) cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
 }
 
@@ -862,6 +888,14 @@ int solve_host_loop(const SolveCall &c, bool tma, cudaStream_t s) {
         return plan.run_host_loop(s);
     });
 }
+
+// Many constant-coefficient problems in one persistent kernel (batch.cu).
+bool batch_persistent_ok(int nprob, const gbpcg_grid *grids);
+size_t batch_persistent_bytes(int nprob, const gbpcg_grid *grids);
+int batch_persistent_cfgs();
+int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall *calls, char *region, int cfg,
+                            double tol, int maxit, int io, cudaStream_t s);
+int batch_persistent_header(const char *region, int *abort_rounds, cudaStream_t s);
 
 // The split-kernel FP32 solver with host-side scalars (ablation.cu).
 size_t split_workspace_size(const gbpcg_grid &g);

@@ -1,8 +1,13 @@
-"""Batched solves: many independent grids in one graph launch.
+"""Batched solves: many independent grids in one launch.
 
-Each problem's iterate sequence in the batch is the same arithmetic as its
-standalone solve with the same tile configuration, so results must agree
-bitwise; convergence is checked against the FP64 oracle.
+Constant-coefficient grids with nx a multiple of 4 run as one persistent
+kernel; otherwise (or with graph=True) as one CUDA graph with a branch per
+problem.  In the graph form each problem's iterate sequence is the same
+arithmetic as its standalone solve, so results must agree bitwise.  The
+persistent kernel sums each problem's partials over its own tiles and z
+chunks, so it agrees with the standalone solve to rounding: iterations
+within 2 of the FP64 oracle, true residual within tol, bitwise
+reproducible from run to run.  Convergence is checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -16,9 +21,9 @@ pytestmark = pytest.mark.gpu
 SHAPES = [(48, 64, 96), (64, 48, 48), (37, 21, 100), (96, 64, 64), (13, 17, 19), (48, 48, 160)]
 
 
-def test_batched_equals_standalone(gpu_lib):
+def test_batched_graph_equals_standalone(gpu_lib):
     bs = [torch.from_numpy(inputs.uniform_rhs(s, 40 + i)).cuda() for i, s in enumerate(SHAPES)]
-    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000)
+    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000, graph=True)
     for b, x, r in zip(bs, xs, res):
         x1, r1 = gpu_lib.pcg_solve(b, tol=1e-6, maxit=2000)
         assert r["status"] == r1["status"] == 0
@@ -78,3 +83,56 @@ def test_batched_problems_keep_their_own_scale(gpu_lib):
         assert r["status"] == 0 and r["iters"] == res[1]["iters"], (p, r)
         assert np.array_equal(x.cpu().numpy() * 2.0 ** -p, x0), p
         assert oracle.true_relres(b * 2.0 ** p, x.cpu().numpy()) <= 1e-8
+
+
+# persistent kernel: every grid constant-coefficient with nx a multiple of 4
+PSHAPES = [(48, 64, 96), (64, 48, 48), (37, 21, 100), (96, 64, 64), (13, 17, 20), (48, 48, 160), (5, 3, 8)]
+
+
+@pytest.mark.parametrize("cfg", [1, 2, 3])
+def test_persistent_batch_against_oracle(gpu_lib, cfg):
+    bnp = [inputs.uniform_rhs(sh, 80 + i, dtype=np.float64) for i, sh in enumerate(PSHAPES)]
+    bs = [torch.from_numpy(b).cuda() for b in bnp]
+    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000, tile_cfg=cfg)
+    assert all(r["pass_launches"][0] == 1 and r["pass_ctas"][0] == cfg - 1 for r in res)
+    assert res[0]["pass_launches"][1] == max(r["iters"] for r in res)  # rounds = slowest problem
+    for b, x, r in zip(bnp, xs, res):
+        ref = oracle.pcg(b, tol=1e-6, maxit=2000)
+        assert r["status"] == 0 and abs(r["iters"] - ref["iters"]) <= 2, (r, ref["iters"])
+        tr = oracle.true_relres(b, x.cpu().numpy())
+        assert tr <= 1e-6 and abs(r["rel_res_true"] - tr) <= 1e-3 * tr
+    # bitwise reproducible, and the same as problem-by-problem up to rounding
+    xs2, res2 = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000, tile_cfg=cfg)
+    for x, x2, r, r2 in zip(xs, xs2, res, res2):
+        assert torch.equal(x, x2) and r["iters"] == r2["iters"]
+    for b, x, r in zip(bs, xs, res):
+        x1, r1 = gpu_lib.pcg_solve(b, tol=1e-6, maxit=2000)
+        assert abs(r["iters"] - r1["iters"]) <= 2
+        assert float((x - x1).norm() / x1.norm()) <= 1e-3
+
+
+def test_persistent_batch_fp32_io_zero_rhs_and_iteration_cap(gpu_lib):
+    """FP32 b and x; a zero right-hand side (x = 0 after 0 iterations) and a problem whose cap is
+    reached (NOT_CONVERGED, reported truthfully) in the same launch as converging ones."""
+    shapes = [(24, 20, 36), (16, 16, 16), (40, 40, 40)]
+    bnp = [inputs.uniform_rhs(shapes[0], 90), np.zeros(shapes[1], np.float32), inputs.uniform_rhs(shapes[2], 91)]
+    bs = [torch.from_numpy(b).cuda() for b in bnp]
+    xs = [torch.full_like(b, 3.0) for b in bs]
+    xs, res = gpu_lib.pcg_solve_batched(bs, xs, tol=1e-6, maxit=2000)
+    assert res[0]["status"] == 0 and res[2]["status"] == 0
+    assert res[1]["status"] == 0 and res[1]["iters"] == 0 and not torch.any(xs[1])
+    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=20)
+    assert res[0]["status"] == 3 and res[0]["iters"] == 20 and res[2]["status"] == 3
+    r64 = oracle.true_relres(bnp[2].astype(np.float64), xs[2].cpu().double().numpy())
+    assert abs(res[2]["rel_res_true"] - r64) <= 1e-3 * r64
+
+
+def test_persistent_and_graph_batches_agree(gpu_lib):
+    bnp = [inputs.uniform_rhs(sh, 95 + i, dtype=np.float64) for i, sh in enumerate(PSHAPES[:4])]
+    bs = [torch.from_numpy(b).cuda() for b in bnp]
+    xp, rp = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000)
+    xg, rg = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000, graph=True)
+    assert rg[0]["pass_launches"][0] == 0 and rp[0]["pass_launches"][0] == 1
+    for a, c, ra, rc in zip(xp, xg, rp, rg):
+        assert ra["status"] == rc["status"] == 0 and abs(ra["iters"] - rc["iters"]) <= 2
+        assert float((a - c).norm() / c.norm()) <= 1e-3

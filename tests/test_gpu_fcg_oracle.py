@@ -5,8 +5,13 @@ The oracle's preconditioner is its FP64 U-net with the GPU's BF16 roundings
 mirrored (weights, network input and every stored activation rounded to
 BF16), so both solvers apply the same nonlinear M up to rounding-boundary
 flips.  Checked: the iteration counts agree within 2, and the relative
-residual history ||r_k|| / ||b|| for k = 1..5 agrees to 1e-4 relative (the
-GPU's history is read from solves capped at k iterations).  Cases: the
+residual history ||r_k|| / ||b|| for k = 1..5 agrees to 1e-4 relative for
+the pass-through weights (one BF16 rounding of the scaled residual, mirrored
+exactly) and to 2e-3 for trained weights (about 1e-4 of each layer's
+activations round to the neighbouring BF16 value when the FP32 and FP64 sums
+straddle a rounding boundary, and those flips compound through nine layers
+into z; measured 3e-4).  The GPU's history is read from solves capped at k
+iterations.  Cases: the
 pass-through (identity) weights, for which M(r) = D^{-1/2} bf16(s / rms(s))
 rms(s) with s = D^{-1/2} r, and weights trained on the GPU; truncation
 m = 1 (the beta form) and m = 24.
@@ -63,7 +68,7 @@ def gpu_history(gpu_lib, w, b, k, m, upto=5):
     return np.array(out)
 
 
-def compare(gpu_lib, w, M, b, k, m, maxit):
+def compare(gpu_lib, w, M, b, k, m, maxit, rtol):
     b64 = b.cpu().numpy()
     k64 = None if k is None else k.cpu().numpy().astype(np.float64)
     x, res = gpu_lib.fcg_solve(w, b, tol=TOL, maxit=maxit, k_block=k, m=m)
@@ -74,7 +79,7 @@ def compare(gpu_lib, w, M, b, k, m, maxit):
     assert ref["hist"][-1] <= TOL
     assert oracle.true_relres(b64, x.cpu().numpy(), k64, 8) <= TOL
     h = gpu_history(gpu_lib, w, b, k, m)
-    np.testing.assert_allclose(h, ref["hist"][1:6], rtol=1e-4, atol=0)
+    np.testing.assert_allclose(h, ref["hist"][1:6], rtol=rtol, atol=0)
 
 
 @pytest.mark.parametrize("m", [1, 24])
@@ -96,7 +101,7 @@ def test_identity_network_fcg_matches_oracle_fcg(gpu_lib, m, varcoeff):
     # the closed form is the oracle network with these weights, exactly
     r0 = b.cpu().numpy()
     np.testing.assert_array_equal(M(r0), oracle_precond(ws_id, k64)(r0))
-    compare(gpu_lib, w.cuda(), M, b, k, m, maxit=1000)
+    compare(gpu_lib, w.cuda(), M, b, k, m, maxit=1000, rtol=1e-4)
 
 
 @pytest.fixture(scope="module")
@@ -115,4 +120,4 @@ def test_trained_network_fcg_matches_oracle_fcg(gpu_lib, trained_weights, m):
     k64 = k.cpu().numpy().astype(np.float64)
     ws = {name: v.numpy().astype(np.float64)
           for name, v in gpu_lib.nn_unpack_weights(trained_weights.cpu()).items()}
-    compare(gpu_lib, trained_weights, oracle_precond(ws, k64), b, k, m, maxit=200)
+    compare(gpu_lib, trained_weights, oracle_precond(ws, k64), b, k, m, maxit=200, rtol=2e-3)
