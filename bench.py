@@ -628,6 +628,44 @@ def main():
                "sequential_ms": seq_ms}
     del rhs, xb
 
+    # f1: the same 256^3 operator assembled as a Sliced-ELL (SELL-32) matrix and solved by the general
+    # sparse PCG (the paper's H100 comparator design), next to the matrix-free solve
+    sell = None
+    if rank == 0:
+        sm = B.sell_from_stencil(b.shape)
+        bs64 = b.ravel().contiguous()
+        xs64 = torch.zeros_like(bs64)
+        sws = None
+        for _ in range(2):
+            xs64.zero_()
+            _, sres = B.sell_pcg_solve(sm, bs64, xs64, tol=TOL, maxit=MAXIT, stream=stream)
+        pv = torch.from_numpy(inputs.uniform_rhs(b.shape, 3)).cuda().ravel()
+        qv = torch.empty_like(pv)
+        reps = 20
+        B.sell_spmv(sm, pv, qv, stream=stream)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            B.sell_spmv(sm, pv, qv, stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        spmv_us = s0.elapsed_time(s1) / reps * 1e3
+        # SpMV algorithmic bytes: stored values and columns (8 B each), the gathered x once, y
+        spmv_bytes = 8 * sm.nnz_stored + 8 * N
+        sell = {"workload": f"poisson {n}^3 assembled as SELL-32 ({sm.nnz_stored} stored entries, "
+                            f"{sm.nnz_stored / N:.3f} per row)",
+                "solve": {"ms": sres["time_ms"], "iters": sres["iters"], "status": sres["status_name"],
+                          "rel_res_true_fp64": sres["rel_res_true"], "replacements": sres["replacements"],
+                          "us_per_iter": 1e3 * sres["time_ms"] / max(1, sres["iters"]),
+                          "algorithmic_bytes_per_row_iter": 108,
+                          "gbs_at_108B": 108 * N / (sres["time_ms"] * 1e-3 / max(1, sres["iters"])) / 1e9},
+                "spmv": {"us": spmv_us, "algorithmic_bytes": spmv_bytes, "gbs": spmv_bytes / (spmv_us * 1e-6) / 1e9,
+                         "frac": spmv_bytes / (spmv_us * 1e-6) / 1e9 / peak},
+                "matrix_free_ms": ms_step}
+        del sm, bs64, xs64, pv, qv
+        torch.cuda.empty_cache()
+
     # a6: the dot and axpy kernels on 2^28 FP32 elements (1 GiB per vector, far above L2), best of 5
     n28 = 1 << 28
     gen = torch.Generator(device="cuda").manual_seed(28)
@@ -698,6 +736,7 @@ def main():
             "batched_config3": batched,
             "microkernels_2e28": micro,
             "ablations": ablations,
+            "sell_spmv_pcg": sell,
             "learned_config4": learned_res,
             "roofline": roofline,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * N * 8,

@@ -296,6 +296,68 @@ int gbpcg_workspace_size_batched(int32_t nprob, const gbpcg_grid *grids, const g
 int gbpcg_pcg_solve_batched(int32_t nprob, const gbpcg_grid *grids, const void *const *b, void *const *x,
                             const gbpcg_opts *opts, gbpcg_result *results, gbpcg_stream stream);
 
+/* ------------------------------------------------------------------------
+ * General sparse matrices in Sliced-ELL form (SELL-32): the format the
+ * paper's H100 comparator stores the seven-point operator in (Sec. VII-A,
+ * cuSPARSE Sliced ELL), and the "more general sparse matrix
+ * representations" its conclusion names.  Rows are grouped in slices of 32
+ * consecutive rows; slice s holds w_s = (slice_ptr[s+1] - slice_ptr[s]) / 32
+ * entries per row, w_s the slice's longest row, stored column-major within
+ * the slice: entry j of row 32 s + l is at slice_ptr[s] + 32 j + l.  Rows
+ * shorter than w_s are padded with value 0 and their own row as column.
+ * slice_ptr has ceil(n / 32) + 1 entries (slice_ptr[0] = 0); col are 32-bit
+ * column indices; inv_diag is the Jacobi preconditioner D^-1.  All arrays
+ * are DEVICE arrays owned by the caller.
+ * ---------------------------------------------------------------------- */
+typedef struct gbpcg_sell {
+    int64_t n;                  /* rows = columns, 1 .. 2^31 - 1 */
+    int32_t slice;              /* rows per slice: 32 */
+    const int64_t *slice_ptr;   /* ceil(n / 32) + 1 */
+    const int32_t *col;         /* slice_ptr[last] entries */
+    const float *val;           /* slice_ptr[last] entries */
+    const float *inv_diag;      /* n */
+} gbpcg_sell;
+
+/* SELL layout of the seven-point operator of `grid` (the matrix of
+ * gbpcg_stencil_apply, block coefficients included): *nnz_stored receives
+ * the stored entries (padding included); slice_ptr (DEVICE, may be NULL for
+ * a size query) receives the slice offsets.  Computed on the host;
+ * synchronises `stream` when it copies slice_ptr. */
+int gbpcg_sell_stencil_layout(const gbpcg_grid *grid, int64_t *slice_ptr, int64_t *nnz_stored,
+                              gbpcg_stream stream);
+/* Fills col, val, inv_diag (DEVICE) of that operator: each row's entries in
+ * column order (z-1, y-1, x-1, centre, x+1, y+1, z+1), absent neighbours
+ * skipped; the same FP32 face weights as the stencil kernels. */
+int gbpcg_sell_from_stencil(const gbpcg_grid *grid, const int64_t *slice_ptr, int32_t *col, float *val,
+                            float *inv_diag, gbpcg_stream stream);
+/* SELL layout of a CSR matrix (row_ptr: DEVICE, n + 1 entries): as
+ * gbpcg_sell_stencil_layout.  Reads row_ptr back to the host; synchronises. */
+int gbpcg_sell_csr_layout(int64_t n, const int64_t *row_ptr, int64_t *slice_ptr, int64_t *nnz_stored,
+                          gbpcg_stream stream);
+/* CSR (DEVICE row_ptr, csr_col, csr_val) -> SELL col, val and inv_diag (1 /
+ * the diagonal entry; 0 for a row without a non-zero diagonal). */
+int gbpcg_sell_from_csr(int64_t n, const int64_t *row_ptr, const int32_t *csr_col, const float *csr_val,
+                        const int64_t *slice_ptr, int32_t *col, float *val, float *inv_diag, gbpcg_stream stream);
+/* y = A x, FP32 (DEVICE x, y of n elements, distinct). */
+int gbpcg_sell_spmv(const gbpcg_sell *matrix, const float *x, float *y, gbpcg_stream stream);
+/* Bytes of workspace gbpcg_sell_pcg_solve needs. */
+int gbpcg_sell_workspace_size(const gbpcg_sell *matrix, size_t *bytes);
+/*
+ * Jacobi-PCG (Sec. VII's iteration) for A x = b with A in SELL form, A
+ * symmetric positive definite.  b (read), x (initial guess in, solution
+ * out): DEVICE FP64 arrays of n elements; opts: io_dtype F64, storage F32,
+ * Jacobi, no flags, tol and maxit as for gbpcg_pcg_solve, workspace of
+ * gbpcg_sell_workspace_size bytes (256-byte aligned).  Per iteration three
+ * kernels (q = A p with p.q; x += alpha p in FP64, r -= alpha q with r.r and
+ * r.z; p = D^-1 r + beta p), the scalars on the device, the loop one CUDA
+ * graph.  The residual is replaced by b - A x computed in FP64 when it has
+ * dropped two decades since the last replacement and when it meets the
+ * tolerance, so convergence is decided on a true residual.  Fills *result
+ * (rel_res_true: FP64 ||b - A x|| / ||b||); synchronises `stream`.
+ */
+int gbpcg_sell_pcg_solve(const gbpcg_sell *matrix, const double *b, double *x, const gbpcg_opts *opts,
+                         gbpcg_result *result, gbpcg_stream stream);
+
 /*
  * Autotuner (no counterpart in the paper; the paper hard-codes its tile
  * layout, Sec. VI-A): times every tile configuration that fits the grid

@@ -18,6 +18,13 @@ Parity status of each function (what pins it, see ``tests/test_oracle.py``):
                   scipy.sparse.linalg.cg on the assembled matrix
   refine          reaches tolerances below the inner tolerance; agrees with a
                   dense direct solve
+  csr_apply       the Kronecker-assembled Poisson matrix reproduces the
+                  matrix-free operator; a random sparse matrix agrees with a
+                  dense product
+  csr_pcg         the same iterates as pcg on the assembled Poisson matrix;
+                  scipy's CG on a random sparse SPD matrix; exact
+                  termination in m steps on a diagonal matrix with m
+                  distinct entries
 """
 from __future__ import annotations
 
@@ -72,6 +79,10 @@ def _load():
             lib.orc_pcg.argtypes = [I, I, I, P, I, I, I, P, P, D, I, I, P, P, P]
             lib.orc_true_relres.restype = D
             lib.orc_true_relres.argtypes = [I, I, I, P, I, I, I, P, P]
+            lib.orc_csr_apply.restype = None
+            lib.orc_csr_apply.argtypes = [L, P, P, P, P, P]
+            lib.orc_csr_pcg.restype = I
+            lib.orc_csr_pcg.argtypes = [L, P, P, P, P, P, D, I, P, P, P]
             lib.orc_threads.restype = I
             lib.orc_threads.argtypes = []
             lib.orc_refine.restype = I
@@ -152,6 +163,36 @@ def true_relres(b, x, k=None, kb=8) -> float:
     nz, ny, nx = b.shape
     kp, kbx, kby, kbz, _keep = _kargs(k, kb)
     return float(_load().orc_true_relres(nx, ny, nz, kp, kbx, kby, kbz, _ptr(b), _ptr(x)))
+
+
+def _csr(row_ptr, col, val):
+    return (np.ascontiguousarray(row_ptr, dtype=np.int64), np.ascontiguousarray(col, dtype=np.int32), _f64(val))
+
+
+def csr_apply(row_ptr, col, val, x) -> np.ndarray:
+    """y = A x for a CSR matrix (row_ptr int64 n+1, col int32, val float64)."""
+    rp, cc, vv = _csr(row_ptr, col, val)
+    x = _f64(x).ravel()
+    y = np.empty_like(x)
+    _load().orc_csr_apply(len(rp) - 1, _ptr(rp), _ptr(cc), _ptr(vv), _ptr(x), _ptr(y))
+    return y
+
+
+def csr_pcg(row_ptr, col, val, b, x0=None, tol=1e-6, maxit=2000, history=False):
+    """Jacobi-PCG on a CSR matrix (the iteration of pcg with a general operator).
+    Returns dict(x, iters, relres, status[, hist])."""
+    rp, cc, vv = _csr(row_ptr, col, val)
+    b = _f64(b).ravel()
+    x = np.zeros_like(b) if x0 is None else _f64(x0).ravel().copy()
+    hist = np.zeros(maxit + 1, dtype=np.float64)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _load().orc_csr_pcg(len(rp) - 1, _ptr(rp), _ptr(cc), _ptr(vv), _ptr(b), _ptr(x), float(tol), int(maxit),
+                             _ptr(hist), ctypes.byref(it), ctypes.byref(rel))
+    out = dict(x=x, iters=it.value, relres=rel.value, status=st)
+    if history:
+        out["hist"] = hist[: it.value + 1].copy()
+    return out
 
 
 def threads() -> int:

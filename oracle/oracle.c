@@ -271,6 +271,91 @@ done:
     return status;
 }
 
+/* ------------------------------------------------ general sparse (CSR) -- */
+
+/* y = A x for A in compressed sparse row form: row i holds the entries
+ * row_ptr[i] .. row_ptr[i+1]-1 with columns col[e] and values val[e];
+ * y_i = sum over the row's entries of val[e] x[col[e]], in entry order. */
+void orc_csr_apply(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, const double *x,
+                   double *y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) s += val[e] * x[col[e]];
+        y[i] = s;
+    }
+}
+
+/* Jacobi-PCG for a CSR matrix: the iteration of orc_pcg (Sec. VII) with the
+ * matrix-free operator replaced by orc_csr_apply and D by the matrix's
+ * diagonal entries (summed when a row repeats its diagonal column). */
+int orc_csr_pcg(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, const double *b,
+                double *x, double tol, int maxit, double *hist, int *iters_out, double *relres_out) {
+    double *r = (double *)malloc(sizeof(double) * (size_t)n);
+    double *z = (double *)malloc(sizeof(double) * (size_t)n);
+    double *p = (double *)malloc(sizeof(double) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    int status = ORC_NOT_CONVERGED, it = 0;
+    double rel = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        d[i] = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e)
+            if (col[e] == i) d[i] += val[e];
+    }
+    const double bn = sqrt(orc_dot(n, b, b));
+    if (bn == 0.0) {
+        memset(x, 0, sizeof(double) * (size_t)n);
+        if (hist) hist[0] = 0.0;
+        status = ORC_OK;
+        goto done;
+    }
+    orc_csr_apply(n, row_ptr, col, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+    memcpy(p, z, sizeof(double) * (size_t)n);
+    double rz = orc_dot(n, r, z);
+    rel = sqrt(orc_dot(n, r, r)) / bn;
+    if (hist) hist[0] = rel;
+    if (rel <= tol) {
+        status = ORC_OK;
+        goto done;
+    }
+    while (it < maxit) {
+        orc_csr_apply(n, row_ptr, col, val, p, q);
+        double pq = orc_dot(n, p, q);
+        if (!(pq > 0.0) || !isfinite(pq) || !isfinite(rz)) {
+            status = ORC_BREAKDOWN;
+            break;
+        }
+        double alpha = rz / pq;
+        orc_axpy(n, alpha, p, x);
+        orc_axpy(n, -alpha, q, r);
+        it += 1;
+        rel = sqrt(orc_dot(n, r, r)) / bn;
+        if (hist) hist[it] = rel;
+        if (rel <= tol) {
+            status = ORC_OK;
+            break;
+        }
+        if (it == maxit) break;
+        for (int64_t i = 0; i < n; ++i) z[i] = r[i] / d[i];
+        double rz_new = orc_dot(n, r, z);
+        double beta = rz_new / rz;
+        for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+    }
+done:
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = rel;
+    free(r);
+    free(z);
+    free(p);
+    free(q);
+    free(d);
+    return status;
+}
+
 /* ||b - A x|| / ||b|| evaluated in FP64 (every solve's result is checked with it). */
 double orc_true_relres(int nx, int ny, int nz, const double *kb, int kbx, int kby, int kbz,
                        const double *b, const double *x) {

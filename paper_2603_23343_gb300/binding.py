@@ -14,6 +14,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -40,7 +41,9 @@ EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbp
            "gbpcg_conv3_backward_weight", "gbpcg_nn_workspace_size", "gbpcg_nn_forward", "gbpcg_nn_backward",
            "gbpcg_nn_loss", "gbpcg_nn_adam", "gbpcg_nn_train_step", "gbpcg_nn_status", "gbpcg_fcg_workspace_size",
            "gbpcg_fcg_solve", "gbpcg_wait_selftest", "gbpcg_nn_tensor_info", "gbpcg_dot_variant_workspace_size",
-           "gbpcg_dot_variant", "gbpcg_stencil_apply_variant"]
+           "gbpcg_dot_variant", "gbpcg_stencil_apply_variant", "gbpcg_sell_stencil_layout", "gbpcg_sell_from_stencil",
+           "gbpcg_sell_csr_layout", "gbpcg_sell_from_csr", "gbpcg_sell_spmv", "gbpcg_sell_workspace_size",
+           "gbpcg_sell_pcg_solve"]
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
 
 NN_NUM_WEIGHTS = 319248
@@ -75,6 +78,23 @@ class Result(ctypes.Structure):
                     rel_res_recursive=self.rel_res_recursive, rel_res_true=self.rel_res_true,
                     time_ms=self.time_ms, pass_ms=list(self.pass_ms), pass_launches=list(self.pass_launches),
                     replacements=self.replacements, refine_steps=self.refine_steps, pass_ctas=list(self.pass_ctas))
+
+
+class Sell(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("slice", ctypes.c_int32), ("slice_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("inv_diag", ctypes.c_void_p)]
+
+
+class SellMatrix:
+    """Device arrays of a SELL-32 matrix (gbpcg_sell) and the C struct that points at them."""
+
+    def __init__(self, n, slice_ptr, col, val, inv_diag):
+        self.n, self.slice_ptr, self.col, self.val, self.inv_diag = n, slice_ptr, col, val, inv_diag
+        self.c = Sell(n, 32, slice_ptr.data_ptr(), col.data_ptr(), val.data_ptr(), inv_diag.data_ptr())
+
+    @property
+    def nnz_stored(self):
+        return self.val.numel()
 
 
 class GbpcgError(RuntimeError):
@@ -145,6 +165,17 @@ def load(path: str = LIB_PATH):
         lib.gbpcg_dot_variant.restype = ctypes.c_int
         lib.gbpcg_stencil_apply_variant.argtypes = [ctypes.POINTER(Grid), I32, P, P, P]
         lib.gbpcg_stencil_apply_variant.restype = ctypes.c_int
+        lib.gbpcg_sell_stencil_layout.argtypes = [ctypes.POINTER(Grid), P, ctypes.POINTER(I64), P]
+        lib.gbpcg_sell_from_stencil.argtypes = [ctypes.POINTER(Grid), P, P, P, P, P]
+        lib.gbpcg_sell_csr_layout.argtypes = [I64, P, P, ctypes.POINTER(I64), P]
+        lib.gbpcg_sell_from_csr.argtypes = [I64, P, P, P, P, P, P, P, P]
+        lib.gbpcg_sell_spmv.argtypes = [ctypes.POINTER(Sell), P, P, P]
+        lib.gbpcg_sell_workspace_size.argtypes = [ctypes.POINTER(Sell), ctypes.POINTER(SZ)]
+        lib.gbpcg_sell_pcg_solve.argtypes = [ctypes.POINTER(Sell), P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result),
+                                             P]
+        for name in ("gbpcg_sell_stencil_layout", "gbpcg_sell_from_stencil", "gbpcg_sell_csr_layout",
+                     "gbpcg_sell_from_csr", "gbpcg_sell_spmv", "gbpcg_sell_workspace_size", "gbpcg_sell_pcg_solve"):
+            getattr(lib, name).restype = ctypes.c_int
         lib.gbpcg_nn_forward.argtypes = [ctypes.POINTER(Grid), P, P, P, P, SZ, P]
         lib.gbpcg_nn_backward.restype = ctypes.c_int
         lib.gbpcg_nn_backward.argtypes = [ctypes.POINTER(Grid), P, P, P, SZ, P]
@@ -270,6 +301,65 @@ def stencil_apply_variant(variant: int, p: torch.Tensor, q: torch.Tensor | None 
     g = make_grid(p.shape)
     _check(load().gbpcg_stencil_apply_variant(ctypes.byref(g), int(variant), _ptr(p), _ptr(q), _stream(stream)))
     return q
+
+
+def sell_from_stencil(shape, k_block=None, kb=8, device="cuda", stream=None) -> SellMatrix:
+    """The seven-point operator of a grid as a SELL-32 matrix on the device
+    (gbpcg_sell_stencil_layout + gbpcg_sell_from_stencil)."""
+    g = make_grid(shape, k_block, kb)
+    nnz = ctypes.c_int64(0)
+    lib = load()
+    _check(lib.gbpcg_sell_stencil_layout(ctypes.byref(g), None, ctypes.byref(nnz), _stream(stream)))
+    n = int(np.prod(shape))
+    sp = torch.empty((n + 31) // 32 + 1, dtype=torch.int64, device=device)
+    _check(lib.gbpcg_sell_stencil_layout(ctypes.byref(g), _ptr(sp), ctypes.byref(nnz), _stream(stream)))
+    col = torch.empty(nnz.value, dtype=torch.int32, device=device)
+    val = torch.empty(nnz.value, dtype=torch.float32, device=device)
+    inv = torch.empty(n, dtype=torch.float32, device=device)
+    _check(lib.gbpcg_sell_from_stencil(ctypes.byref(g), _ptr(sp), _ptr(col), _ptr(val), _ptr(inv), _stream(stream)))
+    return SellMatrix(n, sp, col, val, inv)
+
+
+def sell_from_csr(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, stream=None) -> SellMatrix:
+    """A CSR matrix (CUDA row_ptr int64, col int32, val float32) as SELL-32 (gbpcg_sell_csr_layout +
+    gbpcg_sell_from_csr)."""
+    n = row_ptr.numel() - 1
+    lib = load()
+    nnz = ctypes.c_int64(0)
+    sp = torch.empty((n + 31) // 32 + 1, dtype=torch.int64, device=row_ptr.device)
+    _check(lib.gbpcg_sell_csr_layout(n, _ptr(row_ptr), _ptr(sp), ctypes.byref(nnz), _stream(stream)))
+    scol = torch.empty(nnz.value, dtype=torch.int32, device=row_ptr.device)
+    sval = torch.empty(nnz.value, dtype=torch.float32, device=row_ptr.device)
+    inv = torch.empty(n, dtype=torch.float32, device=row_ptr.device)
+    _check(lib.gbpcg_sell_from_csr(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(sp), _ptr(scol), _ptr(sval),
+                                   _ptr(inv), _stream(stream)))
+    return SellMatrix(n, sp, scol, sval, inv)
+
+
+def sell_spmv(m: SellMatrix, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """y = A x, FP32 (gbpcg_sell_spmv)."""
+    if y is None:
+        y = torch.empty_like(x)
+    _check(load().gbpcg_sell_spmv(ctypes.byref(m.c), _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def sell_pcg_solve(m: SellMatrix, b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000,
+                   workspace=None, stream=None):
+    """Jacobi-PCG on a SELL matrix (gbpcg_sell_pcg_solve); b, x float64 CUDA vectors."""
+    if x is None:
+        x = torch.zeros_like(b)
+    lib = load()
+    if workspace is None:
+        nb = ctypes.c_size_t(0)
+        _check(lib.gbpcg_sell_workspace_size(ctypes.byref(m.c), ctypes.byref(nb)))
+        workspace = torch.empty(nb.value, dtype=torch.uint8, device=b.device)
+    o = make_opts(tol, maxit, F32, F64, False, workspace)
+    r = Result()
+    rc = lib.gbpcg_sell_pcg_solve(ctypes.byref(m.c), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
+                                  _stream(stream))
+    _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
+    return x, r.as_dict()
 
 
 def axpy(alpha: float, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:

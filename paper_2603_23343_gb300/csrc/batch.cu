@@ -6,16 +6,17 @@
 // barriers:
 //
 //   reset states | max |b| | r0 = b - A x0 (FP64)      once
-//   pass A | pass B | [flush | r = b - A x (FP64)]       every round, until all converge
+//   pass A or flush | pass B or r = b - A x (FP64)       every round, until all converge
 //   x += d + alpha p | true residual (FP64)              once
 //
 // A phase is a list of work items over all problems: a pass item is one
 // (x, y) tile of one problem marched through a chunk of z planes (the same
 // z-marching code as the single-problem passes, engine.cuh), a row item a
-// run of grid rows of one problem.  CTA c takes items c, c + G, c + 2G, ...
-// (G CTAs); items of problems that have converged are skipped, so a
-// problem drops out of the work as soon as it is done while the others go
-// on.  Each problem keeps its own scalars (SolveState), partial sums and
+// run of grid rows of one problem.  Each round numbers only the items of
+// unfinished problems and CTA c takes items c, c + G, c + 2G, ... (G CTAs),
+// so a problem drops out of the work as soon as it is done while the others
+// go on; a problem that needs a residual replacement spends one round on it
+// while the others iterate.  Each problem keeps its own scalars (SolveState), partial sums and
 // tickets: the CTA that finishes a problem's last item of a phase adds the
 // problem's partial sums in item order (bitwise reproducible) and takes the
 // scalar step (alpha; beta, convergence, the replacement trigger).
@@ -40,6 +41,7 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchZDepth = 32;  // z planes per pass item
 constexpr int kRowPoints = 16384;  // grid points per row item (at least one row)
 constexpr uint32_t kBarrierPolls = 1u << 22;  // x ~64 ns of sleep: well under a second
+constexpr int kBatchMaxProblems = 1024;  // per-round snapshot held in shared memory
 
 // Tile configurations of the persistent kernel (all 256 threads: the FP64
 // residual code strides rows by 256 threads).
@@ -116,7 +118,7 @@ __device__ __forceinline__ bool batch_barrier(BatchHeader *h) {
 
 // The whole batch.  X: type of b and x (float or double).
 template <int TX, int TY, int S, typename X>
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs A) {
     using T = float;
     using GA = Geometry<T, TX, TY, K_PASSA>;
     using GB = Geometry<T, TX, TY, K_PASSB>;
@@ -191,142 +193,158 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BatchArgs A)
     if (!batch_barrier(hdr)) return;
 
     // ---- the iteration rounds ----
+    // Every round has two slots.  A problem in iteration mode runs pass A in
+    // the first and pass B in the second; a problem whose pass B asked for a
+    // residual replacement spends its next round on it instead (flush in the
+    // first slot, the FP64 residual in the second), while the other problems
+    // iterate.  At the start of a round every CTA takes the same snapshot of
+    // the problems' modes and numbers the round's work items over the active
+    // problems only, so finished problems cost nothing and the items spread
+    // evenly over the CTAs.
+    __shared__ int s_pre[kBatchMaxProblems + 1];
+    __shared__ unsigned char s_mode[kBatchMaxProblems];
     for (int round = 0;; ++round) {
-        // continue while any problem is unfinished (the states are stable between barriers)
-        if (threadIdx.x < 32) {
-            int any = 0;
-            for (int p = threadIdx.x; p < A.nprob; p += 32) any |= !((volatile int *)&A.probs[p].st->done)[0];
-            any = __any_sync(0xffffffffu, any);
-            if (threadIdx.x == 0) s_flag = any;
+        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
+            const SolveState *st = A.probs[p].st;
+            const int done = ((volatile const int *)&st->done)[0];
+            const int rep = ((volatile const int *)&st->replace)[0];
+            const int mode = done ? 0 : rep ? 2 : 1;
+            s_mode[p] = (unsigned char)mode;
+            s_pre[p + 1] = mode == 1 ? A.probs[p].nitems : mode == 2 ? A.probs[p].nrow_items : 0;
         }
         __syncthreads();
-        const int active = s_flag;
-        __syncthreads();  // s_flag is written again before the next barrier
-        if (!active) break;
-
-        // pass A: p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap
-        for (int item = blockIdx.x; item < A.nitems; item += G) {
-            const BatchProblem &P = A.probs[A.item_prob[item]];
-            SolveState *st = P.st;
-            if (((volatile int *)&st->done)[0]) continue;
-            const int local = item - P.item0;
-            const int tile = local % P.tiles, chunk = local / P.tiles;
-            const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-            const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
-            const MarchScalars sc = read_scalars<K_PASSA>(st);
-            const bool odd = sc.it & 1;
-            MarchIO<T, K_PASSA> io;
-            io.H0 = P.z;
-            io.H1 = odd ? P.p0 : P.p1;  // p_{k-1}
-            io.C0 = P.d;
-            io.O0 = odd ? P.p1 : P.p0;  // p_k
-            io.O1 = P.d;
-            io.M0 = &P.hz;
-            io.M1 = odd ? &P.hp0 : &P.hp1;
-            io.MC = &P.cd;
-            float acc[GA::NV];
-            acc[0] = 0.f;
-            ring += march_tile<T, TX, TY, S, K_PASSA, true, OpConst, false>(smem, full, &s_timeout, ring, io, P.op,
-                                                                           P.nx, P.ny, P.nz, x0, y0, k0, k1, sc,
-                                                                           acc);
-            if (s_timeout) {
-                if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
-                return;
+        if (threadIdx.x < 32) {  // inclusive scan of the counts, 32 chunks of contiguous problems
+            const int per = (A.nprob + 31) / 32;
+            const int a = min(A.nprob, (int)threadIdx.x * per), e = min(A.nprob, a + per);
+            int sum = 0;
+            for (int p = a; p < e; ++p) sum += s_pre[p + 1];
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if ((int)threadIdx.x >= o) incl += t;
             }
-            double part[1], tot[1];
-            block_sum<1, kBatchThreads>(acc, part);
-            if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, P.nitems, tot) &&
-                threadIdx.x == 0)
-                passa_finish(st, tot[0], false);
+            int run = incl - sum;
+            for (int p = a; p < e; ++p) {
+                run += s_pre[p + 1];
+                s_pre[p + 1] = run;
+            }
+            if (threadIdx.x == 0) s_pre[0] = 0;
+        }
+        __syncthreads();
+        const int total = s_pre[A.nprob];
+        if (total == 0) break;
+        // problem of round item t: the last p with s_pre[p] <= t
+        auto owner = [&](int t) {
+            int lo = 0, hi = A.nprob - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_pre[mid] <= t) lo = mid;
+                else hi = mid - 1;
+            }
+            return lo;
+        };
+
+        // first slot: pass A (p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap), or the flush
+        for (int t = blockIdx.x; t < total; t += G) {
+            const int pi = owner(t);
+            const BatchProblem &P = A.probs[pi];
+            SolveState *st = P.st;
+            const int local = t - s_pre[pi];
+            if (s_mode[pi] == 1) {
+                const int tile = local % P.tiles, chunk = local / P.tiles;
+                const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
+                const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+                const MarchScalars sc = read_scalars<K_PASSA>(st);
+                const bool odd = sc.it & 1;
+                MarchIO<T, K_PASSA> io;
+                io.H0 = P.z;
+                io.H1 = odd ? P.p0 : P.p1;  // p_{k-1}
+                io.C0 = P.d;
+                io.O0 = odd ? P.p1 : P.p0;  // p_k
+                io.O1 = P.d;
+                io.M0 = &P.hz;
+                io.M1 = odd ? &P.hp0 : &P.hp1;
+                io.MC = &P.cd;
+                float acc[GA::NV];
+                acc[0] = 0.f;
+                ring += march_tile<T, TX, TY, S, K_PASSA, true, OpConst, false>(smem, full, &s_timeout, ring, io,
+                                                                               P.op, P.nx, P.ny, P.nz, x0, y0, k0,
+                                                                               k1, sc, acc);
+                if (s_timeout) {
+                    if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
+                    return;
+                }
+                double part[1], tot[1];
+                block_sum<1, kBatchThreads>(acc, part);
+                if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, P.nitems, tot) &&
+                    threadIdx.x == 0)
+                    passa_finish(st, tot[0], false);
+            } else {
+                // flush: x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
+                const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+                const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
+                const float a = st->pending ? (float)st->alpha : 0.0f;
+                const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
+                X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
+                const X is = (X)inv_s;
+                for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
+                    const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
+                    x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+                    P.d[g] = 0.0f;
+                }
+            }
         }
         if (!batch_barrier(hdr)) return;
 
-        // pass B: q = A p_k, r = D z - alpha q, z = D^-1 r, r.r and r.z
-        for (int item = blockIdx.x; item < A.nitems; item += G) {
-            const BatchProblem &P = A.probs[A.item_prob[item]];
+        // second slot: pass B (q = A p_k, r = D z - alpha q, z = D^-1 r, r.r, r.z), or the FP64
+        // residual r = b - A x of the replacement
+        for (int t = blockIdx.x; t < total; t += G) {
+            const int pi = owner(t);
+            const BatchProblem &P = A.probs[pi];
             SolveState *st = P.st;
-            if (((volatile int *)&st->done)[0]) continue;
-            const int local = item - P.item0;
-            const int tile = local % P.tiles, chunk = local / P.tiles;
-            const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-            const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
-            const MarchScalars sc = read_scalars<K_PASSB>(st);
-            const bool odd = sc.it & 1;
-            MarchIO<T, K_PASSB> io;
-            io.H0 = odd ? P.p1 : P.p0;  // p_k
-            io.H1 = io.H0;
-            io.C0 = P.z;
-            io.O0 = P.z;
-            io.O1 = P.z;
-            io.M0 = odd ? &P.hp1 : &P.hp0;
-            io.M1 = io.M0;
-            io.MC = &P.cz;
-            float acc[GB::NV];
-            acc[0] = acc[1] = 0.f;
-            ring += march_tile<T, TX, TY, S, K_PASSB, true, OpConst, false>(smem, full, &s_timeout, ring, io, P.op,
-                                                                           P.nx, P.ny, P.nz, x0, y0, k0, k1, sc,
-                                                                           acc);
-            if (s_timeout) {
-                if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
-                return;
+            const int local = t - s_pre[pi];
+            if (s_mode[pi] == 1) {
+                const int tile = local % P.tiles, chunk = local / P.tiles;
+                const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
+                const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+                const MarchScalars sc = read_scalars<K_PASSB>(st);
+                const bool odd = sc.it & 1;
+                MarchIO<T, K_PASSB> io;
+                io.H0 = odd ? P.p1 : P.p0;  // p_k
+                io.H1 = io.H0;
+                io.C0 = P.z;
+                io.O0 = P.z;
+                io.O1 = P.z;
+                io.M0 = odd ? &P.hp1 : &P.hp0;
+                io.M1 = io.M0;
+                io.MC = &P.cz;
+                float acc[GB::NV];
+                acc[0] = acc[1] = 0.f;
+                ring += march_tile<T, TX, TY, S, K_PASSB, true, OpConst, false>(smem, full, &s_timeout, ring, io,
+                                                                               P.op, P.nx, P.ny, P.nz, x0, y0, k0,
+                                                                               k1, sc, acc);
+                if (s_timeout) {
+                    if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
+                    return;
+                }
+                double part[2], tot[2];
+                block_sum<2, kBatchThreads>(acc, part);
+                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, P.nitems, tot) &&
+                    threadIdx.x == 0)
+                    passb_finish(st, sc.it, tot[0], tot[1], false);
+            } else {
+                const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+                double part[2], tot[2], unscale;
+                res64_rows<RES_REPLACE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local,
+                                                     P.nrow_items, tot) &&
+                    threadIdx.x == 0)
+                    res64_finish<RES_REPLACE>(st, tot, unscale);
             }
-            double part[2], tot[2];
-            block_sum<2, kBatchThreads>(acc, part);
-            if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, P.nitems, tot) &&
-                threadIdx.x == 0)
-                passb_finish(st, sc.it, tot[0], tot[1], false);
         }
         if (!batch_barrier(hdr)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) hdr->rounds = round + 1;
-
-        // residual replacement where a problem asked for one
-        if (threadIdx.x < 32) {
-            int any = 0;
-            for (int p = threadIdx.x; p < A.nprob; p += 32) {
-                const SolveState *st = A.probs[p].st;
-                any |= ((volatile const int *)&st->replace)[0] && !((volatile const int *)&st->done)[0];
-            }
-            any = __any_sync(0xffffffffu, any);
-            if (threadIdx.x == 0) s_flag = any;
-        }
-        __syncthreads();
-        const int replacing = s_flag;
-        __syncthreads();  // the next round writes s_flag before any barrier
-        if (!replacing) continue;
-        // flush: x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
-        for (int item = blockIdx.x; item < A.nrow_items; item += G) {
-            const BatchProblem &P = A.probs[A.row_prob[item]];
-            const SolveState *st = P.st;
-            if (!st->replace || st->done) continue;
-            const int local = item - P.row0_item;
-            const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
-            const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
-            const float a = st->pending ? (float)st->alpha : 0.0f;
-            const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
-            X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
-            const X is = (X)inv_s;
-            for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
-                const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
-                x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
-                P.d[g] = 0.0f;
-            }
-        }
-        if (!batch_barrier(hdr)) return;
-        // r = b - A x in FP64, z = D^-1 r, the replacement's decisions
-        for (int item = blockIdx.x; item < A.nrow_items; item += G) {
-            const BatchProblem &P = A.probs[A.row_prob[item]];
-            SolveState *st = P.st;
-            if (!((volatile int *)&st->replace)[0] || ((volatile int *)&st->done)[0]) continue;
-            const int local = item - P.row0_item;
-            const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
-            double part[2], tot[2], unscale;
-            res64_rows<RES_REPLACE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
-            if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local,
-                                                 P.nrow_items, tot) &&
-                threadIdx.x == 0)
-                res64_finish<RES_REPLACE>(st, tot, unscale);
-        }
-        if (!batch_barrier(hdr)) return;
     }
 
     // ---- x += (d + alpha_{k-1} p_{k-1}) / s (x = 0 when b = 0) ----
@@ -464,6 +482,7 @@ bool same_key(const PersistKey &a, const PersistKey &b) {
 }  // namespace
 
 bool batch_persistent_ok(int nprob, const gbpcg_grid *grids) {
+    if (nprob > kBatchMaxProblems) return false;
     for (int i = 0; i < nprob; ++i) {
         const gbpcg_grid &g = grids[i];
         if (g.k_block || g.nx % 4) return false;  // Poisson operator, 16-byte rows for the TMA boxes

@@ -313,3 +313,92 @@ def test_input_generator_published_vector():
     u = inputs.uniform_pm1(0, 0, 1000, np.float64)
     assert np.array_equal(u.astype(np.float32).astype(np.float64), u)
     assert u.min() >= -1.0 and u.max() < 1.0
+
+
+# ---------------------------------------------------------- general sparse (CSR) --
+
+def kron_poisson(shape):
+    """The seven-point Dirichlet Poisson matrix assembled independently as a Kronecker sum of 1D
+    second differences (scipy CSR, float64)."""
+    sp = pytest.importorskip("scipy.sparse")
+    nz, ny, nx = shape
+
+    def lap1d(n):
+        h = 1.0 / (n + 1)
+        return sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]) / h**2
+    Ix, Iy, Iz = sp.identity(nx), sp.identity(ny), sp.identity(nz)
+    return (sp.kron(Iz, sp.kron(Iy, lap1d(nx))) + sp.kron(Iz, sp.kron(lap1d(ny), Ix))
+            + sp.kron(lap1d(nz), sp.kron(Iy, Ix))).tocsr()
+
+
+def random_spd_csr(n, seed, deg=6):
+    """A sparse symmetric positive definite matrix: the Laplacian of a random graph (seeded,
+    positive edge weights) plus a positive diagonal shift."""
+    sp = pytest.importorskip("scipy.sparse")
+    m = n * deg // 2
+    u = inputs.uniform_pm1(seed, 0, 3 * m, np.float64)
+    a = ((u[:m] + 1) * 0.5 * n).astype(np.int64) % n
+    b = ((u[m:2 * m] + 1) * 0.5 * n).astype(np.int64) % n
+    w = 1.0 + 0.5 * (u[2 * m:] + 1)
+    keep = a != b
+    W = sp.coo_matrix((w[keep], (a[keep], b[keep])), shape=(n, n))
+    W = (W + W.T).tocsr()
+    L = sp.diags(np.asarray(W.sum(axis=1)).ravel()) - W
+    shift = 0.05 + 0.5 * (inputs.uniform_pm1(seed + 1, 0, n, np.float64) + 1)
+    return (L + sp.diags(shift)).tocsr()
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 3, 7), (9, 8, 6)])
+def test_csr_apply_of_assembled_poisson_is_the_stencil(shape):
+    A = kron_poisson(shape)
+    u = inputs.uniform_rhs(shape, 31, dtype=np.float64)
+    y = oracle.csr_apply(A.indptr, A.indices, A.data, u)
+    ref = oracle.apply(u).ravel()
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_csr_apply_random_matrix_against_dense():
+    A = random_spd_csr(300, 40)
+    x = inputs.uniform_pm1(41, 0, 300, np.float64)
+    np.testing.assert_allclose(oracle.csr_apply(A.indptr, A.indices, A.data, x), A.toarray() @ x, rtol=1e-13,
+                               atol=1e-13)
+
+
+def test_csr_pcg_equals_matrix_free_pcg_on_poisson():
+    shape = (9, 8, 10)
+    A = kron_poisson(shape)
+    b = inputs.uniform_rhs(shape, 33, dtype=np.float64)
+    ref = oracle.pcg(b, tol=1e-10, maxit=500, history=True)
+    res = oracle.csr_pcg(A.indptr, A.indices, A.data, b, tol=1e-10, maxit=500, history=True)
+    assert res["status"] == ref["status"] == oracle.OK
+    assert res["iters"] == ref["iters"]
+    np.testing.assert_allclose(res["hist"], ref["hist"], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(res["x"], ref["x"].ravel(), rtol=0, atol=1e-12 * np.max(np.abs(ref["x"])))
+
+
+def test_csr_pcg_matches_scipy_cg_on_random_spd():
+    sp = pytest.importorskip("scipy.sparse")
+    A = random_spd_csr(2000, 50)
+    b = inputs.uniform_pm1(51, 0, 2000, np.float64)
+    Minv = sp.diags(1.0 / A.diagonal())
+    xs_ref, info, iterates = _scipy_cg_iterates(A, b, Minv, 1e-10, 2000)
+    res = oracle.csr_pcg(A.indptr, A.indices, A.data, b, tol=1e-10, maxit=2000, history=True)
+    assert info == 0 and res["status"] == oracle.OK
+    assert abs(res["iters"] - len(iterates)) <= 1
+    np.testing.assert_allclose(res["x"], xs_ref, rtol=0, atol=1e-8 * np.max(np.abs(xs_ref)))
+    bn = np.linalg.norm(b)
+    for it in range(1, 6):
+        r = np.linalg.norm(b - A @ iterates[it - 1]) / bn
+        assert abs(res["hist"][it] - r) <= 1e-9 * r
+
+
+def test_csr_pcg_exact_termination_two_eigenvalues():
+    """2 x 2 blocks [[2, 1], [1, 2]] on the diagonal: D^-1 A has the two eigenvalues 1/2 and 3/2,
+    so (preconditioned) CG ends in exactly two steps."""
+    sp = pytest.importorskip("scipy.sparse")
+    blk = np.array([[2.0, 1.0], [1.0, 2.0]])
+    A = sp.block_diag([blk * (1.0 + i % 3) for i in range(50)]).tocsr()
+    b = inputs.uniform_pm1(52, 0, 100, np.float64)
+    res = oracle.csr_pcg(A.indptr, A.indices, A.data, b, tol=1e-14, maxit=10)
+    assert res["status"] == oracle.OK and res["iters"] == 2
+    np.testing.assert_allclose(A @ res["x"], b, rtol=0, atol=1e-13)
