@@ -64,7 +64,8 @@ typedef enum {
 
 typedef enum {
     GBPCG_PRECOND_JACOBI = 0,
-    GBPCG_PRECOND_LEARNED = 1 /* gbpcg_fcg_solve only */
+    GBPCG_PRECOND_LEARNED = 1, /* gbpcg_fcg_solve only */
+    GBPCG_PRECOND_MG = 2       /* gbpcg_mg_pcg_solve only */
 } gbpcg_precond;
 
 /* Grid and operator.  k_block == NULL selects the constant-coefficient
@@ -372,6 +373,45 @@ int gbpcg_sell_pcg_solve(const gbpcg_sell *matrix, const double *b, double *x, c
 int gbpcg_autotune(const gbpcg_grid *grid, const gbpcg_opts *opts, const void *b, int32_t *tile_cfg,
                    double *us_per_iter, gbpcg_stream stream);
 int gbpcg_autotune_record(const gbpcg_grid *grid, const gbpcg_opts *opts, int32_t tile_cfg);
+
+/* ------------------------------------------------------------------------
+ * Geometric multigrid preconditioner (the paper's conclusion names multigrid
+ * solvers as future work; it gives no design).  Aggregation hierarchy: coarse
+ * cell I owns the 2 x 2 x 2 fine cells 2I + {0,1}^3, P copies a coarse value
+ * to them, the coarse operator is the Galerkin product P^T A P (again a
+ * seven-point operator: a coarse face carries the sum of the four fine face
+ * weights across it).  Levels are added while every size is even and stays
+ * >= 4 (at most 8 levels); the coarsest level must hold <= 32768 cells.
+ * V-cycle z = M r, omega = 0.9, sigma = 1.5:
+ *   u = omega D^-1 f;  e = V-cycle(P^T (f - A u));  u' = u + sigma P e;
+ *   result u' + omega D^-1 (f - A u');  coarsest: 24 damped Jacobi sweeps.
+ * M is symmetric positive definite, so plain PCG applies.  Grids: nx a
+ * multiple of 4; the operator of gbpcg_stencil_apply (block coefficients
+ * included).
+ * ---------------------------------------------------------------------- */
+
+/* Workspace bytes of gbpcg_mg_vcycle and gbpcg_mg_pcg_solve for a grid. */
+int gbpcg_mg_workspace_size(const gbpcg_grid *grid, size_t *bytes);
+
+/* z = M r, one V-cycle (the hierarchy is built in the call): r, z DEVICE
+ * FP32 (nz, ny, nx), distinct; *levels (may be NULL) receives the number of
+ * levels.  Workspace: DEVICE, gbpcg_mg_workspace_size bytes, 256-byte
+ * aligned. */
+int gbpcg_mg_vcycle(const gbpcg_grid *grid, const float *r, float *z, void *workspace, size_t workspace_bytes,
+                    int32_t *levels, gbpcg_stream stream);
+
+/*
+ * PCG (Sec. VII's iteration) with z = M r for A x = b.  b (read) and x
+ * (initial guess in, solution out): DEVICE FP64, 16-byte aligned.  opts:
+ * precond = GBPCG_PRECOND_MG, io_dtype F64, storage F32, no flags, tol and
+ * maxit as for gbpcg_pcg_solve, workspace of gbpcg_mg_workspace_size bytes.
+ * Vectors FP32, scalars FP64, the updates of x deferred into a correction
+ * vector and residual replacements in FP64 as in gbpcg_pcg_solve; the whole
+ * loop is one CUDA graph (the scalars stay on the device).  Fills *result
+ * (pass_launches[0] = levels of the hierarchy) and synchronises `stream`.
+ */
+int gbpcg_mg_pcg_solve(const gbpcg_grid *grid, const double *b, double *x, const gbpcg_opts *opts,
+                       gbpcg_result *result, gbpcg_stream stream);
 
 /* ------------------------------------------------------------------------
  * Learned preconditioner (no counterpart in the paper, which preconditions

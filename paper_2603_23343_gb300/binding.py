@@ -43,8 +43,8 @@ EXPORTS = ["gbpcg_version", "gbpcg_last_error", "gbpcg_dot_workspace_size", "gbp
            "gbpcg_fcg_solve", "gbpcg_wait_selftest", "gbpcg_nn_tensor_info", "gbpcg_dot_variant_workspace_size",
            "gbpcg_dot_variant", "gbpcg_stencil_apply_variant", "gbpcg_sell_stencil_layout", "gbpcg_sell_from_stencil",
            "gbpcg_sell_csr_layout", "gbpcg_sell_from_csr", "gbpcg_sell_spmv", "gbpcg_sell_workspace_size",
-           "gbpcg_sell_pcg_solve"]
-PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
+           "gbpcg_sell_pcg_solve", "gbpcg_mg_workspace_size", "gbpcg_mg_vcycle", "gbpcg_mg_pcg_solve"]
+PRECOND_JACOBI, PRECOND_LEARNED, PRECOND_MG = 0, 1, 2
 
 NN_NUM_WEIGHTS = 319248
 # (name, input channels, output channels) of the U-net's layers, in weight-array order
@@ -175,6 +175,11 @@ def load(path: str = LIB_PATH):
                                              P]
         for name in ("gbpcg_sell_stencil_layout", "gbpcg_sell_from_stencil", "gbpcg_sell_csr_layout",
                      "gbpcg_sell_from_csr", "gbpcg_sell_spmv", "gbpcg_sell_workspace_size", "gbpcg_sell_pcg_solve"):
+            getattr(lib, name).restype = ctypes.c_int
+        lib.gbpcg_mg_workspace_size.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(SZ)]
+        lib.gbpcg_mg_vcycle.argtypes = [ctypes.POINTER(Grid), P, P, P, SZ, ctypes.POINTER(I32), P]
+        lib.gbpcg_mg_pcg_solve.argtypes = [ctypes.POINTER(Grid), P, P, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
+        for name in ("gbpcg_mg_workspace_size", "gbpcg_mg_vcycle", "gbpcg_mg_pcg_solve"):
             getattr(lib, name).restype = ctypes.c_int
         lib.gbpcg_nn_forward.argtypes = [ctypes.POINTER(Grid), P, P, P, P, SZ, P]
         lib.gbpcg_nn_backward.restype = ctypes.c_int
@@ -358,6 +363,41 @@ def sell_pcg_solve(m: SellMatrix, b: torch.Tensor, x: torch.Tensor | None = None
     r = Result()
     rc = lib.gbpcg_sell_pcg_solve(ctypes.byref(m.c), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
                                   _stream(stream))
+    _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
+    return x, r.as_dict()
+
+
+def mg_workspace(shape, k_block=None, kb=8, device="cuda") -> torch.Tensor:
+    g = make_grid(shape, k_block, kb)
+    n = ctypes.c_size_t(0)
+    _check(load().gbpcg_mg_workspace_size(ctypes.byref(g), ctypes.byref(n)))
+    return torch.empty(n.value, dtype=torch.uint8, device=device)
+
+
+def mg_vcycle(r: torch.Tensor, z: torch.Tensor | None = None, k_block=None, kb=8, workspace=None, stream=None):
+    """(z = M r, levels): one multigrid V-cycle, r float32 (nz, ny, nx) (gbpcg_mg_vcycle)."""
+    if z is None:
+        z = torch.empty_like(r)
+    ws = workspace if workspace is not None else mg_workspace(r.shape, k_block, kb, r.device)
+    g = make_grid(r.shape, k_block, kb)
+    lv = ctypes.c_int32(0)
+    _check(load().gbpcg_mg_vcycle(ctypes.byref(g), _ptr(r), _ptr(z), _ptr(ws), ws.numel(), ctypes.byref(lv),
+                                  _stream(stream)))
+    return z, lv.value
+
+
+def mg_pcg_solve(b: torch.Tensor, x: torch.Tensor | None = None, tol=1e-6, maxit=2000, k_block=None, kb=8,
+                 workspace=None, stream=None):
+    """PCG with the multigrid preconditioner (gbpcg_mg_pcg_solve); b, x float64 (nz, ny, nx)."""
+    if x is None:
+        x = torch.zeros_like(b)
+    ws = workspace if workspace is not None else mg_workspace(b.shape, k_block, kb, b.device)
+    g = make_grid(b.shape, k_block, kb)
+    o = make_opts(tol, maxit, F32, F64, False, ws)
+    o.precond = PRECOND_MG
+    r = Result()
+    rc = load().gbpcg_mg_pcg_solve(ctypes.byref(g), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(r),
+                                   _stream(stream))
     _check(rc, allowed=(OK, NOT_CONVERGED, BREAKDOWN, TIMEOUT))
     return x, r.as_dict()
 

@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgbpcg.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["api.cu", "blas.cu", "pcg.cu", "pcg_f32.cu", "pcg_bf16.cu", "pcg_f16.cu", "nn.cu", "fcg.cu", "ablation.cu", "batch.cu", "sell.cu"]
+SOURCES = ["api.cu", "blas.cu", "pcg.cu", "pcg_f32.cu", "pcg_bf16.cu", "pcg_f16.cu", "nn.cu", "fcg.cu", "ablation.cu", "batch.cu", "sell.cu", "mg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills", f"-I{INCLUDE}"]

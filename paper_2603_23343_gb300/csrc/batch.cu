@@ -298,8 +298,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         if (!batch_barrier(hdr)) return;
 
         // second slot: pass B (q = A p_k, r = D z - alpha q, z = D^-1 r, r.r, r.z), or the FP64
-        // residual r = b - A x of the replacement
-        for (int t = blockIdx.x; t < total; t += G) {
+        // residual r = b - A x of the replacement.  Each CTA takes the items of its first slot in
+        // reverse order, so it starts on the tiles it (and every other CTA) touched last, still in L2.
+        const int t_last = (int)blockIdx.x < total ? (int)blockIdx.x + (int)G * ((total - 1 - (int)blockIdx.x) / (int)G) : -1;
+        for (int t = t_last; t >= 0; t -= G) {
             const int pi = owner(t);
             const BatchProblem &P = A.probs[pi];
             SolveState *st = P.st;

@@ -27,6 +27,10 @@
 //              r = D z - alpha_k q, z = D^-1 r; stores z; sums r.r, r.z
 //              -> beta_k, the convergence test and the residual-replacement
 //              trigger
+//   K_PASSR    (preconditioners other than Jacobi, which keep r itself)
+//              q = A p_k recomputed, r -= alpha_k q; stores r; sums r.r
+//              -> the convergence test and the replacement trigger (beta
+//              follows once the preconditioner has been applied to r)
 #pragma once
 
 #include <type_traits>
@@ -35,7 +39,7 @@
 
 namespace gb {
 
-enum PassKind { K_STENCIL = 0, K_PASSA = 2, K_PASSB = 3 };
+enum PassKind { K_STENCIL = 0, K_PASSA = 2, K_PASSB = 3, K_PASSR = 7 };
 
 // Device-resident solver scalars (one per solve).
 struct __align__(16) SolveState {
@@ -61,7 +65,7 @@ struct __align__(16) SolveState {
     int n_replace;  // residual replacements done
     int true_known; // 1: rr_true, bb_true already hold b - A x of the final x
     unsigned long long rhs_bits;  // max |b| as the bit pattern of a non-negative double
-    unsigned long long pad2;
+    double rzm;     // r.M r of the last residual (preconditioners other than Jacobi)
     unsigned int ticket[8];
 };
 
@@ -294,7 +298,7 @@ struct Geometry {
     static constexpr int HX = TX + 2 * XH, HY = TY + 2;
     static constexpr int NH = KIND == K_PASSA ? 2 : 1;
     static constexpr int NC = KIND == K_STENCIL ? 0 : 1;
-    static constexpr int NV = KIND == K_PASSA ? 1 : KIND == K_PASSB ? 2 : 0;
+    static constexpr int NV = KIND == K_PASSA ? 1 : KIND == K_PASSB ? 2 : KIND == K_PASSR ? 1 : 0;
     static constexpr uint32_t HBYTES = HX * HY * sizeof(T);
     static constexpr uint32_t CBYTES = TX * TY * sizeof(CenterT<T, KIND>);
     static constexpr uint32_t HB = round128(HBYTES), CB = round128(CBYTES);
@@ -345,14 +349,14 @@ struct MarchScalars {
 template <int KIND>
 __device__ __forceinline__ MarchScalars read_scalars(const SolveState *st) {
     MarchScalars sc{};
-    if constexpr (KIND == K_PASSA || KIND == K_PASSB) sc.it = st->it;
+    if constexpr (KIND == K_PASSA || KIND == K_PASSB || KIND == K_PASSR) sc.it = st->it;
     if constexpr (KIND == K_PASSA) {
         sc.first = (sc.it == 0);
         sc.beta = (float)st->beta;
         sc.alpha_prev = (float)st->alpha;
         sc.do_x = st->pending != 0;
     }
-    if constexpr (KIND == K_PASSB) sc.alpha = (float)st->alpha;
+    if constexpr (KIND == K_PASSB || KIND == K_PASSR) sc.alpha = (float)st->alpha;
     return sc;
 }
 
@@ -400,7 +404,7 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
     // Pass B marches down so it starts on the planes pass A touched last,
     // which are still in L2; the next pass A, marching up, starts where pass
     // B ended.
-    constexpr bool REV = KIND == K_PASSB;
+    constexpr bool REV = KIND == K_PASSB || KIND == K_PASSR;
     const int tl = k1 - k0 + 1;
     auto plane = [&](int t) { return REV ? k1 - t : k0 - 1 + t; };
     auto stage = [&](int t) { return (int)((ring + (uint32_t)t) % S); };
@@ -522,6 +526,15 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
                     for (int i = 0; i < V; ++i) out1[i] = fmaf(alpha_prev, po[i], xv[i]);
                     st1 = true;
                 }
+            } else if constexpr (KIND == K_PASSR) {
+                float rv[V];
+                ldv<TC, V>(cen, rv);
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const float r = fmaf(-alpha, q[i], rv[i]);
+                    out0[i] = r;
+                    if (ok[i]) acc[0] = fmaf(r, r, acc[0]);
+                }
             } else {  // K_PASSB
                 float zv[V];
                 ldv<TC, V>(cen, zv);
@@ -591,6 +604,18 @@ __device__ __forceinline__ void passb_finish(SolveState *st, int it, double rr, 
     if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
 }
 
+// Pass R's last-CTA step: the convergence test and the replacement trigger
+// on the recursive residual (beta is formed after the preconditioner).
+__device__ __forceinline__ void passr_finish(SolveState *st, int it, double rr, bool tmo) {
+    st->it = it + 1;
+    st->rr = rr;
+    st->pending = 1;
+    if (!isfinite(rr)) { st->done = 1; st->status = GBPCG_BREAKDOWN; }
+    else if (rr <= st->tol2 * st->bb || rr <= kReplaceDrop2 * st->rr_rep) st->replace = rr <= st->tol2 * st->bb ? 2 : 1;
+    else if (it + 1 >= st->maxit) { st->done = 1; st->status = GBPCG_NOT_CONVERGED; }
+    if (tmo) { st->done = 1; st->status = GBPCG_TIMEOUT; st->replace = 0; }
+}
+
 template <typename T, int TX, int TY, int S, int KIND, bool TMA, typename Op, bool ZFILL = false>
 __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     zmarch_kernel(const __grid_constant__ PassMaps maps, const PassArgs a, const Op op) {
@@ -603,7 +628,7 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     __shared__ int s_timeout;
 
     SolveState *st = a.st;
-    if constexpr (KIND == K_PASSA || KIND == K_PASSB) {
+    if constexpr (KIND == K_PASSA || KIND == K_PASSB || KIND == K_PASSR) {
         if (st->done) return;  // uniform across the grid
     }
     MarchScalars sc = read_scalars<KIND>(st);
@@ -612,7 +637,7 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
 
     int sh0 = 0, sh1 = 0, so0 = 0;
     if constexpr (KIND == K_PASSA) { sh1 = (it + 1) & 1; so0 = it & 1; }
-    if constexpr (KIND == K_PASSB) sh0 = it & 1;
+    if constexpr (KIND == K_PASSB || KIND == K_PASSR) sh0 = it & 1;
     MarchIO<T, KIND> io;
     io.H0 = static_cast<const T *>(a.h0[sh0]);
     io.H1 = static_cast<const T *>(a.h1[sh1]);
@@ -661,7 +686,8 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
             __threadfence();
             const bool tmo = atomicAdd(&st->timeout, 0) != 0;
             if constexpr (KIND == K_PASSA) passa_finish(st, tot[0], tmo);
-            else passb_finish(st, it, tot[0], tot[1], tmo);
+            else if constexpr (KIND == K_PASSR) passr_finish(st, it, tot[0], tmo);
+            else passb_finish(st, it, tot[0], tot[NV - 1], tmo);
             if (a.use_cond) {
                 cudaGraphSetConditional(a.cond, st->done ? 0u : 1u);
                 cudaGraphSetConditional(a.cond_replace, st->replace ? 1u : 0u);

@@ -112,6 +112,7 @@ struct Res64Args {
     const double *tab64;   // FP64 face weights per coefficient block (build_face_table64)
     const double *bscale;  // NULL, or a device scalar multiplying b (inner refinement solves)
     int rhs_auto;          // 1: b and x are scaled by rhs_scale(st->rhs_bits) (plain solves)
+    int store_r;           // 1: store r itself into z (preconditioners other than Jacobi)
     SolveState *st;
     double *partials;
     cudaGraphConditionalHandle cond;
@@ -207,7 +208,7 @@ __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row
                     k0.add(rs * rs);
                 } else {
                     const float dg = BLOCK ? diag64(w) : dg_const;
-                    const T zt = from_f<T>(rf / dg);
+                    const T zt = from_f<T>(a.store_r ? rf : rf / dg);
                     static_cast<T *>(a.z)[g] = zt;
                     if (MODE == RES_INIT) {
                         s0 = fma(r, r, s0);
