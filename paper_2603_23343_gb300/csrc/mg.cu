@@ -110,63 +110,63 @@ __device__ __forceinline__ float mg_offdiag(const MgLevel &L, int i, int j, int 
 
 __device__ __forceinline__ bool mg_stand_down(const MgArgs &a) { return a.st && a.st->done; }
 
+// Launch geometry of the level kernels: x along a row (up to 256 threads),
+// y and z from the block index: no integer division per point.
+struct MgLaunch {
+    dim3 grid, block;
+};
+inline MgLaunch mg_launch(int nx, int ny, int nz) {
+    const int bx = std::min(kMgThreads, (nx + 31) / 32 * 32);
+    return MgLaunch{dim3((unsigned)((nx + bx - 1) / bx), (unsigned)ny, (unsigned)nz), dim3((unsigned)bx)};
+}
+
 // u = omega D^-1 f at level l
 __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int l) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l];
-    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
-    for (int64_t c = (int64_t)blockIdx.x * kMgThreads + threadIdx.x; c < n; c += (int64_t)gridDim.x * kMgThreads) {
-        const int i = (int)(c % L.nx);
-        const int64_t t = c / L.nx;
-        const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-        float w[6], D;
-        mg_weights(a, l, i, j, k, w, D);
-        L.u[c] = kMgOmega * L.f[c] / D;
-    }
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= L.nx) return;
+    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+    float w[6], D;
+    mg_weights(a, l, i, j, k, w, D);
+    L.u[c] = kMgOmega * L.f[c] / D;
 }
 
 // f_{l+1} = P^T (f - A u): one thread per coarse cell, the residual of its eight fine cells
 __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int64_t nc = (int64_t)C.nx * C.ny * C.nz;
-    for (int64_t cc = (int64_t)blockIdx.x * kMgThreads + threadIdx.x; cc < nc; cc += (int64_t)gridDim.x * kMgThreads) {
-        const int I = (int)(cc % C.nx);
-        const int64_t t = cc / C.nx;
-        const int J = (int)(t % C.ny), K = (int)(t / C.ny);
-        float s = 0.f;
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-                    float w[6], D;
-                    mg_weights(a, l, i, j, k, w, D);
-                    const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
-                    s += L.f[c] - fmaf(D, L.u[c], -off);
-                }
-        C.f[cc] = s;
-    }
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= C.nx) return;
+    float s = 0.f;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+                float w[6], D;
+                mg_weights(a, l, i, j, k, w, D);
+                const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
+                s += L.f[c] - fmaf(D, L.u[c], -off);
+            }
+    C.f[((int64_t)K * C.ny + J) * C.nx + I] = s;
 }
 
 // out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1) result
 __global__ void __launch_bounds__(kMgThreads) mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= L.nx) return;
     auto up = [&](int64_t q, int qi, int qj, int qk) {
         return fmaf(kMgSigma, __ldg(e + ((int64_t)(qk >> 1) * C.ny + (qj >> 1)) * C.nx + (qi >> 1)), L.u[q]);
     };
-    for (int64_t c = (int64_t)blockIdx.x * kMgThreads + threadIdx.x; c < n; c += (int64_t)gridDim.x * kMgThreads) {
-        const int i = (int)(c % L.nx);
-        const int64_t t = c / L.nx;
-        const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-        float w[6], D;
-        mg_weights(a, l, i, j, k, w, D);
-        const float uc = up(c, i, j, k);
-        const float off = mg_offdiag(L, i, j, k, c, w, up);
-        L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
-    }
+    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+    float w[6], D;
+    mg_weights(a, l, i, j, k, w, D);
+    const float uc = up(c, i, j, k);
+    const float off = mg_offdiag(L, i, j, k, c, w, up);
+    L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
 }
 
 // coarsest level: kMgCoarseSweeps damped Jacobi sweeps from zero in one CTA;
@@ -209,25 +209,21 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mg_coarse_kernel(const MgArg
 
 // Galerkin coarsening of level l into level l + 1 (one thread per coarse cell)
 __global__ void __launch_bounds__(kMgThreads) mg_galerkin_kernel(const MgArgs a, int l, float4 *Wc) {
-    const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int64_t nc = (int64_t)C.nx * C.ny * C.nz;
-    for (int64_t cc = (int64_t)blockIdx.x * kMgThreads + threadIdx.x; cc < nc; cc += (int64_t)gridDim.x * kMgThreads) {
-        const int I = (int)(cc % C.nx);
-        const int64_t t = cc / C.nx;
-        const int J = (int)(t % C.ny), K = (int)(t / C.ny);
-        float sx = 0.f, sy = 0.f, sz = 0.f, sD = 0.f, inner = 0.f;
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    float w[6], D;
-                    mg_weights(a, l, 2 * I + dx, 2 * J + dy, 2 * K + dz, w, D);
-                    sD += D;
-                    if (dx == 1) sx += w[1]; else inner += w[1];
-                    if (dy == 1) sy += w[3]; else inner += w[3];
-                    if (dz == 1) sz += w[5]; else inner += w[5];
-                }
-        Wc[cc] = make_float4(sx, sy, sz, sD - 2.0f * inner);
-    }
+    const MgLevel &C = a.lv[l + 1];
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
+    if (I >= C.nx) return;
+    float sx = 0.f, sy = 0.f, sz = 0.f, sD = 0.f, inner = 0.f;
+    for (int dz = 0; dz < 2; ++dz)
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) {
+                float w[6], D;
+                mg_weights(a, l, 2 * I + dx, 2 * J + dy, 2 * K + dz, w, D);
+                sD += D;
+                if (dx == 1) sx += w[1]; else inner += w[1];
+                if (dy == 1) sy += w[3]; else inner += w[3];
+                if (dz == 1) sz += w[5]; else inner += w[5];
+            }
+    Wc[((int64_t)K * C.ny + J) * C.nx + I] = make_float4(sx, sy, sz, sD - 2.0f * inner);
 }
 
 // r.z; last CTA: beta (the first time, only r.z), breakdown, the loop condition
@@ -340,26 +336,30 @@ unsigned mg_grid(int64_t n) {
         1, std::min<int64_t>((n + kMgThreads - 1) / kMgThreads, (int64_t)device_sm_count() * 8));
 }
 
-int64_t level_points(const MgArgs &a, int l) { return (int64_t)a.lv[l].nx * a.lv[l].ny * a.lv[l].nz; }
-
 // the coarse operators (once per solve)
 cudaError_t mg_setup(const MgArgs &a, cudaStream_t s) {
-    for (int l = 0; l + 1 < a.L; ++l)
-        mg_galerkin_kernel<<<mg_grid(level_points(a, l + 1)), kMgThreads, 0, s>>>(a, l,
-                                                                                    const_cast<float4 *>(a.lv[l + 1].W));
+    for (int l = 0; l + 1 < a.L; ++l) {
+        const MgLevel &C = a.lv[l + 1];
+        const MgLaunch g = mg_launch(C.nx, C.ny, C.nz);
+        mg_galerkin_kernel<<<g.grid, g.block, 0, s>>>(a, l, const_cast<float4 *>(C.W));
+    }
     return cudaGetLastError();
 }
 
 // z = M f0 (a.lv[0].f -> a.lv[0].w)
 cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     for (int l = 0; l + 1 < a.L; ++l) {
-        mg_pre_kernel<<<mg_grid(level_points(a, l)), kMgThreads, 0, s>>>(a, l);
-        mg_restrict_kernel<<<mg_grid(level_points(a, l + 1)), kMgThreads, 0, s>>>(a, l);
+        const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
+        const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz), gc = mg_launch(C.nx, C.ny, C.nz);
+        mg_pre_kernel<<<gf.grid, gf.block, 0, s>>>(a, l);
+        mg_restrict_kernel<<<gc.grid, gc.block, 0, s>>>(a, l);
     }
     mg_coarse_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, a.L - 1);
     for (int l = a.L - 2; l >= 0; --l) {
+        const MgLevel &L = a.lv[l];
+        const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
         const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
-        mg_post_kernel<<<mg_grid(level_points(a, l)), kMgThreads, 0, s>>>(a, l, e);
+        mg_post_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, e);
     }
     return cudaGetLastError();
 }
@@ -372,6 +372,7 @@ int check_mg_grid(const gbpcg_grid *g) {
         return fail_arg("multigrid: the grid does not coarsen below 32768 cells (each size must be even, "
                         "down to >= 4, often enough)");
     if (g->nx % 4) return fail_arg("multigrid solves need nx a multiple of 4 (16-byte rows)");
+    if (g->ny > 65535 || g->nz > 65535) return fail_arg("multigrid: ny and nz must be at most 65535");
     return GBPCG_OK;
 }
 
