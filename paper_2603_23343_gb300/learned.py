@@ -93,40 +93,3 @@ def identity_weights() -> torch.Tensor:
     ws["c8"][0, 13, 32], ws["c8"][1, 13, 33] = 1.0, 1.0
     ws["c9"][0, 13, 0], ws["c9"][0, 13, 1] = 1.0, -1.0
     return binding.nn_pack_weights(ws)
-
-
-def _main(argv=None):
-    """Fixed workloads for profilers, with seeded initial weights on the seeded lognormal
-    problem at N^3:
-      python -m paper_2603_23343_gb300.learned forward --n N --reps R   (R network applications)
-      python -m paper_2603_23343_gb300.learned train --n N --reps R     (R training steps on the
-          exact pair e ~ U[-1,1), r = A e)"""
-    import argparse
-    ap = argparse.ArgumentParser(prog="python -m paper_2603_23343_gb300.learned")
-    ap.add_argument("command", choices=["forward", "train"])
-    ap.add_argument("--n", type=int, default=128)
-    ap.add_argument("--reps", type=int, default=2)
-    a = ap.parse_args(argv)
-    shape = (a.n, a.n, a.n)
-    k, b = problem(shape, 100)
-    w = initial_weights(0).cuda()
-    if a.command == "train":
-        e64 = torch.from_numpy(inputs.uniform_rhs(shape, 7, 0, np.float64)).cuda()
-        r = binding.stencil_apply(e64, k_block=k).float()
-        tr = binding.NnTrainer(w, shape, k_block=k)
-        for _ in range(a.reps):
-            loss = tr.step(r, e64.float())
-        tr.status()
-        print(f"train {a.n}^3 x{a.reps}: loss {loss.item():.6g}")
-        return
-    ws = binding.nn_workspace(shape)
-    r = b.float()
-    z = torch.empty_like(r)
-    for _ in range(a.reps):
-        binding.nn_forward(w, r, z, k_block=k, workspace=ws)
-    torch.cuda.synchronize()
-    print(f"forward {a.n}^3 x{a.reps}: max |z| = {float(z.abs().max()):.6g}")
-
-
-if __name__ == "__main__":
-    _main()
