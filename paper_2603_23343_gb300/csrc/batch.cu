@@ -53,8 +53,7 @@ struct __align__(128) BatchProblem {
     CUtensorMap hz, hp0, hp1;  // halo boxes of z, p0, p1
     CUtensorMap cd, cz;        // centre boxes of d (pass A) and z (pass B)
     OpConst op;
-    int nx, ny, nz, tiles_x, tiles, zdepth, zchunks;
-    int item0, nitems;          // pass items
+    int nx, ny, nz, tiles_x, tiles;
     int row0_item, nrow_items;  // row items
     int rows_per_item;
     float *z, *p0, *p1, *d;
@@ -72,10 +71,9 @@ struct __align__(64) BatchHeader {
 
 struct BatchArgs {
     BatchProblem *probs;
-    const int *item_prob;  // pass item -> problem
     const int *row_prob;   // row item -> problem
     BatchHeader *hdr;
-    int nprob, nitems, nrow_items;
+    int nprob, nrow_items;
     double tol;
     int maxit;
 };
@@ -203,17 +201,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
     // evenly over the CTAs.
     __shared__ int s_pre[kBatchMaxProblems + 1];
     __shared__ unsigned char s_mode[kBatchMaxProblems];
-    for (int round = 0;; ++round) {
-        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
-            const SolveState *st = A.probs[p].st;
-            const int done = ((volatile const int *)&st->done)[0];
-            const int rep = ((volatile const int *)&st->replace)[0];
-            const int mode = done ? 0 : rep ? 2 : 1;
-            s_mode[p] = (unsigned char)mode;
-            s_pre[p + 1] = mode == 1 ? A.probs[p].nitems : mode == 2 ? A.probs[p].nrow_items : 0;
-        }
-        __syncthreads();
-        if (threadIdx.x < 32) {  // inclusive scan of the counts, 32 chunks of contiguous problems
+    __shared__ unsigned short s_dep[kBatchMaxProblems];
+    __shared__ int s_depth;
+    // inclusive scan of s_pre[1 .. nprob] by warp 0 (32 chunks of contiguous problems); total
+    // returned in every lane of warp 0
+    auto scan = [&]() {
+        if (threadIdx.x < 32) {
             const int per = (A.nprob + 31) / 32;
             const int a = min(A.nprob, (int)threadIdx.x * per), e = min(A.nprob, a + per);
             int sum = 0;
@@ -231,6 +224,39 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             }
             if (threadIdx.x == 0) s_pre[0] = 0;
         }
+    };
+    for (int round = 0;; ++round) {
+        // modes, and the tile-planes of the iterating problems
+        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
+            const SolveState *st = A.probs[p].st;
+            const int done = ((volatile const int *)&st->done)[0];
+            const int rep = ((volatile const int *)&st->replace)[0];
+            const int mode = done ? 0 : rep ? 2 : 1;
+            s_mode[p] = (unsigned char)mode;
+            s_pre[p + 1] = mode == 1 ? A.probs[p].tiles * A.probs[p].nz : 0;
+        }
+        __syncthreads();
+        scan();
+        __syncthreads();
+        // z planes per pass item this round: about two items per CTA over the iterating
+        // problems, between 4 and 32 planes (deep items while the batch is large, shallow ones
+        // once few problems remain, so the work still spreads over the GPU)
+        if (threadIdx.x == 0) {
+            const int tp = s_pre[A.nprob];
+            s_depth = max(4, min(kBatchZDepth, (tp + 2 * (int)G - 1) / (2 * (int)G)));
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
+            const BatchProblem &P = A.probs[p];
+            // at least enough planes per item that the problem's pass-B partials fit its slots
+            const int need = (2 * P.tiles * P.nz + 4 * (int)kMaxPassBlocks - 1) / (4 * (int)kMaxPassBlocks);
+            const int dep = min(P.nz, max(s_depth, need));
+            s_dep[p] = (unsigned short)dep;
+            const int mode = s_mode[p];
+            s_pre[p + 1] = mode == 1 ? P.tiles * ((P.nz + dep - 1) / dep) : mode == 2 ? P.nrow_items : 0;
+        }
+        __syncthreads();
+        scan();
         __syncthreads();
         const int total = s_pre[A.nprob];
         if (total == 0) break;
@@ -252,9 +278,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             SolveState *st = P.st;
             const int local = t - s_pre[pi];
             if (s_mode[pi] == 1) {
+                const int dep = s_dep[pi], nit = s_pre[pi + 1] - s_pre[pi];
                 const int tile = local % P.tiles, chunk = local / P.tiles;
                 const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-                const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+                const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
                 const MarchScalars sc = read_scalars<K_PASSA>(st);
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSA> io;
@@ -277,7 +304,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 }
                 double part[1], tot[1];
                 block_sum<1, kBatchThreads>(acc, part);
-                if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, P.nitems, tot) &&
+                if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, nit, tot) &&
                     threadIdx.x == 0)
                     passa_finish(st, tot[0], false);
             } else {
@@ -307,9 +334,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             SolveState *st = P.st;
             const int local = t - s_pre[pi];
             if (s_mode[pi] == 1) {
+                const int dep = s_dep[pi], nit = s_pre[pi + 1] - s_pre[pi];
                 const int tile = local % P.tiles, chunk = local / P.tiles;
                 const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-                const int k0 = chunk * P.zdepth, k1 = min(P.nz, k0 + P.zdepth);
+                const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
                 const MarchScalars sc = read_scalars<K_PASSB>(st);
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSB> io;
@@ -332,7 +360,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 }
                 double part[2], tot[2];
                 block_sum<2, kBatchThreads>(acc, part);
-                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, P.nitems, tot) &&
+                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, nit, tot) &&
                     threadIdx.x == 0)
                     passb_finish(st, sc.it, tot[0], tot[1], false);
             } else {
@@ -410,18 +438,17 @@ BatchKernel batch_kernel_for(int cfg) {
     }
 }
 
-// Geometry of one problem under a configuration.
+// Geometry of one problem under a configuration (pass items: the rounds
+// choose their own z depth; row items: the setup, replacement and finalize
+// slots).
 struct ProbGeom {
-    int tiles_x, tiles, zdepth, zchunks, nitems, rows_per_item, nrow_items;
+    int tiles_x, tiles, rows_per_item, nrow_items;
 };
 ProbGeom prob_geom(const gbpcg_grid &g, int cfg) {
     const BcDims d = bc_dims(cfg);
     ProbGeom p;
     p.tiles_x = (g.nx + d.tx - 1) / d.tx;
     p.tiles = p.tiles_x * ((g.ny + d.ty - 1) / d.ty);
-    p.zdepth = std::min(g.nz, kBatchZDepth);
-    p.zchunks = (g.nz + p.zdepth - 1) / p.zdepth;
-    p.nitems = p.tiles * p.zchunks;
     // at least kRowPoints points per row item, and few enough items for the partial-sum slots
     p.rows_per_item = std::max({1, kRowPoints / g.nx, (g.ny * g.nz + 4095) / 4096});
     p.nrow_items = (g.ny * g.nz + p.rows_per_item - 1) / p.rows_per_item;
@@ -429,34 +456,20 @@ ProbGeom prob_geom(const gbpcg_grid &g, int cfg) {
 }
 
 struct BatchLayout {
-    size_t hdr, probs, items, rows, total;
-    int nitems, nrow_items;
+    size_t hdr, probs, rows, total;
 };
 
 // The batch's own region at the front of the workspace: header, problem
-// table, item-to-problem maps (sized for the configuration with the most
-// items, so one workspace serves every configuration).
+// table and the row-item-to-problem map.
 BatchLayout batch_layout(int nprob, const gbpcg_grid *grids) {
     BatchLayout L;
-    int items = 0, rows = 0;
-    for (int c = 0; c < BC_COUNT; ++c) {
-        int it = 0, rw = 0;
-        for (int i = 0; i < nprob; ++i) {
-            const ProbGeom p = prob_geom(grids[i], c);
-            it += p.nitems;
-            rw += p.nrow_items;
-        }
-        items = std::max(items, it);
-        rows = std::max(rows, rw);
-    }
+    int rows = 0;
+    for (int i = 0; i < nprob; ++i) rows += prob_geom(grids[i], 0).nrow_items;  // the same for every cfg
     size_t o = 0;
     L.hdr = o; o += round256(sizeof(BatchHeader));
     L.probs = o; o += round256(sizeof(BatchProblem) * (size_t)nprob);
-    L.items = o; o += round256(sizeof(int) * (size_t)items);
     L.rows = o; o += round256(sizeof(int) * (size_t)rows);
     L.total = o;
-    L.nitems = items;
-    L.nrow_items = rows;
     return L;
 }
 
@@ -488,8 +501,8 @@ bool batch_persistent_ok(int nprob, const gbpcg_grid *grids) {
     for (int i = 0; i < nprob; ++i) {
         const gbpcg_grid &g = grids[i];
         if (g.k_block || g.nx % 4) return false;  // Poisson operator, 16-byte rows for the TMA boxes
-        for (int c = 0; c < BC_COUNT; ++c)
-            if (prob_geom(g, c).nitems * 2 > 4 * (int)kMaxPassBlocks) return false;
+        for (int c = 0; c < BC_COUNT; ++c)  // a round's item depth keeps every problem within its slots
+            if (prob_geom(g, c).tiles > 4096) return false;
     }
     return true;
 }
@@ -507,8 +520,8 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
     const BatchLayout BL = batch_layout(nprob, grids);
     const BcDims dims = bc_dims(cfg);
     std::vector<BatchProblem> probs(nprob);
-    std::vector<int> item_prob, row_prob;
-    int nitems = 0, nrow = 0;
+    std::vector<int> row_prob;
+    int nrow = 0;
     for (int i = 0; i < nprob; ++i) {
         const gbpcg_grid &g = grids[i];
         const SolveCall &c = calls[i];
@@ -538,14 +551,11 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
         if (rc) return GBPCG_ERR_CUDA;
         P.op = make_op_const(g.nx, g.ny, g.nz);
         P.nx = g.nx; P.ny = g.ny; P.nz = g.nz;
-        P.tiles_x = pg.tiles_x; P.tiles = pg.tiles; P.zdepth = pg.zdepth; P.zchunks = pg.zchunks;
-        P.item0 = nitems; P.nitems = pg.nitems;
+        P.tiles_x = pg.tiles_x; P.tiles = pg.tiles;
         P.row0_item = nrow; P.nrow_items = pg.nrow_items; P.rows_per_item = pg.rows_per_item;
-        if ((size_t)pg.nitems * 2 > 4 * kMaxPassBlocks || (size_t)pg.nrow_items * 3 > 4 * kMaxPassBlocks)
-            return fail_arg("persistent batch: a grid has more work items than its partial-sum slots");
-        for (int k = 0; k < pg.nitems; ++k) item_prob.push_back(i);
+        if ((size_t)pg.nrow_items * 3 > 4 * kMaxPassBlocks)
+            return fail_arg("persistent batch: a grid has more row items than its partial-sum slots");
         for (int k = 0; k < pg.nrow_items; ++k) row_prob.push_back(i);
-        nitems += pg.nitems;
         nrow += pg.nrow_items;
         auto cc = [](int m) { double h = 1.0 / (m + 1); return 1.0 / (h * h); };
         Res64Args &ra = P.ra;
@@ -562,7 +572,6 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
     }
     BatchHeader *hdr = reinterpret_cast<BatchHeader *>(region + BL.hdr);
     BatchProblem *dprobs = reinterpret_cast<BatchProblem *>(region + BL.probs);
-    int *ditems = reinterpret_cast<int *>(region + BL.items);
     int *drows = reinterpret_cast<int *>(region + BL.rows);
 
     const BatchKernel K = io == GBPCG_F64 ? batch_kernel_for<double>(cfg) : batch_kernel_for<float>(cfg);
@@ -574,11 +583,9 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
 
     BatchArgs A;
     A.probs = dprobs;
-    A.item_prob = ditems;
     A.row_prob = drows;
     A.hdr = hdr;
     A.nprob = nprob;
-    A.nitems = nitems;
     A.nrow_items = nrow;
     A.tol = tol;
     A.maxit = maxit;
@@ -586,7 +593,6 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
     // the table is copied on every call (the stream orders it before the kernel); its contents
     // depend only on the key, so a cached graph stays valid
     GB_CUDA(cudaMemcpyAsync(dprobs, probs.data(), sizeof(BatchProblem) * nprob, cudaMemcpyHostToDevice, s));
-    GB_CUDA(cudaMemcpyAsync(ditems, item_prob.data(), sizeof(int) * item_prob.size(), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemcpyAsync(drows, row_prob.data(), sizeof(int) * row_prob.size(), cudaMemcpyHostToDevice, s));
     GB_CUDA(cudaMemsetAsync(hdr, 0, sizeof(BatchHeader), s));
     // the host arrays must outlive the copies

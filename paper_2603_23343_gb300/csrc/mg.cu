@@ -110,63 +110,92 @@ __device__ __forceinline__ float mg_offdiag(const MgLevel &L, int i, int j, int 
 
 __device__ __forceinline__ bool mg_stand_down(const MgArgs &a) { return a.st && a.st->done; }
 
-// Launch geometry of the level kernels: x along a row (up to 256 threads),
-// y and z from the block index: no integer division per point.
+// Launch geometry of the level kernels: a block is bx threads along x times
+// by rows along y and marches through zper planes; x, y and z come from the
+// block and thread indices (no integer division per point), and there are
+// about as many blocks as two waves of resident CTAs.
 struct MgLaunch {
     dim3 grid, block;
+    int zper;
 };
 inline MgLaunch mg_launch(int nx, int ny, int nz) {
     const int bx = std::min(kMgThreads, (nx + 31) / 32 * 32);
-    return MgLaunch{dim3((unsigned)((nx + bx - 1) / bx), (unsigned)ny, (unsigned)nz), dim3((unsigned)bx)};
+    const int by = std::max(1, std::min(kMgThreads / bx, ny));
+    const int64_t gxy = (int64_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by);
+    const int64_t want = (int64_t)device_sm_count() * 16;
+    const int gz = (int)std::max<int64_t>(1, std::min<int64_t>(nz, (want + gxy - 1) / gxy));
+    const int zper = (nz + gz - 1) / gz;
+    return MgLaunch{dim3((unsigned)((nx + bx - 1) / bx), (unsigned)((ny + by - 1) / by), (unsigned)((nz + zper - 1) / zper)),
+                    dim3((unsigned)bx, (unsigned)by), zper};
 }
 
 // u = omega D^-1 f at level l
-__global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int l) {
+__global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= L.nx) return;
-    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-    float w[6], D;
-    mg_weights(a, l, i, j, k, w, D);
-    L.u[c] = kMgOmega * L.f[c] / D;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= L.nx || j >= L.ny) return;
+    const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
+    for (int k = k0; k < k1; ++k) {
+        const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+        float w[6], D;
+        mg_weights(a, l, i, j, k, w, D);
+        L.u[c] = kMgOmega * L.f[c] / D;
+    }
 }
 
 // f_{l+1} = P^T (f - A u): one thread per coarse cell, the residual of its eight fine cells
-__global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l) {
+__global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
-    if (I >= C.nx) return;
-    float s = 0.f;
-    for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-                const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-                float w[6], D;
-                mg_weights(a, l, i, j, k, w, D);
-                const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
-                s += L.f[c] - fmaf(D, L.u[c], -off);
-            }
-    C.f[((int64_t)K * C.ny + J) * C.nx + I] = s;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= C.nx || J >= C.ny) return;
+    const int K0 = blockIdx.z * zper, K1 = min(C.nz, K0 + zper);
+    for (int K = K0; K < K1; ++K) {
+        float s = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+                    float w[6], D;
+                    mg_weights(a, l, i, j, k, w, D);
+                    const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
+                    s += L.f[c] - fmaf(D, L.u[c], -off);
+                }
+        C.f[((int64_t)K * C.ny + J) * C.nx + I] = s;
+    }
 }
 
-// out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1) result
-__global__ void __launch_bounds__(kMgThreads) mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e) {
+// out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1)
+// result: at a neighbour the parent is the point's own parent on the odd
+// side of the pair, the next coarse cell on the even side
+__global__ void __launch_bounds__(kMgThreads)
+    mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
-    if (i >= L.nx) return;
-    auto up = [&](int64_t q, int qi, int qj, int qk) {
-        return fmaf(kMgSigma, __ldg(e + ((int64_t)(qk >> 1) * C.ny + (qj >> 1)) * C.nx + (qi >> 1)), L.u[q]);
-    };
-    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-    float w[6], D;
-    mg_weights(a, l, i, j, k, w, D);
-    const float uc = up(c, i, j, k);
-    const float off = mg_offdiag(L, i, j, k, c, w, up);
-    L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= L.nx || j >= L.ny) return;
+    const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
+    const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny, cy = C.nx, cz = (int64_t)C.nx * C.ny;
+    const bool io = i & 1, jo = j & 1;
+    for (int k = k0; k < k1; ++k) {
+        const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+        const int64_t cc = ((int64_t)(k >> 1) * C.ny + (j >> 1)) * C.nx + (i >> 1);
+        const bool ko = k & 1;
+        float w[6], D;
+        mg_weights(a, l, i, j, k, w, D);
+        const float ec = __ldg(e + cc);
+        const float uc = fmaf(kMgSigma, ec, L.u[c]);
+        float off = 0.f;
+        if (w[0] != 0.f) off = fmaf(w[0], fmaf(kMgSigma, io ? ec : __ldg(e + cc - 1), L.u[c - 1]), off);
+        if (w[1] != 0.f) off = fmaf(w[1], fmaf(kMgSigma, io ? __ldg(e + cc + 1) : ec, L.u[c + 1]), off);
+        if (w[2] != 0.f) off = fmaf(w[2], fmaf(kMgSigma, jo ? ec : __ldg(e + cc - cy), L.u[c - sy]), off);
+        if (w[3] != 0.f) off = fmaf(w[3], fmaf(kMgSigma, jo ? __ldg(e + cc + cy) : ec, L.u[c + sy]), off);
+        if (w[4] != 0.f) off = fmaf(w[4], fmaf(kMgSigma, ko ? ec : __ldg(e + cc - cz), L.u[c - sz]), off);
+        if (w[5] != 0.f) off = fmaf(w[5], fmaf(kMgSigma, ko ? __ldg(e + cc + cz) : ec, L.u[c + sz]), off);
+        L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
+    }
 }
 
 // coarsest level: kMgCoarseSweeps damped Jacobi sweeps from zero in one CTA;
@@ -208,22 +237,25 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mg_coarse_kernel(const MgArg
 }
 
 // Galerkin coarsening of level l into level l + 1 (one thread per coarse cell)
-__global__ void __launch_bounds__(kMgThreads) mg_galerkin_kernel(const MgArgs a, int l, float4 *Wc) {
+__global__ void __launch_bounds__(kMgThreads) mg_galerkin_kernel(const MgArgs a, int l, float4 *Wc, int zper) {
     const MgLevel &C = a.lv[l + 1];
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y, K = blockIdx.z;
-    if (I >= C.nx) return;
-    float sx = 0.f, sy = 0.f, sz = 0.f, sD = 0.f, inner = 0.f;
-    for (int dz = 0; dz < 2; ++dz)
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx) {
-                float w[6], D;
-                mg_weights(a, l, 2 * I + dx, 2 * J + dy, 2 * K + dz, w, D);
-                sD += D;
-                if (dx == 1) sx += w[1]; else inner += w[1];
-                if (dy == 1) sy += w[3]; else inner += w[3];
-                if (dz == 1) sz += w[5]; else inner += w[5];
-            }
-    Wc[((int64_t)K * C.ny + J) * C.nx + I] = make_float4(sx, sy, sz, sD - 2.0f * inner);
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I >= C.nx || J >= C.ny) return;
+    const int K0 = blockIdx.z * zper, K1 = min(C.nz, K0 + zper);
+    for (int K = K0; K < K1; ++K) {
+        float sx = 0.f, sy = 0.f, sz = 0.f, sD = 0.f, inner = 0.f;
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    float w[6], D;
+                    mg_weights(a, l, 2 * I + dx, 2 * J + dy, 2 * K + dz, w, D);
+                    sD += D;
+                    if (dx == 1) sx += w[1]; else inner += w[1];
+                    if (dy == 1) sy += w[3]; else inner += w[3];
+                    if (dz == 1) sz += w[5]; else inner += w[5];
+                }
+        Wc[((int64_t)K * C.ny + J) * C.nx + I] = make_float4(sx, sy, sz, sD - 2.0f * inner);
+    }
 }
 
 // r.z; last CTA: beta (the first time, only r.z), breakdown, the loop condition
@@ -341,7 +373,7 @@ cudaError_t mg_setup(const MgArgs &a, cudaStream_t s) {
     for (int l = 0; l + 1 < a.L; ++l) {
         const MgLevel &C = a.lv[l + 1];
         const MgLaunch g = mg_launch(C.nx, C.ny, C.nz);
-        mg_galerkin_kernel<<<g.grid, g.block, 0, s>>>(a, l, const_cast<float4 *>(C.W));
+        mg_galerkin_kernel<<<g.grid, g.block, 0, s>>>(a, l, const_cast<float4 *>(C.W), g.zper);
     }
     return cudaGetLastError();
 }
@@ -351,15 +383,15 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     for (int l = 0; l + 1 < a.L; ++l) {
         const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
         const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz), gc = mg_launch(C.nx, C.ny, C.nz);
-        mg_pre_kernel<<<gf.grid, gf.block, 0, s>>>(a, l);
-        mg_restrict_kernel<<<gc.grid, gc.block, 0, s>>>(a, l);
+        mg_pre_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
+        mg_restrict_kernel<<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
     }
     mg_coarse_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, a.L - 1);
     for (int l = a.L - 2; l >= 0; --l) {
         const MgLevel &L = a.lv[l];
         const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
         const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
-        mg_post_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, e);
+        mg_post_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
     }
     return cudaGetLastError();
 }
