@@ -136,11 +136,14 @@ __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int 
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
+    const float *__restrict__ f = L.f;
+    float *__restrict__ u = L.u;
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
         const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
         float w[6], D;
         mg_weights(a, l, i, j, k, w, D);
-        L.u[c] = kMgOmega * L.f[c] / D;
+        u[c] = kMgOmega * f[c] / D;
     }
 }
 
@@ -151,19 +154,26 @@ __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a,
     const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I >= C.nx || J >= C.ny) return;
     const int K0 = blockIdx.z * zper, K1 = min(C.nz, K0 + zper);
+    const float *__restrict__ u = L.u;
+    const float *__restrict__ f = L.f;
+    float *__restrict__ fc = C.f;
+#pragma unroll 2
     for (int K = K0; K < K1; ++K) {
         float s = 0.f;
+#pragma unroll
         for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
             for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
                     const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
                     const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
                     float w[6], D;
                     mg_weights(a, l, i, j, k, w, D);
-                    const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
-                    s += L.f[c] - fmaf(D, L.u[c], -off);
+                    const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return u[q]; });
+                    s += f[c] - fmaf(D, u[c], -off);
                 }
-        C.f[((int64_t)K * C.ny + J) * C.nx + I] = s;
+        fc[((int64_t)K * C.ny + J) * C.nx + I] = s;
     }
 }
 
@@ -179,6 +189,10 @@ __global__ void __launch_bounds__(kMgThreads)
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
     const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny, cy = C.nx, cz = (int64_t)C.nx * C.ny;
     const bool io = i & 1, jo = j & 1;
+    const float *__restrict__ u = L.u;
+    const float *__restrict__ f = L.f;
+    float *__restrict__ out = L.w;
+#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
         const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
         const int64_t cc = ((int64_t)(k >> 1) * C.ny + (j >> 1)) * C.nx + (i >> 1);
@@ -186,15 +200,15 @@ __global__ void __launch_bounds__(kMgThreads)
         float w[6], D;
         mg_weights(a, l, i, j, k, w, D);
         const float ec = __ldg(e + cc);
-        const float uc = fmaf(kMgSigma, ec, L.u[c]);
+        const float uc = fmaf(kMgSigma, ec, u[c]);
         float off = 0.f;
-        if (w[0] != 0.f) off = fmaf(w[0], fmaf(kMgSigma, io ? ec : __ldg(e + cc - 1), L.u[c - 1]), off);
-        if (w[1] != 0.f) off = fmaf(w[1], fmaf(kMgSigma, io ? __ldg(e + cc + 1) : ec, L.u[c + 1]), off);
-        if (w[2] != 0.f) off = fmaf(w[2], fmaf(kMgSigma, jo ? ec : __ldg(e + cc - cy), L.u[c - sy]), off);
-        if (w[3] != 0.f) off = fmaf(w[3], fmaf(kMgSigma, jo ? __ldg(e + cc + cy) : ec, L.u[c + sy]), off);
-        if (w[4] != 0.f) off = fmaf(w[4], fmaf(kMgSigma, ko ? ec : __ldg(e + cc - cz), L.u[c - sz]), off);
-        if (w[5] != 0.f) off = fmaf(w[5], fmaf(kMgSigma, ko ? __ldg(e + cc + cz) : ec, L.u[c + sz]), off);
-        L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
+        if (w[0] != 0.f) off = fmaf(w[0], fmaf(kMgSigma, io ? ec : __ldg(e + cc - 1), u[c - 1]), off);
+        if (w[1] != 0.f) off = fmaf(w[1], fmaf(kMgSigma, io ? __ldg(e + cc + 1) : ec, u[c + 1]), off);
+        if (w[2] != 0.f) off = fmaf(w[2], fmaf(kMgSigma, jo ? ec : __ldg(e + cc - cy), u[c - sy]), off);
+        if (w[3] != 0.f) off = fmaf(w[3], fmaf(kMgSigma, jo ? __ldg(e + cc + cy) : ec, u[c + sy]), off);
+        if (w[4] != 0.f) off = fmaf(w[4], fmaf(kMgSigma, ko ? ec : __ldg(e + cc - cz), u[c - sz]), off);
+        if (w[5] != 0.f) off = fmaf(w[5], fmaf(kMgSigma, ko ? __ldg(e + cc + cz) : ec, u[c + sz]), off);
+        out[c] = fmaf(kMgOmega / D, f[c] - fmaf(D, uc, -off), uc);
     }
 }
 
