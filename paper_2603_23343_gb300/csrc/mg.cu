@@ -129,86 +129,170 @@ inline MgLaunch mg_launch(int nx, int ny, int nz) {
                     dim3((unsigned)bx, (unsigned)by), zper};
 }
 
-// u = omega D^-1 f at level l
+// Four consecutive floats (16-byte aligned) <-> registers.
+__device__ __forceinline__ void ld4f(const float *p, float v[4]) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+
+// u = omega D^-1 f at level l; V consecutive points per thread (V = 4 needs nx % 4 == 0)
+template <int V>
 __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= L.nx || j >= L.ny) return;
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i0 >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
     const float *__restrict__ f = L.f;
     float *__restrict__ u = L.u;
-#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-        const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-        float w[6], D;
-        mg_weights(a, l, i, j, k, w, D);
-        u[c] = kMgOmega * f[c] / D;
+        const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i0;
+        float fv[V], out[V];
+        if constexpr (V == 4) ld4f(f + c, fv);
+        else fv[0] = f[c];
+#pragma unroll
+        for (int m = 0; m < V; ++m) {
+            float w[6], D;
+            mg_weights(a, l, i0 + m, j, k, w, D);
+            out[m] = kMgOmega * fv[m] / D;
+        }
+        if constexpr (V == 4) *reinterpret_cast<float4 *>(u + c) = make_float4(out[0], out[1], out[2], out[3]);
+        else u[c] = out[0];
     }
 }
 
-// f_{l+1} = P^T (f - A u): one thread per coarse cell, the residual of its eight fine cells
+// The stencil input of V consecutive points of a row and of their neighbours:
+// centre values c[V], the x neighbours left of point 0 and right of point
+// V-1, the rows above / below and the planes before / after.  Values outside
+// the grid read as 0 (their weights are 0 anyway).
+template <int V>
+struct Nbr {
+    float c[V], xl, xr, ym[V], yp[V], zm[V], zp[V];
+};
+template <int V, typename GetV, typename Get1>
+__device__ __forceinline__ void load_nbr(const MgLevel &L, int i0, int j, int k, GetV getv, Get1 get1, Nbr<V> &n) {
+    getv(i0, j, k, n.c);
+    n.xl = i0 > 0 ? get1(i0 - 1, j, k) : 0.f;
+    n.xr = i0 + V < L.nx ? get1(i0 + V, j, k) : 0.f;
+#pragma unroll
+    for (int m = 0; m < V; ++m) n.ym[m] = n.yp[m] = n.zm[m] = n.zp[m] = 0.f;
+    if (j > 0) getv(i0, j - 1, k, n.ym);
+    if (j < L.ny - 1) getv(i0, j + 1, k, n.yp);
+    if (k > 0) getv(i0, j, k - 1, n.zm);
+    if (k < L.nz - 1) getv(i0, j, k + 1, n.zp);
+}
+
+// (A v)_m = D v_m - sum of the interior neighbours' w v for point m of a row segment
+template <int V>
+__device__ __forceinline__ float apply_m(const Nbr<V> &n, int m, const float w[6], float D) {
+    const float xm = m == 0 ? n.xl : n.c[m - 1];
+    const float xp = m == V - 1 ? n.xr : n.c[m + 1];
+    float off = w[0] * xm;
+    off = fmaf(w[1], xp, off);
+    off = fmaf(w[2], n.ym[m], off);
+    off = fmaf(w[3], n.yp[m], off);
+    off = fmaf(w[4], n.zm[m], off);
+    off = fmaf(w[5], n.zp[m], off);
+    return fmaf(D, n.c[m], -off);
+}
+
+// f_{l+1} = P^T (f - A u).  V = 1: one thread per coarse cell; V = 2: two
+// neighbouring coarse cells per thread, their four fine columns read as one
+// 16-byte vector per fine row (needs nx % 4 == 0).
+template <int V>
 __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-    if (I >= C.nx || J >= C.ny) return;
+    const int I0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, J = blockIdx.y * blockDim.y + threadIdx.y;
+    if (I0 >= C.nx || J >= C.ny) return;
     const int K0 = blockIdx.z * zper, K1 = min(C.nz, K0 + zper);
     const float *__restrict__ u = L.u;
     const float *__restrict__ f = L.f;
     float *__restrict__ fc = C.f;
-#pragma unroll 2
+    constexpr int FV = 2 * V;  // fine points per fine row
+    auto at = [&](int i, int j, int k) { return ((int64_t)k * L.ny + j) * L.nx + i; };
+    auto getv = [&](int i, int j, int k, float *v) {
+        const int64_t q = at(i, j, k);
+        if constexpr (FV == 4) ld4f(u + q, v);
+        else { v[0] = u[q]; v[1] = u[q + 1]; }
+    };
+    auto get1 = [&](int i, int j, int k) { return u[at(i, j, k)]; };
     for (int K = K0; K < K1; ++K) {
-        float s = 0.f;
+        float sum[V];
+#pragma unroll
+        for (int m = 0; m < V; ++m) sum[m] = 0.f;
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
-            for (int dy = 0; dy < 2; ++dy)
+            for (int dy = 0; dy < 2; ++dy) {
+                const int i0 = 2 * I0, j = 2 * J + dy, k = 2 * K + dz;
+                const int64_t c0 = ((int64_t)k * L.ny + j) * L.nx + i0;
+                Nbr<FV> n;
+                load_nbr<FV>(L, i0, j, k, getv, get1, n);
+                float fv[FV];
+                if constexpr (FV == 4) ld4f(f + c0, fv);
+                else { fv[0] = f[c0]; fv[1] = f[c0 + 1]; }
 #pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                    const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
+                for (int m = 0; m < FV; ++m) {
                     float w[6], D;
-                    mg_weights(a, l, i, j, k, w, D);
-                    const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return u[q]; });
-                    s += f[c] - fmaf(D, u[c], -off);
+                    mg_weights(a, l, i0 + m, j, k, w, D);
+                    sum[m >> 1] += fv[m] - apply_m<FV>(n, m, w, D);
                 }
-        fc[((int64_t)K * C.ny + J) * C.nx + I] = s;
+            }
+        const int64_t cc = ((int64_t)K * C.ny + J) * C.nx + I0;
+        if constexpr (V == 2) *reinterpret_cast<float2 *>(fc + cc) = make_float2(sum[0], sum[1]);
+        else fc[cc] = sum[0];
     }
 }
 
 // out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1)
-// result: at a neighbour the parent is the point's own parent on the odd
-// side of the pair, the next coarse cell on the even side
+// result, formed at every stencil input; V consecutive points per thread.
+template <int V>
 __global__ void __launch_bounds__(kMgThreads)
     mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= L.nx || j >= L.ny) return;
+    const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i0 >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
-    const int64_t sy = L.nx, sz = (int64_t)L.nx * L.ny, cy = C.nx, cz = (int64_t)C.nx * C.ny;
-    const bool io = i & 1, jo = j & 1;
     const float *__restrict__ u = L.u;
     const float *__restrict__ f = L.f;
     float *__restrict__ out = L.w;
-#pragma unroll 4
     for (int k = k0; k < k1; ++k) {
-        const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
-        const int64_t cc = ((int64_t)(k >> 1) * C.ny + (j >> 1)) * C.nx + (i >> 1);
-        const bool ko = k & 1;
-        float w[6], D;
-        mg_weights(a, l, i, j, k, w, D);
-        const float ec = __ldg(e + cc);
-        const float uc = fmaf(kMgSigma, ec, u[c]);
-        float off = 0.f;
-        if (w[0] != 0.f) off = fmaf(w[0], fmaf(kMgSigma, io ? ec : __ldg(e + cc - 1), u[c - 1]), off);
-        if (w[1] != 0.f) off = fmaf(w[1], fmaf(kMgSigma, io ? __ldg(e + cc + 1) : ec, u[c + 1]), off);
-        if (w[2] != 0.f) off = fmaf(w[2], fmaf(kMgSigma, jo ? ec : __ldg(e + cc - cy), u[c - sy]), off);
-        if (w[3] != 0.f) off = fmaf(w[3], fmaf(kMgSigma, jo ? __ldg(e + cc + cy) : ec, u[c + sy]), off);
-        if (w[4] != 0.f) off = fmaf(w[4], fmaf(kMgSigma, ko ? ec : __ldg(e + cc - cz), u[c - sz]), off);
-        if (w[5] != 0.f) off = fmaf(w[5], fmaf(kMgSigma, ko ? __ldg(e + cc + cz) : ec, u[c + sz]), off);
-        out[c] = fmaf(kMgOmega / D, f[c] - fmaf(D, uc, -off), uc);
+        const int64_t c0 = ((int64_t)k * L.ny + j) * L.nx + i0;
+        // u' = u + sigma e[parent] at fine points (i, j, k) (V of them from i, i a multiple of V)
+        auto fine = [&](int i, int jj, int kk) { return ((int64_t)kk * L.ny + jj) * L.nx + i; };
+        auto parent = [&](int i, int jj, int kk) {
+            return ((int64_t)(kk >> 1) * C.ny + (jj >> 1)) * C.nx + (i >> 1);
+        };
+        auto getv = [&](int i, int jj, int kk, float *v) {
+            const int64_t q = fine(i, jj, kk), pc = parent(i, jj, kk);
+            if constexpr (V == 4) {
+                float uv[4];
+                ld4f(u + q, uv);
+                const float2 ep = __ldg(reinterpret_cast<const float2 *>(e + pc));
+                v[0] = fmaf(kMgSigma, ep.x, uv[0]);
+                v[1] = fmaf(kMgSigma, ep.x, uv[1]);
+                v[2] = fmaf(kMgSigma, ep.y, uv[2]);
+                v[3] = fmaf(kMgSigma, ep.y, uv[3]);
+            } else {
+                v[0] = fmaf(kMgSigma, __ldg(e + pc), u[q]);
+            }
+        };
+        auto get1 = [&](int i, int jj, int kk) { return fmaf(kMgSigma, __ldg(e + parent(i, jj, kk)), u[fine(i, jj, kk)]); };
+        Nbr<V> n;
+        load_nbr<V>(L, i0, j, k, getv, get1, n);
+        float fv[V], res[V];
+        if constexpr (V == 4) ld4f(f + c0, fv);
+        else fv[0] = f[c0];
+#pragma unroll
+        for (int m = 0; m < V; ++m) {
+            float w[6], D;
+            mg_weights(a, l, i0 + m, j, k, w, D);
+            res[m] = fmaf(kMgOmega / D, fv[m] - apply_m<V>(n, m, w, D), n.c[m]);
+        }
+        if constexpr (V == 4) *reinterpret_cast<float4 *>(out + c0) = make_float4(res[0], res[1], res[2], res[3]);
+        else out[c0] = res[0];
     }
 }
 
@@ -394,18 +478,32 @@ cudaError_t mg_setup(const MgArgs &a, cudaStream_t s) {
 
 // z = M f0 (a.lv[0].f -> a.lv[0].w)
 cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
+    // levels whose rows split into 16-byte vectors take four points per thread (and their
+    // restriction two coarse cells per thread)
+    auto vec = [&](int l) { return a.lv[l].nx % 4 == 0; };
     for (int l = 0; l + 1 < a.L; ++l) {
         const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-        const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz), gc = mg_launch(C.nx, C.ny, C.nz);
-        mg_pre_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
-        mg_restrict_kernel<<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+        if (vec(l)) {
+            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz), gc = mg_launch(C.nx / 2, C.ny, C.nz);
+            mg_pre_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
+            mg_restrict_kernel<2><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+        } else {
+            const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz), gc = mg_launch(C.nx, C.ny, C.nz);
+            mg_pre_kernel<1><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
+            mg_restrict_kernel<1><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+        }
     }
     mg_coarse_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, a.L - 1);
     for (int l = a.L - 2; l >= 0; --l) {
         const MgLevel &L = a.lv[l];
-        const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
         const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
-        mg_post_kernel<<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        if (vec(l)) {
+            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
+            mg_post_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        } else {
+            const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
+            mg_post_kernel<1><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        }
     }
     return cudaGetLastError();
 }
