@@ -616,7 +616,7 @@ def main():
     pts_iters = sum(int(np.prod(sh)) * r["iters"] for sh, r in zip(shapes, bres))
     g_pts_iters = sum(int(np.prod(sh)) * r["iters"] for sh, r in zip(shapes, gres))
     batched = {"problems": 64, "points": int(sum(int(np.prod(sh)) for sh in shapes)), "ms": batch_ms,
-               "kernel_launches": bres[0]["pass_launches"][0], "rounds": bres[0]["pass_launches"][1],
+               "kernel_launches": bres[0]["pass_launches"][0], "phases": bres[0]["pass_launches"][1],
                "persistent_tiles": ["64x16", "128x8", "32x32"][bres[0]["pass_ctas"][0]],
                "all_converged": all(r["status"] == 0 for r in bres),
                "iters_min_max": [min(r["iters"] for r in bres), max(r["iters"] for r in bres)],

@@ -279,12 +279,15 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
  *
  * Constant-coefficient grids with nx a multiple of 4 run as ONE persistent
  * kernel (a cooperative launch of as many CTAs as the GPU holds, inside a
- * cached one-node CUDA graph): it walks the pass-A / pass-B tiles of every
- * unfinished problem, one round per iteration, separated by grid-wide
- * barriers; a problem drops out of the work when it converges; residual
- * replacements, the setup and the finalize are phases of the same kernel.
- * Each barrier wait is bounded: if one gives up, the unfinished problems
- * report GBPCG_TIMEOUT.  result.pass_launches = {1, rounds run},
+ * cached one-node CUDA graph): every problem runs its own sequence of phases
+ * (pass A, pass B, and a flush and an FP64 residual for each residual
+ * replacement), any CTA claiming any available work item (a tile of z
+ * planes, or a run of rows) of any unfinished problem; the CTA that
+ * completes a phase takes the problem's scalar step and opens its next
+ * phase.  Setup and finalize are phases of all problems at once between
+ * grid barriers.  Every wait is bounded: if one gives up, the unfinished
+ * problems report GBPCG_TIMEOUT.  result.pass_launches = {1, phases run
+ * over all problems (2 per iteration and 2 per replacement)},
  * pass_ctas[0] = the tile configuration (0: 64x16, 1: 128x8, 2: 32x32):
  * opts->tile_cfg = c + 1 selects configuration c, else
  * GBPCG_FLAG_AUTOTUNE times the three and keeps the fastest per set of

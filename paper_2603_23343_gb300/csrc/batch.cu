@@ -2,29 +2,34 @@
 // ONE persistent kernel launch.
 //
 // The grid is as many CTAs as the GPU holds at once (a cooperative launch,
-// so every CTA is resident) and walks phases separated by grid-wide
-// barriers:
+// so every CTA is resident).  Setup and finalize are phases of all problems
+// at once, separated by grid-wide barriers:
 //
-//   reset states | max |b| | r0 = b - A x0 (FP64)      once
-//   pass A or flush | pass B or r = b - A x (FP64)       every round, until all converge
-//   x += d + alpha p | true residual (FP64)              once
+//   reset states | max |b| | r0 = b - A x0 (FP64) | phase control    once
+//   ... every problem through its own phases, no barrier ...
+//   x += d + alpha p | true residual (FP64)                           once
 //
-// A phase is a list of work items over all problems: a pass item is one
-// (x, y) tile of one problem marched through a chunk of z planes (the same
-// z-marching code as the single-problem passes, engine.cuh), a row item a
-// run of grid rows of one problem.  Each round numbers only the items of
-// unfinished problems and CTA c takes items c, c + G, c + 2G, ... (G CTAs),
-// so a problem drops out of the work as soon as it is done while the others
-// go on; a problem that needs a residual replacement spends one round on it
-// while the others iterate.  Each problem keeps its own scalars (SolveState), partial sums and
-// tickets: the CTA that finishes a problem's last item of a phase adds the
-// problem's partial sums in item order (bitwise reproducible) and takes the
-// scalar step (alpha; beta, convergence, the replacement trigger).
+// In between, each problem runs its own sequence of phases: pass A, pass B,
+// pass A, ... and, when a pass B asks for a residual replacement, a flush
+// and an FP64 residual before the next pass A.  A phase is a set of work
+// items: a pass item is one (x, y) tile of the problem marched through a
+// run of z planes (the same z-marching code as the single-problem passes,
+// engine.cuh), a row item a run of grid rows.  Any CTA claims any available
+// item of any unfinished problem (an atomic counter in the problem's phase
+// word, whose upper half numbers the phase), preferring the problem it
+// worked on last; the CTA that completes a phase's last item adds the
+// problem's partial sums in item order (bitwise reproducible), takes the
+// scalar step (alpha; beta, convergence, the replacement trigger) and opens
+// the problem's next phase.  So one problem's pass B runs while another's
+// pass A does, a finished problem drops out, and no CTA waits for work
+// while any is available.  The z depth of a pass item is chosen when its
+// phase opens: about two items per CTA over the unfinished problems, 4 to 32
+// planes.
 //
-// The grid barrier is a counter and a generation word in device memory.
-// Every wait on it is bounded: after kBarrierPolls polls the waiting CTA
-// raises an abort flag and leaves, every other CTA leaves at its next
-// barrier, and the problems that had not finished report GBPCG_TIMEOUT.
+// Every wait is bounded: the grid barrier (a counter and a generation word)
+// after kBarrierPolls polls, a CTA finding no work after kIdlePolls tries;
+// either raises an abort flag that every CTA checks, and the problems that
+// had not finished report GBPCG_TIMEOUT.
 #include <algorithm>
 #include <cstring>
 #include <list>
@@ -41,7 +46,8 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchZDepth = 32;  // z planes per pass item
 constexpr int kRowPoints = 16384;  // grid points per row item (at least one row)
 constexpr uint32_t kBarrierPolls = 1u << 22;  // x ~64 ns of sleep: well under a second
-constexpr int kBatchMaxProblems = 1024;  // per-round snapshot held in shared memory
+constexpr int kBatchMaxProblems = 4096;
+constexpr uint32_t kIdlePolls = 1u << 21;  // claims that found no work in a row (~0.5 us each): about a second
 
 // Tile configurations of the persistent kernel (all 256 threads: the FP64
 // residual code strides rows by 256 threads).
@@ -66,16 +72,33 @@ struct __align__(64) BatchHeader {
     unsigned bar_count;
     unsigned bar_gen;
     int abort;
-    int rounds;
+    int phases;              // phases run over all problems
+    int active;              // problems not yet finished
+    int pad;
+    long long tile_planes;   // sum over unfinished problems of tiles x planes
+};
+
+// What a problem's current phase is (its work items are claimed through
+// ProbCtl::claim).
+enum PhaseKind { PH_A = 0, PH_B = 1, PH_FLUSH = 2, PH_RESID = 3, PH_DONE = 4 };
+
+struct __align__(64) ProbCtl {
+    unsigned long long claim;  // (phase number << 32) | items of the phase claimed so far
+    int kind;                  // PhaseKind of the current phase
+    int nitems;                // its work items
+    int depth;                 // pass phases: z planes per item
+    int phases;                // phases this problem has run
 };
 
 struct BatchArgs {
     BatchProblem *probs;
+    ProbCtl *ctl;
     const int *row_prob;   // row item -> problem
     BatchHeader *hdr;
     int nprob, nrow_items;
     double tol;
     int maxit;
+    int depth0;            // z planes per item of the first pass phase
 };
 
 // Grid-wide barrier (bounded): false once any CTA has given up.
@@ -124,7 +147,6 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S];
     __shared__ int s_timeout;
-    __shared__ int s_flag;
     BatchHeader *hdr = A.hdr;
     if (threadIdx.x == 0) {
         s_timeout = 0;
@@ -190,98 +212,137 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
     }
     if (!batch_barrier(hdr)) return;
 
-    // ---- the iteration rounds ----
-    // Every round has two slots.  A problem in iteration mode runs pass A in
-    // the first and pass B in the second; a problem whose pass B asked for a
-    // residual replacement spends its next round on it instead (flush in the
-    // first slot, the FP64 residual in the second), while the other problems
-    // iterate.  At the start of a round every CTA takes the same snapshot of
-    // the problems' modes and numbers the round's work items over the active
-    // problems only, so finished problems cost nothing and the items spread
-    // evenly over the CTAs.
-    __shared__ int s_pre[kBatchMaxProblems + 1];
-    __shared__ unsigned char s_mode[kBatchMaxProblems];
-    __shared__ unsigned short s_dep[kBatchMaxProblems];
-    __shared__ int s_depth;
-    // inclusive scan of s_pre[1 .. nprob] by warp 0 (32 chunks of contiguous problems); total
-    // returned in every lane of warp 0
-    auto scan = [&]() {
-        if (threadIdx.x < 32) {
-            const int per = (A.nprob + 31) / 32;
-            const int a = min(A.nprob, (int)threadIdx.x * per), e = min(A.nprob, a + per);
-            int sum = 0;
-            for (int p = a; p < e; ++p) sum += s_pre[p + 1];
-            int incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if ((int)threadIdx.x >= o) incl += t;
-            }
-            int run = incl - sum;
-            for (int p = a; p < e; ++p) {
-                run += s_pre[p + 1];
-                s_pre[p + 1] = run;
-            }
-            if (threadIdx.x == 0) s_pre[0] = 0;
-        }
-    };
-    for (int round = 0;; ++round) {
-        // modes, and the tile-planes of the iterating problems
-        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
-            const SolveState *st = A.probs[p].st;
-            const int done = ((volatile const int *)&st->done)[0];
-            const int rep = ((volatile const int *)&st->replace)[0];
-            const int mode = done ? 0 : rep ? 2 : 1;
-            s_mode[p] = (unsigned char)mode;
-            s_pre[p + 1] = mode == 1 ? A.probs[p].tiles * A.probs[p].nz : 0;
-        }
-        __syncthreads();
-        scan();
-        __syncthreads();
-        // z planes per pass item this round: about two items per CTA over the iterating
-        // problems, between 4 and 32 planes (deep items while the batch is large, shallow ones
-        // once few problems remain, so the work still spreads over the GPU)
+    // ---- the iterations: every problem advances through its own phases ----
+    // pass A -> pass B -> pass A ..., or after a pass B that asked for a residual replacement,
+    // flush -> FP64 residual -> pass A.  A phase is a set of work items (tiles of z planes, or
+    // runs of rows); any CTA claims any available item of any problem, and the CTA that
+    // completes a phase's last item takes the problem's scalar step and opens its next phase.
+    // No barrier separates problems: one problem's pass B runs while another's pass A does.
+    for (int p = blockIdx.x; p < A.nprob; p += G)
         if (threadIdx.x == 0) {
-            const int tp = s_pre[A.nprob];
-            s_depth = max(4, min(kBatchZDepth, (tp + 2 * (int)G - 1) / (2 * (int)G)));
-        }
-        __syncthreads();
-        for (int p = threadIdx.x; p < A.nprob; p += kBatchThreads) {
             const BatchProblem &P = A.probs[p];
-            // at least enough planes per item that the problem's pass-B partials fit its slots
+            ProbCtl &c = A.ctl[p];
+            const bool fin = P.st->done != 0;
             const int need = (2 * P.tiles * P.nz + 4 * (int)kMaxPassBlocks - 1) / (4 * (int)kMaxPassBlocks);
-            const int dep = min(P.nz, max(s_depth, need));
-            s_dep[p] = (unsigned short)dep;
-            const int mode = s_mode[p];
-            s_pre[p + 1] = mode == 1 ? P.tiles * ((P.nz + dep - 1) / dep) : mode == 2 ? P.nrow_items : 0;
+            const int dep = min(P.nz, max(A.depth0, need));
+            c.kind = fin ? PH_DONE : PH_A;
+            c.depth = dep;
+            c.nitems = fin ? 0 : P.tiles * ((P.nz + dep - 1) / dep);
+            c.phases = 0;
+            c.claim = 0ull;
+            if (!fin) {
+                atomicAdd(&hdr->active, 1);
+                atomicAdd((unsigned long long *)&hdr->tile_planes, (unsigned long long)((long long)P.tiles * P.nz));
+            }
+        }
+    if (!batch_barrier(hdr)) return;
+
+    // z planes per pass item of a phase opening now: about two items per CTA over the
+    // unfinished problems' tile-planes, 4 to 32 planes, and enough planes that the problem's
+    // pass-B partial sums fit its slots
+    auto pass_depth = [&](const BatchProblem &P) {
+        const long long tp = ((volatile long long *)&hdr->tile_planes)[0];
+        const int d = (int)max(4LL, min((long long)kBatchZDepth, (tp + 2LL * G - 1) / (2LL * G)));
+        const int need = (2 * P.tiles * P.nz + 4 * (int)kMaxPassBlocks - 1) / (4 * (int)kMaxPassBlocks);
+        return min(P.nz, max(d, need));
+    };
+    // thread 0 of the CTA that completed a phase: open the problem's next phase
+    auto advance = [&](ProbCtl *c, const BatchProblem &P, int next) {
+        int n = 0, d = c->depth;
+        if (next == PH_A) {
+            d = pass_depth(P);
+            n = P.tiles * ((P.nz + d - 1) / d);
+        } else if (next == PH_B) {
+            n = P.tiles * ((P.nz + d - 1) / d);
+        } else if (next == PH_FLUSH || next == PH_RESID) {
+            n = P.nrow_items;
+        } else {
+            atomicSub(&hdr->active, 1);
+            atomicAdd((unsigned long long *)&hdr->tile_planes, (unsigned long long)(-(long long)P.tiles * P.nz));
+        }
+        c->kind = next;
+        c->nitems = n;
+        c->depth = d;
+        c->phases += 1;
+        atomicAdd(&hdr->phases, 1);
+        __threadfence();
+        const unsigned long long ph = (((volatile unsigned long long *)&c->claim)[0] >> 32) + 1ull;
+        atomicExch(&c->claim, ph << 32);
+    };
+
+    __shared__ int s_p, s_i;
+    int cur = (int)(blockIdx.x % (unsigned)A.nprob);
+    uint32_t idle = 0;
+    for (;;) {
+        // claim a work item: warp 0 looks at every problem from the last one this CTA worked on
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int got_p = -1, got_i = 0;
+            for (int base = 0; base < A.nprob && got_p < 0; base += 32) {
+                const int q = base + lane;
+                bool cand = false;
+                if (q < A.nprob) {
+                    int p = cur + q;
+                    if (p >= A.nprob) p -= A.nprob;
+                    volatile ProbCtl *c = &A.ctl[p];
+                    cand = c->kind != PH_DONE && (int)(c->claim & 0xffffffffull) < c->nitems;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (lane == 0) {
+                    while (m && got_p < 0) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        int p = cur + base + bit;
+                        if (p >= A.nprob) p -= A.nprob;
+                        ProbCtl *c = &A.ctl[p];
+                        const unsigned long long old = atomicAdd(&c->claim, 1ull);
+                        __threadfence();
+                        const int idx = (int)(old & 0xffffffffull);
+                        // the phase in `old` cannot close before this item completes, so its
+                        // kind and item count are the ones read now
+                        if (((volatile int *)&c->kind)[0] != PH_DONE && idx < ((volatile int *)&c->nitems)[0]) {
+                            got_p = p;
+                            got_i = idx;
+                        }
+                    }
+                }
+                got_p = __shfl_sync(0xffffffffu, got_p, 0);
+                got_i = __shfl_sync(0xffffffffu, got_i, 0);
+            }
+            if (lane == 0) {
+                s_p = got_p;
+                s_i = got_i;
+            }
         }
         __syncthreads();
-        scan();
-        __syncthreads();
-        const int total = s_pre[A.nprob];
-        if (total == 0) break;
-        // problem of round item t: the last p with s_pre[p] <= t
-        auto owner = [&](int t) {
-            int lo = 0, hi = A.nprob - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_pre[mid] <= t) lo = mid;
-                else hi = mid - 1;
+        const int pi = s_p, local = s_i;
+        __syncthreads();  // s_p and s_i are written again at the next claim
+        if (pi < 0) {
+            if (((volatile int *)&hdr->active)[0] == 0) break;
+            if (((volatile int *)&hdr->abort)[0]) return;
+            if (++idle > kIdlePolls) {
+                if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
+                return;
             }
-            return lo;
-        };
-
-        // first slot: pass A (p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap), or the flush
-        for (int t = blockIdx.x; t < total; t += G) {
-            const int pi = owner(t);
-            const BatchProblem &P = A.probs[pi];
-            SolveState *st = P.st;
-            const int local = t - s_pre[pi];
-            if (s_mode[pi] == 1) {
-                const int dep = s_dep[pi], nit = s_pre[pi + 1] - s_pre[pi];
-                const int tile = local % P.tiles, chunk = local / P.tiles;
-                const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-                const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
+            __nanosleep(256);
+            continue;
+        }
+        idle = 0;
+        cur = pi;
+        // stores of the phase before (other CTAs, generic proxy) before this item's TMA loads
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const BatchProblem &P = A.probs[pi];
+        SolveState *st = P.st;
+        ProbCtl *ctl = &A.ctl[pi];
+        const int kind = ((volatile int *)&ctl->kind)[0];
+        const int nit = ((volatile int *)&ctl->nitems)[0];
+        const int dep = ((volatile int *)&ctl->depth)[0];
+        if (kind == PH_A || kind == PH_B) {
+            const int tile = local % P.tiles, chunk = local / P.tiles;
+            const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
+            const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
+            if (kind == PH_A) {
+                // p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap
                 const MarchScalars sc = read_scalars<K_PASSA>(st);
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSA> io;
@@ -302,42 +363,16 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                     if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
                     return;
                 }
+                asm volatile("fence.proxy.async.global;" ::: "memory");
                 double part[1], tot[1];
                 block_sum<1, kBatchThreads>(acc, part);
                 if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, nit, tot) &&
-                    threadIdx.x == 0)
+                    threadIdx.x == 0) {
                     passa_finish(st, tot[0], false);
-            } else {
-                // flush: x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
-                const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
-                const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
-                const float a = st->pending ? (float)st->alpha : 0.0f;
-                const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
-                X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
-                const X is = (X)inv_s;
-                for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
-                    const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
-                    x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
-                    P.d[g] = 0.0f;
+                    advance(ctl, P, st->done ? PH_DONE : PH_B);
                 }
-            }
-        }
-        if (!batch_barrier(hdr)) return;
-
-        // second slot: pass B (q = A p_k, r = D z - alpha q, z = D^-1 r, r.r, r.z), or the FP64
-        // residual r = b - A x of the replacement.  Each CTA takes the items of its first slot in
-        // reverse order, so it starts on the tiles it (and every other CTA) touched last, still in L2.
-        const int t_last = (int)blockIdx.x < total ? (int)blockIdx.x + (int)G * ((total - 1 - (int)blockIdx.x) / (int)G) : -1;
-        for (int t = t_last; t >= 0; t -= G) {
-            const int pi = owner(t);
-            const BatchProblem &P = A.probs[pi];
-            SolveState *st = P.st;
-            const int local = t - s_pre[pi];
-            if (s_mode[pi] == 1) {
-                const int dep = s_dep[pi], nit = s_pre[pi + 1] - s_pre[pi];
-                const int tile = local % P.tiles, chunk = local / P.tiles;
-                const int x0 = (tile % P.tiles_x) * TX, y0 = (tile / P.tiles_x) * TY;
-                const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
+            } else {
+                // q = A p_k, r = D z - alpha q, z = D^-1 r, r.r, r.z
                 const MarchScalars sc = read_scalars<K_PASSB>(st);
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSB> io;
@@ -358,24 +393,53 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                     if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
                     return;
                 }
+                asm volatile("fence.proxy.async.global;" ::: "memory");
                 double part[2], tot[2];
                 block_sum<2, kBatchThreads>(acc, part);
                 if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, nit, tot) &&
-                    threadIdx.x == 0)
+                    threadIdx.x == 0) {
                     passb_finish(st, sc.it, tot[0], tot[1], false);
+                    advance(ctl, P, st->done ? PH_DONE : st->replace ? PH_FLUSH : PH_A);
+                }
+            }
+        } else {
+            const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+            if (kind == PH_FLUSH) {
+                // x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
+                const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
+                const float a = st->pending ? (float)st->alpha : 0.0f;
+                const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
+                X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
+                const X is = (X)inv_s;
+                for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
+                    const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
+                    x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+                    P.d[g] = 0.0f;
+                }
+                // the next pass A reads d through the TMA (async proxy)
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                __syncthreads();
+                const double part[1] = {0.0};
+                double tot[1];
+                if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[0], local, nit, tot) &&
+                    threadIdx.x == 0)
+                    advance(ctl, P, PH_RESID);
             } else {
-                const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
+                // r = b - A x in FP64, z = D^-1 r, the replacement's decisions
                 double part[2], tot[2], unscale;
                 res64_rows<RES_REPLACE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
-                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local,
-                                                     P.nrow_items, tot) &&
-                    threadIdx.x == 0)
+                asm volatile("fence.proxy.async.global;" ::: "memory");  // z, read by the next pass A's TMA
+                if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local, nit,
+                                                     tot) &&
+                    threadIdx.x == 0) {
                     res64_finish<RES_REPLACE>(st, tot, unscale);
+                    advance(ctl, P, st->done ? PH_DONE : PH_A);
+                }
             }
         }
-        if (!batch_barrier(hdr)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) hdr->rounds = round + 1;
     }
+    if (!batch_barrier(hdr)) return;
 
     // ---- x += (d + alpha_{k-1} p_{k-1}) / s (x = 0 when b = 0) ----
     for (int item = blockIdx.x; item < A.nrow_items; item += G) {
@@ -456,11 +520,11 @@ ProbGeom prob_geom(const gbpcg_grid &g, int cfg) {
 }
 
 struct BatchLayout {
-    size_t hdr, probs, rows, total;
+    size_t hdr, probs, ctl, rows, total;
 };
 
 // The batch's own region at the front of the workspace: header, problem
-// table and the row-item-to-problem map.
+// table, per-problem phase control and the row-item-to-problem map.
 BatchLayout batch_layout(int nprob, const gbpcg_grid *grids) {
     BatchLayout L;
     int rows = 0;
@@ -468,6 +532,7 @@ BatchLayout batch_layout(int nprob, const gbpcg_grid *grids) {
     size_t o = 0;
     L.hdr = o; o += round256(sizeof(BatchHeader));
     L.probs = o; o += round256(sizeof(BatchProblem) * (size_t)nprob);
+    L.ctl = o; o += round256(sizeof(ProbCtl) * (size_t)nprob);
     L.rows = o; o += round256(sizeof(int) * (size_t)rows);
     L.total = o;
     return L;
@@ -583,12 +648,18 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
 
     BatchArgs A;
     A.probs = dprobs;
+    A.ctl = reinterpret_cast<ProbCtl *>(region + BL.ctl);
     A.row_prob = drows;
     A.hdr = hdr;
     A.nprob = nprob;
     A.nrow_items = nrow;
     A.tol = tol;
     A.maxit = maxit;
+    {
+        long long tp = 0;
+        for (int i = 0; i < nprob; ++i) tp += (long long)probs[i].tiles * probs[i].nz;
+        A.depth0 = (int)std::max(4LL, std::min((long long)kBatchZDepth, (tp + 2LL * grid - 1) / (2LL * grid)));
+    }
 
     // the table is copied on every call (the stream orders it before the kernel); its contents
     // depend only on the key, so a cached graph stays valid
@@ -664,8 +735,8 @@ int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall 
 
 // Rounds run and whether a bounded barrier wait gave up, from the batch
 // region (enqueued on s; valid after it synchronises).
-int batch_persistent_header(const char *region, int *rounds_abort, cudaStream_t s) {
-    GB_CUDA(cudaMemcpyAsync(rounds_abort, region + offsetof(BatchHeader, abort), 2 * sizeof(int),
+int batch_persistent_header(const char *region, int *abort_phases, cudaStream_t s) {
+    GB_CUDA(cudaMemcpyAsync(abort_phases, region + offsetof(BatchHeader, abort), 2 * sizeof(int),
                             cudaMemcpyDeviceToHost, s));
     return GBPCG_OK;
 }

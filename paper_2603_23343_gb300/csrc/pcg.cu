@@ -558,7 +558,7 @@ static int persistent_batch(int nprob, const gbpcg_grid *grids, const void *cons
     std::vector<SolveState> hs(nprob);
     for (int i = 0; i < nprob; ++i)
         GB_CUDA(cudaMemcpyAsync(&hs[i], ws + off[i] + L[i].state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-    int hdr[2] = {0, 0};  // abort, rounds
+    int hdr[2] = {0, 0};  // abort, phases run
     if (int rc = batch_persistent_header(ws, hdr, s)) return rc;
     GB_CUDA(cudaStreamSynchronize(s));
     float ms = 0.f;
@@ -575,7 +575,7 @@ static int persistent_batch(int nprob, const gbpcg_grid *grids, const void *cons
         r.time_ms = ms;
         r.replacements = hs[i].n_replace;
         r.pass_launches[0] = 1;        // kernel launches of the whole batch
-        r.pass_launches[1] = hdr[1];   // rounds the persistent kernel ran
+        r.pass_launches[1] = hdr[1];   // phases the persistent kernel ran, over all problems
         r.pass_ctas[0] = cfg;          // persistent tile configuration used
         if (r.status != GBPCG_OK && worst == GBPCG_OK) worst = r.status;
     }

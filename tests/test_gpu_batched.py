@@ -95,8 +95,8 @@ def test_persistent_batch_against_oracle(gpu_lib, cfg):
     bs = [torch.from_numpy(b).cuda() for b in bnp]
     xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000, tile_cfg=cfg)
     assert all(r["pass_launches"][0] == 1 and r["pass_ctas"][0] == cfg - 1 for r in res)
-    # a round is one iteration or one residual replacement of each unfinished problem
-    assert res[0]["pass_launches"][1] == max(r["iters"] + r["replacements"] for r in res)
+    # two phases per iteration (pass A, pass B) and two per residual replacement (flush, residual)
+    assert res[0]["pass_launches"][1] == sum(2 * r["iters"] + 2 * r["replacements"] for r in res)
     for b, x, r in zip(bnp, xs, res):
         ref = oracle.pcg(b, tol=1e-6, maxit=2000)
         assert r["status"] == 0 and abs(r["iters"] - ref["iters"]) <= 2, (r, ref["iters"])
