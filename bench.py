@@ -85,7 +85,7 @@ def learned_leg(B, learned, stream, full: bool):
     heaviest convolution (c8, 48 -> 16 channels at 256^3) against the tensor peak."""
     import torch
     train_seeds = range(10, 100) if full else range(10, 42)
-    eval_seeds = range(100, 110) if full else range(100, 102)
+    eval_seeds = range(100, 110)
     steps = 4000
     t0 = time.perf_counter()
     pairs = learned.make_pairs((128, 128, 128), seeds=train_seeds)
@@ -103,8 +103,16 @@ def learned_leg(B, learned, stream, full: bool):
         _, rj = B.pcg_solve(bb, xj, tol=TOL, maxit=20000, k_block=k)
         fws = B.fcg_workspace(bb.shape, k_block=k, tol=TOL, maxit=20000)
         _, rl = B.fcg_solve(w, bb, tol=TOL, maxit=20000, k_block=k, workspace=fws)
+        mws = B.mg_workspace(bb.shape, k_block=k)
+        xm = torch.zeros_like(bb)
+        B.mg_pcg_solve(bb, xm, tol=TOL, maxit=2000, k_block=k, workspace=mws)
+        xm.zero_()
+        _, rm = B.mg_pcg_solve(bb, xm, tol=TOL, maxit=2000, k_block=k, workspace=mws)
+        del mws, xm
         evals.append({"seed": sd, "jacobi": {"iters": rj["iters"], "ms": rj["time_ms"],
                                              "rel_res_true_fp64": rj["rel_res_true"]},
+                      "multigrid": {"iters": rm["iters"], "ms": rm["time_ms"], "status": rm["status_name"],
+                                    "rel_res_true_fp64": rm["rel_res_true"]},
                       "learned_fcg": {"iters": rl["iters"], "ms": rl["time_ms"], "network_ms": rl["pass_ms"][0],
                                       "fcg_iters": rl["pass_launches"][0], "fallback_iters": rl["pass_launches"][1],
                                       "status": rl["status_name"], "rel_res_true_fp64": rl["rel_res_true"]}})
@@ -148,6 +156,9 @@ def learned_leg(B, learned, stream, full: bool):
         "loss_first_last": [float(np.mean(losses[:20])), float(np.mean(losses[-200:]))],
         "eval": evals,
         "iters_ratio_learned_over_jacobi": float(np.mean(iters_l) / np.mean(iters_j)),
+        "iters_ratio_per_seed": [float(a / b) for a, b in zip(iters_l, iters_j)],
+        "ms_ratio_multigrid_over_jacobi": float(np.mean([e["multigrid"]["ms"] for e in evals]) /
+                                                np.mean([e["jacobi"]["ms"] for e in evals])),
         "ms_ratio_learned_over_jacobi": float(np.mean([e["learned_fcg"]["ms"] for e in evals]) /
                                               np.mean([e["jacobi"]["ms"] for e in evals])),
         "network_256": {"ms": net_ms, "tflops": net_flop / (net_ms * 1e-3) / 1e12,

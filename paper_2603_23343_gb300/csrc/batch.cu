@@ -83,7 +83,10 @@ struct __align__(64) BatchHeader {
 enum PhaseKind { PH_A = 0, PH_B = 1, PH_FLUSH = 2, PH_RESID = 3, PH_DONE = 4 };
 
 struct __align__(64) ProbCtl {
-    unsigned long long claim;  // (phase number << 32) | items of the phase claimed so far
+    // (items of the current phase << 32) | items of it claimed so far: one atomic add returns
+    // an index together with the item count of the phase it belongs to, so a claim that
+    // overshoots a phase can never be mistaken for an item of the phase opened after it
+    unsigned long long claim;
     int kind;                  // PhaseKind of the current phase
     int nitems;                // its work items
     int depth;                 // pass phases: z planes per item
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         const int local = item - P.row0_item;
         const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
         double part[3], tot[3], unscale;
-        res64_rows<RES_INIT, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+        res64_rows<RES_INIT, X, X, false, T, true>(P.ra, r0, r1, 1, part, &unscale);
         if (group_sum_last<3, kBatchThreads>(part, P.partials, &P.st->ticket[4 + RES_INIT], local, P.nrow_items,
                                              tot) &&
             threadIdx.x == 0)
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             c.depth = dep;
             c.nitems = fin ? 0 : P.tiles * ((P.nz + dep - 1) / dep);
             c.phases = 0;
-            c.claim = 0ull;
+            c.claim = (unsigned long long)(unsigned)c.nitems << 32;
             if (!fin) {
                 atomicAdd(&hdr->active, 1);
                 atomicAdd((unsigned long long *)&hdr->tile_planes, (unsigned long long)((long long)P.tiles * P.nz));
@@ -266,8 +269,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         c->phases += 1;
         atomicAdd(&hdr->phases, 1);
         __threadfence();
-        const unsigned long long ph = (((volatile unsigned long long *)&c->claim)[0] >> 32) + 1ull;
-        atomicExch(&c->claim, ph << 32);
+        atomicExch(&c->claim, (unsigned long long)(unsigned)n << 32);
     };
 
     __shared__ int s_p, s_i;
@@ -284,8 +286,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 if (q < A.nprob) {
                     int p = cur + q;
                     if (p >= A.nprob) p -= A.nprob;
-                    volatile ProbCtl *c = &A.ctl[p];
-                    cand = c->kind != PH_DONE && (int)(c->claim & 0xffffffffull) < c->nitems;
+                    const unsigned long long w = ((volatile unsigned long long *)&A.ctl[p].claim)[0];
+                    cand = (unsigned)w < (unsigned)(w >> 32);
                 }
                 unsigned m = __ballot_sync(0xffffffffu, cand);
                 if (lane == 0) {
@@ -297,12 +299,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                         ProbCtl *c = &A.ctl[p];
                         const unsigned long long old = atomicAdd(&c->claim, 1ull);
                         __threadfence();
-                        const int idx = (int)(old & 0xffffffffull);
-                        // the phase in `old` cannot close before this item completes, so its
-                        // kind and item count are the ones read now
-                        if (((volatile int *)&c->kind)[0] != PH_DONE && idx < ((volatile int *)&c->nitems)[0]) {
+                        // an index below the count in the same word is an item of the phase
+                        // that word belongs to; that phase cannot close before the item
+                        // completes, so the kind and depth read afterwards are its own
+                        if ((unsigned)old < (unsigned)(old >> 32)) {
                             got_p = p;
-                            got_i = idx;
+                            got_i = (int)(unsigned)old;
                         }
                     }
                 }
@@ -405,10 +407,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         } else {
             const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
             if (kind == PH_FLUSH) {
-                // x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
-                const T *p = ((st->it - 1) & 1) ? P.p1 : P.p0;
-                const float a = st->pending ? (float)st->alpha : 0.0f;
-                const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
+                // x += (d + alpha_{k-1} p_{k-1}) / s, d = 0 (scalars read past this SM's L1)
+                const volatile SolveState *vs = st;
+                const T *p = ((vs->it - 1) & 1) ? P.p1 : P.p0;
+                const float a = vs->pending ? (float)vs->alpha : 0.0f;
+                const double inv_s = 1.0 / rhs_scale(vs->rhs_bits);
                 X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
                 const X is = (X)inv_s;
                 for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             } else {
                 // r = b - A x in FP64, z = D^-1 r, the replacement's decisions
                 double part[2], tot[2], unscale;
-                res64_rows<RES_REPLACE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+                res64_rows<RES_REPLACE, X, X, false, T, true>(P.ra, r0, r1, 1, part, &unscale);
                 asm volatile("fence.proxy.async.global;" ::: "memory");  // z, read by the next pass A's TMA
                 if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local, nit,
                                                      tot) &&
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         const int local = item - P.row0_item;
         const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
         double part[1], tot[1], unscale;
-        res64_rows<RES_TRUE, X, X, false, T>(P.ra, r0, r1, 1, part, &unscale);
+        res64_rows<RES_TRUE, X, X, false, T, true>(P.ra, r0, r1, 1, part, &unscale);
         if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_TRUE], local, P.nrow_items, tot) &&
             threadIdx.x == 0)
             res64_finish<RES_TRUE>(st, tot, unscale);

@@ -346,8 +346,12 @@ struct MarchScalars {
     bool do_x;         // pass A: d still lacks alpha_{k-1} p_{k-1}
 };
 
+// The scalars are read with volatile loads: in a persistent kernel another
+// SM may have written them during this launch, and a plain load could hit a
+// stale line in this SM's L1.
 template <int KIND>
-__device__ __forceinline__ MarchScalars read_scalars(const SolveState *st) {
+__device__ __forceinline__ MarchScalars read_scalars(const SolveState *st_) {
+    const volatile SolveState *st = st_;
     MarchScalars sc{};
     if constexpr (KIND == K_PASSA || KIND == K_PASSB || KIND == K_PASSR) sc.it = st->it;
     if constexpr (KIND == K_PASSA) {
@@ -578,7 +582,8 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
 }
 
 // Pass A's last-CTA step: alpha_k = rz / pq, or BREAKDOWN.
-__device__ __forceinline__ void passa_finish(SolveState *st, double pq, bool tmo) {
+__device__ __forceinline__ void passa_finish(SolveState *st_, double pq, bool tmo) {
+    volatile SolveState *st = st_;  // see read_scalars
     st->pq = pq;
     st->pending = 0;
     st->replace = 0;
@@ -589,7 +594,8 @@ __device__ __forceinline__ void passa_finish(SolveState *st, double pq, bool tmo
 
 // Pass B's last-CTA step: beta_k, the convergence test and the residual-
 // replacement trigger.
-__device__ __forceinline__ void passb_finish(SolveState *st, int it, double rr, double rz, bool tmo) {
+__device__ __forceinline__ void passb_finish(SolveState *st_, int it, double rr, double rz, bool tmo) {
+    volatile SolveState *st = st_;  // see read_scalars
     st->it = it + 1;
     st->rr = rr;
     st->pending = 1;
@@ -606,7 +612,8 @@ __device__ __forceinline__ void passb_finish(SolveState *st, int it, double rr, 
 
 // Pass R's last-CTA step: the convergence test and the replacement trigger
 // on the recursive residual (beta is formed after the preconditioner).
-__device__ __forceinline__ void passr_finish(SolveState *st, int it, double rr, bool tmo) {
+__device__ __forceinline__ void passr_finish(SolveState *st_, int it, double rr, bool tmo) {
+    volatile SolveState *st = st_;  // see read_scalars
     st->it = it + 1;
     st->rr = rr;
     st->pending = 1;

@@ -155,11 +155,12 @@ constexpr int res64_nv() { return MODE == RES_INIT ? 3 : MODE == RES_REPLACE ? 2
 // One CTA's part of the residual sums over rows row0, row0 + rstep, ...
 // below row1 (a row = nx consecutive points, row index j + ny k); the
 // block sums land in part[] (valid in thread 0) and *unscale receives the
-// factor that undoes the sums' power-of-two scaling.
-template <int MODE, typename X, typename Bt, bool BLOCK, typename T>
+// factor that undoes the sums' power-of-two scaling.  CG: x was written
+// earlier in the same launch (persistent kernels), read it through L2.
+template <int MODE, typename X, typename Bt, bool BLOCK, typename T, bool CG = false>
 __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row1, int rstep,
                                            double (&part)[res64_nv<MODE>()], double *unscale_out) {
-    const SolveState *st = a.st;
+    const volatile SolveState *st = a.st;  // written by other SMs during a persistent launch
     const X *__restrict__ x = static_cast<const X *>(a.x);
     const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -195,7 +196,7 @@ __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row
             const int64_t base = (int64_t)row * nx;
             for (int i = threadIdx.x; i < nx; i += 256) {
                 const int64_t g = base + i;
-                const Nbr64 u = load_nbr64(x, g, i, j, k, nx, ny, nz);
+                const Nbr64 u = load_nbr64<X, CG>(x, g, i, j, k, nx, ny, nz);
                 if (BLOCK) face_weights64_tab(w, i, j, k, nx, ny, a.tab64, cf);
                 const double ax = apply64<BLOCK>(u, w);
                 const double bl = (double)__ldg(b + g);
@@ -253,8 +254,9 @@ __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row
 // RES_TRUE records the reported true residual, RES_INIT the start state,
 // RES_REPLACE the replacement's decisions.
 template <int MODE>
-__device__ __forceinline__ void res64_finish(SolveState *st, const double (&tot)[res64_nv<MODE>()],
+__device__ __forceinline__ void res64_finish(SolveState *st_, const double (&tot)[res64_nv<MODE>()],
                                              double unscale) {
+    volatile SolveState *st = st_;  // written by other SMs during a persistent launch: no stale L1 lines
     if (MODE == RES_TRUE) {
         st->rr_true = tot[0] * unscale;
         st->bb_true = st->bb;

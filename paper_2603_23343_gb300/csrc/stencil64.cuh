@@ -28,11 +28,14 @@ struct Nbr64 {
     double c, xm, xp, ym, yp, zm, zp;
 };
 
-template <typename X>
+// CG: load through L2 only (ld.global.cg), for x written earlier in the same
+// launch by other SMs; otherwise the read-only path (ld.global.nc), which is
+// valid only for data no thread writes during the launch.
+template <typename X, bool CG = false>
 __device__ __forceinline__ Nbr64 load_nbr64(const X *__restrict__ x, int64_t g, int i, int j, int k, int nx, int ny,
                                             int nz) {
     const int64_t pl = (int64_t)nx * ny;
-    auto L = [&](int64_t o) { return (double)__ldg(x + o); };
+    auto L = [&](int64_t o) { return CG ? (double)__ldcg(x + o) : (double)__ldg(x + o); };
     Nbr64 u;
     u.c = L(g);
     u.xm = i > 0 ? L(g - 1) : 0.0;
