@@ -277,7 +277,8 @@ int gbpcg_pcg_solve(const gbpcg_grid *grid, const void *b, void *x, const gbpcg_
  * (gbpcg_workspace_size_batched) holds every problem's scratch.  Returns
  * GBPCG_OK when all problems converged, else the first other status.
  *
- * Constant-coefficient grids with nx a multiple of 4 run as ONE persistent
+ * Up to 4096 constant-coefficient grids with nx a multiple of 4 (and at most
+ * 4096 tiles each) run as ONE persistent
  * kernel (a cooperative launch of as many CTAs as the GPU holds, inside a
  * cached one-node CUDA graph): every problem runs its own sequence of phases
  * (pass A, pass B, and a flush and an FP64 residual for each residual

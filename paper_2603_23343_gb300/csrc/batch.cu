@@ -15,8 +15,8 @@
 // items: a pass item is one (x, y) tile of the problem marched through a
 // run of z planes (the same z-marching code as the single-problem passes,
 // engine.cuh), a row item a run of grid rows.  Any CTA claims any available
-// item of any unfinished problem (an atomic counter in the problem's phase
-// word, whose upper half numbers the phase), preferring the problem it
+// item of any unfinished problem (an atomic counter in the problem's claim
+// word, whose upper half holds the phase's item count), preferring the problem it
 // worked on last; the CTA that completes a phase's last item adds the
 // problem's partial sums in item order (bitwise reproducible), takes the
 // scalar step (alpha; beta, convergence, the replacement trigger) and opens
@@ -43,7 +43,7 @@ namespace gb {
 namespace {
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchZDepth = 32;  // z planes per pass item
+constexpr int kBatchZDepth = 32;  // most z planes per pass item
 constexpr int kRowPoints = 16384;  // grid points per row item (at least one row)
 constexpr uint32_t kBarrierPolls = 1u << 22;  // x ~64 ns of sleep: well under a second
 constexpr int kBatchMaxProblems = 4096;
@@ -505,9 +505,9 @@ BatchKernel batch_kernel_for(int cfg) {
     }
 }
 
-// Geometry of one problem under a configuration (pass items: the rounds
-// choose their own z depth; row items: the setup, replacement and finalize
-// slots).
+// Geometry of one problem under a configuration (pass items: a pass phase
+// chooses its z depth when it opens; row items: set-up, flush, FP64 residual
+// and finalize).
 struct ProbGeom {
     int tiles_x, tiles, rows_per_item, nrow_items;
 };
@@ -569,7 +569,7 @@ bool batch_persistent_ok(int nprob, const gbpcg_grid *grids) {
     for (int i = 0; i < nprob; ++i) {
         const gbpcg_grid &g = grids[i];
         if (g.k_block || g.nx % 4) return false;  // Poisson operator, 16-byte rows for the TMA boxes
-        for (int c = 0; c < BC_COUNT; ++c)  // a round's item depth keeps every problem within its slots
+        for (int c = 0; c < BC_COUNT; ++c)  // the pass depth keeps every item count within the partial-sum slots
             if (prob_geom(g, c).tiles > 4096) return false;
     }
     return true;
@@ -582,7 +582,7 @@ int batch_persistent_cfgs() { return BC_COUNT; }
 // Sets up the problem table in the workspace's batch region and launches the
 // persistent kernel (inside a cached one-node CUDA graph when the cooperative
 // launch can be captured, else directly).  calls[i] describes problem i
-// (its workspace piece, b, x); maxit caps the rounds.
+// (its workspace piece, b, x); maxit caps each problem's iterations.
 int batch_persistent_launch(int nprob, const gbpcg_grid *grids, const SolveCall *calls, char *region, int cfg,
                             double tol, int maxit, int io, cudaStream_t s) {
     const BatchLayout BL = batch_layout(nprob, grids);

@@ -77,6 +77,56 @@ def train(pairs, w0: torch.Tensor, steps: int, lr: float = 1e-3, kb: int = 8, se
     return tr.w, losses.cpu().numpy(), time.perf_counter() - t0
 
 
+def combination_schedule(steps: int, nprob: int, per_problem: int, seed: int = 0):
+    """(a, b, c) for train_combined: step i combines pairs a[i] and b[i] (indices into the pair
+    list, distinct, of the same problem) with coefficients c[i, 0], c[i, 1] ~ N(0, 1); seeded."""
+    if nprob < 1 or per_problem < 2:
+        raise ValueError("need at least one problem with at least two pairs")
+    prob = inputs.choice(seed, 0, steps, list(range(nprob))).astype(np.int64)
+    a = inputs.choice(seed + 1, 0, steps, list(range(per_problem))).astype(np.int64)
+    shift = inputs.choice(seed + 2, 0, steps, list(range(1, per_problem))).astype(np.int64)
+    b = (a + shift) % per_problem
+    c = inputs.standard_normal(seed + 3, 0, 2 * steps).reshape(steps, 2)
+    return prob * per_problem + a, prob * per_problem + b, c
+
+
+def train_combined(pairs, per_problem: int, w0: torch.Tensor, steps: int, lr: float = 1e-3, kb: int = 8,
+                   seed: int = 0, lr_final: float | None = None):
+    """Adam as in train, but every step sees a fresh exact pair: c_a (r_a, e_a) + c_b (r_b, e_b) for
+    two distinct pairs a, b of one problem (pairs[i * per_problem:(i + 1) * per_problem] share one
+    coefficient field) and seeded standard-normal c_a, c_b.  A^{-1} is linear, so the combination
+    is again a residual and its exact correction; `steps` steps train on `steps` distinct pairs
+    without storing them.  The combinations are formed by the library's axpy kernel.  Returns
+    (weights, per-step losses, seconds)."""
+    nprob = len(pairs) // per_problem
+    if nprob * per_problem != len(pairs):
+        raise ValueError("pairs must hold per_problem pairs of each problem, problem by problem")
+    ia, ib, coef = combination_schedule(steps, nprob, per_problem, seed)
+    shape = tuple(pairs[0][1].shape)
+    tr = binding.NnTrainer(w0, shape, k_block=pairs[0][0], kb=kb)
+    r = torch.empty_like(pairs[0][1])
+    e = torch.empty_like(pairs[0][2])
+    losses = torch.zeros(steps, dtype=torch.float64, device=tr.w.device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        ka, ra, ea = pairs[int(ia[i])]
+        _, rb, eb = pairs[int(ib[i])]
+        ca, cb = float(coef[i, 0]), float(coef[i, 1])
+        r.zero_()
+        e.zero_()
+        binding.axpy(ca, ra, r)
+        binding.axpy(cb, rb, r)
+        binding.axpy(ca, ea, e)
+        binding.axpy(cb, eb, e)
+        tr.set_coefficients(ka, kb)
+        step_lr = lr if lr_final is None else lr * (lr_final / lr) ** (i / max(1, steps - 1))
+        losses[i] = tr.step(r, e, lr=step_lr)
+    tr.status()
+    torch.cuda.synchronize()
+    return tr.w, losses.cpu().numpy(), time.perf_counter() - t0
+
+
 def initial_weights(seed: int = 0) -> torch.Tensor:
     """Seeded He-style initial weights, packed (float32, CPU)."""
     return binding.nn_pack_weights(inputs.unet_init_weights(seed, binding.NN_LAYERS))
