@@ -42,6 +42,10 @@ namespace gb {
 
 namespace {
 
+// The solver scalars are shared between SMs within this launch: they are
+// read and written through volatile accesses (never a stale L1 line).
+__device__ __forceinline__ volatile SolveState *vol(SolveState *s) { return s; }
+
 constexpr int kBatchThreads = 256;
 constexpr int kBatchZDepth = 32;  // most z planes per pass item
 constexpr int kRowPoints = 16384;  // grid points per row item (at least one row)
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         if (group_sum_last<3, kBatchThreads>(part, P.partials, &P.st->ticket[4 + RES_INIT], local, P.nrow_items,
                                              tot) &&
             threadIdx.x == 0)
-            res64_finish<RES_INIT>(P.st, tot, unscale);
+            res64_finish<RES_INIT>(vol(P.st), tot, unscale);
     }
     if (!batch_barrier(hdr)) return;
 
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         if (threadIdx.x == 0) {
             const BatchProblem &P = A.probs[p];
             ProbCtl &c = A.ctl[p];
-            const bool fin = P.st->done != 0;
+            const bool fin = vol(P.st)->done != 0;
             const int need = (2 * P.tiles * P.nz + 4 * (int)kMaxPassBlocks - 1) / (4 * (int)kMaxPassBlocks);
             const int dep = min(P.nz, max(A.depth0, need));
             c.kind = fin ? PH_DONE : PH_A;
@@ -345,7 +349,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             const int k0 = chunk * dep, k1 = min(P.nz, k0 + dep);
             if (kind == PH_A) {
                 // p_k = z_k + beta p_{k-1}, d += alpha_{k-1} p_{k-1}, p.Ap
-                const MarchScalars sc = read_scalars<K_PASSA>(st);
+                const MarchScalars sc = read_scalars<K_PASSA>(vol(st));
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSA> io;
                 io.H0 = P.z;
@@ -370,12 +374,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 block_sum<1, kBatchThreads>(acc, part);
                 if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[K_PASSA], local, nit, tot) &&
                     threadIdx.x == 0) {
-                    passa_finish(st, tot[0], false);
-                    advance(ctl, P, st->done ? PH_DONE : PH_B);
+                    passa_finish(vol(st), tot[0], false);
+                    advance(ctl, P, vol(st)->done ? PH_DONE : PH_B);
                 }
             } else {
                 // q = A p_k, r = D z - alpha q, z = D^-1 r, r.r, r.z
-                const MarchScalars sc = read_scalars<K_PASSB>(st);
+                const MarchScalars sc = read_scalars<K_PASSB>(vol(st));
                 const bool odd = sc.it & 1;
                 MarchIO<T, K_PASSB> io;
                 io.H0 = odd ? P.p1 : P.p0;  // p_k
@@ -400,15 +404,15 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 block_sum<2, kBatchThreads>(acc, part);
                 if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[K_PASSB], local, nit, tot) &&
                     threadIdx.x == 0) {
-                    passb_finish(st, sc.it, tot[0], tot[1], false);
-                    advance(ctl, P, st->done ? PH_DONE : st->replace ? PH_FLUSH : PH_A);
+                    passb_finish(vol(st), sc.it, tot[0], tot[1], false);
+                    advance(ctl, P, vol(st)->done ? PH_DONE : vol(st)->replace ? PH_FLUSH : PH_A);
                 }
             }
         } else {
             const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
             if (kind == PH_FLUSH) {
-                // x += (d + alpha_{k-1} p_{k-1}) / s, d = 0 (scalars read past this SM's L1)
-                const volatile SolveState *vs = st;
+                // x += (d + alpha_{k-1} p_{k-1}) / s, d = 0
+                const volatile SolveState *vs = vol(st);
                 const T *p = ((vs->it - 1) & 1) ? P.p1 : P.p0;
                 const float a = vs->pending ? (float)vs->alpha : 0.0f;
                 const double inv_s = 1.0 / rhs_scale(vs->rhs_bits);
@@ -436,8 +440,8 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 if (group_sum_last<2, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_REPLACE], local, nit,
                                                      tot) &&
                     threadIdx.x == 0) {
-                    res64_finish<RES_REPLACE>(st, tot, unscale);
-                    advance(ctl, P, st->done ? PH_DONE : PH_A);
+                    res64_finish<RES_REPLACE>(vol(st), tot, unscale);
+                    advance(ctl, P, vol(st)->done ? PH_DONE : PH_A);
                 }
             }
         }
@@ -447,7 +451,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
     // ---- x += (d + alpha_{k-1} p_{k-1}) / s (x = 0 when b = 0) ----
     for (int item = blockIdx.x; item < A.nrow_items; item += G) {
         const BatchProblem &P = A.probs[A.row_prob[item]];
-        const SolveState *st = P.st;
+        const volatile SolveState *st = vol(P.st);
         const int local = item - P.row0_item;
         const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
         X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
@@ -470,14 +474,14 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
     for (int item = blockIdx.x; item < A.nrow_items; item += G) {
         const BatchProblem &P = A.probs[A.row_prob[item]];
         SolveState *st = P.st;
-        if (st->true_known) continue;
+        if (vol(st)->true_known) continue;
         const int local = item - P.row0_item;
         const int r0 = local * P.rows_per_item, r1 = min(P.ny * P.nz, r0 + P.rows_per_item);
         double part[1], tot[1], unscale;
         res64_rows<RES_TRUE, X, X, false, T, true>(P.ra, r0, r1, 1, part, &unscale);
         if (group_sum_last<1, kBatchThreads>(part, P.partials, &st->ticket[4 + RES_TRUE], local, P.nrow_items, tot) &&
             threadIdx.x == 0)
-            res64_finish<RES_TRUE>(st, tot, unscale);
+            res64_finish<RES_TRUE>(vol(st), tot, unscale);
     }
 }
 

@@ -107,7 +107,7 @@ struct OpConst {
     template <int V>
     __device__ __forceinline__ void applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
                                            const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
-                                           int k, int nx, int ny, float q[V], float dg[V]) const;
+                                           int k, int nx, int ny, float q[V], float dg[V], float rdg[V]) const;
 };
 
 // Block-constant coefficient k (one float per kbx*kby*kbz block): face
@@ -145,36 +145,42 @@ struct OpBlock {
     template <int V>
     __device__ __forceinline__ void applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
                                            const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
-                                           int k, int nx_, int ny_, float q[V], float dg[V]) const;
+                                           int k, int nx_, int ny_, float q[V], float dg[V], float rdg[V]) const;
 };
 
 // The operator at one thread's V consecutive x points: c = centre values,
 // xl / xr = the x neighbours left of point 0 and right of point V-1, y and
 // z neighbours per point.  Point positions past the grid edge (masked lanes)
-// are clamped into the grid before any coefficient lookup.
+// are clamped into the grid before any coefficient lookup.  rdg receives the
+// correctly rounded reciprocal of each diagonal (the Jacobi step multiplies
+// by it; the compiler drops it where a pass does not use it).
 template <int V, typename Op>
 __device__ __forceinline__ void applyv_pointwise(const Op &op, const float c[V], float xl, float xr, const float ym[V],
                                                  const float yp[V], const float zm[V], const float zp[V], int gx,
-                                                 int gy, int k, int nx, int ny, float q[V], float dg[V]) {
+                                                 int gy, int k, int nx, int ny, float q[V], float dg[V],
+                                                 float rdg[V]) {
 #pragma unroll
     for (int i = 0; i < V; ++i) {
         const float xm = i == 0 ? xl : c[i - 1];
         const float xp = i == V - 1 ? xr : c[i + 1];
         op.apply(c[i], xm, xp, ym[i], yp[i], zm[i], zp[i], min(gx + i, nx - 1), min(gy, ny - 1), k, q[i], dg[i]);
+        rdg[i] = Op::kConst ? op.inv_d : __frcp_rn(dg[i]);
     }
 }
 
 template <int V>
 __device__ __forceinline__ void OpConst::applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
                                                 const float yp[V], const float zm[V], const float zp[V], int gx,
-                                                int gy, int k, int nx, int ny, float q[V], float dg[V]) const {
-    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx, ny, q, dg);
+                                                int gy, int k, int nx, int ny, float q[V], float dg[V],
+                                                float rdg[V]) const {
+    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx, ny, q, dg, rdg);
 }
 template <int V>
 __device__ __forceinline__ void OpBlock::applyv(Cache &, const float c[V], float xl, float xr, const float ym[V],
                                                 const float yp[V], const float zm[V], const float zp[V], int gx,
-                                                int gy, int k, int nx_, int ny_, float q[V], float dg[V]) const {
-    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+                                                int gy, int k, int nx_, int ny_, float q[V], float dg[V],
+                                                float rdg[V]) const {
+    applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg, rdg);
 }
 
 // Block-constant coefficient through a per-block face table built once per
@@ -210,20 +216,35 @@ struct OpTable {
     }
     // A thread's block column (bx, by, x/y offsets) is fixed; its table entry
     // changes only when the march crosses a z block, so it is kept in
-    // registers and reloaded then.
+    // registers and reloaded then.  The z block and offset follow the march
+    // plane by plane (no integer division per plane).
     struct Cache {
-        int bz = -1, bx = 0, by = 0, ix0 = 0, iy = 0;
+        int bz = -1, bx = 0, by = 0, ix0 = 0, iy = 0, iz = 0, k = -2;
         float4 t0, t1;
     };
     template <int V>
     __device__ __forceinline__ void applyv(Cache &cc, const float c[V], float xl, float xr, const float ym[V],
                                            const float yp[V], const float zm[V], const float zp[V], int gx, int gy,
-                                           int k, int nx_, int ny_, float q[V], float dg[V]) const {
+                                           int k, int nx_, int ny_, float q[V], float dg[V], float rdg[V]) const {
         if (!(V == 4 ? grouped4 : grouped8)) {
-            applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg);
+            applyv_pointwise<V>(*this, c, xl, xr, ym, yp, zm, zp, gx, gy, k, nx_, ny_, q, dg, rdg);
             return;
         }
-        const int bz = k / kbz, iz = k - bz * kbz;
+        int bz, iz;
+        if (cc.bz >= 0 && k == cc.k + 1) {
+            bz = cc.bz;
+            iz = cc.iz + 1;
+            if (iz == kbz) { iz = 0; ++bz; }
+        } else if (cc.bz >= 0 && k == cc.k - 1) {
+            bz = cc.bz;
+            iz = cc.iz - 1;
+            if (iz < 0) { iz = kbz - 1; --bz; }
+        } else {
+            bz = k / kbz;
+            iz = k - bz * kbz;
+        }
+        cc.k = k;
+        cc.iz = iz;
         if (bz != cc.bz) {
             if (cc.bz < 0) {
                 const int i0 = min(gx, (nx - 1) & ~(V - 1)), j = min(gy, ny - 1);  // gx is a multiple of V
@@ -240,15 +261,28 @@ struct OpTable {
         const float w2 = cy * (cc.iy == 0 ? t0.w : kc), w3 = cy * (cc.iy == kby - 1 ? t1.x : kc);
         const float w4 = cz * (iz == 0 ? t1.y : kc), w5 = cz * (iz == kbz - 1 ? t1.z : kc);
         const float wyz = (w2 + w3) + (w4 + w5);
+        // kbx and ix0 are multiples of V: only point 0 can sit on a block's -x face and only
+        // point V-1 on its +x face; the others have x weights cx k on both sides.  Three
+        // diagonals (and three reciprocals) cover the V points.
+        const float wi = cx * kc;
+        const float wf = cx * (cc.ix0 == 0 ? t0.y : kc), wl = cx * (cc.ix0 + V - 1 == kbx - 1 ? t0.z : kc);
+        const float di = (wi + wi) + wyz, d0 = (wf + wi) + wyz, dl = (wi + wl) + wyz;
+        const float ri = __frcp_rn(di), r0 = __frcp_rn(d0), rl = __frcp_rn(dl);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
-            const int ix = cc.ix0 + i;
             const float xm = i == 0 ? xl : c[i - 1];
             const float xp = i == V - 1 ? xr : c[i + 1];
-            const float w0 = cx * (ix == 0 ? t0.y : kc), w1 = cx * (ix == kbx - 1 ? t0.z : kc);
-            q[i] = w0 * (c[i] - xm) + w1 * (c[i] - xp) + w2 * (c[i] - ym[i]) + w3 * (c[i] - yp[i]) +
-                   w4 * (c[i] - zm[i]) + w5 * (c[i] - zp[i]);
-            dg[i] = (w0 + w1) + wyz;
+            const float w0 = i == 0 ? wf : wi, w1 = i == V - 1 ? wl : wi;
+            // (A u)_c = dg c - sum of w_f u_f, as for the constant operator
+            float sn = w0 * xm;
+            sn = fmaf(w1, xp, sn);
+            sn = fmaf(w2, ym[i], sn);
+            sn = fmaf(w3, yp[i], sn);
+            sn = fmaf(w4, zm[i], sn);
+            sn = fmaf(w5, zp[i], sn);
+            dg[i] = i == 0 ? d0 : i == V - 1 ? dl : di;
+            q[i] = fmaf(dg[i], c[i], -sn);
+            rdg[i] = i == 0 ? r0 : i == V - 1 ? rl : ri;
         }
     }
 };
@@ -346,12 +380,14 @@ struct MarchScalars {
     bool do_x;         // pass A: d still lacks alpha_{k-1} p_{k-1}
 };
 
-// The scalars are read with volatile loads: in a persistent kernel another
-// SM may have written them during this launch, and a plain load could hit a
-// stale line in this SM's L1.
-template <int KIND>
-__device__ __forceinline__ MarchScalars read_scalars(const SolveState *st_) {
-    const volatile SolveState *st = st_;
+// SP is `const SolveState *`, or `const volatile SolveState *` in a
+// persistent kernel, where another SM may have written the scalars during
+// the same launch.  (Volatile accesses cost an L2 round trip each, which on
+// the serial last-CTA step of every pass shows up in the pass time, so the
+// single-problem passes use plain ones: their scalars were written by an
+// earlier launch.)  The same holds for the finish steps below.
+template <int KIND, typename SP>
+__device__ __forceinline__ MarchScalars read_scalars(SP st) {
     MarchScalars sc{};
     if constexpr (KIND == K_PASSA || KIND == K_PASSB || KIND == K_PASSR) sc.it = st->it;
     if constexpr (KIND == K_PASSA) {
@@ -463,12 +499,17 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
         issue(t);
         issued_hi = t;
     }
-    float qa[V], qb[V], qc[V];
+    // The three planes around the output plane live in q0, q1, q2; each step
+    // loads the next plane over the oldest, and the roles (below, centre,
+    // above) rotate with the step instead of the values moving: the march
+    // loop is unrolled three times, one copy per rotation (below).
+    float q0[V], q1[V], q2[V];
 #pragma unroll
-    for (int i = 0; i < V; ++i) qa[i] = qb[i] = qc[i] = 0.f;
+    for (int i = 0; i < V; ++i) q0[i] = q1[i] = q2[i] = 0.f;
     typename Op::Cache opc;
     const int cidx = (ly + 1) * HX + XH + V * lx;  // this thread's first point in a halo box
-    for (int t = 0; t <= tl; ++t) {
+    // one march step t; qa, qb, qc = planes pl(t-2), pl(t-1), pl(t) (qc loaded here); false: stop
+    auto step = [&](int t, float (&qa)[V], float (&qb)[V], float (&qc)[V]) -> bool {
         const int s = stage(t);
         const unsigned char *base = smem + (size_t)s * SB;
         if constexpr (TMA) {
@@ -491,8 +532,6 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
             }
             __syncthreads();
         }
-#pragma unroll
-        for (int i = 0; i < V; ++i) { qa[i] = qb[i]; qb[i] = qc[i]; }
         in_valv(base, cidx, qc);
         if (t >= 2) {
             // ---- output plane k = pl(t-1) from its own stage ----
@@ -505,9 +544,9 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
             // boundary zeros (the box holds no x halo)
             const float xl = (full_row<TX>() && lx == 0) ? 0.0f : in_val(bk, cidx - 1);
             const float xr = (full_row<TX>() && lx == TX / V - 1) ? 0.0f : in_val(bk, cidx + V);
-            float q[V], dg[V];
+            float q[V], dg[V], rdg[V];
             op.template applyv<V>(opc, qb, xl, xr, ym, yp, REV ? qc : qa, REV ? qa : qc, gx, gy, k, nx, ny, q,
-                                  dg);
+                                  dg, rdg);
             const size_t g = ((size_t)k * ny + gy) * nx + gx;
             const TC *cen = reinterpret_cast<const TC *>(bk + NH * HB) + ly * TX + V * lx;
             float out0[V], out1[V];
@@ -545,7 +584,7 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
-                    const float z = Op::kConst ? r * op.inv_d : r / dg[i];
+                    const float z = r * rdg[i];  // D^-1 r, the reciprocal correctly rounded
                     out0[i] = z;
                     if (ok[i]) {
                         acc[0] = fmaf(r, r, acc[0]);
@@ -566,10 +605,27 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
             }
         }
         __syncthreads();
-        if (*s_timeout) break;
+        if (*s_timeout) return false;
         if (t >= 1 && t - 1 + S <= tl) {
             issue(t - 1 + S);
             issued_hi = t - 1 + S;
+        }
+        return true;
+    };
+    // The 16-bit pass A is bound by memory bandwidth, and the threefold
+    // copy costs it registers (occupancy): it moves the values instead.
+    constexpr bool ROTATE = !(KIND == K_PASSA && sizeof(T) == 2);
+    if constexpr (ROTATE) {
+        for (int t = 0; t <= tl;) {
+            if (!step(t, q1, q2, q0) || ++t > tl) break;
+            if (!step(t, q2, q0, q1) || ++t > tl) break;
+            if (!step(t, q0, q1, q2) || ++t > tl) break;
+        }
+    } else {
+        for (int t = 0; t <= tl; ++t) {
+#pragma unroll
+            for (int i = 0; i < V; ++i) { q0[i] = q1[i]; q1[i] = q2[i]; }
+            if (!step(t, q0, q1, q2)) break;
         }
     }
     if constexpr (TMA) {
@@ -582,8 +638,8 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
 }
 
 // Pass A's last-CTA step: alpha_k = rz / pq, or BREAKDOWN.
-__device__ __forceinline__ void passa_finish(SolveState *st_, double pq, bool tmo) {
-    volatile SolveState *st = st_;  // see read_scalars
+template <typename SP>
+__device__ __forceinline__ void passa_finish(SP st, double pq, bool tmo) {
     st->pq = pq;
     st->pending = 0;
     st->replace = 0;
@@ -594,8 +650,8 @@ __device__ __forceinline__ void passa_finish(SolveState *st_, double pq, bool tm
 
 // Pass B's last-CTA step: beta_k, the convergence test and the residual-
 // replacement trigger.
-__device__ __forceinline__ void passb_finish(SolveState *st_, int it, double rr, double rz, bool tmo) {
-    volatile SolveState *st = st_;  // see read_scalars
+template <typename SP>
+__device__ __forceinline__ void passb_finish(SP st, int it, double rr, double rz, bool tmo) {
     st->it = it + 1;
     st->rr = rr;
     st->pending = 1;
@@ -612,8 +668,8 @@ __device__ __forceinline__ void passb_finish(SolveState *st_, int it, double rr,
 
 // Pass R's last-CTA step: the convergence test and the replacement trigger
 // on the recursive residual (beta is formed after the preconditioner).
-__device__ __forceinline__ void passr_finish(SolveState *st_, int it, double rr, bool tmo) {
-    volatile SolveState *st = st_;  // see read_scalars
+template <typename SP>
+__device__ __forceinline__ void passr_finish(SP st, int it, double rr, bool tmo) {
     st->it = it + 1;
     st->rr = rr;
     st->pending = 1;

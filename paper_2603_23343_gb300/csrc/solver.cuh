@@ -160,7 +160,8 @@ constexpr int res64_nv() { return MODE == RES_INIT ? 3 : MODE == RES_REPLACE ? 2
 template <int MODE, typename X, typename Bt, bool BLOCK, typename T, bool CG = false>
 __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row1, int rstep,
                                            double (&part)[res64_nv<MODE>()], double *unscale_out) {
-    const volatile SolveState *st = a.st;  // written by other SMs during a persistent launch
+    // a persistent launch (CG) reads scalars other SMs wrote during the launch
+    typename std::conditional<CG, const volatile SolveState *, const SolveState *>::type st = a.st;
     const X *__restrict__ x = static_cast<const X *>(a.x);
     const Bt *__restrict__ b = static_cast<const Bt *>(a.b);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -253,10 +254,9 @@ __device__ __forceinline__ void res64_rows(const Res64Args &a, int row0, int row
 // The last contribution's step after the residual sums (thread 0):
 // RES_TRUE records the reported true residual, RES_INIT the start state,
 // RES_REPLACE the replacement's decisions.
-template <int MODE>
-__device__ __forceinline__ void res64_finish(SolveState *st_, const double (&tot)[res64_nv<MODE>()],
-                                             double unscale) {
-    volatile SolveState *st = st_;  // written by other SMs during a persistent launch: no stale L1 lines
+// SP: `SolveState *`, or `volatile SolveState *` in a persistent kernel.
+template <int MODE, typename SP>
+__device__ __forceinline__ void res64_finish(SP st, const double (&tot)[res64_nv<MODE>()], double unscale) {
     if (MODE == RES_TRUE) {
         st->rr_true = tot[0] * unscale;
         st->bb_true = st->bb;
