@@ -148,12 +148,23 @@ struct OpBlock {
                                            int k, int nx_, int ny_, float q[V], float dg[V], float rdg[V]) const;
 };
 
+// 1/x by the hardware's approximate reciprocal (PTX rcp.approx.ftz.f32: at
+// most one unit in the last place off, for the normal positive diagonals it
+// is given).  The Jacobi step z = r * rcp(D) is then a fixed diagonal scaling
+// of r, as a preconditioner must be; the FP64 residual steps divide exactly,
+// which differs from it by the same unit in the last place.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // The operator at one thread's V consecutive x points: c = centre values,
 // xl / xr = the x neighbours left of point 0 and right of point V-1, y and
 // z neighbours per point.  Point positions past the grid edge (masked lanes)
 // are clamped into the grid before any coefficient lookup.  rdg receives the
-// correctly rounded reciprocal of each diagonal (the Jacobi step multiplies
-// by it; the compiler drops it where a pass does not use it).
+// reciprocal of each diagonal (the Jacobi step multiplies by it; the
+// compiler drops it where a pass does not use it).
 template <int V, typename Op>
 __device__ __forceinline__ void applyv_pointwise(const Op &op, const float c[V], float xl, float xr, const float ym[V],
                                                  const float yp[V], const float zm[V], const float zp[V], int gx,
@@ -164,7 +175,7 @@ __device__ __forceinline__ void applyv_pointwise(const Op &op, const float c[V],
         const float xm = i == 0 ? xl : c[i - 1];
         const float xp = i == V - 1 ? xr : c[i + 1];
         op.apply(c[i], xm, xp, ym[i], yp[i], zm[i], zp[i], min(gx + i, nx - 1), min(gy, ny - 1), k, q[i], dg[i]);
-        rdg[i] = Op::kConst ? op.inv_d : __frcp_rn(dg[i]);
+        rdg[i] = Op::kConst ? op.inv_d : rcp_approx(dg[i]);
     }
 }
 
@@ -215,12 +226,13 @@ struct OpTable {
         dg = ((w0 + w1) + (w2 + w3)) + (w4 + w5);
     }
     // A thread's block column (bx, by, x/y offsets) is fixed; its table entry
-    // changes only when the march crosses a z block, so it is kept in
-    // registers and reloaded then.  The z block and offset follow the march
-    // plane by plane (no integer division per plane).
+    // changes only when the march crosses a z block, so the weights derived
+    // from it are kept in registers and recomputed then.  The z block and
+    // offset follow the march plane by plane (no integer division per plane).
     struct Cache {
         int bz = -1, bx = 0, by = 0, ix0 = 0, iy = 0, iz = 0, k = -2;
-        float4 t0, t1;
+        float kc, kzm, kzp;       // block k and its -z / +z face values
+        float w2, w3, wi, wf, wl; // y- / y+ weights; interior, point 0 (-x) and point V-1 (+x) x weights
     };
     template <int V>
     __device__ __forceinline__ void applyv(Cache &cc, const float c[V], float xl, float xr, const float ym[V],
@@ -254,30 +266,35 @@ struct OpTable {
                 cc.iy = j - cc.by * kby;
             }
             cc.bz = bz;
-            lookup(cc.bx, cc.by, bz, cc.t0, cc.t1);
+            float4 t0, t1;
+            lookup(cc.bx, cc.by, bz, t0, t1);
+            const float kc = t0.x;
+            cc.kc = kc;
+            cc.kzm = t1.y;
+            cc.kzp = t1.z;
+            cc.w2 = cy * (cc.iy == 0 ? t0.w : kc);
+            cc.w3 = cy * (cc.iy == kby - 1 ? t1.x : kc);
+            // kbx and ix0 are multiples of V: only point 0 can sit on a block's -x face and only
+            // point V-1 on its +x face; the others have x weights cx k on both sides
+            cc.wi = cx * kc;
+            cc.wf = cx * (cc.ix0 == 0 ? t0.y : kc);
+            cc.wl = cx * (cc.ix0 + V - 1 == kbx - 1 ? t0.z : kc);
         }
-        const float4 t0 = cc.t0, t1 = cc.t1;
-        const float kc = t0.x;
-        const float w2 = cy * (cc.iy == 0 ? t0.w : kc), w3 = cy * (cc.iy == kby - 1 ? t1.x : kc);
-        const float w4 = cz * (iz == 0 ? t1.y : kc), w5 = cz * (iz == kbz - 1 ? t1.z : kc);
-        const float wyz = (w2 + w3) + (w4 + w5);
-        // kbx and ix0 are multiples of V: only point 0 can sit on a block's -x face and only
-        // point V-1 on its +x face; the others have x weights cx k on both sides.  Three
-        // diagonals (and three reciprocals) cover the V points.
-        const float wi = cx * kc;
-        const float wf = cx * (cc.ix0 == 0 ? t0.y : kc), wl = cx * (cc.ix0 + V - 1 == kbx - 1 ? t0.z : kc);
-        const float di = (wi + wi) + wyz, d0 = (wf + wi) + wyz, dl = (wi + wl) + wyz;
-        const float ri = __frcp_rn(di), r0 = __frcp_rn(d0), rl = __frcp_rn(dl);
+        const float w4 = cz * (iz == 0 ? cc.kzm : cc.kc), w5 = cz * (iz == kbz - 1 ? cc.kzp : cc.kc);
+        const float wyz = (cc.w2 + cc.w3) + (w4 + w5);
+        // three diagonals cover the V points (and three reciprocals, rcp_approx)
+        const float di = (cc.wi + cc.wi) + wyz, d0 = (cc.wf + cc.wi) + wyz, dl = (cc.wi + cc.wl) + wyz;
+        const float ri = rcp_approx(di), r0 = rcp_approx(d0), rl = rcp_approx(dl);
 #pragma unroll
         for (int i = 0; i < V; ++i) {
             const float xm = i == 0 ? xl : c[i - 1];
             const float xp = i == V - 1 ? xr : c[i + 1];
-            const float w0 = i == 0 ? wf : wi, w1 = i == V - 1 ? wl : wi;
+            const float w0 = i == 0 ? cc.wf : cc.wi, w1 = i == V - 1 ? cc.wl : cc.wi;
             // (A u)_c = dg c - sum of w_f u_f, as for the constant operator
             float sn = w0 * xm;
             sn = fmaf(w1, xp, sn);
-            sn = fmaf(w2, ym[i], sn);
-            sn = fmaf(w3, yp[i], sn);
+            sn = fmaf(cc.w2, ym[i], sn);
+            sn = fmaf(cc.w3, yp[i], sn);
             sn = fmaf(w4, zm[i], sn);
             sn = fmaf(w5, zp[i], sn);
             dg[i] = i == 0 ? d0 : i == V - 1 ? dl : di;
@@ -584,7 +601,7 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const float r = fmaf(-alpha, q[i], dg[i] * zv[i]);
-                    const float z = r * rdg[i];  // D^-1 r, the reciprocal correctly rounded
+                    const float z = r * rdg[i];  // D^-1 r
                     out0[i] = z;
                     if (ok[i]) {
                         acc[0] = fmaf(r, r, acc[0]);

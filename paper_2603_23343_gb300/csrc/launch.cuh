@@ -46,7 +46,6 @@ struct PassGeom {
     int cfg;
     int tiles_x, tiles_y, zchunk, zchunks;
     int zparts;  // CTAs per z chunk (grid y = chunks x zparts)
-    int threads;
     size_t smem;
     dim3 grid() const { return dim3((unsigned)(tiles_x * tiles_y), (unsigned)zchunks, 1); }
     unsigned nblocks() const { return (unsigned)(tiles_x * tiles_y * zchunks); }
@@ -66,7 +65,6 @@ inline PassGeom make_geom(int cfg, int nx, int ny, int nz, int ctas_per_sm, size
     CfgDims d = cfg_dims(cfg);
     PassGeom g;
     g.cfg = cfg;
-    g.threads = d.tx / 4 * d.ty;
     g.smem = smem;
     g.tiles_x = (nx + d.tx - 1) / d.tx;
     g.tiles_y = (ny + d.ty - 1) / d.ty;

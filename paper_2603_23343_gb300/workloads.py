@@ -1,9 +1,11 @@
 """Fixed, seeded workloads for profilers (ncu and the like), one per hot path, each
 run through the C ABI on cuda:0:
 
-  python -m paper_2603_23343_gb300.workloads passes  --n N --reps R
+  python -m paper_2603_23343_gb300.workloads passes  --n N --reps R [--storage S] [--coef C]
       R profile-mode Jacobi-PCG solves of the N^3 Poisson problem (b ~ U[-1,1) seed 0): the
-      pass kernels launch one by one, outside any graph, so a profiler sees every launch
+      pass kernels launch one by one, outside any graph, so a profiler sees every launch.
+      --storage fp16 / bf16: 16-bit iteration vectors with FP64 refinement (tol 1e-8);
+      --coef lognormal: the lognormal block-coefficient problem (8^3 blocks, seed 1)
   python -m paper_2603_23343_gb300.workloads batch   --n N --reps R
       R persistent batched solves of 16 Poisson problems with sizes drawn from {N/2, N}
       (seed 2): one cooperative kernel launch each
@@ -29,12 +31,21 @@ import torch
 from . import binding, inputs, learned
 
 
-def passes(n, reps):
-    b = torch.from_numpy(inputs.poisson_problem(n, 0, np.float64)).cuda()
-    ws = binding.alloc_workspace(b.shape, io_dtype=binding.F64)
+def passes(n, reps, storage="fp32", coef="poisson"):
+    kd = None
+    if coef == "lognormal":
+        k, b64 = inputs.varcoeff_problem(n, n, n, seed=1, kb=8, dtype=np.float64)
+        kd = torch.from_numpy(k).cuda()
+    else:
+        b64 = inputs.poisson_problem(n, 0, np.float64)
+    b = torch.from_numpy(b64).cuda()
+    st = {"fp32": None, "fp16": torch.float16, "bf16": torch.bfloat16}[storage]
+    kw = dict(tol=1e-6, maxit=2000) if st is None else dict(tol=1e-8, maxit=8000, storage=st, max_outer=20)
+    ws = binding.alloc_workspace(b.shape, kd, io_dtype=binding.F64, storage=binding._DTYPES.get(st, binding.F32))
     for _ in range(reps):
-        x, r = binding.pcg_solve(b, torch.zeros_like(b), tol=1e-6, maxit=2000, workspace=ws, profile=True)
-    print(f"passes {n}^3 x{reps}: {r['iters']} iterations, pass A {1e3 * r['pass_ms'][0] / r['pass_launches'][0]:.1f} us, "
+        x, r = binding.pcg_solve(b, torch.zeros_like(b), k_block=kd, workspace=ws, profile=True, **kw)
+    print(f"passes {n}^3 {coef} {storage} x{reps}: {r['iters']} iterations, "
+          f"pass A {1e3 * r['pass_ms'][0] / r['pass_launches'][0]:.1f} us, "
           f"pass B {1e3 * r['pass_ms'][1] / r['pass_launches'][1]:.1f} us")
 
 
@@ -100,10 +111,15 @@ def main(argv=None):
     ap.add_argument("workload", choices=["passes", "batch", "sell", "vcycle", "forward", "train"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32", help="passes only")
+    ap.add_argument("--coef", choices=["poisson", "lognormal"], default="poisson", help="passes only")
     a = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("the workloads need a CUDA GPU")
-    globals()[a.workload](a.n, a.reps)
+    if a.workload == "passes":
+        passes(a.n, a.reps, a.storage, a.coef)
+    else:
+        globals()[a.workload](a.n, a.reps)
 
 
 if __name__ == "__main__":
