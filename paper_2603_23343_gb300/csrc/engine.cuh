@@ -719,13 +719,15 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     if constexpr (KIND == K_PASSA) { sh1 = (it + 1) & 1; so0 = it & 1; }
     if constexpr (KIND == K_PASSB || KIND == K_PASSR) sh0 = it & 1;
     MarchIO<T, KIND> io;
-    io.H0 = static_cast<const T *>(a.h0[sh0]);
-    io.H1 = static_cast<const T *>(a.h1[sh1]);
+    // selects between fixed parameter slots: a run-time index into the
+    // kernel's parameter arrays would copy them to local memory in every thread
+    io.H0 = static_cast<const T *>(sh0 ? a.h0[1] : a.h0[0]);
+    io.H1 = static_cast<const T *>(sh1 ? a.h1[1] : a.h1[0]);
     io.C0 = static_cast<const TC *>(a.c0);
-    io.O0 = static_cast<T *>(a.o0[so0]);
+    io.O0 = static_cast<T *>(so0 ? a.o0[1] : a.o0[0]);
     io.O1 = static_cast<TC *>(a.o1);
-    io.M0 = &maps.h0[sh0];
-    io.M1 = &maps.h1[sh1];
+    io.M0 = sh0 ? &maps.h0[1] : &maps.h0[0];
+    io.M1 = sh1 ? &maps.h1[1] : &maps.h1[0];
     io.MC = &maps.c0;
 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
