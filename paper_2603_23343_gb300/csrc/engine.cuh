@@ -290,15 +290,15 @@ struct OpTable {
             const float xm = i == 0 ? xl : c[i - 1];
             const float xp = i == V - 1 ? xr : c[i + 1];
             const float w0 = i == 0 ? cc.wf : cc.wi, w1 = i == V - 1 ? cc.wl : cc.wi;
-            // (A u)_c = dg c - sum of w_f u_f, as for the constant operator
-            float sn = w0 * xm;
-            sn = fmaf(w1, xp, sn);
-            sn = fmaf(cc.w2, ym[i], sn);
-            sn = fmaf(cc.w3, yp[i], sn);
-            sn = fmaf(w4, zm[i], sn);
-            sn = fmaf(w5, zp[i], sn);
+            // (A u)_c = sum of w_f (u_c - u_f): for smooth u the differences are small and
+            // nearly exact, where dg u_c - sum w_f u_f would cancel at the scale of dg u_c
+            float sq = w0 * (c[i] - xm);
+            sq = fmaf(w1, c[i] - xp, sq);
+            sq = fmaf(cc.w2, c[i] - ym[i], sq);
+            sq = fmaf(cc.w3, c[i] - yp[i], sq);
+            sq = fmaf(w4, c[i] - zm[i], sq);
+            q[i] = fmaf(w5, c[i] - zp[i], sq);
             dg[i] = i == 0 ? d0 : i == V - 1 ? dl : di;
-            q[i] = fmaf(dg[i], c[i], -sn);
             rdg[i] = i == 0 ? r0 : i == V - 1 ? rl : ri;
         }
     }

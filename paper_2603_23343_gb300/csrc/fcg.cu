@@ -118,11 +118,13 @@ __global__ void __launch_bounds__(kFcgThreads)
     if (fcg_reduce<kMaxDirs + 1>(acc, partials, &st->ticket[0], tot) && threadIdx.x == 0) {
         const double rz = tot[0];
         bool ok = rz > 0.0 && isfinite(rz);
-        for (int j = 0; j < d.nd; ++j) {
-            const double c = tot[1 + j] / st->pq[d.slot[j]];
-            ok = ok && isfinite(c);
-            st->c[j] = c;
-        }
+#pragma unroll
+        for (int j = 0; j < kMaxDirs; ++j)  // static indices: no local copy of the parameter arrays
+            if (j < d.nd) {
+                const double c = tot[1 + j] / st->pq[d.slot[j]];
+                ok = ok && isfinite(c);
+                st->c[j] = c;
+            }
         st->rz = rz;
         if (!ok) st->bad = 2;
     }
