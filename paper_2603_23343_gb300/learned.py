@@ -94,14 +94,17 @@ def train_combined(pairs, per_problem: int, w0: torch.Tensor, steps: int, lr: fl
                    seed: int = 0, lr_final: float | None = None):
     """Adam as in train, but every step sees a fresh exact pair: c_a (r_a, e_a) + c_b (r_b, e_b) for
     two distinct pairs a, b of one problem (pairs[i * per_problem:(i + 1) * per_problem] share one
-    coefficient field) and seeded standard-normal c_a, c_b.  A^{-1} is linear, so the combination
-    is again a residual and its exact correction; `steps` steps train on `steps` distinct pairs
-    without storing them.  The combinations are formed by the library's axpy kernel.  Returns
-    (weights, per-step losses, seconds)."""
+    coefficient field), with c = seeded standard normals divided by the pair's residual norm, so
+    that a rough early residual (norm ~1) does not drown a smooth late one (norm ~1e-3).  A^{-1}
+    is linear, so the combination is again a residual and its exact correction; `steps` steps
+    train on `steps` distinct pairs without storing them.  The norms and combinations are formed
+    by the library's dot and axpy kernels.  Returns (weights, per-step losses, seconds)."""
     nprob = len(pairs) // per_problem
     if nprob * per_problem != len(pairs):
         raise ValueError("pairs must hold per_problem pairs of each problem, problem by problem")
     ia, ib, coef = combination_schedule(steps, nprob, per_problem, seed)
+    inv_norm = [1.0 / max(float(binding.dot(r, r)), 1e-300) ** 0.5 for _, r, _ in pairs]
+    coef = coef * np.array([[inv_norm[a], inv_norm[b]] for a, b in zip(ia, ib)])
     shape = tuple(pairs[0][1].shape)
     tr = binding.NnTrainer(w0, shape, k_block=pairs[0][0], kb=kb)
     r = torch.empty_like(pairs[0][1])
