@@ -18,6 +18,8 @@
 //   u = omega D^-1 f;  f_{l+1} = P^T (f - A u)        (two kernels)
 //   e = V-cycle(l + 1)
 //   out = u' + omega D^-1 (f - A u'),  u' = u + sigma P e   (one kernel)
+// Levels of at most kMgTailCells cells, the coarsest with them, run these
+// steps inside one CTA (mg_tail_kernel) instead of a launch per step.
 // Pre- and post-smoothing are adjoint, so M is symmetric (positive definite
 // for omega < 1, 0 < sigma < 2).  omega = 0.9 and sigma = 1.5 took the
 // fewest iterations in a sweep of the oracle at 32^3 and 64^3.
@@ -45,6 +47,8 @@ constexpr int kMgCoarseSweeps = 24;
 constexpr int64_t kMgMaxCoarsest = 32768;
 constexpr int kMgThreads = 256;
 constexpr int kMgCoarseThreads = 1024;
+constexpr int64_t kMgTailCells = 4096;  // levels this small run inside the one-CTA tail kernel
+constexpr int kMgSmemCells = 4096;      // a coarsest level this small sweeps in shared memory
 
 struct MgLevel {
     int nx, ny, nz;
@@ -296,10 +300,9 @@ __global__ void __launch_bounds__(kMgThreads)
     }
 }
 
-// coarsest level: kMgCoarseSweeps damped Jacobi sweeps from zero in one CTA;
+// coarsest level: kMgCoarseSweeps damped Jacobi sweeps from zero by one CTA;
 // the result lands in lv[l].u (sweeps alternate between u and w)
-__global__ void __launch_bounds__(kMgCoarseThreads) mg_coarse_kernel(const MgArgs a, int l) {
-    if (mg_stand_down(a)) return;
+__device__ __forceinline__ void mg_coarse_sweeps(const MgArgs &a, int l) {
     const MgLevel &L = a.lv[l];
     const int64_t n = (int64_t)L.nx * L.ny * L.nz;
     float *src = L.u, *dst = L.w;
@@ -331,6 +334,118 @@ __global__ void __launch_bounds__(kMgCoarseThreads) mg_coarse_kernel(const MgArg
         float *tmp = src;
         src = dst;
         dst = tmp;
+    }
+}
+
+// (i, j, k) of flat cell c of a level (32-bit: the tail's levels are small)
+__device__ __forceinline__ void mg_cell(const MgLevel &L, int c, int &i, int &j, int &k) {
+    const int t = c / L.nx;
+    i = c - t * L.nx;
+    k = t / L.ny;
+    j = t - k * L.ny;
+}
+
+// The coarsest level's sweeps with src / dst in shared memory (n <= kMgSmemCells):
+// the same arithmetic as mg_coarse_sweeps; the result is written to lv[l].u
+__device__ __forceinline__ void mg_coarse_sweeps_smem(const MgArgs &a, int l, float *sa, float *sb) {
+    const MgLevel &L = a.lv[l];
+    const int n = L.nx * L.ny * L.nz;
+    for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) {
+        int i, j, k;
+        mg_cell(L, c, i, j, k);
+        float w[6], D;
+        mg_weights(a, l, i, j, k, w, D);
+        sa[c] = kMgOmega * L.f[c] / D;
+    }
+    __syncthreads();
+    float *src = sa, *dst = sb;
+    for (int sweep = 1; sweep < kMgCoarseSweeps; ++sweep) {
+        for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) {
+            int i, j, k;
+            mg_cell(L, c, i, j, k);
+            float w[6], D;
+            mg_weights(a, l, i, j, k, w, D);
+            const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return src[q]; });
+            dst[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, src[c], -off), src[c]);
+        }
+        __syncthreads();
+        float *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) L.u[c] = src[c];
+    __syncthreads();
+}
+
+// The small levels l0 .. L-1 of the V-cycle in one CTA (every level but
+// possibly the coarsest holds at most kMgTailCells cells; the coarsest at most
+// kMgMaxCoarsest, in 32-bit range): pre-smoothing and
+// restriction down to the coarsest level, its sweeps, post-smoothing back up
+// to l0 (the same steps as the level kernels, with a CTA barrier between
+// them instead of a kernel launch: on levels of a few thousand cells the
+// launches cost more than the work).  Level l0's result lands in lv[l0].w,
+// or in lv[l0].u when l0 is the coarsest level; a one-level hierarchy copies
+// it into lv[0].w, the V-cycle's output.
+__global__ void __launch_bounds__(kMgCoarseThreads) mg_tail_kernel(const MgArgs a, int l0) {
+    if (mg_stand_down(a)) return;
+    const int lc = a.L - 1;
+    for (int l = l0; l < lc; ++l) {
+        const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
+        const int n = L.nx * L.ny * L.nz, nc = C.nx * C.ny * C.nz;
+        for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) {
+            int i, j, k;
+            mg_cell(L, c, i, j, k);
+            float w[6], D;
+            mg_weights(a, l, i, j, k, w, D);
+            L.u[c] = kMgOmega * L.f[c] / D;
+        }
+        __syncthreads();
+        for (int cc = threadIdx.x; cc < nc; cc += kMgCoarseThreads) {
+            int I, J, K;
+            mg_cell(C, cc, I, J, K);
+            float sum = 0.f;
+            for (int dz = 0; dz < 2; ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                        const int c = (k * L.ny + j) * L.nx + i;
+                        float w[6], D;
+                        mg_weights(a, l, i, j, k, w, D);
+                        const float off = mg_offdiag(L, i, j, k, c, w, [&](int64_t q, int, int, int) { return L.u[q]; });
+                        sum += L.f[c] - fmaf(D, L.u[c], -off);
+                    }
+            C.f[cc] = sum;
+        }
+        __syncthreads();
+    }
+    __shared__ float s_sweep[2][kMgSmemCells];
+    if ((int64_t)a.lv[lc].nx * a.lv[lc].ny * a.lv[lc].nz <= kMgSmemCells)
+        mg_coarse_sweeps_smem(a, lc, s_sweep[0], s_sweep[1]);
+    else
+        mg_coarse_sweeps(a, lc);
+    for (int l = lc - 1; l >= l0; --l) {
+        const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
+        const float *e = (l + 1 == lc) ? C.u : C.w;
+        const int n = L.nx * L.ny * L.nz;
+        // u' = u + sigma P e at a fine cell
+        auto up = [&](int64_t q, int i, int j, int k) {
+            return fmaf(kMgSigma, e[((int64_t)(k >> 1) * C.ny + (j >> 1)) * C.nx + (i >> 1)], L.u[q]);
+        };
+        for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) {
+            int i, j, k;
+            mg_cell(L, c, i, j, k);
+            float w[6], D;
+            mg_weights(a, l, i, j, k, w, D);
+            const float uc = up(c, i, j, k);
+            const float off = mg_offdiag(L, i, j, k, c, w, up);
+            L.w[c] = fmaf(kMgOmega / D, L.f[c] - fmaf(D, uc, -off), uc);
+        }
+        __syncthreads();
+    }
+    if (lc == 0) {
+        const MgLevel &L = a.lv[0];
+        const int n = L.nx * L.ny * L.nz;
+        for (int c = threadIdx.x; c < n; c += kMgCoarseThreads) L.w[c] = L.u[c];
     }
 }
 
@@ -481,7 +596,10 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     // levels whose rows split into 16-byte vectors take four points per thread (and their
     // restriction two coarse cells per thread)
     auto vec = [&](int l) { return a.lv[l].nx % 4 == 0; };
-    for (int l = 0; l + 1 < a.L; ++l) {
+    // levels from l0 down (at most kMgTailCells cells each) run in one CTA
+    int l0 = a.L - 1;
+    while (l0 > 0 && (int64_t)a.lv[l0 - 1].nx * a.lv[l0 - 1].ny * a.lv[l0 - 1].nz <= kMgTailCells) --l0;
+    for (int l = 0; l < l0; ++l) {
         const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
         if (vec(l)) {
             const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz), gc = mg_launch(C.nx / 2, C.ny, C.nz);
@@ -493,8 +611,8 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
             mg_restrict_kernel<1><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
         }
     }
-    mg_coarse_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, a.L - 1);
-    for (int l = a.L - 2; l >= 0; --l) {
+    mg_tail_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, l0);
+    for (int l = l0 - 1; l >= 0; --l) {
         const MgLevel &L = a.lv[l];
         const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
         if (vec(l)) {

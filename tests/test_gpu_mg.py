@@ -50,8 +50,12 @@ def case(shape, varcoeff, seed):
 
 
 @pytest.mark.parametrize("shape,varcoeff", [((32, 32, 32), False), ((16, 24, 32), True), ((64, 64, 64), True),
-                                            ((8, 8, 12), False), ((20, 12, 44), False)])
+                                            ((8, 8, 12), False), ((20, 12, 44), False), ((6, 4, 8), True),
+                                            ((4, 4, 4), False), ((128, 64, 64), False)])
 def test_vcycle_elementwise(gpu_lib, shape, varcoeff):
+    """One V-cycle against the oracle's, element by element: hierarchies of one level (6 x 4 x 8,
+    4^3: the coarsest sweeps are the whole cycle), of levels all inside the one-CTA tail (32^3
+    and smaller), and with level kernels above it (64^3, 128 x 64 x 64)."""
     k, kd = case(shape, varcoeff, 20)
     r = inputs.uniform_rhs(shape, 21)
     z, levels = gpu_lib.mg_vcycle(torch.from_numpy(r).cuda(), k_block=kd)
