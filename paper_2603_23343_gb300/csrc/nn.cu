@@ -108,6 +108,13 @@ static int conv_tc_launch(int X, int Y, int Z, int ci, const __nv_bfloat16 *in, 
         const uint32_t hbox[4] = {8, (uint32_t)kHaloX, (uint32_t)kHaloRows + 2, 1};
         rc = make_map_nd(&maps.act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, in, 4, dims, strides, hbox);
         if (rc) return rc;
+        // weights as (channel, co, tap): one box carries a plane's 9 taps of 8 channels in the
+        // [tap][co][8 channels] order of the B operand (one copy per stage half instead of nine)
+        const uint64_t w3d[3] = {(uint64_t)ci, (uint64_t)CO, 27};
+        const uint64_t w3s[2] = {(uint64_t)27 * ci * 2, (uint64_t)ci * 2};
+        const uint32_t w3b[3] = {8, (uint32_t)CO, 9};
+        rc = make_map_nd(&maps.wgt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 3, w3d, w3s, w3b);
+        if (rc) return rc;
         constexpr uint32_t hsmem = HaloCfg<CO>::SMEM;
         static std::once_flag honce;
         std::call_once(honce, [] {
