@@ -565,8 +565,17 @@ def main():
         kd = torch.from_numpy(k512).cuda()
         bd = torch.from_numpy(b512).cuda()
 
+        # the oracle's own 512^3 solution (to 1e-10) on a lattice of 16^3 points, stored by
+        # tests/golden/make_golden.py --config2 (an hour and more of FP64 CPU time to recompute)
+        with open(os.path.join(ROOT, "tests", "golden", "pcg_lognormal512_seed1_lattice.json")) as f:
+            lat = json.load(f)
+        lsl = slice(lat["lattice_start"], None, lat["lattice_step"])
+        x_lat = np.asarray(lat["x_lattice"])
+
         def check512(xh):
-            return {"oracle_true_relres": oracle.true_relres(b512, xh, k512_64, 8)}
+            return {"oracle_true_relres": oracle.true_relres(b512, xh, k512_64, 8),
+                    "err_vs_oracle_lattice": float(np.linalg.norm(xh[lsl, lsl, lsl].ravel() - x_lat)
+                                                   / np.linalg.norm(x_lat))}
         c2 = {}
         c2["fp32_plain"] = timed_solve(bd, tol=1e-8, maxit=20000, k_block=kd, kb=8, oracle_check=check512)
         c2["fp16"] = timed_solve(bd, tol=1e-8, maxit=8000, k_block=kd, kb=8, storage=torch.float16, max_outer=20,

@@ -402,3 +402,19 @@ def test_csr_pcg_exact_termination_two_eigenvalues():
     res = oracle.csr_pcg(A.indptr, A.indices, A.data, b, tol=1e-14, maxit=10)
     assert res["status"] == oracle.OK and res["iters"] == 2
     np.testing.assert_allclose(A @ res["x"], b, rtol=0, atol=1e-13)
+
+
+def test_config2_lattice_fixture_is_a_converged_oracle_solve():
+    """The stored 512^3 lognormal solution (tests/golden/make_golden.py --config2, the oracle
+    alone): a converged run to 1e-10 whose recursive and true residuals agree, sampled on the
+    stated 16^3 lattice, with a nonzero solution."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pcg_lognormal512_seed1_lattice.json")) as f:
+        g = json.load(f)
+    assert g["n"] == 512 and g["seed"] == 1 and g["kb"] == 8 and g["status"] == 0
+    assert g["relres"] <= g["tol"] == 1e-10 and abs(g["true_relres"] - g["relres"]) <= 1e-3 * g["relres"]
+    m = len(range(g["lattice_start"], g["n"], g["lattice_step"]))
+    assert len(g["x_lattice"]) == m ** 3 == 16 ** 3
+    xl = np.asarray(g["x_lattice"])
+    assert np.all(np.isfinite(xl)) and 0 < np.linalg.norm(xl) <= g["x_norm2"]
