@@ -56,7 +56,7 @@ def batch(n, reps):
     bs = [torch.from_numpy(inputs.uniform_rhs(sh, 100 + i, dtype=np.float64)).cuda() for i, sh in enumerate(shapes)]
     for _ in range(reps):
         xs, res = binding.pcg_solve_batched(bs, tol=1e-6, maxit=3000)
-    print(f"batch of 16 ({sizes}) x{reps}: {res[0]['pass_launches'][1]} rounds, {res[0]['time_ms']:.2f} ms, "
+    print(f"batch of 16 ({sizes}) x{reps}: {res[0]['pass_launches'][1]} phases, {res[0]['time_ms']:.2f} ms, "
           f"all converged: {all(r['status'] == 0 for r in res)}")
 
 
