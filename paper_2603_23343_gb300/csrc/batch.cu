@@ -418,9 +418,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
                 const double inv_s = 1.0 / rhs_scale(vs->rhs_bits);
                 X *x = static_cast<X *>(const_cast<void *>(P.ra.x));
                 const X is = (X)inv_s;
+                // p, d and x were written in this launch by other SMs: loads through L2 only
                 for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
-                    const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
-                    x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+                    const X inc = (X)fmaf(a, __ldcg(p + g), __ldcg(P.d + g));
+                    const X xo = __ldcg(x + g);
+                    x[g] = inv_s == 1.0 ? xo + inc : xo + inc * is;
                     P.d[g] = 0.0f;
                 }
                 // the next pass A reads d through the TMA (async proxy)
@@ -463,9 +465,11 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         const float a = st->pending ? (float)st->alpha : 0.0f;
         const double inv_s = 1.0 / rhs_scale(st->rhs_bits);
         const X is = (X)inv_s;
+        // p, d and x were written in this launch by other SMs: loads through L2 only
         for (int64_t g = (int64_t)r0 * P.nx + threadIdx.x; g < (int64_t)r1 * P.nx; g += kBatchThreads) {
-            const X inc = (X)fmaf(a, to_f(p[g]), P.d[g]);
-            x[g] = inv_s == 1.0 ? x[g] + inc : x[g] + inc * is;
+            const X inc = (X)fmaf(a, __ldcg(p + g), __ldcg(P.d + g));
+            const X xo = __ldcg(x + g);
+            x[g] = inv_s == 1.0 ? xo + inc : xo + inc * is;
         }
     }
     if (!batch_barrier(hdr)) return;

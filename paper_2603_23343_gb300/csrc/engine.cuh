@@ -325,6 +325,7 @@ struct PassArgs {
     cudaGraphConditionalHandle cond_replace;  // IF condition of the residual replacement
     int use_cond;
     float scale;  // stencil apply: output multiplier (1 normally)
+    int l2hint;   // pass A: p_{k-1} and d marked evict-first in L2 (march_tile)
 };
 
 constexpr uint32_t round128(uint32_t v) { return (v + 127u) & ~127u; }
@@ -385,6 +386,7 @@ struct MarchIO {
     T *O0;
     TC *O1;
     const CUtensorMap *M0, *M1, *MC;
+    bool l2hint = false;  // pass A: p_{k-1} and d leave L2 first (see march_tile)
 };
 
 // The solver scalars a pass reads when it starts (iteration k = it).
@@ -454,6 +456,8 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
     const float alpha = sc.alpha, beta = sc.beta, alpha_prev = sc.alpha_prev;
     const bool load_h1 = NH == 2 && !first;
     const bool load_c = G::NC == 1 && !(KIND == K_PASSA && !do_x);
+    uint64_t dpol = 0;
+    if (KIND == K_PASSA && TMA && io.l2hint) dpol = l2_policy_evict_first();
 
     // Planes are visited in march order: step t = 0..tl loads plane pl(t),
     // forward pl(t) = k0 - 1 + t, reverse pl(t) = k1 - t (the first and the
@@ -477,8 +481,20 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
                 const uint32_t bytes = G::HBYTES + (load_h1 ? G::HBYTES : 0u) + (cen ? G::CBYTES : 0u);
                 mbar_arrive_expect_tx(&full[s], bytes);
                 tma_load_3d(base, io.M0, &full[s], x0 - XH, y0 - 1, m);
-                if (load_h1) tma_load_3d(base + HB, io.M1, &full[s], x0 - XH, y0 - 1, m);
-                if (cen) tma_load_3d(base + NH * HB, io.MC, &full[s], x0, y0, m);
+                if (KIND == K_PASSA && io.l2hint) {
+                    // pass A's p_{k-1} (overwritten next iteration) and d (read again only by the
+                    // next pass A) leave L2 first: pass B reads what pass A read and wrote besides
+                    // (z_k, p_k).  Measured: a gain where that data nearly fits in L2 (256^3: pass
+                    // A 58.2 -> 56.7 us, pass B 41.0 -> 39.1 us), a loss on grids far larger
+                    // (512^3 pass A 440 -> 461 us) and in the persistent batch, so the solver
+                    // sets it by grid size.
+                    const uint64_t pol = l2_policy_evict_first();
+                    if (load_h1) tma_load_3d_hint(base + HB, io.M1, &full[s], x0 - XH, y0 - 1, m, pol);
+                    if (cen) tma_load_3d_hint(base + NH * HB, io.MC, &full[s], x0, y0, m, pol);
+                } else {
+                    if (load_h1) tma_load_3d(base + HB, io.M1, &full[s], x0 - XH, y0 - 1, m);
+                    if (cen) tma_load_3d(base + NH * HB, io.MC, &full[s], x0, y0, m);
+                }
             }
         } else {
             manual_box<T, NT>(io.H0, reinterpret_cast<T *>(base), nx, ny, nz, x0 - XH, y0 - 1, m, HX, TY + 2);
@@ -611,7 +627,16 @@ __device__ __forceinline__ uint32_t march_tile(unsigned char *smem, uint64_t *fu
             }
             if (ok[0] && ok[V - 1] && TMA) {
                 stv<T, V>(io.O0 + g, out0);
-                if (st1) stv<TC, V>(io.O1 + g, out1);
+                if constexpr (KIND == K_PASSA && std::is_same<TC, float>::value) {
+                    if (st1 && io.l2hint) {  // d: evict first (above)
+#pragma unroll
+                        for (int i = 0; i < V; i += 4) st4f_hint(io.O1 + g + i, out1 + i, dpol);
+                    } else if (st1) {
+                        stv<TC, V>(io.O1 + g, out1);
+                    }
+                } else {
+                    if (st1) stv<TC, V>(io.O1 + g, out1);
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
@@ -729,6 +754,7 @@ __global__ void __launch_bounds__(TX / (16 / sizeof(T)) * TY)
     io.M0 = sh0 ? &maps.h0[1] : &maps.h0[0];
     io.M1 = sh1 ? &maps.h1[1] : &maps.h1[0];
     io.MC = &maps.c0;
+    io.l2hint = a.l2hint != 0;
 
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int tile = blockIdx.x;

@@ -420,6 +420,7 @@ struct SolvePlan {
     double *tab64;
     PassGeom ga, gb;
     PassMaps ma, mb;
+    static constexpr int64_t kL2HintPoints = (int64_t)1 << 25;  // 33.5 M points (322^3)
     PassArgs aa, ab;
     Res64Args ra;
     double tol;
@@ -471,6 +472,8 @@ struct SolvePlan {
             a->scale = 1.0f;
         }
         aa.tiles_x = ga.tiles_x; aa.zchunk = ga.zchunk; aa.zparts = ga.zparts;
+        // L2 hints in pass A where pass B's data (8 B per point) is within about twice the L2
+        aa.l2hint = (int64_t)nx * ny * nz <= kL2HintPoints ? 1 : 0;
         aa.h0[0] = aa.h0[1] = z; aa.h1[0] = p0; aa.h1[1] = p1; aa.c0 = d; aa.o0[0] = p0; aa.o0[1] = p1; aa.o1 = d;
         ab.tiles_x = gb.tiles_x; ab.zchunk = gb.zchunk; ab.zparts = gb.zparts;
         ab.h0[0] = p0; ab.h0[1] = p1; ab.h1[0] = ab.h1[1] = p0; ab.c0 = z; ab.o0[0] = ab.o0[1] = z; ab.o1 = z;
