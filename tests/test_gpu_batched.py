@@ -137,3 +137,37 @@ def test_persistent_and_graph_batches_agree(gpu_lib):
     for a, c, ra, rc in zip(xp, xg, rp, rg):
         assert ra["status"] == rc["status"] == 0 and abs(ra["iters"] - rc["iters"]) <= 2
         assert float((a - c).norm() / c.norm()) <= 1e-3
+
+
+def test_persistent_batch_single_problem(gpu_lib):
+    """A batch of one: the persistent kernel carries a lone problem through every phase (its
+    pass items then take the whole GPU) and agrees with the standalone solve and the oracle."""
+    b = inputs.uniform_rhs((40, 40, 44), 96, dtype=np.float64)
+    bd = torch.from_numpy(b).cuda()
+    xs, res = gpu_lib.pcg_solve_batched([bd], tol=1e-6, maxit=2000)
+    assert res[0]["pass_launches"][0] == 1 and res[0]["status"] == 0, res[0]
+    ref = oracle.pcg(b, tol=1e-6, maxit=2000)
+    assert abs(res[0]["iters"] - ref["iters"]) <= 2, (res[0]["iters"], ref["iters"])
+    tr = oracle.true_relres(b, xs[0].cpu().numpy())
+    assert tr <= 1e-6 and abs(res[0]["rel_res_true"] - tr) <= 1e-3 * tr
+    x1, r1 = gpu_lib.pcg_solve(bd, tol=1e-6, maxit=2000)
+    assert float((xs[0] - x1).norm() / x1.norm()) <= 1e-3
+
+
+def test_persistent_batch_hundreds_of_small_problems(gpu_lib):
+    """300 problems of 8 to 16 points per axis in one launch: the CTAs' search for work spans ten
+    windows of 32 problems and every claim word is contended; every problem converges with the
+    oracle's iteration count (+-2) and a true residual within the tolerance."""
+    sizes = (8, 12, 16)
+    pick = inputs.choice(97, 0, 900, list(sizes)).reshape(300, 3)
+    shapes = [tuple(int(v) for v in row) for row in pick]
+    bnp = [inputs.uniform_rhs(sh, 1000 + i, dtype=np.float64) for i, sh in enumerate(shapes)]
+    bs = [torch.from_numpy(b).cuda() for b in bnp]
+    xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=2000)
+    assert res[0]["pass_launches"][0] == 1
+    assert res[0]["pass_launches"][1] == sum(2 * r["iters"] + 2 * r["replacements"] for r in res)
+    for b, x, r in zip(bnp, xs, res):
+        ref = oracle.pcg(b, tol=1e-6, maxit=2000)
+        assert r["status"] == 0 and abs(r["iters"] - ref["iters"]) <= 2, (r, ref["iters"])
+        tr = oracle.true_relres(b, x.cpu().numpy())
+        assert tr <= 1e-6 and abs(r["rel_res_true"] - tr) <= 1e-3 * tr
