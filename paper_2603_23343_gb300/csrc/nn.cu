@@ -735,28 +735,48 @@ static int wgrad(int X, int Y, int Z, int ci, int co, const __nv_bfloat16 *x, co
 // with k_f the harmonic mean of the two cells' block coefficients on interior
 // faces and the cell's own coefficient on boundary faces (kb == NULL: k = 1).
 // It depends on the operator only, so a solve computes it once.
+// Grid of the per-voxel kernels: 256 threads along x, one block row per y,
+// and along z as many blocks as bring the grid to about 16 per SM (the
+// kernels stride over the remaining planes, so per-thread set-up, such as
+// nn_input_kernel's FP64 rms, is shared by several planes).
+static dim3 xyz_grid(int X, int Y, int Z) {
+    const int64_t gxy = (int64_t)((X + 255) / 256) * Y;
+    const int64_t want = (int64_t)device_sm_count() * 16;
+    const int64_t gz = std::max<int64_t>(1, std::min<int64_t>({(int64_t)Z, 65535, (want + gxy - 1) / gxy}));
+    return dim3((unsigned)((X + 255) / 256), (unsigned)Y, (unsigned)gz);
+}
+
+// Threads take x, blocks y (blockIdx.y) and z (blockIdx.z, striding by
+// gridDim.z): no division of a flat index per element; the block indices of
+// a thread's column and of its x and y neighbours are fixed per thread.
 __global__ void __launch_bounds__(256)
     jacobi_scale_kernel(int X, int Y, int Z, const float *__restrict__ kb, int kbx, int kby, int kbz,
                         float *__restrict__ dsc) {
-    const int64_t n = (int64_t)X * Y * Z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= X) return;
     const float cx = (float)(X + 1) * (float)(X + 1), cy = (float)(Y + 1) * (float)(Y + 1),
                 cz = (float)(Z + 1) * (float)(Z + 1);
     const int nbx = (X + kbx - 1) / kbx, nby = (Y + kby - 1) / kby;
-    auto kat = [&](int x, int y, int z) { return kb[((int64_t)(z / kbz) * nby + y / kby) * nbx + x / kbx]; };
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int bx = x / kbx, bxm = x > 0 ? (x - 1) / kbx : 0, bxp = x + 1 < X ? (x + 1) / kbx : 0;
+    const int by = y / kby, bym = y > 0 ? (y - 1) / kby : 0, byp = y + 1 < Y ? (y + 1) / kby : 0;
+    for (int z = blockIdx.z; z < Z; z += gridDim.z) {
+        const int64_t v = ((int64_t)z * Y + y) * X + x;
         float d;
         if (!kb) {
             d = 2.0f * (cx + cy + cz);
         } else {
-            const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
-            const float kc = kat(x, y, z);
-            auto face = [&](int xx, int yy, int zz) {
-                if (xx < 0 || xx >= X || yy < 0 || yy >= Y || zz < 0 || zz >= Z) return kc;
-                const float kn = kat(xx, yy, zz);
+            const int bz = z / kbz, bzm = z > 0 ? (z - 1) / kbz : 0, bzp = z + 1 < Z ? (z + 1) / kbz : 0;
+            auto K = [&](int px, int py, int pz) { return kb[((int64_t)pz * nby + py) * nbx + px]; };
+            const float kc = K(bx, by, bz);
+            // face coefficient: harmonic mean with the neighbour's block, the cell's own on the boundary
+            auto face = [&](bool inside, int px, int py, int pz) {
+                if (!inside) return kc;
+                const float kn = K(px, py, pz);
                 return 2.0f * kc * kn / (kc + kn);
             };
-            d = cx * (face(x - 1, y, z) + face(x + 1, y, z)) + cy * (face(x, y - 1, z) + face(x, y + 1, z)) +
-                cz * (face(x, y, z - 1) + face(x, y, z + 1));
+            d = cx * (face(x > 0, bxm, by, bz) + face(x + 1 < X, bxp, by, bz)) +
+                cy * (face(y > 0, bx, bym, bz) + face(y + 1 < Y, bx, byp, bz)) +
+                cz * (face(z > 0, bx, by, bzm) + face(z + 1 < Z, bx, by, bzp));
         }
         dsc[v] = 1.0f / sqrtf(d);
     }
@@ -776,17 +796,17 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     nn_input_kernel(int X, int Y, int Z, const float *__restrict__ sr, const double *ss, const float *__restrict__ kb,
                     int kbx, int kby, int kbz, __nv_bfloat16 *__restrict__ xin, double *scale) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;  // z: blockIdx.z, striding
     const int64_t n = (int64_t)X * Y * Z;
     const double rms = sqrt(*ss / (double)n);
     const float inv = rms > 0.0 ? (float)(1.0 / rms) : 1.0f;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *scale = rms;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) *scale = rms;
+    if (x >= X) return;
     const int nbx = (X + kbx - 1) / kbx, nby = (Y + kby - 1) / kby;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        float lk = 0.0f;
-        if (kb) {
-            const int x = (int)(v % X), y = (int)((v / X) % Y), z = (int)(v / ((int64_t)X * Y));
-            lk = logf(kb[((int64_t)(z / kbz) * nby + y / kby) * nbx + x / kbx]);
-        }
+    const int bx = x / kbx, by = y / kby;
+    for (int z = blockIdx.z; z < Z; z += gridDim.z) {
+        const int64_t v = ((int64_t)z * Y + y) * X + x;
+        const float lk = kb ? logf(kb[((int64_t)(z / kbz) * nby + by) * nbx + bx]) : 0.0f;
         __nv_bfloat162 p;
         p.x = __float2bfloat16_rn(sr[v] * inv);
         p.y = __float2bfloat16_rn(lk);
@@ -1098,8 +1118,8 @@ int nn_weight_prep(const float *w, void *ws, const NnLayout &L, cudaStream_t s) 
 // D^{-1/2} of the grid's operator into the workspace.
 int nn_diag_prep(const gbpcg_grid &g, void *ws, const NnLayout &L, cudaStream_t s) {
     NnPtrs P{static_cast<char *>(ws)};
-    jacobi_scale_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(L.X[0], L.Y[0], L.Z[0], g.k_block, g.kbx, g.kby, g.kbz,
-                                                                P.at<float>(L.dsc));
+    jacobi_scale_kernel<<<xyz_grid(L.X[0], L.Y[0], L.Z[0]), 256, 0, s>>>(L.X[0], L.Y[0], L.Z[0], g.k_block, g.kbx,
+                                                                        g.kby, g.kbz, P.at<float>(L.dsc));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "jacobi_scale launch");
 }
@@ -1120,8 +1140,8 @@ int nn_forward_prepped(const gbpcg_grid &g, const float *r, float *z, void *ws, 
     GB_CUDA(cudaGetLastError());
     GB_TRY(gbpcg_dot(L.V[0], GBPCG_F32, sr, sr, sc + S_RR, P.base + L.dotws, gbpcg_dot_workspace_size(),
                      (gbpcg_stream)s));
-    nn_input_kernel<<<blocks_for(L.V[0], 256), 256, 0, s>>>(X0, Y0, Z0, sr, sc + S_RR, g.k_block, g.kbx, g.kby, g.kbz,
-                                                            P.at<bf16>(L.xin), sc + S_SCALE);
+    nn_input_kernel<<<xyz_grid(X0, Y0, Z0), 256, 0, s>>>(X0, Y0, Z0, sr, sc + S_RR, g.k_block, g.kbx, g.kby, g.kbz,
+                                                         P.at<bf16>(L.xin), sc + S_SCALE);
     GB_CUDA(cudaGetLastError());
     bf16 *a1 = P.at<bf16>(L.a1), *k8 = P.at<bf16>(L.k8), *p1 = P.at<bf16>(L.p1), *a3 = P.at<bf16>(L.a3),
          *k7 = P.at<bf16>(L.k7), *p2 = P.at<bf16>(L.p2), *a5 = P.at<bf16>(L.a5), *a6 = P.at<bf16>(L.a6),
@@ -1211,6 +1231,7 @@ int nn_check(const gbpcg_grid *g, const void *ws, size_t ws_bytes, bool training
     if (!nn_shape_ok(g->nx, g->ny, g->nz))
         return fail_arg("learned preconditioner: grid sizes must be multiples of 4 whose levels tile into 128 voxels "
                         "(e.g. powers of two >= 32)");
+    if (g->ny > 65535) return fail_arg("learned preconditioner: ny must be at most 65535 (one block row per y)");
     *L = nn_layout(g->nx, g->ny, g->nz, training);
     if (!ws || ws_bytes < L->total) return fail_arg("learned preconditioner: workspace too small");
     if (reinterpret_cast<uintptr_t>(ws) & 255u) return fail_arg("workspace must be 256-byte aligned");
