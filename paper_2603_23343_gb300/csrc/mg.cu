@@ -63,6 +63,7 @@ struct MgArgs {
     MgLevel lv[kMgMaxLevels];
     int block;     // level 0: block coefficients (ob.weights) or constant (ob.cx, cy, cz)
     OpBlock ob;
+    const float4 *tab;  // block coefficients: the solver's per-block face table (the same weights, no divisions)
     const SolveState *st;  // inside a solve: every kernel stands down once st->done (NULL outside)
 };
 
@@ -71,7 +72,22 @@ struct MgArgs {
 __device__ __forceinline__ void mg_weights(const MgArgs &a, int l, int i, int j, int k, float w[6], float &D) {
     const MgLevel &L = a.lv[l];
     if (l == 0) {
-        if (a.block) {
+        if (a.block && a.tab) {
+            // the face table holds the harmonic means (or the block's k on the domain boundary):
+            // bitwise the weights of OpBlock::weights, without their divisions
+            const OpBlock &o = a.ob;
+            const int bx = i / o.kbx, by = j / o.kby, bz = k / o.kbz;
+            const int ix = i - bx * o.kbx, iy = j - by * o.kby, iz = k - bz * o.kbz;
+            const float4 *t = a.tab + 2 * (((int64_t)bz * o.nby + by) * o.nbx + bx);
+            const float4 t0 = __ldg(t), t1 = __ldg(t + 1);
+            const float kc = t0.x;
+            w[0] = o.cx * (ix == 0 ? t0.y : kc);
+            w[1] = o.cx * (ix == o.kbx - 1 ? t0.z : kc);
+            w[2] = o.cy * (iy == 0 ? t0.w : kc);
+            w[3] = o.cy * (iy == o.kby - 1 ? t1.x : kc);
+            w[4] = o.cz * (iz == 0 ? t1.y : kc);
+            w[5] = o.cz * (iz == o.kbz - 1 ? t1.z : kc);
+        } else if (a.block) {
             a.ob.weights(i, j, k, w);
         } else {
             w[0] = w[1] = a.ob.cx;
@@ -203,24 +219,32 @@ __device__ __forceinline__ float apply_m(const Nbr<V> &n, int m, const float w[6
 // f_{l+1} = P^T (f - A u).  V = 1: one thread per coarse cell; V = 2: two
 // neighbouring coarse cells per thread, their four fine columns read as one
 // 16-byte vector per fine row (needs nx % 4 == 0).
-template <int V>
+// FROM_F (level 0 with constant coefficients, where D is one number): the
+// pre-smoothed u = (omega / D) f is formed from f at every use instead of
+// being read, and the pre-smoothing kernel is not run (one multiply per
+// value; it rounds once more than omega f / D).
+template <int V, bool FROM_F = false>
 __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
     const int I0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, J = blockIdx.y * blockDim.y + threadIdx.y;
     if (I0 >= C.nx || J >= C.ny) return;
     const int K0 = blockIdx.z * zper, K1 = min(C.nz, K0 + zper);
-    const float *__restrict__ u = L.u;
+    const float *__restrict__ u = FROM_F ? L.f : L.u;
     const float *__restrict__ f = L.f;
     float *__restrict__ fc = C.f;
     constexpr int FV = 2 * V;  // fine points per fine row
+    const float wd = kMgOmega / (2.0f * ((a.ob.cx + a.ob.cy) + a.ob.cz));  // FROM_F: omega / D, D constant
+    auto toU = [&](float x) { return FROM_F ? x * wd : x; };
     auto at = [&](int i, int j, int k) { return ((int64_t)k * L.ny + j) * L.nx + i; };
     auto getv = [&](int i, int j, int k, float *v) {
         const int64_t q = at(i, j, k);
         if constexpr (FV == 4) ld4f(u + q, v);
         else { v[0] = u[q]; v[1] = u[q + 1]; }
+#pragma unroll
+        for (int m = 0; m < FV; ++m) v[m] = toU(v[m]);
     };
-    auto get1 = [&](int i, int j, int k) { return u[at(i, j, k)]; };
+    auto get1 = [&](int i, int j, int k) { return toU(u[at(i, j, k)]); };
     for (int K = K0; K < K1; ++K) {
         float sum[V];
 #pragma unroll
@@ -251,7 +275,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a,
 
 // out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1)
 // result, formed at every stencil input; V consecutive points per thread.
-template <int V>
+template <int V, bool FROM_F = false>
 __global__ void __launch_bounds__(kMgThreads)
     mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e, int zper) {
     if (mg_stand_down(a)) return;
@@ -259,7 +283,9 @@ __global__ void __launch_bounds__(kMgThreads)
     const int i0 = (blockIdx.x * blockDim.x + threadIdx.x) * V, j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
-    const float *__restrict__ u = L.u;
+    const float *__restrict__ u = FROM_F ? L.f : L.u;  // FROM_F: u = omega f / D (see mg_restrict_kernel)
+    const float wd = kMgOmega / (2.0f * ((a.ob.cx + a.ob.cy) + a.ob.cz));
+    auto toU = [&](float x) { return FROM_F ? x * wd : x; };
     const float *__restrict__ f = L.f;
     float *__restrict__ out = L.w;
     for (int k = k0; k < k1; ++k) {
@@ -275,15 +301,17 @@ __global__ void __launch_bounds__(kMgThreads)
                 float uv[4];
                 ld4f(u + q, uv);
                 const float2 ep = __ldg(reinterpret_cast<const float2 *>(e + pc));
-                v[0] = fmaf(kMgSigma, ep.x, uv[0]);
-                v[1] = fmaf(kMgSigma, ep.x, uv[1]);
-                v[2] = fmaf(kMgSigma, ep.y, uv[2]);
-                v[3] = fmaf(kMgSigma, ep.y, uv[3]);
+                v[0] = fmaf(kMgSigma, ep.x, toU(uv[0]));
+                v[1] = fmaf(kMgSigma, ep.x, toU(uv[1]));
+                v[2] = fmaf(kMgSigma, ep.y, toU(uv[2]));
+                v[3] = fmaf(kMgSigma, ep.y, toU(uv[3]));
             } else {
-                v[0] = fmaf(kMgSigma, __ldg(e + pc), u[q]);
+                v[0] = fmaf(kMgSigma, __ldg(e + pc), toU(u[q]));
             }
         };
-        auto get1 = [&](int i, int jj, int kk) { return fmaf(kMgSigma, __ldg(e + parent(i, jj, kk)), u[fine(i, jj, kk)]); };
+        auto get1 = [&](int i, int jj, int kk) {
+            return fmaf(kMgSigma, __ldg(e + parent(i, jj, kk)), toU(u[fine(i, jj, kk)]));
+        };
         Nbr<V> n;
         load_nbr<V>(L, i0, j, k, getv, get1, n);
         float fv[V], res[V];
@@ -565,6 +593,7 @@ MgArgs mg_args(const gbpcg_grid &g, char *ws, const MgLayout &M, float *f0, floa
         }
     }
     a.block = g.k_block ? 1 : 0;
+    a.tab = g.k_block ? reinterpret_cast<const float4 *>(ws + M.base.tab) : nullptr;
     if (g.k_block) {
         a.ob = make_op_block(g);
     } else {
@@ -601,7 +630,11 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     while (l0 > 0 && (int64_t)a.lv[l0 - 1].nx * a.lv[l0 - 1].ny * a.lv[l0 - 1].nz <= kMgTailCells) --l0;
     for (int l = 0; l < l0; ++l) {
         const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-        if (vec(l)) {
+        if (vec(l) && l == 0 && !a.block) {
+            // constant coefficients: u = omega f / D is formed inside restriction and post-smoothing
+            const MgLaunch gc = mg_launch(C.nx / 2, C.ny, C.nz);
+            mg_restrict_kernel<2, true><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+        } else if (vec(l)) {
             const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz), gc = mg_launch(C.nx / 2, C.ny, C.nz);
             mg_pre_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
             mg_restrict_kernel<2><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
@@ -615,7 +648,10 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     for (int l = l0 - 1; l >= 0; --l) {
         const MgLevel &L = a.lv[l];
         const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
-        if (vec(l)) {
+        if (vec(l) && l == 0 && !a.block) {
+            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
+            mg_post_kernel<4, true><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        } else if (vec(l)) {
             const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
             mg_post_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
         } else {
@@ -846,6 +882,13 @@ int gbpcg_mg_vcycle(const gbpcg_grid *grid, const float *r, float *z, void *work
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(workspace);
     const MgArgs a = mg_args(*grid, ws, M, const_cast<float *>(r), z, nullptr);
+    if (grid->k_block) {  // the per-block face table the level-0 weights come from
+        const int nbx = (grid->nx + grid->kbx - 1) / grid->kbx, nby = (grid->ny + grid->kby - 1) / grid->kby,
+                  nbz = (grid->nz + grid->kbz - 1) / grid->kbz;
+        const int64_t nb = (int64_t)nbx * nby * nbz;
+        const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
+        build_face_table<<<blocks, 256, 0, s>>>(grid->k_block, nbx, nby, nbz, const_cast<float4 *>(a.tab));
+    }
     GB_CUDA(mg_setup(a, s));
     GB_CUDA(mg_vcycle(a, s));
     if (levels) *levels = a.L;
