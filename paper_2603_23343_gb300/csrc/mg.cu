@@ -64,19 +64,32 @@ struct MgArgs {
     int block;     // level 0: block coefficients (ob.weights) or constant (ob.cx, cy, cz)
     OpBlock ob;
     const float4 *tab;  // block coefficients: the solver's per-block face table (the same weights, no divisions)
+    float rkbx, rkby, rkbz;  // 1 / the block edges (mg_div)
     const SolveState *st;  // inside a solve: every kernel stands down once st->done (NULL outside)
 };
 
+// n / d for 0 <= n < 2^22 and d >= 1, with rd = 1/d rounded to FP32:
+// (n + 1/2) / d lies at least 1/(2d) from an integer, and the two FP32
+// roundings (of rd and of the product) move it by at most
+// 2^-23 (n + 1/2) / d < 1/(2d), so truncation gives the exact quotient.
+__device__ __forceinline__ int mg_div(int n, float rd) { return (int)(((float)n + 0.5f) * rd); }
+
 // Weights of point (i, j, k) of level l: w[0..5] = faces x-, x+, y-, y+, z-,
 // z+ towards interior neighbours (0 across the boundary), and D.
+// Which weights a kernel computes: W_ANY decides at run time (level and
+// coefficient kind); the level kernels are compiled for one case each, so
+// that a Poisson solve's kernels carry none of the table path's registers.
+enum MgWeights { W_ANY = 0, W_CONST0 = 1, W_TAB0 = 2, W_STORED = 3 };
+
+template <int WK = W_ANY>
 __device__ __forceinline__ void mg_weights(const MgArgs &a, int l, int i, int j, int k, float w[6], float &D) {
     const MgLevel &L = a.lv[l];
-    if (l == 0) {
-        if (a.block && a.tab) {
+    if (WK == W_CONST0 || WK == W_TAB0 || (WK == W_ANY && l == 0)) {
+        if (WK == W_TAB0 || (WK == W_ANY && a.block && a.tab)) {
             // the face table holds the harmonic means (or the block's k on the domain boundary):
             // bitwise the weights of OpBlock::weights, without their divisions
             const OpBlock &o = a.ob;
-            const int bx = i / o.kbx, by = j / o.kby, bz = k / o.kbz;
+            const int bx = mg_div(i, a.rkbx), by = mg_div(j, a.rkby), bz = mg_div(k, a.rkbz);
             const int ix = i - bx * o.kbx, iy = j - by * o.kby, iz = k - bz * o.kbz;
             const float4 *t = a.tab + 2 * (((int64_t)bz * o.nby + by) * o.nbx + bx);
             const float4 t0 = __ldg(t), t1 = __ldg(t + 1);
@@ -87,7 +100,7 @@ __device__ __forceinline__ void mg_weights(const MgArgs &a, int l, int i, int j,
             w[3] = o.cy * (iy == o.kby - 1 ? t1.x : kc);
             w[4] = o.cz * (iz == 0 ? t1.y : kc);
             w[5] = o.cz * (iz == o.kbz - 1 ? t1.z : kc);
-        } else if (a.block) {
+        } else if (WK == W_ANY && a.block) {
             a.ob.weights(i, j, k, w);
         } else {
             w[0] = w[1] = a.ob.cx;
@@ -156,7 +169,7 @@ __device__ __forceinline__ void ld4f(const float *p, float v[4]) {
 }
 
 // u = omega D^-1 f at level l; V consecutive points per thread (V = 4 needs nx % 4 == 0)
-template <int V>
+template <int V, int WK>
 __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l];
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int 
 #pragma unroll
         for (int m = 0; m < V; ++m) {
             float w[6], D;
-            mg_weights(a, l, i0 + m, j, k, w, D);
+            mg_weights<WK>(a, l, i0 + m, j, k, w, D);
             out[m] = kMgOmega * fv[m] / D;
         }
         if constexpr (V == 4) *reinterpret_cast<float4 *>(u + c) = make_float4(out[0], out[1], out[2], out[3]);
@@ -223,7 +236,7 @@ __device__ __forceinline__ float apply_m(const Nbr<V> &n, int m, const float w[6
 // pre-smoothed u = (omega / D) f is formed from f at every use instead of
 // being read, and the pre-smoothing kernel is not run (one multiply per
 // value; it rounds once more than omega f / D).
-template <int V, bool FROM_F = false>
+template <int V, int WK, bool FROM_F = false>
 __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a, int l, int zper) {
     if (mg_stand_down(a)) return;
     const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
@@ -263,7 +276,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a,
 #pragma unroll
                 for (int m = 0; m < FV; ++m) {
                     float w[6], D;
-                    mg_weights(a, l, i0 + m, j, k, w, D);
+                    mg_weights<WK>(a, l, i0 + m, j, k, w, D);
                     sum[m >> 1] += fv[m] - apply_m<FV>(n, m, w, D);
                 }
             }
@@ -275,7 +288,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_restrict_kernel(const MgArgs a,
 
 // out = u' + omega D^-1 (f - A u'), u' = u + sigma P e with e the level-(l+1)
 // result, formed at every stencil input; V consecutive points per thread.
-template <int V, bool FROM_F = false>
+template <int V, int WK, bool FROM_F = false>
 __global__ void __launch_bounds__(kMgThreads)
     mg_post_kernel(const MgArgs a, int l, const float *__restrict__ e, int zper) {
     if (mg_stand_down(a)) return;
@@ -320,7 +333,7 @@ __global__ void __launch_bounds__(kMgThreads)
 #pragma unroll
         for (int m = 0; m < V; ++m) {
             float w[6], D;
-            mg_weights(a, l, i0 + m, j, k, w, D);
+            mg_weights<WK>(a, l, i0 + m, j, k, w, D);
             res[m] = fmaf(kMgOmega / D, fv[m] - apply_m<V>(n, m, w, D), n.c[m]);
         }
         if constexpr (V == 4) *reinterpret_cast<float4 *>(out + c0) = make_float4(res[0], res[1], res[2], res[3]);
@@ -595,6 +608,11 @@ MgArgs mg_args(const gbpcg_grid &g, char *ws, const MgLayout &M, float *f0, floa
     a.block = g.k_block ? 1 : 0;
     a.tab = g.k_block ? reinterpret_cast<const float4 *>(ws + M.base.tab) : nullptr;
     if (g.k_block) {
+        a.rkbx = 1.0f / (float)g.kbx;
+        a.rkby = 1.0f / (float)g.kby;
+        a.rkbz = 1.0f / (float)g.kbz;
+    }
+    if (g.k_block) {
         a.ob = make_op_block(g);
     } else {
         memset(&a.ob, 0, sizeof(a.ob));
@@ -628,36 +646,52 @@ cudaError_t mg_vcycle(const MgArgs &a, cudaStream_t s) {
     // levels from l0 down (at most kMgTailCells cells each) run in one CTA
     int l0 = a.L - 1;
     while (l0 > 0 && (int64_t)a.lv[l0 - 1].nx * a.lv[l0 - 1].ny * a.lv[l0 - 1].nz <= kMgTailCells) --l0;
-    for (int l = 0; l < l0; ++l) {
+    // the kernels of one level, compiled for its kind of weights
+    auto down = [&](auto wk_tag, int l) {
+        constexpr int WK = decltype(wk_tag)::value;
         const MgLevel &L = a.lv[l], &C = a.lv[l + 1];
-        if (vec(l) && l == 0 && !a.block) {
+        if (vec(l) && WK == W_CONST0) {
             // constant coefficients: u = omega f / D is formed inside restriction and post-smoothing
             const MgLaunch gc = mg_launch(C.nx / 2, C.ny, C.nz);
-            mg_restrict_kernel<2, true><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+            mg_restrict_kernel<2, WK, true><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
         } else if (vec(l)) {
             const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz), gc = mg_launch(C.nx / 2, C.ny, C.nz);
-            mg_pre_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
-            mg_restrict_kernel<2><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+            mg_pre_kernel<4, WK><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
+            mg_restrict_kernel<2, WK><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
         } else {
             const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz), gc = mg_launch(C.nx, C.ny, C.nz);
-            mg_pre_kernel<1><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
-            mg_restrict_kernel<1><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
+            mg_pre_kernel<1, WK><<<gf.grid, gf.block, 0, s>>>(a, l, gf.zper);
+            mg_restrict_kernel<1, WK><<<gc.grid, gc.block, 0, s>>>(a, l, gc.zper);
         }
+    };
+    auto up = [&](auto wk_tag, int l) {
+        constexpr int WK = decltype(wk_tag)::value;
+        const MgLevel &L = a.lv[l];
+        const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
+        if (vec(l) && WK == W_CONST0) {
+            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
+            mg_post_kernel<4, WK, true><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        } else if (vec(l)) {
+            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
+            mg_post_kernel<4, WK><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        } else {
+            const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
+            mg_post_kernel<1, WK><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
+        }
+    };
+    using Const0 = std::integral_constant<int, W_CONST0>;
+    using Tab0 = std::integral_constant<int, W_TAB0>;
+    using Stored = std::integral_constant<int, W_STORED>;
+    for (int l = 0; l < l0; ++l) {
+        if (l > 0) down(Stored{}, l);
+        else if (a.block) down(Tab0{}, 0);
+        else down(Const0{}, 0);
     }
     mg_tail_kernel<<<1, kMgCoarseThreads, 0, s>>>(a, l0);
     for (int l = l0 - 1; l >= 0; --l) {
-        const MgLevel &L = a.lv[l];
-        const float *e = (l + 1 == a.L - 1) ? a.lv[l + 1].u : a.lv[l + 1].w;
-        if (vec(l) && l == 0 && !a.block) {
-            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
-            mg_post_kernel<4, true><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
-        } else if (vec(l)) {
-            const MgLaunch gf = mg_launch(L.nx / 4, L.ny, L.nz);
-            mg_post_kernel<4><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
-        } else {
-            const MgLaunch gf = mg_launch(L.nx, L.ny, L.nz);
-            mg_post_kernel<1><<<gf.grid, gf.block, 0, s>>>(a, l, e, gf.zper);
-        }
+        if (l > 0) up(Stored{}, l);
+        else if (a.block) up(Tab0{}, 0);
+        else up(Const0{}, 0);
     }
     return cudaGetLastError();
 }
