@@ -108,12 +108,17 @@ __device__ __forceinline__ void mg_weights(const MgArgs &a, int l, int i, int j,
             w[4] = w[5] = a.ob.cz;
         }
         D = ((w[0] + w[1]) + (w[2] + w[3])) + (w[4] + w[5]);
-        if (i == 0) w[0] = 0.f;
-        if (i == L.nx - 1) w[1] = 0.f;
-        if (j == 0) w[2] = 0.f;
-        if (j == L.ny - 1) w[3] = 0.f;
-        if (k == 0) w[4] = 0.f;
-        if (k == L.nz - 1) w[5] = 0.f;
+        // The level kernels (WK != W_ANY) load stencil inputs outside the grid as zero, so a
+        // boundary face's weight multiplies zero there and need not be cleared; the run-time
+        // form clears it (its callers index neighbours only where the weight is nonzero).
+        if (WK == W_ANY) {
+            if (i == 0) w[0] = 0.f;
+            if (i == L.nx - 1) w[1] = 0.f;
+            if (j == 0) w[2] = 0.f;
+            if (j == L.ny - 1) w[3] = 0.f;
+            if (k == 0) w[4] = 0.f;
+            if (k == L.nz - 1) w[5] = 0.f;
+        }
         return;
     }
     const int64_t c = ((int64_t)k * L.ny + j) * L.nx + i;
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(kMgThreads) mg_pre_kernel(const MgArgs a, int 
         for (int m = 0; m < V; ++m) {
             float w[6], D;
             mg_weights<WK>(a, l, i0 + m, j, k, w, D);
-            out[m] = kMgOmega * fv[m] / D;
+            out[m] = fv[m] * __fdividef(kMgOmega, D);
         }
         if constexpr (V == 4) *reinterpret_cast<float4 *>(u + c) = make_float4(out[0], out[1], out[2], out[3]);
         else u[c] = out[0];
@@ -298,6 +303,7 @@ __global__ void __launch_bounds__(kMgThreads)
     const int k0 = blockIdx.z * zper, k1 = min(L.nz, k0 + zper);
     const float *__restrict__ u = FROM_F ? L.f : L.u;  // FROM_F: u = omega f / D (see mg_restrict_kernel)
     const float wd = kMgOmega / (2.0f * ((a.ob.cx + a.ob.cy) + a.ob.cz));
+    const float wd_const = kMgOmega / (((a.ob.cx + a.ob.cx) + (a.ob.cy + a.ob.cy)) + (a.ob.cz + a.ob.cz));
     auto toU = [&](float x) { return FROM_F ? x * wd : x; };
     const float *__restrict__ f = L.f;
     float *__restrict__ out = L.w;
@@ -334,7 +340,9 @@ __global__ void __launch_bounds__(kMgThreads)
         for (int m = 0; m < V; ++m) {
             float w[6], D;
             mg_weights<WK>(a, l, i0 + m, j, k, w, D);
-            res[m] = fmaf(kMgOmega / D, fv[m] - apply_m<V>(n, m, w, D), n.c[m]);
+            // omega / D: one number for constant coefficients (hoisted), else the fast division
+            const float od = WK == W_CONST0 ? wd_const : __fdividef(kMgOmega, D);
+            res[m] = fmaf(od, fv[m] - apply_m<V>(n, m, w, D), n.c[m]);
         }
         if constexpr (V == 4) *reinterpret_cast<float4 *>(out + c0) = make_float4(res[0], res[1], res[2], res[3]);
         else out[c0] = res[0];
