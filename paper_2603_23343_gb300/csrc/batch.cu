@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         atomicExch(&c->claim, (unsigned long long)(unsigned)n << 32);
     };
 
-    __shared__ int s_p, s_i;
+    __shared__ int s_p, s_i, s_q;
     int cur = (int)(blockIdx.x % (unsigned)A.nprob);
     uint32_t idle = 0;
     for (;;) {
@@ -318,14 +318,21 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
             if (lane == 0) {
                 s_p = got_p;
                 s_i = got_i;
+                // with nothing claimed, thread 0 alone reads whether the batch has finished or
+                // given up: warps that read `active` at different moments would leave the loop at
+                // different __syncthreads, and the CTA's warps would then run out of step with
+                // one another across the grid barriers that follow
+                s_q = got_p >= 0 ? 0
+                      : ((volatile int *)&hdr->active)[0] == 0 ? 1
+                      : ((volatile int *)&hdr->abort)[0] ? 2 : 0;
             }
         }
         __syncthreads();
-        const int pi = s_p, local = s_i;
-        __syncthreads();  // s_p and s_i are written again at the next claim
+        const int pi = s_p, local = s_i, quit = s_q;
+        __syncthreads();  // s_p, s_i and s_q are written again at the next claim
         if (pi < 0) {
-            if (((volatile int *)&hdr->active)[0] == 0) break;
-            if (((volatile int *)&hdr->abort)[0]) return;
+            if (quit == 1) break;
+            if (quit == 2) return;
             if (++idle > kIdlePolls) {
                 if (threadIdx.x == 0) atomicExch(&hdr->abort, 1);
                 return;

@@ -128,6 +128,27 @@ def test_persistent_batch_fp32_io_zero_rhs_and_iteration_cap(gpu_lib):
     assert abs(res[2]["rel_res_true"] - r64) <= 1e-3 * r64
 
 
+def test_persistent_batch_capped_true_residual_repeated(gpu_lib):
+    """The true residual reported for problems stopped by the iteration cap is that of the x
+    returned, call after call.  The persistent kernel's CTAs leave the iteration loop when the
+    last problem finishes; a CTA whose warps took that exit at different moments used to run
+    ahead of the grid barriers and evaluate b - A x before the final x update had landed (about
+    one call in ten); forty calls catch that with near certainty."""
+    shapes = [(24, 20, 36), (16, 16, 16), (40, 40, 40)]
+    bnp = [inputs.uniform_rhs(shapes[0], 90), np.zeros(shapes[1], np.float32), inputs.uniform_rhs(shapes[2], 91)]
+    bs = [torch.from_numpy(b).cuda() for b in bnp]
+    r64 = None
+    for _ in range(40):
+        xs, res = gpu_lib.pcg_solve_batched(bs, tol=1e-6, maxit=20)
+        if r64 is None:
+            r64 = [oracle.true_relres(b.astype(np.float64), x.cpu().double().numpy()) if b.any() else 0.0
+                   for b, x in zip(bnp, xs)]
+        for i in (0, 2):
+            assert res[i]["status"] == 3 and res[i]["iters"] == 20
+            assert abs(res[i]["rel_res_true"] - r64[i]) <= 1e-3 * r64[i], (i, res[i]["rel_res_true"], r64[i])
+        assert res[1]["rel_res_true"] == 0.0 and not torch.any(xs[1])
+
+
 def test_persistent_and_graph_batches_agree(gpu_lib):
     bnp = [inputs.uniform_rhs(sh, 95 + i, dtype=np.float64) for i, sh in enumerate(PSHAPES[:4])]
     bs = [torch.from_numpy(b).cuda() for b in bnp]
