@@ -73,6 +73,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The sum of three 16-column blocks of this thread's TMEM lane (at ta, tb, tc):
+// three loads in flight, then one wait, in one asm statement so that no use of
+// the registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld16_sum3(uint32_t ta, uint32_t tb, uint32_t tc, float v[16]) {
+    uint32_t r[48];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
+        "%29, %30, %31}, [%49];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, "
+        "%45, %46, %47}, [%50];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+          "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+          "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(ta), "r"(tb), "r"(tc)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        v[i] = __uint_as_float(r[i]) + __uint_as_float(r[16 + i]) + __uint_as_float(r[32 + i]);
+}
+
 // UMMA shared-memory descriptor, K-major, no swizzle: start address, leading
 // byte offset (between 8-element K groups), stride byte offset (between
 // 8-row M/N groups), descriptor version 1.
@@ -119,6 +145,7 @@ struct ConvArgs {
     const __nv_bfloat16 *mask;  // optional: out *= (mask > 0), mask channels [moff, moff + co) of mstride
     int mstride, moff;
     int *err;            // set to 1 if a bounded wait gave up
+    int nseg, stages;    // z-marching kernel: z segments per column, stages in its ring
 };
 
 constexpr int kConvStages = 6;
@@ -413,6 +440,281 @@ __global__ void __launch_bounds__(128) conv3_tc_halo_kernel(const __grid_constan
 }  // namespace gb
 
 namespace gb {
+
+// ------------------------------------------------------------------------
+// z-marching kernel for 16 output channels (c2, c8), X a multiple of 128.
+//
+// A CTA owns a column of output voxels, 128 x R = 3 rows (the last column of a
+// grid whose Y is not a multiple of 3 is masked), over a z segment
+// [zs, ze), and marches its source planes m = zs - 1 .. ze.  One stage holds
+// one 16-channel chunk of plane m's slab (R + 2 rows x 130 voxels, zero
+// filled outside the grid by TMA) and feeds all three output planes it
+// touches: o = m + 1 (taps dz = -1), m (dz = 0) and m - 1 (dz = +1).  Each
+// slab is loaded once instead of once per output plane: the halo kernel's
+// limit was the L2 delivery of those slabs, about 25 KB per 2,300 SM cycles.
+//
+// Within a plane, the three taps dy = -1, 0, +1 of one (dz, dx) read the same
+// slab row for different output rows, so one MMA serves every tap a slab row
+// feeds: for slab row r (r = -1 .. R) and tap (dz, dx),
+//   P_r[x, (dy, o)] += sum_i in[m, y0 + r, x + dx, i] W[o, (dz, dy, dx), i]
+// over dy in [max(-1, r - R + 1), min(1, r)] (output rows rho = r - dy inside
+// the column), N = 16, 32 or 48.  Each P_r has its own TMEM columns (3 R x 16
+// for a plane, each column an output partial sum) and the epilogue adds
+//   out[rho, x, o] = sum_dy P_{rho + dy}[x, (dy, o)]
+// within TMEM lane x.  Per (source plane, chunk) that is 3 x 3 x (R + 2) = 45
+// MMAs for three output planes of R rows, against 81 with one MMA per (row,
+// tap).  Three output planes are open at a time; their accumulators rotate
+// through 3 x 144 of the SM's 512 TMEM columns (one CTA per SM).
+//
+// Roles: warp 4 lane 0 loads the layer's weights once (all 27 taps stay in
+// shared memory, in [chunk][dz][half][dx][dy][co][8] order from a 5D view of
+// the (Co, 27, Ci) array) and then streams the slabs by TMA; warp 5 lane 0
+// issues the MMAs; warps 0-3 drain each output plane once its last source
+// plane is in (warp w reads TMEM lanes 32w .. 32w + 31).  In a stage the MMAs
+// into planes m - 1 and m go first; the first MMAs into plane m + 1 reuse the
+// accumulator of plane m - 2 and wait, at chunk 0, for its epilogue.
+
+constexpr int kZmMaxStages = 8;
+
+struct ZmCfg {
+    static constexpr int CO = 16, R = 3, NR = R + 2;
+    static constexpr uint32_t A_HALF = ((uint32_t)(16 * kHaloX * NR) + 127) & ~127u;
+    static constexpr uint32_t A_STAGE = (2 * A_HALF + 1023) & ~1023u;
+    static constexpr uint32_t A_TX = 2u * 16 * kHaloX * NR;  // bytes the two slab boxes bring
+    static constexpr uint32_t B_HALF = 9u * CO * 16u;         // 9 taps (one dz) of 8 channels
+    static constexpr int ACC = 3 * R * CO;                    // TMEM columns of one output plane
+    static constexpr uint32_t NCOL = 512;
+    // resident weights: 6 boxes (3 dz x 2 halves) per 16-channel chunk
+    __host__ __device__ static constexpr uint32_t wbytes(int kc) {
+        return ((uint32_t)(6 * kc) * B_HALF + 1023) & ~1023u;
+    }
+    // taps dy_lo(r) .. dy_hi(r) of slab row r, and the first TMEM column of P_r
+    __host__ __device__ static constexpr int dy_lo(int r) { return r - R + 1 > -1 ? r - R + 1 : -1; }
+    __host__ __device__ static constexpr int dy_hi(int r) { return r < 1 ? r : 1; }
+    __host__ __device__ static constexpr int nblk(int r) { return dy_hi(r) - dy_lo(r) + 1; }
+    __host__ __device__ static constexpr int col(int r) {
+        int c = 0;
+        for (int q = -1; q < r; ++q) c += nblk(q) * CO;
+        return c;
+    }
+    static_assert(3 * ACC <= (int)NCOL, "three open output planes in TMEM");
+};
+
+// Geometry of work item `item`: column (x0, y0) and z segment [zs, ze).
+struct ZmItem {
+    int x0, y0, zs, ze;
+};
+__device__ __forceinline__ ZmItem zm_item(const ConvArgs &a, int item, int tiles_x, int ncols) {
+    const int c = item % ncols, g = item / ncols;
+    ZmItem t;
+    t.x0 = (c % tiles_x) * 128;
+    t.y0 = (c / tiles_x) * ZmCfg::R;
+    t.zs = (int)((int64_t)g * a.Z / a.nseg);
+    t.ze = (int)((int64_t)(g + 1) * a.Z / a.nseg);
+    return t;
+}
+
+template <typename OUT>
+__global__ void __launch_bounds__(192, 1) conv3_tc_zmarch_kernel(const __grid_constant__ ConvMaps maps,
+                                                                  const ConvArgs a) {
+    using H = ZmCfg;
+    constexpr int R = H::R, CO = H::CO;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[kZmMaxStages], empty[kZmMaxStages], acc_full[3], acc_empty[3], wbar, done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_err;
+    volatile int *err = &s_err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kc = a.ci / 16, S = a.stages;
+    const int tiles_x = a.X / 128, ncols = tiles_x * ((a.Y + R - 1) / R);
+    const int nitems = ncols * a.nseg;
+    const uint32_t wb = H::wbytes(kc);
+
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 3; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&wbar, 1);
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, H::NCOL);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // the layer's weights, once: box (channel half, dz) of chunk cc at
+            // ((cc * 3 + dz + 1) * 2 + half) * B_HALF
+            mbar_arrive_expect_tx(&wbar, (uint32_t)(6 * kc) * H::B_HALF);
+            for (int cc = 0; cc < kc; ++cc)
+                for (int dzi = 0; dzi < 3; ++dzi)
+                    for (int h = 0; h < 2; ++h)
+                        tma_load_5d(smem + (size_t)((cc * 3 + dzi) * 2 + h) * H::B_HALF, &maps.wgt, &wbar,
+                                    cc * 16 + h * 8, 0, 0, 0, dzi);
+            unsigned char *stages = smem + wb;
+            uint32_t step = 0;  // stages issued so far (ring slot step % S, its use step / S)
+            for (int item = blockIdx.x; item < nitems && !*err; item += gridDim.x) {
+                const ZmItem t = zm_item(a, item, tiles_x, ncols);
+                for (int m = t.zs - 1; m <= t.ze && !*err; ++m)
+                    for (int cc = 0; cc < kc; ++cc) {
+                        const int s = (int)(step % (uint32_t)S);
+                        if (step >= (uint32_t)S && !mbar_wait_bounded(&empty[s], ((step / S) - 1) & 1)) {
+                            *err = 1;
+                            break;
+                        }
+                        unsigned char *st = stages + (size_t)s * H::A_STAGE;
+                        mbar_arrive_expect_tx(&full[s], H::A_TX);
+                        for (int h = 0; h < 2; ++h)
+                            tma_load_4d(st + h * H::A_HALF, &maps.act, &full[s], cc * 16 + h * 8, t.x0 - 1, t.y0 - 1,
+                                        m);
+                        ++step;
+                    }
+            }
+            // every issued copy has landed before the CTA can exit
+            for (int s = 0; s < S; ++s)
+                if (step > (uint32_t)s) {
+                    const uint32_t last = (uint32_t)s + ((step - 1 - (uint32_t)s) / S) * S;
+                    if (!mbar_wait_bounded(&full[s], (last / S) & 1)) *err = 1;
+                }
+            if (!mbar_wait_bounded(&wbar, 0)) *err = 1;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t sbase = smem_u32(smem), stb = sbase + wb;
+            bool ok = mbar_wait_bounded(&wbar, 0);
+            if (!ok) *err = 1;
+            tc_fence_after();
+            uint32_t step = 0, J0 = 0;  // stages consumed; output planes of this CTA's earlier items
+            for (int item = blockIdx.x; item < nitems && ok && !*err; item += gridDim.x) {
+                const ZmItem t = zm_item(a, item, tiles_x, ncols);
+                for (int m = t.zs - 1; m <= t.ze && ok; ++m) {
+                    // output planes source plane m feeds: m + 1 (dz = -1), m (dz = 0), m - 1 (dz = +1)
+                    const bool f_next = m + 1 >= t.zs && m + 1 < t.ze;
+                    const bool f_cur = m >= t.zs && m < t.ze;
+                    const bool f_prev = m - 1 >= t.zs && m - 1 < t.ze;
+                    for (int cc = 0; cc < kc; ++cc, ++step) {
+                        const int s = (int)(step % (uint32_t)S);
+                        if (!mbar_wait_bounded(&full[s], (step / S) & 1)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t adesc = umma_desc_kmajor(stb + (uint32_t)s * H::A_STAGE, H::A_HALF, 128);
+                        // one tap plane dz of this chunk into the accumulator of output plane J
+                        auto taps = [&](int dzi, uint32_t J, bool first) {
+                            const uint32_t acc = tmem + (J % 3) * (uint32_t)H::ACC;
+                            const uint64_t bdesc =
+                                umma_desc_kmajor(sbase + (uint32_t)((cc * 3 + dzi) * 2) * H::B_HALF, H::B_HALF, 128);
+#pragma unroll
+                            for (int dxi = 0; dxi < 3; ++dxi)
+#pragma unroll
+                                for (int r = -1; r <= R; ++r) {
+                                    // A: slab row r shifted by dx; B: taps (dx, dy_lo(r) .. dy_hi(r)); both
+                                    // offsets are 16-byte multiples added to the descriptors' address field
+                                    const uint32_t aoff = (uint32_t)((r + 1) * kHaloX + dxi);
+                                    const uint32_t boff = (uint32_t)((dxi * 3 + H::dy_lo(r) + 1) * CO);
+                                    mma_bf16(acc + (uint32_t)H::col(r), adesc + aoff, bdesc + boff,
+                                             idesc_bf16(128, H::nblk(r) * CO), (first && dxi == 0) ? 0u : 1u);
+                                }
+                        };
+                        if (f_prev) taps(2, J0 + (uint32_t)(m - 1 - t.zs), false);
+                        if (f_cur) taps(1, J0 + (uint32_t)(m - t.zs), false);
+                        if (f_next) {
+                            const uint32_t J = J0 + (uint32_t)(m + 1 - t.zs);
+                            // plane J's accumulator held plane J - 3 until its epilogue released it
+                            if (cc == 0 && J >= 3) {
+                                if (!mbar_wait_bounded(&acc_empty[J % 3], ((J / 3) - 1) & 1)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc_fence_after();
+                            }
+                            taps(0, J, cc == 0);
+                        }
+                        mma_commit(&empty[s]);
+                        // plane m - 1 has all its source planes once the last chunk of plane m is in
+                        if (cc == kc - 1 && f_prev) mma_commit(&acc_full[(J0 + (uint32_t)(m - 1 - t.zs)) % 3]);
+                    }
+                }
+                J0 += (uint32_t)(t.ze - t.zs);
+            }
+            if (!ok) *err = 1;
+            mma_commit(&done);
+        }
+    } else if (warp < 4) {
+        uint32_t J = 0;  // output planes drained so far
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const ZmItem t = zm_item(a, item, tiles_x, ncols);
+            const int x = t.x0 + warp * 32 + lane;
+            for (int o = t.zs; o < t.ze; ++o, ++J) {
+                const int b = (int)(J % 3);
+                // warp-uniform: every lane polls the same barrier, the warp agrees on the outcome
+                ok = __all_sync(0xffffffffu, !*err && mbar_wait_bounded(&acc_full[b], (J / 3) & 1));
+                if (!ok) {
+                    if (lane == 0) *err = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * H::ACC);
+#pragma unroll
+                for (int rho = 0; rho < R; ++rho) {
+                    if (t.y0 + rho >= a.Y) continue;  // the masked rows of a grid's last column
+                    const int64_t v = ((int64_t)o * a.Y + t.y0 + rho) * a.X + x;
+                    OUT *out = static_cast<OUT *>(a.out) + v * a.cstride + a.coff;
+                    const __nv_bfloat16 *mk = a.mask ? a.mask + v * a.mstride + a.moff : nullptr;
+                    // dy = -1 from P_{rho-1}, 0 from P_rho, +1 from P_{rho+1}
+                    float f[16];
+                    tmem_ld16_sum3(lane_base + (uint32_t)(H::col(rho - 1) + (-1 - H::dy_lo(rho - 1)) * CO),
+                                   lane_base + (uint32_t)(H::col(rho) + (0 - H::dy_lo(rho)) * CO),
+                                   lane_base + (uint32_t)(H::col(rho + 1) + (1 - H::dy_lo(rho + 1)) * CO), f);
+                    float mv[16];
+                    if (mk) {
+                        ld8(mk, mv);
+                        ld8(mk + 8, mv + 8);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (a.relu) f[i] = f[i] < 0.0f ? 0.0f : f[i];
+                        if (mk && !(mv[i] > 0.0f)) f[i] = 0.0f;
+                    }
+                    if constexpr (std::is_same<OUT, float>::value) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4) st4(out + i, f + i);
+                    } else {
+                        st8(out, f);
+                        st8(out + 8, f + 8);
+                    }
+                }
+                // the TMEM reads have completed (the loads waited) before the MMAs may reuse the columns
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[b]);
+            }
+        }
+    }
+    __syncwarp();
+    // the MMAs issued (all of them, on every path) have completed before TMEM is freed
+    const bool fin = mbar_wait_bounded(&done, 0);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, H::NCOL);
+    if (threadIdx.x == 0 && (s_err || !fin)) atomicExch(a.err, 1);
+}
 
 // ------------------------------------------------------------------------
 // Weight gradient on the tensor cores:

@@ -103,6 +103,56 @@ static int conv_tc_launch(int X, int Y, int Z, int ci, const __nv_bfloat16 *in, 
     const uint32_t wb[2] = {8, (uint32_t)CO};
     rc = make_map_nd(&maps.wgt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 2, wd, wst, wb);
     if (rc) return rc;
+    if constexpr (CO == 16) {
+        const int kc = ci / 16;
+        const uint32_t wbytes = ZmCfg::wbytes(kc);
+        // shared memory a CTA may use, less a margin for the static barriers
+        constexpr uint32_t kSmemBudget = 227u * 1024u - 2048u;
+        const int stages =
+            wbytes >= kSmemBudget ? 0 : (int)std::min<uint32_t>(kZmMaxStages, (kSmemBudget - wbytes) / ZmCfg::A_STAGE);
+        if (X % 128 == 0 && stages >= 3) {
+            // rows of 128: the z-marching kernel; A box (8, 130, 5, 1), one source plane per load
+            const uint32_t zbox[4] = {8, (uint32_t)kHaloX, (uint32_t)ZmCfg::NR, 1};
+            rc = make_map_nd(&maps.act, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, in, 4, dims, strides, zbox);
+            if (rc) return rc;
+            // weights (Co, 27, Ci) viewed as (channel, co, dy, dx, dz): one box holds a source plane's
+            // 9 taps of 8 channels as [dx][dy][co][8 channels], so the dy taps of one dx are
+            // consecutive rows of the B operand
+            const uint64_t w5d[5] = {(uint64_t)ci, (uint64_t)CO, 3, 3, 3};
+            const uint64_t w5s[4] = {(uint64_t)27 * ci * 2, (uint64_t)3 * ci * 2, (uint64_t)ci * 2,
+                                     (uint64_t)9 * ci * 2};
+            const uint32_t w5b[5] = {8, (uint32_t)CO, 3, 3, 1};
+            rc = make_map_nd(&maps.wgt, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, w, 5, w5d, w5s, w5b);
+            if (rc) return rc;
+            static std::once_flag zonce;
+            std::call_once(zonce, [] {
+                cudaFuncSetAttribute(conv3_tc_zmarch_kernel<OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBudget);
+            });
+            // one CTA per SM (it holds all 512 TMEM columns); z segments per column chosen so that
+            // the CTA with the most work marches the fewest source planes
+            const int G = device_sm_count();
+            const int64_t ncols = (int64_t)(X / 128) * ((Y + ZmCfg::R - 1) / ZmCfg::R);
+            int nseg = 1;
+            int64_t best = INT64_MAX;
+            for (int ns = 1; ns <= Z; ++ns) {
+                const int64_t rounds = (ncols * ns + G - 1) / G;
+                const int64_t cost = rounds * ((Z + ns - 1) / ns + 2);
+                if (cost < best) {
+                    best = cost;
+                    nseg = ns;
+                }
+            }
+            if (ncols * nseg > INT32_MAX) return fail_arg("convolution grid too large");
+            a.nseg = nseg;
+            a.stages = stages;
+            const int64_t grid = std::min<int64_t>(ncols * nseg, G);
+            const uint32_t smem = wbytes + (uint32_t)stages * ZmCfg::A_STAGE;
+            conv3_tc_zmarch_kernel<OUT><<<(unsigned)grid, 192, smem, s>>>(maps, a);
+            cudaError_t e = cudaGetLastError();
+            return e == cudaSuccess ? GBPCG_OK : fail_cuda(e, "conv3_tc_zmarch launch");
+        }
+    }
     if (X % 128 == 0 && Y % kHaloRows == 0 && Z <= 65535) {
         // rows of 128: the halo-slab kernel, whose A box is (8, 130, rows + 2, 1)
         const uint32_t hbox[4] = {8, (uint32_t)kHaloX, (uint32_t)kHaloRows + 2, 1};
