@@ -168,7 +168,7 @@ def learned_leg(B, learned, stream, full: bool):
                                               np.mean([e["jacobi"]["ms"] for e in evals])),
         "network_256": {"ms": net_ms, "tflops": net_flop / (net_ms * 1e-3) / 1e12,
                         "flop": net_flop},
-        "roofline_conv_c8_256": {"bound": "tensor", "kernel": "conv3_tc_halo_kernel<16> (48->16 channels)",
+        "roofline_conv_c8_256": {"bound": "tensor", "kernel": "conv3_tc_zmarch_kernel (48->16 channels)",
                                  "achieved": c8_tf, "peak": burst, "unit": "TFLOP/s", "frac": c8_tf / burst,
                                  "peak_source": src + " bf16 burst", "flop_per_launch": c8_flop,
                                  "avg_launch_us": c8_ms * 1e3, "traffic": None},
