@@ -71,6 +71,22 @@ def test_conv3_forward_tensor_cores(gpu_lib, shape, ci, co):
     assert np.all(np.abs(y - ref) <= 2e-5 * bound + 1e-30), np.max(np.abs(y - ref) / (bound + 1e-30))
 
 
+# 16 output channels on rows of 128 take the z-marching kernel, whose CTAs own 3-row columns over z
+# segments.  (8, 59, 1024): 160 columns for 152 SMs, so each CTA marches up to three segments of
+# four planes (its accumulators rotate through twelve output planes) and the last column has two
+# rows inside the grid; (40, 7, 256): two-plane segments, the last column one row deep.
+@pytest.mark.parametrize("shape,ci,relu", [((8, 59, 1024), 16, False), ((8, 59, 1024), 48, True),
+                                           ((40, 7, 256), 48, False)])
+def test_conv3_forward_zmarch_segments(gpu_lib, shape, ci, relu):
+    x, w = conv_case(shape, ci, 16, 500 + ci)
+    y = gpu_lib.conv3_forward(dev_bf16(x), dev_bf16(w), relu=relu).cpu().double().numpy()
+    ref = onn.conv3(x, w)
+    if relu:
+        ref = onn.relu(ref)
+    bound = onn.conv3(np.abs(x), np.abs(w))
+    assert np.all(np.abs(y - ref) <= 2e-5 * bound + 1e-30), np.max(np.abs(y - ref) / (bound + 1e-30))
+
+
 @pytest.mark.parametrize("ci,co", [(16, 32), (48, 16)])
 def test_conv3_forward_relu(gpu_lib, ci, co):
     x, w = conv_case((4, 8, 32), ci, co, 7)
