@@ -390,16 +390,21 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// One output channel (the network's last layer, 16 -> 1), marching in z: a thread owns four
-// consecutive x outputs of one row over a z range and keeps the partial sums of three output
-// planes in registers.  Input plane m is read once (three rows, six voxels, CI channels) and
-// added, tap by tap, into output planes m + 1, m and m - 1; plane m - 1 is then complete and
-// written.  Per output: 27 CI multiply-adds from CI / 8 x 4.5 sixteen-byte loads, against 27 x
-// CI / 8 loads when every output reads its own 27 neighbours.
+// One output channel (the network's last layer, 16 -> 1), marching in z: warp w of a block owns
+// 128 consecutive x outputs of one row (lane l: x = x0 + l + 32 j, j = 0..3) over a z range and
+// keeps the partial sums of three output planes in registers.  For input plane m and row y + dy a
+// thread loads its own four voxels only (one warp load covers 32 consecutive voxels: 16-byte
+// pieces 32 bytes apart, not one piece per 128-byte line) and forms, per voxel, the nine products
+// of its CI channels with taps (dz, dy, dx).  Output x adds the dx = 0 product of voxel x, and the
+// dx = -1 product of voxel x - 1 and the dx = +1 product of voxel x + 1, which arrive from the
+// neighbouring lanes by shuffles; lanes 0 and 31 also form the product of the voxel just outside
+// the warp's 128 (x0 - 1, x0 + 128).  Input plane m feeds output planes m + 1, m and m - 1; plane
+// m - 1 is then complete and written.  Per output: 27 CI multiply-adds from CI / 8 x 3 sixteen-byte
+// loads per input plane.
 constexpr int kC1Rows = 8, kC1Chunk = 16;
 
 template <int CI, typename TO>
-__global__ void __launch_bounds__(32 * kC1Rows)
+__global__ void __launch_bounds__(32 * kC1Rows, 2)
     conv3_c1_march_kernel(int X, int Y, int Z, const __nv_bfloat16 *__restrict__ in,
                           const __nv_bfloat16 *__restrict__ w, TO *__restrict__ out, int relu,
                           const __nv_bfloat16 *__restrict__ mask, int mstride, int moff, const double *scale,
@@ -409,58 +414,101 @@ __global__ void __launch_bounds__(32 * kC1Rows)
     for (int e = threadIdx.x; e < 27 * CI; e += blockDim.x) ws[e] = __bfloat162float(w[e]);
     __syncthreads();
     const float sc = scale ? (float)*scale : 1.0f;
-    const int x0 = (blockIdx.x * 32 + (threadIdx.x & 31)) * 4;
+    const int lane = threadIdx.x & 31;
+    const int x0 = blockIdx.x * 128;
     const int y = blockIdx.y * kC1Rows + (threadIdx.x >> 5);
     const int zb = blockIdx.z * kC1Chunk, ze = min(Z, zb + kC1Chunk);
-    const bool active = x0 < X && y < Y;  // X % 4 == 0: a thread's four outputs are all inside or all out
-    float ap[4], ac[4], an[4];             // partial sums of output planes m - 1, m, m + 1
+    // the edge voxel lane 0 (x0 - 1, tap dx = -1) or lane 31 (x0 + 128, tap dx = +1) also forms
+    const int ex = lane == 0 ? x0 - 1 : x0 + 128, edx = lane == 0 ? 0 : 2;
+    float ap[4], ac[4], an[4];  // partial sums of output planes m - 1, m, m + 1 at x0 + lane + 32 j
 #pragma unroll
     for (int j = 0; j < 4; ++j) ap[j] = ac[j] = an[j] = 0.0f;
     for (int m = zb - 1; m <= ze; ++m) {
         // which of the three output planes this input plane still feeds (uniform over the block)
         const bool fn = m + 1 >= zb && m + 1 < ze, fc = m >= zb && m < ze, fp = m - 1 >= zb && m - 1 < ze;
-        if (active && m >= 0 && m < Z) {
+        if (y < Y && m >= 0 && m < Z) {  // uniform over the warp
 #pragma unroll 1
             for (int r = 0; r < 3; ++r) {
                 const int yy = y + r - 1;
                 if (yy < 0 || yy >= Y) continue;
                 const __nv_bfloat16 *row = in + ((int64_t)m * Y + yy) * X * CI;
+                float P[4][3][3];  // [voxel j][dz + 1][dx + 1]
+                float E[3];        // the edge voxel's product with tap dx = edx, per dz + 1
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+                        for (int d3 = 0; d3 < 3; ++d3) P[j][a3][d3] = 0.0f;
+#pragma unroll
+                for (int a3 = 0; a3 < 3; ++a3) E[a3] = 0.0f;
 #pragma unroll
                 for (int cb = 0; cb < CI; cb += 8) {
-                    float v[6][8];
+                    float v[4][8], ve[8];
 #pragma unroll
-                    for (int xi = 0; xi < 6; ++xi) {
-                        const int xx = x0 - 1 + xi;
-                        if (xx >= 0 && xx < X) {
-                            ld8(row + (int64_t)xx * CI + cb, v[xi]);
+                    for (int j = 0; j < 4; ++j) {
+                        const int xx = x0 + lane + 32 * j;
+                        if (xx < X) {
+                            ld8(row + (int64_t)xx * CI + cb, v[j]);
                         } else {
 #pragma unroll
-                            for (int c = 0; c < 8; ++c) v[xi][c] = 0.0f;
+                            for (int c = 0; c < 8; ++c) v[j][c] = 0.0f;
                         }
                     }
-                    auto add = [&](float (&a)[4], int dzi) {
+                    if (ex >= 0 && ex < X) {
+                        ld8(row + (int64_t)ex * CI + cb, ve);
+                    } else {
 #pragma unroll
-                        for (int dxi = 0; dxi < 3; ++dxi) {
-                            const float *wt = ws + (dzi * 9 + r * 3 + dxi) * CI + cb;
+                        for (int c = 0; c < 8; ++c) ve[c] = 0.0f;
+                    }
+#pragma unroll
+                    for (int a3 = 0; a3 < 3; ++a3) {
+                        if (!(a3 == 0 ? fn : a3 == 1 ? fc : fp)) continue;
+#pragma unroll
+                        for (int d3 = 0; d3 < 3; ++d3) {
+                            const float *wt = ws + (a3 * 9 + r * 3 + d3) * CI + cb;
 #pragma unroll
                             for (int c = 0; c < 8; ++c) {
                                 const float wv = wt[c];
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) a[j] = fmaf(wv, v[j + dxi][c], a[j]);
+                                for (int j = 0; j < 4; ++j) P[j][a3][d3] = fmaf(wv, v[j][c], P[j][a3][d3]);
                             }
                         }
-                    };
-                    if (fn) add(an, 0);  // dz = -1: output plane m + 1 reads input plane m
-                    if (fc) add(ac, 1);
-                    if (fp) add(ap, 2);  // dz = +1: output plane m - 1
+                        const float *we = ws + (a3 * 9 + r * 3 + edx) * CI + cb;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) E[a3] = fmaf(we[c], ve[c], E[a3]);
+                    }
+                }
+                // output x0 + lane + 32 j adds P[j][.][1] of its own voxel, P[.][.][0] of voxel x - 1
+                // (lane - 1, or lane 31 of the previous j, or lane 0's edge product) and
+                // P[.][.][2] of voxel x + 1 (lane + 1, or lane 0 of the next j, or lane 31's edge)
+#pragma unroll
+                for (int a3 = 0; a3 < 3; ++a3) {
+                    if (!(a3 == 0 ? fn : a3 == 1 ? fc : fp)) continue;
+                    const float e_lo = __shfl_sync(0xffffffffu, E[a3], 0);
+                    const float e_hi = __shfl_sync(0xffffffffu, E[a3], 31);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float lo = __shfl_up_sync(0xffffffffu, P[j][a3][0], 1);
+                        float hi = __shfl_down_sync(0xffffffffu, P[j][a3][2], 1);
+                        const float lo_w = __shfl_sync(0xffffffffu, P[j > 0 ? j - 1 : 0][a3][0], 31);
+                        const float hi_w = __shfl_sync(0xffffffffu, P[j < 3 ? j + 1 : 3][a3][2], 0);
+                        if (lane == 0) lo = j > 0 ? lo_w : e_lo;
+                        if (lane == 31) hi = j < 3 ? hi_w : e_hi;
+                        const float sum = P[j][a3][1] + lo + hi;
+                        if (a3 == 0) an[j] += sum;       // dz = -1: output plane m + 1 reads input plane m
+                        else if (a3 == 1) ac[j] += sum;
+                        else ap[j] += sum;               // dz = +1: output plane m - 1
+                    }
                 }
             }
         }
-        if (fp && active) {  // output plane m - 1 has all three input planes
-            const int64_t v0 = ((int64_t)(m - 1) * Y + y) * X + x0;
+        if (fp && y < Y) {  // output plane m - 1 has all three input planes
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t v = v0 + j;
+                const int xx = x0 + lane + 32 * j;
+                if (xx >= X) continue;
+                const int64_t v = ((int64_t)(m - 1) * Y + y) * X + xx;
                 float f = ap[j] * (vscale ? sc * vscale[v] : sc);
                 if (relu) f = f < 0.0f ? 0.0f : f;  // NaN passes
                 if (mask && !(__bfloat162float(mask[v * mstride + moff]) > 0.0f)) f = 0.0f;
@@ -481,8 +529,8 @@ static int conv_simt_launch(int X, int Y, int Z, const __nv_bfloat16 *in, const 
                             const __nv_bfloat16 *mask, int mstride, int moff, const double *scale,
                             const float *vscale, cudaStream_t s) {
     if constexpr (CO == 1 && CI % 8 == 0) {
-        if (X % 4 == 0) {
-            const dim3 grid((unsigned)((X / 4 + 31) / 32), (unsigned)((Y + kC1Rows - 1) / kC1Rows),
+        {
+            const dim3 grid((unsigned)((X + 127) / 128), (unsigned)((Y + kC1Rows - 1) / kC1Rows),
                             (unsigned)((Z + kC1Chunk - 1) / kC1Chunk));
             conv3_c1_march_kernel<CI, TO><<<grid, 32 * kC1Rows, 0, s>>>(X, Y, Z, in, w, out, relu, mask, mstride,
                                                                         moff, scale, vscale);
