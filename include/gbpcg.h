@@ -449,8 +449,9 @@ int gbpcg_mg_pcg_solve(const gbpcg_grid *grid, const double *b, double *x, const
  * into 128-voxel tiles of whole x-rows or whole planes (any multiple of 512,
  * or powers of two >= 32).  Workspaces: DEVICE, 256-byte aligned, from the
  * matching *_workspace_size; a bounded wait that gives up inside a
- * convolution zeroes that tile's output and sets an error word in the
- * workspace (see gbpcg_nn_status).
+ * convolution sets an error word in the workspace (see gbpcg_nn_status),
+ * and that call's output is then unspecified (flexible CG checks the word
+ * every iteration and falls back to Jacobi).
  * ---------------------------------------------------------------------- */
 
 #define GBPCG_NN_NUM_WEIGHTS 319248
